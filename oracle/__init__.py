@@ -1,0 +1,177 @@
+"""CPU oracle of the TPC tracking chain -- TEST INFRASTRUCTURE ONLY.
+
+ctypes binding of ``oracle.cpp``.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+it.  It shares no code with the CUDA library; the options arrive as a plain
+dict of values (the same dict the tests hand to the CUDA path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_DT = {"i4": np.int32, "f4": np.float32, "f8": np.float64, "u8": np.uint64}
+
+
+class _Opt(ctypes.Structure):
+    _fields_ = [
+        ("bz", ctypes.c_float),
+        ("sigma_y", ctypes.c_float),
+        ("sigma_z", ctypes.c_float),
+        ("ms_theta", ctypes.c_float),
+        ("link_wy", ctypes.c_float),
+        ("link_wz", ctypes.c_float),
+        ("link_chi2", ctypes.c_float),
+        ("seed_c", ctypes.c_float * 5),
+        ("follow_chi2", ctypes.c_float),
+        ("max_snp", ctypes.c_float),
+        ("score_w", ctypes.c_float),
+        ("shared_frac", ctypes.c_float),
+        ("merge_chi2", ctypes.c_float),
+        ("merge_dy", ctypes.c_float),
+        ("merge_dz", ctypes.c_float),
+        ("int_chi2", ctypes.c_float),
+        ("final_chi2", ctypes.c_float),
+        ("max_miss", ctypes.c_int32),
+        ("min_hits", ctypes.c_int32),
+        ("merge_max_gap", ctypes.c_int32),
+        ("inner_rows", ctypes.c_int32),
+        ("cand_k", ctypes.c_int32),
+        ("brute_force", ctypes.c_int32),
+        ("n_rows", ctypes.c_int32),
+        ("n_sectors", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so: strict IEEE evaluation (no contraction, no fast math)."""
+    src = os.path.join(_HERE, "oracle.cpp")
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(src):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", src, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.orc_track.restype = ctypes.c_int
+        lib.orc_track.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 5 + [
+            ctypes.POINTER(_Opt), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        lib.orc_info.restype = ctypes.c_long
+        lib.orc_info.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p]
+        lib.orc_copy.restype = ctypes.c_int
+        lib.orc_copy.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p, ctypes.c_long]
+        lib.orc_names.restype = ctypes.c_long
+        lib.orc_names.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_long]
+        lib.orc_op.restype = ctypes.c_int
+        lib.orc_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Opt), ctypes.c_void_p,
+                               ctypes.c_void_p]
+        lib.orc_free.restype = None
+        lib.orc_free.argtypes = [ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def _opt(opts: dict) -> _Opt:
+    o = _Opt()
+    for name, typ in _Opt._fields_:
+        if name == "seed_c":
+            for i, v in enumerate(opts["seed_c"]):
+                o.seed_c[i] = float(v)
+        elif typ is ctypes.c_float:
+            setattr(o, name, float(opts[name]))
+        else:
+            setattr(o, name, int(opts[name]))
+    return o
+
+
+class Result(dict):
+    """Named arrays produced by one oracle run."""
+
+
+def _collect(lib, h) -> Result:
+    n = lib.orc_names(h, None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib.orc_names(h, buf, n)
+    res = Result()
+    for name in buf.value.decode().split():
+        dt = ctypes.create_string_buffer(8)
+        nb = lib.orc_info(h, name.encode(), dt)
+        a = np.empty(nb // np.dtype(_DT[dt.value.decode()]).itemsize, dtype=_DT[dt.value.decode()])
+        if nb:
+            lib.orc_copy(h, name.encode(), a.ctypes.data, nb)
+        res[name] = a
+    return res
+
+
+def track(y, z, row, sector, row_x, opts: dict, *, fp64: bool = False) -> Result:
+    """Run the oracle chain on host arrays; ``fp64`` selects the double build."""
+    lib = _load()
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    row = np.ascontiguousarray(row, dtype=np.uint8)
+    sector = np.ascontiguousarray(sector, dtype=np.uint8)
+    rx = np.ascontiguousarray(row_x, dtype=np.float64)
+    o = _opt(opts)
+    h = ctypes.c_void_p()
+    rc = lib.orc_track(len(y), y.ctypes.data, z.ctypes.data, row.ctypes.data, sector.ctypes.data,
+                       rx.ctypes.data, ctypes.byref(o), int(fp64), ctypes.byref(h))
+    if rc:
+        raise ValueError(f"oracle rejected the input (code {rc})")
+    try:
+        return _collect(lib, h)
+    finally:
+        lib.orc_free(h)
+
+
+def _op(op: int, io: np.ndarray, row_x, opts: dict, fp64: bool) -> tuple[int, np.ndarray]:
+    lib = _load()
+    io = np.ascontiguousarray(io, dtype=np.float64).copy()
+    rx = np.ascontiguousarray(row_x, dtype=np.float64)
+    o = _opt(opts)
+    rc = lib.orc_op(op, int(fp64), ctypes.byref(o), rx.ctypes.data, io.ctypes.data)
+    return rc, io
+
+
+def propagate(p, c, x0, x1, row_x, opts, fp64=True):
+    """EKF helix propagation (with scattering noise) of (p[5], c[15]) from x0 to x1."""
+    io = np.zeros(32)
+    io[:5], io[5:20], io[20], io[21] = p, c, x0, x1
+    rc, io = _op(0, io, row_x, opts, fp64)
+    return (None if rc else (io[:5], io[5:20], io[20]))
+
+
+def update(p, c, my, mz, row_x, opts, fp64=True):
+    """Kalman update with a (y, z) measurement; returns (p, c, chi2)."""
+    io = np.zeros(32)
+    io[:5], io[5:20], io[20], io[21] = p, c, my, mz
+    rc, io = _op(1, io, row_x, opts, fp64)
+    return io[:5], io[5:20], io[22]
+
+
+def rotate(p, c, x, direction, row_x, opts, fp64=True):
+    """Re-express the state in the adjacent sector frame (+1: +20 deg, -1: -20 deg)."""
+    io = np.zeros(32)
+    io[:5], io[5:20], io[20], io[21] = p, c, x, direction
+    rc, io = _op(2, io, row_x, opts, fp64)
+    return (None if rc else (io[:5], io[5:20], io[20]))
+
+
+def seed(points, row_x, opts, fp64=True):
+    """Three-point seed; points = [(x, y, z)] * 3.  Returns (p, c, x) or None."""
+    io = np.zeros(32)
+    io[:9] = np.asarray(points, dtype=np.float64).ravel()
+    rc, io = _op(3, io, row_x, opts, fp64)
+    return (None if rc else (io[9:14], io[14:29], io[29]))

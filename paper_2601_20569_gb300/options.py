@@ -1,0 +1,76 @@
+"""Tracker options: physical inputs and every cut of the reconstruction.
+
+The paper (Sec. 2, Sec. 3) describes the cuts qualitatively and prints no
+values; the defaults below are this library's readings of it:
+
+* shared-cluster fraction 10 % (Sec. 2 default; 20 % is the loose setting of
+  the mitigation described in Sec. 2);
+* the "inner region" where Phase II re-attaches clusters = the 20 innermost
+  pad rows (Sec. 2 and Sec. 4 both single out rows below 20);
+* Phase II candidate depth (tracks may fall back to their k-th candidate) = 4.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import asdict, dataclass, field
+
+MODE_STRICT = 0  # FP32, no FMA contraction: bit-identical to the strict CPU oracle
+MODE_FAST = 1    # FP32 with FMA contraction
+
+
+@dataclass
+class TrackerOptions:
+    bz: float = 0.5                 # tesla
+    sigma_y: float = 0.1            # cluster resolution [cm]
+    sigma_z: float = 0.1
+    ms_theta: float = 1e-3          # scattering angle per pad row [rad]
+    link_wy: float = 2.5            # CA neighbour window [cm]
+    link_wz: float = 2.5
+    link_chi2: float = 1.0          # max squared distance of the middle cluster to the d-u line [cm^2]
+    seed_c: tuple = (1.0, 1.0, 0.25, 0.25, 100.0)  # seed covariance diagonal
+    follow_chi2: float = 9.0        # cluster pick-up cut during following (2 dof)
+    max_snp: float = 0.95
+    score_w: float = 2.0            # selector score = n_clusters - score_w * chi2/ndf
+    shared_frac: float = 0.10
+    merge_chi2: float = 30.0        # 5-dof match at the common x
+    merge_dy: float = 3.0
+    merge_dz: float = 3.0
+    int_chi2: float = 25.0          # interpolation cut / Phase II candidate cut (2 dof)
+    final_chi2: float = 16.0        # simple cut of the last fit iteration
+    max_miss: int = 10              # consecutive empty rows ending the following
+    min_hits: int = 10
+    merge_max_gap: int = 20         # rows between merged segments
+    inner_rows: int = 20
+    cand_k: int = 4
+    brute_force: int = 0            # oracle only: scan whole rows
+    n_rows: int = 152
+    n_sectors: int = 36
+
+    def as_dict(self) -> dict:
+        return asdict(self)
+
+
+FLOAT_FIELDS = ("bz", "sigma_y", "sigma_z", "ms_theta", "link_wy", "link_wz", "link_chi2")
+FLOAT_FIELDS2 = ("follow_chi2", "max_snp", "score_w", "shared_frac", "merge_chi2", "merge_dy",
+                 "merge_dz", "int_chi2", "final_chi2")
+INT_FIELDS = ("max_miss", "min_hits", "merge_max_gap", "inner_rows", "cand_k", "brute_force",
+              "n_rows", "n_sectors")
+
+
+def ctypes_fields():
+    """Field layout shared by the C option structs (floats, then ints)."""
+    f = [(k, ctypes.c_float) for k in FLOAT_FIELDS]
+    f.append(("seed_c", ctypes.c_float * 5))
+    f += [(k, ctypes.c_float) for k in FLOAT_FIELDS2]
+    f += [(k, ctypes.c_int32) for k in INT_FIELDS]
+    return f
+
+
+def fill(struct, opts: dict):
+    for k in FLOAT_FIELDS + FLOAT_FIELDS2:
+        setattr(struct, k, float(opts[k]))
+    for k in INT_FIELDS:
+        setattr(struct, k, int(opts[k]))
+    for i, v in enumerate(opts["seed_c"]):
+        struct.seed_c[i] = float(v)
+    return struct
