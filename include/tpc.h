@@ -1,0 +1,166 @@
+/* tpc.h -- C ABI of the GB300 TPC time-frame tracker (libtpc.so).
+ *
+ * Reconstructs TPC tracks from the clusters of one continuous-readout time
+ * frame, following the three phases of the paper's Sec. 2 ("sector tracking,
+ * track merging and track fit") with the Phase I/II fit of Sec. 3:
+ *
+ *   per-row cluster grids -> cellular-automaton neighbour finding and cleaning
+ *   -> start hits -> Kalman tracklet construction -> ambiguity solving
+ *   -> sector refit and sector-to-sector merging -> three-iteration refit with
+ *   space-charge distortion correction and inner-region re-attachment.
+ *
+ * Conventions
+ *   - Sector s in 0..35: side A (z > 0) is 0..17, side C is 18..35; sector
+ *     axis at azimuth ((s % 18) + 0.5) * 20 deg; local x along the axis (pad
+ *     row normal), y along the row, z the measured drift coordinate [cm].
+ *   - Track state at x: (y, z, sin(phi), tan(lambda), q/pT [c/GeV]); the
+ *     covariance is stored as 15 floats, lower triangle row by row
+ *     (yy, zy, zz, sy, sz, ss, ty, tz, ts, tt, qy, qz, qs, qt, qq).
+ *   - A cluster id is its index in the caller's input arrays.
+ *
+ * Ownership and errors
+ *   - Input pointers marked "device" are caller-owned CUDA device memory,
+ *     read-only and valid for the duration of the call.
+ *   - Output buffers (tpc_tracks) are owned by the context and stay valid
+ *     until the next call on the same context.
+ *   - Every call returns a tpc_status; no C++ exception crosses the ABI.  A
+ *     failed call leaves a message for tpc_last_error().  Work is enqueued on
+ *     the caller's stream; device-detected errors (invalid cluster, capacity)
+ *     are read back at the end of the call with one small copy, which makes
+ *     the call synchronous with respect to that stream.
+ *   - One context serves one stream at a time (calls are not thread-safe on
+ *     the same context).
+ */
+#ifndef TPC_H
+#define TPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPC_OK = 0,
+  TPC_ERR_INVALID_ARG = 1,   /* null pointer, bad size or option */
+  TPC_ERR_INVALID_INPUT = 2, /* NaN/Inf coordinate, row >= n_rows, sector >= n_sectors */
+  TPC_ERR_CAPACITY = 3,      /* an internal buffer is too small; *needed reports the size */
+  TPC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  TPC_ERR_OOM = 5,           /* device allocation failed */
+  TPC_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  TPC_ERR_STATE = 7          /* call order violated (e.g. backward without refit) */
+} tpc_status;
+
+typedef struct tpc_ctx tpc_ctx;
+
+/* Detector geometry (host memory, copied at init).  row_x: n_rows pad-row
+ * radii [cm], increasing. */
+typedef struct {
+  int32_t n_sectors; /* 36 */
+  int32_t n_rows;    /* 152 */
+  const float* row_x;
+} tpc_geometry;
+
+/* Space-charge correction map: uniform cubic B-spline control points,
+ * [3][n_z][n_r][n_phi] floats (components dx, dy, dz in sector-local cm, added
+ * to a measured cluster).  phi is periodic over the 18 azimuthal sectors
+ * (coordinate u = sector + 0.5 + 0.5*(y/x)/tan(10 deg), control point j at
+ * u = (j + 0.5) * 18 / n_phi); r = sqrt(x^2 + y^2) spans [r_min, r_max] and z
+ * [z_min, z_max] with clamping, control point j at t = j - 1 knot spacings.
+ * coeff is a device pointer; NULL means no correction. */
+typedef struct {
+  int32_t n_phi, n_r, n_z;
+  float r_min, r_max, z_min, z_max;
+  const float* coeff;
+} tpc_map;
+
+/* Reconstruction options: physical inputs and every cut (the paper states the
+ * cuts only qualitatively; defaults are given in the Python binding). */
+typedef struct {
+  float bz;                 /* tesla */
+  float sigma_y, sigma_z;   /* cluster resolution [cm] */
+  float ms_theta;           /* multiple-scattering angle per pad row [rad] */
+  float link_wy, link_wz;   /* CA neighbour search window [cm] */
+  float link_chi2;          /* max squared distance of the middle cluster to the d-u line [cm^2] */
+  float seed_c[5];          /* seed covariance diagonal */
+  float follow_chi2;        /* cluster pick-up cut of the track following (2 dof) */
+  float max_snp;            /* |sin(phi)| limit of the sector model */
+  float score_w;            /* ambiguity score = n_clusters - score_w * chi2/ndf */
+  float shared_frac;        /* allowed shared-cluster fraction (paper default 10 %) */
+  float merge_chi2, merge_dy, merge_dz; /* merging: 5-dof chi2 cut and position gates */
+  float int_chi2;           /* interpolation cut of fit iteration 2, candidate cut (2 dof) */
+  float final_chi2;         /* simple chi2 cut of fit iteration 3 */
+  int32_t max_miss;         /* consecutive empty rows ending the following */
+  int32_t min_hits;         /* minimum clusters of a tracklet / track */
+  int32_t merge_max_gap;    /* max rows between merged segments */
+  int32_t inner_rows;       /* rows of the inner region (Phase II re-attachment) */
+  int32_t cand_k;           /* candidates kept per (track, row), <= 8 */
+  int32_t mode;             /* 0 = strict FP32 (no FMA), 1 = fast FP32 (FMA) */
+  int64_t cap_clusters;     /* max clusters per frame */
+  int64_t cap_tracklets;    /* max tracklets per frame (0: n/16 + 4096) */
+  int64_t cap_tracks;       /* max tracks per frame (0: cap_tracklets) */
+} tpc_options;
+
+/* Clusters of one time frame (device memory, structure of arrays). */
+typedef struct {
+  int64_t n;
+  const float* y;
+  const float* z;
+  const uint16_t* q;   /* carried, unused by the tracking */
+  const uint8_t* row;
+  const uint8_t* sector;
+} tpc_clusters;
+
+/* Tracks of one frame (device memory owned by the context). */
+typedef struct {
+  int64_t n_tracks;
+  int64_t n_cluster_refs;
+  const float* params;      /* [n_tracks][5] at the innermost cluster */
+  const float* cov;         /* [n_tracks][15] */
+  const float* chi2;        /* [n_tracks] */
+  const float* x;           /* [n_tracks] local x of params */
+  const int32_t* ndf;       /* [n_tracks] */
+  const int32_t* sector;    /* [n_tracks] sector frame of params */
+  const int32_t* n_clusters;/* [n_tracks] */
+  const int32_t* cl_offset; /* [n_tracks + 1] CSR offsets into cl_ids */
+  const int32_t* cl_ids;    /* cluster ids, innermost first */
+  const int32_t* key;       /* [n_tracks] identity: input id of the start cluster of
+                               the track's first segment */
+  const int32_t* attach;    /* [n_clusters of the frame]: owning track index or -1 */
+} tpc_tracks;
+
+/* Create a context: copies the geometry, derives the model constants from
+ * bz and the options, allocates device buffers for opt->cap_clusters
+ * clusters.  map may be NULL.  Sec. 2 (sector structure), Sec. 5 (the
+ * deterministic mode is mode 0). */
+tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
+                    const tpc_options* opt, tpc_ctx** out);
+
+/* Track one time frame (Sec. 1: the time frame is the unit of reconstruction;
+ * Sec. 2: sector tracking, merging, fit; Sec. 3: Phase I/II fit).  On
+ * TPC_ERR_CAPACITY, *needed (if not NULL) receives the required size of the
+ * buffer that overflowed. */
+tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_tracks* out,
+                               void* cuda_stream, int64_t* needed);
+
+/* Replace the correction map (device pointer copied by reference; the caller
+ * keeps it alive while the context uses it). */
+tpc_status tpc_set_map(tpc_ctx* ctx, const tpc_map* map);
+
+/* Copy an internal per-stage buffer to host memory (testing and debugging).
+ * name selects the buffer; *bytes receives its size; nothing is copied when
+ * cap_bytes is too small (TPC_ERR_CAPACITY).  Synchronises the last stream. */
+tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_t cap_bytes,
+                          int64_t* bytes);
+
+/* Message of the last failed call on this context (never NULL). */
+const char* tpc_last_error(const tpc_ctx* ctx);
+
+/* Release all device memory of the context. */
+void tpc_destroy(tpc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPC_H */

@@ -1,0 +1,116 @@
+// Internal types of the CUDA tracker shared by the host orchestration and the
+// kernels (never exported through the C ABI).
+#pragma once
+
+#include <cstdint>
+
+namespace tpc {
+
+constexpr int kMaxRows = 160;      // pad rows supported by the per-tracklet row arrays
+constexpr int kMaxCand = 8;        // Phase II candidates per (track, row)
+
+// Derived model constants and cuts, passed by value to every kernel.
+struct KParams {
+  float kb;          // curvature per unit q/pT, -Bz * 0.00299792458
+  float tan_half;    // tan(10 deg)
+  float rot_c, rot_s;  // cos/sin of 20 deg
+  float sy2, sz2;    // measurement variances
+  float ms2;         // scattering angle variance per row
+  float pitch_inv;   // rows per cm
+  float link_wy, link_wz, link_chi2;
+  float seed_c[5];
+  float follow_chi2, max_snp, score_w, shared_frac;
+  float merge_chi2, merge_dy, merge_dz;
+  float int_chi2, final_chi2;
+  int max_miss, min_hits, merge_max_gap, inner_rows, cand_k;
+  int n_rows, n_sectors;
+  float grid_dy;     // target y bin size [cm]
+  float grid_occ;    // target clusters per bin
+};
+
+// Search grid of one (sector, row): bins iz*nY + iy, clusters of a bin are
+// contiguous in the sorted arrays.
+struct RowGrid {
+  int bin0;   // first global bin
+  int nY, nZ;
+  int cl0;    // first sorted cluster of the row
+  int ncl;
+  float y0, invDy, z0, invDz;
+};
+
+// Device error word bits.
+enum : int {
+  kErrInput = 1,
+  kErrCapTracklets = 2,
+  kErrCapBins = 4,
+  kErrCapTracks = 8,
+  kErrCapRefs = 16,
+  kErrCapCand = 32,
+};
+
+// Small device-side counters read back at the end of a call.
+struct Counters {
+  int err;
+  int n_starts;
+  int n_bins;
+  int n_tracks;      // accepted sector tracks
+  int n_merged;      // final tracks after merging
+  int n_refs;        // cluster references of the final tracks
+  int n_cand;
+  int need_tracklets;
+  int need_tracks;
+  int pad[7];
+};
+
+// Working set of one frame on the device.
+struct FrameDev {
+  // input
+  const float* y;
+  const float* z;
+  const uint8_t* row;
+  const uint8_t* sector;
+  long n;
+  const float* row_x;  // [n_rows]
+  // a1 grid
+  int* row_cnt;            // [n_sectors*n_rows]
+  unsigned* row_zmin;      // ordered-int encoded
+  unsigned* row_zmax;
+  RowGrid* rows;           // [n_sectors*n_rows]
+  int* bin_cnt;            // [cap_bins + 1]
+  int* bin_first;          // [cap_bins + 1]
+  int* cl_bin;             // [n] per input cluster
+  int* cl_slot;            // [n]
+  long cap_bins;
+  float* sy;               // [n] sorted
+  float* sz;
+  int* sid;                // sorted -> input id
+  uint16_t* srow;          // sorted -> sector*n_rows + row
+  // a2/a3
+  int* lup;
+  int* ldn;
+  int* cup;
+  int* cdn;
+  // a4
+  int* flags;              // [n] scratch for compaction
+  int* scan_tmp;           // block partials
+  int* starts;             // [cap_tl]
+  // a5
+  long cap_tl;
+  float* tl_par;           // [cap_tl*5]
+  float* tl_cov;           // [cap_tl*15]
+  float* tl_x;
+  float* tl_chi2;
+  int* tl_n;
+  int* tl_rlo;
+  int* tl_rhi;
+  int* tl_hits;            // [cap_tl*kMaxRows] row-indexed sorted cluster or -1
+  // a6
+  unsigned long long* owner_key;  // [n] sorted index space
+  int* tl_acc;
+  int* tl_nkept;
+  int* tl_kept;            // [cap_tl*kMaxRows] outermost first
+  int* sec_owner;          // [n] sorted index space: tracklet index or -1
+  Counters* cnt;
+};
+
+}  // namespace tpc

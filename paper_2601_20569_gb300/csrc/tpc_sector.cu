@@ -1,0 +1,603 @@
+// Sector tracking kernels (Sec. 2 of the paper): per-row cluster grids,
+// cellular-automaton neighbour finding and cleaning, start hits, Kalman
+// tracklet construction and ambiguity solving (with the Phase I criterion of
+// Sec. 3).  This translation unit is compiled twice: with --fmad=false into
+// namespace tpc::strict (bit-identical to the strict CPU evaluation) and with
+// FMA contraction into tpc::fast.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tpc_kernels.h"
+#include "tpc_model.cuh"
+
+namespace tpc {
+namespace TPC_NS {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ unsigned f2o(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ int bin_of(float v, float v0, float inv, int n) {
+  return clampi((int)floorf((v - v0) * inv), 0, n - 1);
+}
+
+// Visit sorted clusters of a row grid whose bins cover [ylo,yhi] x [zlo,zhi]
+// (a superset of the clusters inside the box: bin index is monotone in the
+// coordinate).
+template <typename Fn>
+__device__ __forceinline__ void for_window(const int* __restrict__ bin_first, const RowGrid& g,
+                                           float ylo, float yhi, float zlo, float zhi, Fn&& fn) {
+  if (g.ncl == 0 || !(ylo <= yhi) || !(zlo <= zhi)) return;
+  const int iy0 = bin_of(ylo, g.y0, g.invDy, g.nY), iy1 = bin_of(yhi, g.y0, g.invDy, g.nY);
+  const int iz0 = bin_of(zlo, g.z0, g.invDz, g.nZ), iz1 = bin_of(zhi, g.z0, g.invDz, g.nZ);
+  for (int iz = iz0; iz <= iz1; ++iz) {
+    const int b = g.bin0 + iz * g.nY;
+    const int lo = bin_first[b + iy0], hi = bin_first[b + iy1 + 1];
+    for (int k = lo; k < hi; ++k) fn(k);
+  }
+}
+
+// ------------------------------------------------------------------ a1 grid
+__global__ void k_row_stats(FrameDev F, KParams P) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F.n) return;
+  const int r = F.row[i], s = F.sector[i];
+  const float y = F.y[i], z = F.z[i];
+  if (r >= P.n_rows || s >= P.n_sectors || !isfinite(y) || !isfinite(z)) {
+    atomicOr(&F.cnt->err, kErrInput);
+    return;
+  }
+  const int rr = s * P.n_rows + r;
+  atomicAdd(&F.row_cnt[rr], 1);
+  atomicMin(&F.row_zmin[rr], f2o(z));
+  atomicMax(&F.row_zmax[rr], f2o(z));
+}
+
+__device__ __forceinline__ int block_exscan(int v, int* sh_warp, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    int w = lane < nw ? sh_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) sh_warp[lane] = w;
+  }
+  __syncthreads();
+  const int base = wid ? sh_warp[wid - 1] : 0;
+  if (total) *total = sh_warp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// One block: bin layout of every (sector,row) and the row/bin offsets.
+__global__ void k_row_grid(FrameDev F, KParams P) {
+  __shared__ int sh[32];
+  __shared__ int carry_bins, carry_cl;
+  const int nrr = P.n_sectors * P.n_rows;
+  if (threadIdx.x == 0) { carry_bins = 0; carry_cl = 0; }
+  __syncthreads();
+  for (int base = 0; base < nrr; base += blockDim.x) {
+    const int rr = base + threadIdx.x;
+    RowGrid g{};
+    int nb = 0, cnt = 0;
+    if (rr < nrr) {
+      const int r = rr % P.n_rows;
+      cnt = F.row_cnt[rr];
+      const float x = F.row_x[r];
+      const float ymax = x * P.tan_half + 0.5f;
+      int nY = (int)(2.0f * ymax / P.grid_dy);
+      nY = clampi(nY, 1, 64);
+      g.nY = nY;
+      g.y0 = -ymax;
+      g.invDy = (float)nY / (2.0f * ymax);
+      int nZ = 1;
+      float zlo = 0.0f, zr = 0.0f;
+      if (cnt > 0) {
+        zlo = o2f(F.row_zmin[rr]);
+        zr = o2f(F.row_zmax[rr]) - zlo;
+        const float want = ceilf((float)cnt / ((float)nY * P.grid_occ));
+        const float zmax_bins = floorf(zr) + 1.0f;  // bins of at least ~1 cm
+        nZ = (int)fminf(fminf(want, zmax_bins), (float)((1 << 20) / nY));
+        nZ = max(nZ, 1);
+      }
+      g.nZ = nZ;
+      g.z0 = zlo;
+      g.invDz = zr > 0.0f ? (float)nZ / zr : 0.0f;
+      g.ncl = cnt;
+      nb = nY * nZ;
+    }
+    int tot_b, tot_c;
+    const int ob = block_exscan(nb, sh, &tot_b);
+    const int oc = block_exscan(cnt, sh, &tot_c);
+    if (rr < nrr) {
+      g.bin0 = carry_bins + ob;
+      g.cl0 = carry_cl + oc;
+      F.rows[rr] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { carry_bins += tot_b; carry_cl += tot_c; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    F.cnt->n_bins = carry_bins;
+    if (carry_bins > F.cap_bins) atomicOr(&F.cnt->err, kErrCapBins);
+  }
+}
+
+__global__ void k_bin_hist(FrameDev F, KParams P) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F.n || F.cnt->err) return;
+  const int rr = F.sector[i] * P.n_rows + F.row[i];
+  const RowGrid g = F.rows[rr];
+  const int iy = bin_of(F.y[i], g.y0, g.invDy, g.nY);
+  const int iz = bin_of(F.z[i], g.z0, g.invDz, g.nZ);
+  const int b = g.bin0 + iz * g.nY + iy;
+  F.cl_bin[i] = b;
+  F.cl_slot[i] = atomicAdd(&F.bin_cnt[b], 1);
+}
+
+__global__ void k_scatter(FrameDev F, KParams P) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F.n || F.cnt->err) return;
+  const int pos = F.bin_first[F.cl_bin[i]] + F.cl_slot[i];
+  F.sy[pos] = F.y[i];
+  F.sz[pos] = F.z[i];
+  F.sid[pos] = (int)i;
+  F.srow[pos] = (uint16_t)(F.sector[i] * P.n_rows + F.row[i]);
+}
+
+// Order the clusters of each bin by input id (deterministic layout).
+__global__ void k_bin_sort(FrameDev F) {
+  const int nb = F.cnt->n_bins;
+  if (F.cnt->err) return;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    const int lo = F.bin_first[b], hi = F.bin_first[b + 1];
+    for (int k = lo + 1; k < hi; ++k) {
+      const int id = F.sid[k];
+      const float y = F.sy[k], z = F.sz[k];
+      int j = k - 1;
+      while (j >= lo && F.sid[j] > id) {
+        F.sid[j + 1] = F.sid[j];
+        F.sy[j + 1] = F.sy[j];
+        F.sz[j + 1] = F.sz[j];
+        --j;
+      }
+      F.sid[j + 1] = id;
+      F.sy[j + 1] = y;
+      F.sz[j + 1] = z;
+    }
+  }
+}
+
+// ------------------------------------------------------------- a2 neighbours
+__global__ void k_links(FrameDev F, KParams P) {
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= F.n || F.cnt->err) return;
+  const int rr = F.srow[k];
+  const int r = rr % P.n_rows;
+  int bu = -1, bd = -1;
+  if (r >= 1 && r <= P.n_rows - 2) {
+    const float yc = F.sy[k], zc = F.sz[k];
+    const float xd = F.row_x[r - 1], xc = F.row_x[r], xu = F.row_x[r + 1];
+    const float f = (xc - xd) / (xu - xd);
+    const RowGrid gu = F.rows[rr + 1], gd = F.rows[rr - 1];
+    const float m = 0.01f;
+    const float ylo = yc - P.link_wy - m, yhi = yc + P.link_wy + m;
+    const float zlo = zc - P.link_wz - m, zhi = zc + P.link_wz + m;
+    float best = 0.0f;
+    int buid = 0, bdid = 0;
+    for_window(F.bin_first, gu, ylo, yhi, zlo, zhi, [&](int u) {
+      const float yu = F.sy[u], zu = F.sz[u];
+      if (!(fabsf(yu - yc) <= P.link_wy && fabsf(zu - zc) <= P.link_wz)) return;
+      const int uid = F.sid[u];
+      for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
+        const float yd = F.sy[d], zd = F.sz[d];
+        if (!(fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)) return;
+        const float yp = yd + (yu - yd) * f;
+        const float zp = zd + (zu - zd) * f;
+        const float ey = yp - yc, ez = zp - zc;
+        const float d2 = ey * ey + ez * ez;
+        if (!(d2 < P.link_chi2)) return;
+        const int did = F.sid[d];
+        if (bu < 0 || d2 < best || (d2 == best && (uid < buid || (uid == buid && did < bdid)))) {
+          best = d2;
+          bu = u;
+          bd = d;
+          buid = uid;
+          bdid = did;
+        }
+      });
+    });
+  }
+  F.lup[k] = bu;
+  F.ldn[k] = bd;
+}
+
+// --------------------------------------------------------------- a3 cleaner
+__global__ void k_clean(FrameDev F) {
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= F.n || F.cnt->err) return;
+  const int u = F.lup[k], d = F.ldn[k];
+  F.cup[k] = (u >= 0 && F.ldn[u] == (int)k) ? u : -1;
+  F.cdn[k] = (d >= 0 && F.lup[d] == (int)k) ? d : -1;
+}
+
+// ------------------------------------------------------------ a4 start hits
+// Compaction without atomics: per-block counts, scan of the counts, then each
+// block writes its flagged elements at its offset in order.
+constexpr int kCompactItems = 4;  // elements per thread
+
+__device__ __forceinline__ bool is_start(const FrameDev& F, long k) {
+  const int u = F.cup[k];
+  return F.cdn[k] < 0 && u >= 0 && F.cup[u] >= 0;
+}
+
+__global__ void k_start_count(FrameDev F) {
+  __shared__ int sh[32];
+  const long base = (long)blockIdx.x * blockDim.x * kCompactItems;
+  int c = 0;
+  if (!F.cnt->err)
+    for (int j = 0; j < kCompactItems; ++j) {
+      const long k = base + (long)j * blockDim.x + threadIdx.x;
+      if (k < F.n && is_start(F, k)) ++c;
+    }
+  int tot;
+  block_exscan(c, sh, &tot);
+  if (threadIdx.x == 0) F.scan_tmp[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block counts in one block; writes the total.
+__global__ void k_scan_partials(int* part, int nparts, int* total) {
+  __shared__ int sh[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nparts; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < nparts ? part[i] : 0;
+    int tot;
+    const int ex = block_exscan(v, sh, &tot);
+    if (i < nparts) part[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_start_write(FrameDev F) {
+  __shared__ int sh[32];
+  __shared__ int off;
+  if (F.cnt->err) return;
+  const long base = (long)blockIdx.x * blockDim.x * kCompactItems;
+  if (threadIdx.x == 0) off = F.scan_tmp[blockIdx.x];
+  __syncthreads();
+  for (int j = 0; j < kCompactItems; ++j) {
+    const long k = base + (long)j * blockDim.x + threadIdx.x;
+    const int flag = (k < F.n && is_start(F, k)) ? 1 : 0;
+    int tot;
+    const int ex = block_exscan(flag, sh, &tot);
+    const int pos = off + ex;
+    if (flag && pos < F.cap_tl) F.starts[pos] = (int)k;
+    __syncthreads();
+    if (threadIdx.x == 0) off += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_start_check(FrameDev F) {
+  if (F.cnt->n_starts > F.cap_tl) {
+    atomicOr(&F.cnt->err, kErrCapTracklets);
+    atomicMax(&F.cnt->need_tracklets, F.cnt->n_starts);
+  }
+}
+
+// ------------------------------------------------------------ a5 tracklets
+struct Pick {
+  int k;
+  float chi2;
+};
+
+// Best cluster of row (s, r) with chi2 < follow_chi2 (ties: smaller input id);
+// the y/z box is the widened 2x2 Mahalanobis bound of the cut.
+__device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const Trk<float>& t,
+                                    int rr) {
+  const float hy = sqrtf(P.follow_chi2 * (t.c[0] + P.sy2)) * 1.001f + 0.01f;
+  const float hz = sqrtf(P.follow_chi2 * (t.c[2] + P.sz2)) * 1.001f + 0.01f;
+  const float ylo = t.p[0] - hy, yhi = t.p[0] + hy;
+  const float zlo = t.p[1] - hz, zhi = t.p[1] + hz;
+  const RowGrid g = F.rows[rr];
+  int best = -1, bid = 0;
+  float bchi = 0.0f;
+  for_window(F.bin_first, g, ylo, yhi, zlo, zhi, [&](int k) {
+    const float yk = F.sy[k], zk = F.sz[k];
+    if (!(yk >= ylo && yk <= yhi)) return;
+    if (fabsf(zk - t.p[1]) > hz) return;
+    const float chi2 = chi2_of(t, yk, zk, P);
+    if (!(chi2 < P.follow_chi2)) return;
+    const int id = F.sid[k];
+    if (best < 0 || chi2 < bchi || (chi2 == bchi && id < bid)) {
+      best = k;
+      bchi = chi2;
+      bid = id;
+    }
+  });
+  return best;
+}
+
+__global__ void __launch_bounds__(128) k_tracklets(FrameDev F, KParams P) {
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  if (F.cnt->err) return;
+  const int NR = P.n_rows;
+  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+    const int start = F.starts[ti];
+    int* H = F.tl_hits + (long)ti * kMaxRows;
+    // chain length and seed points (first, middle, last)
+    int L = 1, last_c = start;
+    while (F.cup[last_c] >= 0) {
+      last_c = F.cup[last_c];
+      ++L;
+    }
+    int mid = start;
+    for (int i = 0; i < (L - 1) / 2; ++i) mid = F.cup[mid];
+    const int rr0 = F.srow[start];
+    const int r0 = rr0 % NR;
+    const int sbase = rr0 - r0;  // sector * n_rows
+    float xs[3], ys[3], zs[3];
+    {
+      const int sel[3] = {start, mid, last_c};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        xs[i] = F.row_x[F.srow[sel[i]] % NR];
+        ys[i] = F.sy[sel[i]];
+        zs[i] = F.sz[sel[i]];
+      }
+    }
+    Trk<float> t;
+    F.tl_n[ti] = 0;
+    if (!seed3(xs, ys, zs, P, t)) continue;
+    {
+      const Resid R = residual(t, F.sy[start], F.sz[start], P);
+      update(t, R);
+      H[r0] = start;
+    }
+    Trk<float> last = t;
+    int top = r0;
+    bool alive = true;
+    int c = start;
+    for (int i = 1; i < L; ++i) {
+      c = F.cup[c];
+      const int r = F.srow[c] % NR;
+      if (!propagate(t, F.row_x[r], P)) {
+        alive = false;
+        break;
+      }
+      const Resid R = residual(t, F.sy[c], F.sz[c], P);
+      update(t, R);
+      H[r] = c;
+      last = t;
+      top = r;
+    }
+    if (alive) {
+      int miss = 0;
+      for (int r = top + 1; r < NR; ++r) {
+        if (!propagate(t, F.row_x[r], P)) break;
+        if (fabsf(t.p[0]) > t.x * P.tan_half) break;
+        const int k = pick(F, P, t, sbase + r);
+        if (k >= 0) {
+          const Resid R = residual(t, F.sy[k], F.sz[k], P);
+          update(t, R);
+          H[r] = k;
+          last = t;
+          top = r;
+          miss = 0;
+        } else {
+          H[r] = -1;
+          if (++miss >= P.max_miss) break;
+        }
+      }
+    }
+    // downward pass: reset covariance at the top, refit, extend below the start
+    t = last;
+    reset_cov(t.c, P);
+    float chi2 = 0.0f;
+    int n = 0;
+    {
+      const int k = H[top];
+      const Resid R = residual(t, F.sy[k], F.sz[k], P);
+      chi2 = chi2 + R.chi2;
+      update(t, R);
+      ++n;
+    }
+    Trk<float> inner = t;
+    int rlo = top;
+    int miss = 0;
+    for (int r = top - 1; r >= 0; --r) {
+      if (!propagate(t, F.row_x[r], P)) break;
+      if (fabsf(t.p[0]) > t.x * P.tan_half) break;
+      if (r >= r0) {
+        const int k = H[r];
+        if (k < 0) continue;
+        const Resid R = residual(t, F.sy[k], F.sz[k], P);
+        chi2 = chi2 + R.chi2;
+        update(t, R);
+        ++n;
+        inner = t;
+        rlo = r;
+      } else {
+        const int k = pick(F, P, t, sbase + r);
+        if (k >= 0) {
+          const Resid R = residual(t, F.sy[k], F.sz[k], P);
+          chi2 = chi2 + R.chi2;
+          update(t, R);
+          H[r] = k;
+          ++n;
+          inner = t;
+          rlo = r;
+          miss = 0;
+        } else {
+          H[r] = -1;
+          if (++miss >= P.max_miss) break;
+        }
+      }
+    }
+    if (n < P.min_hits) continue;
+    F.tl_n[ti] = n;
+    F.tl_rlo[ti] = rlo;
+    F.tl_rhi[ti] = top;
+    F.tl_chi2[ti] = chi2;
+    F.tl_x[ti] = inner.x;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = inner.p[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = inner.c[i];
+  }
+}
+
+// ------------------------------------------------------------- a6 selector
+__device__ __forceinline__ unsigned long long tracklet_key(const FrameDev& F, const KParams& P,
+                                                           int ti) {
+  const int n = F.tl_n[ti];
+  const float score = (float)n - P.score_w * (F.tl_chi2[ti] / (float)(2 * n - 5));
+  const unsigned sid = (unsigned)F.sid[F.starts[ti]];
+  return ((unsigned long long)f2o(score) << 32) | (unsigned long long)(0xFFFFFFFFu - sid);
+}
+
+__global__ void k_sel_owner(FrameDev F, KParams P) {
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  if (F.cnt->err) return;
+  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+    if (F.tl_n[ti] == 0) continue;
+    const unsigned long long key = tracklet_key(F, P, ti);
+    const int* H = F.tl_hits + (long)ti * kMaxRows;
+    for (int r = F.tl_rlo[ti]; r <= F.tl_rhi[ti]; ++r) {
+      const int k = H[r];
+      if (k >= 0) atomicMax(&F.owner_key[k], key);
+    }
+  }
+}
+
+__global__ void k_sel_walk(FrameDev F, KParams P) {
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  if (F.cnt->err) return;
+  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+    F.tl_acc[ti] = 0;
+    F.tl_nkept[ti] = 0;
+    if (F.tl_n[ti] == 0) continue;
+    const unsigned long long key = tracklet_key(F, P, ti);
+    const int* H = F.tl_hits + (long)ti * kMaxRows;
+    int* K = F.tl_kept + (long)ti * kMaxRows;
+    int kept = 0, shared = 0;
+    for (int r = F.tl_rhi[ti]; r >= F.tl_rlo[ti]; --r) {
+      const int k = H[r];
+      if (k < 0) continue;
+      if (F.owner_key[k] == key) {
+        K[kept++] = k;
+      } else if ((float)(shared + 1) <= P.shared_frac * (float)(kept + 1)) {
+        K[kept++] = k;
+        ++shared;
+      }
+    }
+    F.tl_nkept[ti] = kept;
+    if (kept >= P.min_hits) {
+      F.tl_acc[ti] = 1;
+      for (int r = F.tl_rhi[ti]; r >= F.tl_rlo[ti]; --r) {
+        const int k = H[r];
+        if (k >= 0 && F.owner_key[k] == key) F.sec_owner[k] = ti;
+      }
+    }
+  }
+}
+
+inline unsigned blocks_for(long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void sector_tracking(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  const long n = F.n;
+  if (n > 0) k_row_stats<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+  k_row_grid<<<1, 1024, 0, s>>>(F, P);
+  if (n > 0) k_bin_hist<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+  scan_exclusive(F.bin_cnt, F.bin_first, F.cap_bins + 1, F.scan_tmp, s);
+  if (n > 0) {
+    k_scatter<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+    k_bin_sort<<<sms * 8, kBlock, 0, s>>>(F);
+    k_links<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+    k_clean<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
+  }
+  const int nb = (int)blocks_for(n > 0 ? n : 1, kBlock * kCompactItems);
+  k_start_count<<<nb, kBlock, 0, s>>>(F);
+  k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb, &F.cnt->n_starts);
+  k_start_write<<<nb, kBlock, 0, s>>>(F);
+  k_start_check<<<1, 1, 0, s>>>(F);
+  k_tracklets<<<sms * 16, 128, 0, s>>>(F, P);
+  k_sel_owner<<<sms * 8, kBlock, 0, s>>>(F, P);
+  k_sel_walk<<<sms * 8, kBlock, 0, s>>>(F, P);
+}
+
+// ------------------------------------------------------------------- scan
+namespace {
+constexpr int kScanItems = 8;
+
+__global__ void k_scan_reduce(const int* in, long n, int* part) {
+  __shared__ int sh[32];
+  const long base = (long)blockIdx.x * blockDim.x * kScanItems;
+  int s = 0;
+  for (int j = 0; j < kScanItems; ++j) {
+    const long i = base + (long)j * blockDim.x + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  int tot;
+  block_exscan(s, sh, &tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_apply(const int* in, int* out, long n, const int* part) {
+  __shared__ int sh[32];
+  __shared__ int off;
+  const long base = (long)blockIdx.x * blockDim.x * kScanItems;
+  if (threadIdx.x == 0) off = part[blockIdx.x];
+  __syncthreads();
+  for (int j = 0; j < kScanItems; ++j) {
+    const long i = base + (long)j * blockDim.x + threadIdx.x;
+    const int v = i < n ? in[i] : 0;
+    int tot;
+    const int ex = block_exscan(v, sh, &tot);
+    if (i < n) out[i] = off + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) off += tot;
+    __syncthreads();
+  }
+}
+}  // namespace
+
+void scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s) {
+  const int nb = (int)blocks_for(n, kBlock * kScanItems);
+  k_scan_reduce<<<nb, kBlock, 0, s>>>(in, n, tmp);
+  k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb, tmp + nb);
+  k_scan_apply<<<nb, kBlock, 0, s>>>(in, out, n, tmp);
+}
+
+}  // namespace TPC_NS
+}  // namespace tpc

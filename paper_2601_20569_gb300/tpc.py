@@ -1,0 +1,209 @@
+"""Python binding of libtpc.so (ctypes): argument marshalling only.
+
+Every step of the reconstruction runs in the CUDA library; PyTorch provides
+device memory and streams.  There is no CPU fallback: if the library is not
+built or cannot be loaded, constructing a Tracker raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .options import TrackerOptions
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtpc.so")
+_lib = None
+
+STATUS = {0: "TPC_OK", 1: "TPC_ERR_INVALID_ARG", 2: "TPC_ERR_INVALID_INPUT",
+          3: "TPC_ERR_CAPACITY", 4: "TPC_ERR_CUDA", 5: "TPC_ERR_OOM", 6: "TPC_ERR_TIMEOUT",
+          7: "TPC_ERR_STATE"}
+
+
+class TpcError(RuntimeError):
+    def __init__(self, status: int, msg: str, needed: int = 0):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.needed = needed
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_sectors", ctypes.c_int32), ("n_rows", ctypes.c_int32),
+                ("row_x", ctypes.c_void_p)]
+
+
+class Map(ctypes.Structure):
+    _fields_ = [("n_phi", ctypes.c_int32), ("n_r", ctypes.c_int32), ("n_z", ctypes.c_int32),
+                ("r_min", ctypes.c_float), ("r_max", ctypes.c_float), ("z_min", ctypes.c_float),
+                ("z_max", ctypes.c_float), ("coeff", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("bz", ctypes.c_float), ("sigma_y", ctypes.c_float), ("sigma_z", ctypes.c_float),
+        ("ms_theta", ctypes.c_float), ("link_wy", ctypes.c_float), ("link_wz", ctypes.c_float),
+        ("link_chi2", ctypes.c_float), ("seed_c", ctypes.c_float * 5),
+        ("follow_chi2", ctypes.c_float), ("max_snp", ctypes.c_float), ("score_w", ctypes.c_float),
+        ("shared_frac", ctypes.c_float), ("merge_chi2", ctypes.c_float),
+        ("merge_dy", ctypes.c_float), ("merge_dz", ctypes.c_float), ("int_chi2", ctypes.c_float),
+        ("final_chi2", ctypes.c_float), ("max_miss", ctypes.c_int32),
+        ("min_hits", ctypes.c_int32), ("merge_max_gap", ctypes.c_int32),
+        ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
+        ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
+        ("cap_tracks", ctypes.c_int64),
+    ]
+
+
+class Clusters(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("q", ctypes.c_void_p), ("row", ctypes.c_void_p), ("sector", ctypes.c_void_p)]
+
+
+class Tracks(ctypes.Structure):
+    _fields_ = [("n_tracks", ctypes.c_int64), ("n_cluster_refs", ctypes.c_int64),
+                ("params", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("ndf", ctypes.c_void_p), ("sector", ctypes.c_void_p),
+                ("n_clusters", ctypes.c_void_p), ("cl_offset", ctypes.c_void_p),
+                ("cl_ids", ctypes.c_void_p), ("key", ctypes.c_void_p), ("attach", ctypes.c_void_p)]
+
+
+def load():
+    """Load libtpc.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtpc.so not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    lib.tpc_init.argtypes = [P(Geometry), ctypes.c_float, P(Map), P(Options),
+                             P(ctypes.c_void_p)]
+    lib.tpc_track_timeframe.argtypes = [ctypes.c_void_p, P(Clusters), P(Tracks), ctypes.c_void_p,
+                                        P(ctypes.c_int64)]
+    lib.tpc_set_map.argtypes = [ctypes.c_void_p, P(Map)]
+    lib.tpc_debug_copy.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p,
+                                   ctypes.c_int64, P(ctypes.c_int64)]
+    lib.tpc_last_error.argtypes = [ctypes.c_void_p]
+    lib.tpc_last_error.restype = ctypes.c_char_p
+    lib.tpc_destroy.argtypes = [ctypes.c_void_p]
+    lib.tpc_destroy.restype = None
+    for name in ("tpc_init", "tpc_track_timeframe", "tpc_set_map", "tpc_debug_copy"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def make_options(opts: dict | TrackerOptions | None = None, *, mode: int = 0,
+                 cap_clusters: int = 1 << 20, cap_tracklets: int = 0,
+                 cap_tracks: int = 0) -> Options:
+    if opts is None:
+        opts = TrackerOptions()
+    d = opts.as_dict() if isinstance(opts, TrackerOptions) else dict(opts)
+    o = Options()
+    for name, typ in Options._fields_:
+        if name == "seed_c":
+            for i, v in enumerate(d["seed_c"]):
+                o.seed_c[i] = float(v)
+        elif name == "mode":
+            o.mode = int(d.get("mode", mode))
+        elif name == "cap_clusters":
+            o.cap_clusters = int(cap_clusters)
+        elif name == "cap_tracklets":
+            o.cap_tracklets = int(cap_tracklets)
+        elif name == "cap_tracks":
+            o.cap_tracks = int(cap_tracks)
+        elif typ is ctypes.c_float:
+            setattr(o, name, float(d[name]))
+        else:
+            setattr(o, name, int(d[name]))
+    return o
+
+
+_DBG_DTYPE = {
+    "rows": None, "bin_first": np.int32, "sy": np.float32, "sz": np.float32, "sid": np.int32,
+    "srow": np.uint16, "lup": np.int32, "ldn": np.int32, "cup": np.int32, "cdn": np.int32,
+    "starts": np.int32, "tl_n": np.int32, "tl_rlo": np.int32, "tl_rhi": np.int32,
+    "tl_chi2": np.float32, "tl_x": np.float32, "tl_par": np.float32, "tl_cov": np.float32,
+    "tl_hits": np.int32, "tl_kept": np.int32, "tl_acc": np.int32, "tl_nkept": np.int32,
+    "owner_key": np.uint64, "sec_owner": np.int32, "counters": np.int32,
+}
+ROWGRID_DTYPE = np.dtype([("bin0", "<i4"), ("nY", "<i4"), ("nZ", "<i4"), ("cl0", "<i4"),
+                          ("ncl", "<i4"), ("y0", "<f4"), ("invDy", "<f4"), ("z0", "<f4"),
+                          ("invDz", "<f4")])
+
+
+class Tracker:
+    """One reconstruction context (device buffers sized for ``cap_clusters``)."""
+
+    def __init__(self, row_x, opts: dict | TrackerOptions | None = None, *, mode: int = 0,
+                 cap_clusters: int = 1 << 20, cap_tracklets: int = 0, cap_tracks: int = 0,
+                 bz: float | None = None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the tracker needs a CUDA device")
+        self.lib = load()
+        self.opts = make_options(opts, mode=mode, cap_clusters=cap_clusters,
+                                 cap_tracklets=cap_tracklets, cap_tracks=cap_tracks)
+        self._row_x = np.ascontiguousarray(row_x, dtype=np.float32)
+        geo = Geometry(36, len(self._row_x), self._row_x.ctypes.data)
+        self._ctx = ctypes.c_void_p()
+        torch.cuda.init()
+        rc = self.lib.tpc_init(ctypes.byref(geo), float(self.opts.bz if bz is None else bz), None,
+                               ctypes.byref(self.opts), ctypes.byref(self._ctx))
+        if rc:
+            raise TpcError(rc, "tpc_init failed")
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self.lib.tpc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    __del__ = close
+
+    def last_error(self) -> str:
+        return self.lib.tpc_last_error(self._ctx).decode()
+
+    @staticmethod
+    def to_device(y, z, q, row, sector, device="cuda"):
+        import torch
+
+        def t(a, dt):
+            return torch.as_tensor(np.ascontiguousarray(a, dtype=dt)).to(device)
+
+        return (t(y, np.float32), t(z, np.float32), t(q, np.uint16).view(torch.int16)
+                if q is not None else None, t(row, np.uint8), t(sector, np.uint8))
+
+    def track(self, y, z, q, row, sector, stream=None) -> Tracks:
+        """Track one frame given device tensors (float32 y, z; uint8 row, sector)."""
+        import torch
+
+        n = int(y.shape[0])
+        cl = Clusters(n, y.data_ptr(), z.data_ptr(), q.data_ptr() if q is not None else None,
+                      row.data_ptr(), sector.data_ptr())
+        out = Tracks()
+        needed = ctypes.c_int64(0)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = self.lib.tpc_track_timeframe(self._ctx, ctypes.byref(cl), ctypes.byref(out),
+                                          ctypes.c_void_p(s.cuda_stream), ctypes.byref(needed))
+        if rc:
+            raise TpcError(rc, self.last_error(), needed.value)
+        return out
+
+    def debug(self, name: str) -> np.ndarray:
+        nb = ctypes.c_int64(0)
+        rc = self.lib.tpc_debug_copy(self._ctx, name.encode(), None, 0, ctypes.byref(nb))
+        if rc:
+            raise TpcError(rc, self.last_error())
+        dt = ROWGRID_DTYPE if name == "rows" else np.dtype(_DBG_DTYPE.get(name, np.uint8))
+        a = np.empty(nb.value // dt.itemsize, dtype=dt)
+        if nb.value:
+            rc = self.lib.tpc_debug_copy(self._ctx, name.encode(), a.ctypes.data, nb.value,
+                                         ctypes.byref(nb))
+            if rc:
+                raise TpcError(rc, self.last_error())
+        return a
