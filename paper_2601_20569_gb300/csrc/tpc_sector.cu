@@ -519,8 +519,8 @@ __global__ void k_sel_walk(FrameDev F, KParams P) {
         ++shared;
       }
     }
-    F.tl_nkept[ti] = kept;
     if (kept >= P.min_hits) {
+      F.tl_nkept[ti] = kept;
       F.tl_acc[ti] = 1;
       for (int r = F.tl_rhi[ti]; r >= F.tl_rlo[ti]; --r) {
         const int k = H[r];
