@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput of TPC time-frame tracking on GB300: clusters/s.
+
+One step = the whole reconstruction chain over a batch of synthetic 2.8 ms
+Pb-Pb time frames (50 kHz: Poisson(140) collisions per frame, ~2e7 clusters
+each, per-sector occupancy varying ~10x).  Inputs are generated on the host
+(seeded), uploaded once and stay resident in HBM for the device-timed value;
+the end-to-end figure copies each step's clusters from pinned host memory and
+reads the results back inside its timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs are independent replicas (one process per GPU, each with its
+own frames): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "clusters/s tracked per GB300 (2.8 ms Pb-Pb time frame) vs oracle; % HBM roofline"
+UNIT = "clusters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=8)
+    ap.add_argument("--workload", default="timeframe")
+    ap.add_argument("--mode", default="fast", choices=["fast", "strict"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warm-up plus one step and exit (for ncu launch lists)")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_frames(args, rank):
+    from paper_2601_20569_gb300 import synth
+
+    frames = []
+    for k in range(args.frames):
+        frames.append(synth.generate(args.workload, frame=rank * args.frames + k))
+    return frames
+
+
+def cpu_baseline(frames, seconds):
+    """The strict CPU oracle, as it stands, on a bounded sample: whole sectors
+    of the first frame until about `seconds` of CPU time are spent."""
+    import numpy as np
+
+    import oracle
+    from paper_2601_20569_gb300 import synth
+    from paper_2601_20569_gb300.options import TrackerOptions
+
+    f = frames[0]
+    opts = TrackerOptions().as_dict()
+    order = np.argsort(f.sector, kind="stable")
+    bounds = np.searchsorted(f.sector[order], np.arange(37))
+    n_done, t_done, sectors = 0, 0.0, 0
+    for s in range(36):
+        idx = order[bounds[s]:bounds[s + 1]]
+        t0 = time.perf_counter()
+        oracle.track(f.y[idx], f.z[idx], f.row[idx], f.sector[idx], synth.row_x(), opts)
+        t_done += time.perf_counter() - t0
+        n_done += len(idx)
+        sectors += 1
+        if t_done >= seconds:
+            break
+    return {"value": n_done / t_done, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sectors} of 36 sectors of frame 0 ({n_done} clusters, "
+                      f"{t_done:.1f} s), strict FP32 oracle, single thread"}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm, on the host cores."""
+    import numpy as np
+
+    import oracle
+    from paper_2601_20569_gb300 import synth
+    from paper_2601_20569_gb300.options import TrackerOptions
+
+    f = synth.generate(args.workload, frame=0)
+    opts = TrackerOptions().as_dict()
+    # one step = a bounded sample: the clusters of two sectors of frame 0
+    sel = np.nonzero(f.sector < 2)[0]
+    run = lambda: oracle.track(f.y[sel], f.z[sel], f.row[sel], f.sector[sel], synth.row_x(), opts)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    dt = time.perf_counter() - t0
+    v = len(sel) * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": f"{args.workload} (sample: sectors 0-1 of "
+                                                     f"frame 0, {len(sel)} clusters per step)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"sectors 0-1 of frame 0 ({len(sel)} clusters) per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# Algorithmic bytes per unit of each stage (the minimum the stage must move).
+def stage_bytes(name: str, n_clusters: int, tl_hits: int, n_tracklets: int) -> float:
+    if name == "grid":       # read y,z,row,sector; write sorted y,z,id,row
+        return n_clusters * (10 + 14)
+    if name == "links":      # read sorted y,z,id once; write 2 links; cleaner: read+write links
+        return n_clusters * (12 + 8 + 8 + 8)
+    if name == "starts":     # read cleaned links; write start list
+        return n_clusters * 8 + n_tracklets * 4
+    if name == "tracklets":  # two passes reading y,z,id of each used cluster, hit writes, state
+        return tl_hits * (2 * 12 + 4) + n_tracklets * 4 * 24
+    if name == "select":     # owner max and walk: hits read twice, owner key read/written
+        return tl_hits * (4 * 2 + 8 * 2) + n_tracklets * 16
+    return 0.0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2601_20569_gb300 import build as libbuild
+    from paper_2601_20569_gb300 import synth, tpc
+    from paper_2601_20569_gb300.options import MODE_FAST, MODE_STRICT, TrackerOptions
+
+    libbuild.build()
+    frames = make_frames(args, rank)
+    n_per_step = sum(f.n for f in frames)
+    cap = max(f.n for f in frames)
+    mode = MODE_FAST if args.mode == "fast" else MODE_STRICT
+    tr = tpc.Tracker(synth.row_x(), TrackerOptions(), mode=mode, cap_clusters=cap)
+    dev = [tr.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        launches = 0
+        for d in dev:
+            tr.track(*d, stream=stream)
+            launches += tr.last_launches()
+        return launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if args.profile_only:
+        step()
+        torch.cuda.synchronize()
+        return
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            launches += step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_per_step * world * args.steps / (ms / 1e3)
+
+    # per-stage device times (CUDA events on the launching stream), a separate pass
+    tr.profile(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    stages = tr.stage_stats()
+    tr.profile(False)
+    tl_n = tr.debug("tl_n")
+    tl_hits_last = int(tl_n.sum())
+    n_tl_last = int(tl_n.size)
+    # scale per-frame counts of the last frame to the whole step by cluster share
+    scale = n_per_step / frames[-1].n
+    hbm, peak_kind = peaks()
+    dom = max(stages, key=lambda s: s["ms"])
+    launches_per_call = max(1, dom["launches"] // max(1, dom["calls"]))
+    per_launch_ms = dom["ms"] / max(1, dom["calls"])  # one stage call per frame
+    bytes_call = stage_bytes(dom["name"], n_per_step / len(frames), tl_hits_last * scale / len(frames),
+                             n_tl_last * scale / len(frames))
+    achieved = bytes_call / (per_launch_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "kernel": f"stage '{dom['name']}' ({launches_per_call} kernels per frame)",
+            "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # end to end through the public API: pinned host clusters in, tracks out
+    host = []
+    for f in frames:
+        host.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+                          (f.y, f.z, f.q.view(np.int16), f.row, f.sector)))
+    dbuf = [tuple(torch.empty_like(h, device="cuda") for h in hs) for hs in host]
+    attach_host = torch.empty(cap, dtype=torch.int32).pin_memory()
+    h2d = sum(sum(h.numel() * h.element_size() for h in hs) for hs in host)
+    d2h = 0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for hs, ds, f in zip(host, dbuf, frames):
+            for h, d in zip(hs, ds):
+                d.copy_(h, non_blocking=True)
+            tr.track(ds[0], ds[1], ds[2], ds[3], ds[4], stream=stream)
+            own = tr.result_attach()
+            attach_host[:f.n].copy_(own, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    d2h = sum(4 * f.n for f in frames)
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": n_per_step * world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {args.frames} x 2.8 ms frames, 50 kHz Pb-Pb, "
+                               f"{n_per_step} clusters per step", "frames": args.frames,
+                   "clusters_per_step": n_per_step, "mode": args.mode,
+                   "l2": "inputs larger than L2 (each frame > 129 MB resident)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "stages_ms_per_frame": {s["name"]: s["ms"] / max(1, s["calls"]) for s in stages},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(frames, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

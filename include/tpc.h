@@ -153,6 +153,20 @@ tpc_status tpc_set_map(tpc_ctx* ctx, const tpc_map* map);
 tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_t cap_bytes,
                           int64_t* bytes);
 
+/* Per-stage timing: when enabled, every tracking call records CUDA events
+ * on its stream between the hot-path stages and accumulates their durations
+ * (enabling resets the totals). */
+tpc_status tpc_profile(tpc_ctx* ctx, int enable);
+
+/* Totals of stage i (0-based, in execution order): name, summed milliseconds,
+ * number of profiled calls, kernels launched.  TPC_ERR_INVALID_ARG past the
+ * last stage. */
+tpc_status tpc_stage_stats(const tpc_ctx* ctx, int32_t i, const char** name, double* ms_total,
+                           int64_t* calls, int64_t* launches);
+
+/* Kernels launched by the last tracking call. */
+int64_t tpc_last_launches(const tpc_ctx* ctx);
+
 /* Message of the last failed call on this context (never NULL). */
 const char* tpc_last_error(const tpc_ctx* ctx);
 

@@ -391,7 +391,7 @@ struct Frame {
   long n = 0;
   std::vector<Real> y, z;
   std::vector<int> row, sector;
-  // a1: ids of each (sector,row), sorted by (y, id)
+  // a1: ids of each (sector,row), sorted by (z, id)
   std::vector<std::vector<int>> rows;
   int rid(int s, int r, const Params<Real>& P) const { return s * P.n_rows + r; }
 };
@@ -402,12 +402,12 @@ void build_rows(Frame<Real>& F, const Params<Real>& P) {
   for (long i = 0; i < F.n; ++i) F.rows[F.rid(F.sector[i], F.row[i], P)].push_back((int)i);
   for (auto& v : F.rows)
     std::sort(v.begin(), v.end(), [&](int a, int b) {
-      if (F.y[a] != F.y[b]) return F.y[a] < F.y[b];
+      if (F.z[a] != F.z[b]) return F.z[a] < F.z[b];
       return a < b;
     });
 }
 
-// Visit ids of row (s,r) whose y lies within [lo, hi] (a superset filter; the
+// Visit ids of row (s,r) whose z lies within [lo, hi] (a superset filter; the
 // callers apply their exact tests).  brute_force visits the whole row.
 template <typename Real, typename Fn>
 void for_row_range(const Frame<Real>& F, const Params<Real>& P, int s, int r, Real lo, Real hi,
@@ -417,8 +417,8 @@ void for_row_range(const Frame<Real>& F, const Params<Real>& P, int s, int r, Re
     for (int id : v) fn(id);
     return;
   }
-  auto it = std::lower_bound(v.begin(), v.end(), lo, [&](int id, Real val) { return F.y[id] < val; });
-  for (; it != v.end() && F.y[*it] <= hi; ++it) fn(*it);
+  auto it = std::lower_bound(v.begin(), v.end(), lo, [&](int id, Real val) { return F.z[id] < val; });
+  for (; it != v.end() && F.z[*it] <= hi; ++it) fn(*it);
 }
 
 // ------------------------------------------------------------- a2 neighbours
@@ -441,10 +441,10 @@ void find_links(const Frame<Real>& F, const Params<Real>& P, std::vector<int>& u
     auto inwin = [&](int id) {
       return std::fabs(F.y[id] - yc) <= P.link_wy && std::fabs(F.z[id] - zc) <= P.link_wz;
     };
-    for_row_range(F, P, s, r + 1, yc - P.link_wy - margin, yc + P.link_wy + margin, [&](int id) {
+    for_row_range(F, P, s, r + 1, zc - P.link_wz - margin, zc + P.link_wz + margin, [&](int id) {
       if (inwin(id)) U.push_back(id);
     });
-    for_row_range(F, P, s, r - 1, yc - P.link_wy - margin, yc + P.link_wy + margin, [&](int id) {
+    for_row_range(F, P, s, r - 1, zc - P.link_wz - margin, zc + P.link_wz + margin, [&](int id) {
       if (inwin(id)) D.push_back(id);
     });
     const Real xd = P.row_x[r - 1], xc = P.row_x[r], xu = P.row_x[r + 1];
@@ -507,7 +507,10 @@ int pick(const Frame<Real>& F, const Params<Real>& P, const Track<Real>& t, int 
   const Real hz = std::sqrt(P.follow_chi2 * (t.c[2] + P.meas_sz2)) * Real(1.001) + Real(0.01);
   int best = -1;
   Resid<Real> bres{};
-  for_row_range(F, P, s, r, t.p[0] - hy, t.p[0] + hy, [&](int id) {
+  const Real ylo = t.p[0] - hy, yhi = t.p[0] + hy;
+  const Real margin = Real(0.01);
+  for_row_range(F, P, s, r, t.p[1] - hz - margin, t.p[1] + hz + margin, [&](int id) {
+    if (!(F.y[id] >= ylo && F.y[id] <= yhi)) return;
     if (std::fabs(F.z[id] - t.p[1]) > hz) return;
     const Resid<Real> R = residual(t, F.y[id], F.z[id], P);
     if (!(R.chi2 < P.follow_chi2)) return;

@@ -15,8 +15,32 @@
 
 using namespace tpc;
 
+namespace {
+using StageFn = int (*)(FrameDev&, const KParams&, int, cudaStream_t);
+struct StageDef {
+  const char* name;
+  StageFn strict_fn;
+  StageFn fast_fn;
+};
+// Hot-path stages in execution order.
+const StageDef kStages[] = {
+    {"grid", strict::stage_grid, fast::stage_grid},
+    {"links", strict::stage_links, fast::stage_links},
+    {"starts", strict::stage_starts, fast::stage_starts},
+    {"tracklets", strict::stage_tracklets, fast::stage_tracklets},
+    {"select", strict::stage_select, fast::stage_select},
+};
+constexpr int kNumStages = sizeof(kStages) / sizeof(kStages[0]);
+}  // namespace
+
 struct tpc_ctx {
   tpc_options opt{};
+  bool prof = false;
+  cudaEvent_t ev[kNumStages + 1] = {};
+  double stage_ms[kNumStages] = {};
+  long stage_calls[kNumStages] = {};
+  long stage_launches[kNumStages] = {};
+  long launches_last = 0;
   KParams P{};
   int sms = 0;
   int n_rows = 0, n_sectors = 0;
@@ -222,13 +246,26 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
     CK(cudaMemsetAsync(F.owner_key, 0, sizeof(unsigned long long) * n, s));
     CK(cudaMemsetAsync(F.sec_owner, 0xFF, sizeof(int) * n, s));
   }
-  if (ctx->opt.mode == 0)
-    strict::sector_tracking(F, ctx->P, ctx->sms, s);
-  else
-    fast::sector_tracking(F, ctx->P, ctx->sms, s);
+  ctx->launches_last = 0;
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
+  for (int i = 0; i < kNumStages; ++i) {
+    const StageFn fn = ctx->opt.mode == 0 ? kStages[i].strict_fn : kStages[i].fast_fn;
+    const int k = fn(F, ctx->P, ctx->sms, s);
+    ctx->launches_last += k;
+    ctx->stage_launches[i] += k;
+    if (ctx->prof) CK(cudaEventRecord(ctx->ev[i + 1], s));
+  }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&ctx->host_cnt, F.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (ctx->prof) {
+    for (int i = 0; i < kNumStages; ++i) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+      ctx->stage_ms[i] += ms;
+      ctx->stage_calls[i] += 1;
+    }
+  }
   const Counters& c = ctx->host_cnt;
   std::memset(out, 0, sizeof(*out));
   if (c.err & kErrInput) return fail(ctx, TPC_ERR_INVALID_INPUT, "invalid cluster (NaN/Inf, row or sector out of range)");
@@ -241,6 +278,7 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
     return fail(ctx, TPC_ERR_CAPACITY, "start hits %d exceed tracklet capacity %ld", c.n_starts,
                 F.cap_tl);
   }
+  out->attach = F.sec_owner;
   return TPC_OK;
 }
 
@@ -290,6 +328,33 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   return TPC_OK;
 }
 
+tpc_status tpc_profile(tpc_ctx* ctx, int enable) {
+  if (!ctx) return TPC_ERR_INVALID_ARG;
+  if (enable && !ctx->ev[0]) {
+    for (auto& e : ctx->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(ctx, TPC_ERR_CUDA, "event create");
+  }
+  ctx->prof = enable != 0;
+  for (int i = 0; i < kNumStages; ++i) {
+    ctx->stage_ms[i] = 0.0;
+    ctx->stage_calls[i] = 0;
+    ctx->stage_launches[i] = 0;
+  }
+  return TPC_OK;
+}
+
+tpc_status tpc_stage_stats(const tpc_ctx* ctx, int32_t i, const char** name, double* ms_total,
+                           int64_t* calls, int64_t* launches) {
+  if (!ctx || i < 0 || i >= kNumStages) return TPC_ERR_INVALID_ARG;
+  if (name) *name = kStages[i].name;
+  if (ms_total) *ms_total = ctx->stage_ms[i];
+  if (calls) *calls = ctx->stage_calls[i];
+  if (launches) *launches = ctx->stage_launches[i];
+  return TPC_OK;
+}
+
+int64_t tpc_last_launches(const tpc_ctx* ctx) { return ctx ? ctx->launches_last : 0; }
+
 const char* tpc_last_error(const tpc_ctx* ctx) {
   return ctx ? ctx->err.c_str() : "null context";
 }
@@ -297,6 +362,8 @@ const char* tpc_last_error(const tpc_ctx* ctx) {
 void tpc_destroy(tpc_ctx* ctx) {
   if (!ctx) return;
   for (void* p : ctx->allocs) cudaFree(p);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 

@@ -8,9 +8,14 @@
 
 namespace tpc {
 
-#define TPC_DECLARE_LAUNCHERS                                                        \
-  void sector_tracking(FrameDev& F, const KParams& P, int sms, cudaStream_t s);    \
-  void scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s);
+// Each launcher enqueues one stage on stream s and returns its kernel count.
+#define TPC_DECLARE_LAUNCHERS                                                       \
+  int stage_grid(FrameDev& F, const KParams& P, int sms, cudaStream_t s);         \
+  int stage_links(FrameDev& F, const KParams& P, int sms, cudaStream_t s);        \
+  int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
+  int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s);    \
+  int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
+  int scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s);
 
 namespace strict {
 TPC_DECLARE_LAUNCHERS

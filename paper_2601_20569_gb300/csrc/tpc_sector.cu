@@ -530,30 +530,55 @@ __global__ void k_sel_walk(FrameDev F, KParams P) {
   }
 }
 
-inline unsigned blocks_for(long n, int b) { return (unsigned)((n + b - 1) / b); }
-
 }  // namespace
 
-void sector_tracking(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+inline unsigned blocks_for(long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Stage launchers; each returns the number of kernels it enqueued.
+int stage_grid(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const long n = F.n;
-  if (n > 0) k_row_stats<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
-  k_row_grid<<<1, 1024, 0, s>>>(F, P);
-  if (n > 0) k_bin_hist<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
-  scan_exclusive(F.bin_cnt, F.bin_first, F.cap_bins + 1, F.scan_tmp, s);
+  int k = 0;
+  if (n > 0) { k_row_stats<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); ++k; }
+  k_row_grid<<<1, 1024, 0, s>>>(F, P); ++k;
+  if (n > 0) { k_bin_hist<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); ++k; }
+  k += scan_exclusive(F.bin_cnt, F.bin_first, F.cap_bins + 1, F.scan_tmp, s);
   if (n > 0) {
     k_scatter<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
     k_bin_sort<<<sms * 8, kBlock, 0, s>>>(F);
-    k_links<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
-    k_clean<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
+    k += 2;
   }
+  return k;
+}
+
+int stage_links(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  (void)sms;
+  const long n = F.n;
+  if (n <= 0) return 0;
+  k_links<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+  k_clean<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
+  return 2;
+}
+
+int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  (void)P; (void)sms;
+  const long n = F.n;
   const int nb = (int)blocks_for(n > 0 ? n : 1, kBlock * kCompactItems);
   k_start_count<<<nb, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb, &F.cnt->n_starts);
   k_start_write<<<nb, kBlock, 0, s>>>(F);
   k_start_check<<<1, 1, 0, s>>>(F);
+  return 4;
+}
+
+int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_tracklets<<<sms * 16, 128, 0, s>>>(F, P);
+  return 1;
+}
+
+int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_sel_owner<<<sms * 8, kBlock, 0, s>>>(F, P);
   k_sel_walk<<<sms * 8, kBlock, 0, s>>>(F, P);
+  return 2;
 }
 
 // ------------------------------------------------------------------- scan
@@ -592,11 +617,12 @@ __global__ void k_scan_apply(const int* in, int* out, long n, const int* part) {
 }
 }  // namespace
 
-void scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s) {
+int scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s) {
   const int nb = (int)blocks_for(n, kBlock * kScanItems);
   k_scan_reduce<<<nb, kBlock, 0, s>>>(in, n, tmp);
   k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb, tmp + nb);
   k_scan_apply<<<nb, kBlock, 0, s>>>(in, out, n, tmp);
+  return 3;
 }
 
 }  // namespace TPC_NS

@@ -69,6 +69,22 @@ class Tracks(ctypes.Structure):
                 ("cl_ids", ctypes.c_void_p), ("key", ctypes.c_void_p), ("attach", ctypes.c_void_p)]
 
 
+class _DevArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), True), "version": 2}
+
+
+def wrap_device(ptr, shape, typestr):
+    """Zero-copy torch view of library-owned device memory (valid until the next call)."""
+    import torch
+
+    if not ptr or 0 in tuple(shape):
+        dt = {"<i4": torch.int32, "<f4": torch.float32}[typestr]
+        return torch.empty(shape, dtype=dt, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+
+
 def load():
     """Load libtpc.so (raises if it was not built: there is no fallback)."""
     global _lib
@@ -88,6 +104,13 @@ def load():
                                    ctypes.c_int64, P(ctypes.c_int64)]
     lib.tpc_last_error.argtypes = [ctypes.c_void_p]
     lib.tpc_last_error.restype = ctypes.c_char_p
+    lib.tpc_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.tpc_profile.restype = ctypes.c_int
+    lib.tpc_stage_stats.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_char_p),
+                                    P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_int64)]
+    lib.tpc_stage_stats.restype = ctypes.c_int
+    lib.tpc_last_launches.argtypes = [ctypes.c_void_p]
+    lib.tpc_last_launches.restype = ctypes.c_int64
     lib.tpc_destroy.argtypes = [ctypes.c_void_p]
     lib.tpc_destroy.restype = None
     for name in ("tpc_init", "tpc_track_timeframe", "tpc_set_map", "tpc_debug_copy"):
@@ -192,7 +215,37 @@ class Tracker:
                                           ctypes.c_void_p(s.cuda_stream), ctypes.byref(needed))
         if rc:
             raise TpcError(rc, self.last_error(), needed.value)
+        self._last = (out, n)
         return out
+
+    def result_attach(self):
+        """Device tensor view (int32[n_clusters]) of the last call's attachments."""
+        out, n = self._last
+        return wrap_device(out.attach, (n,), "<i4")
+
+    def profile(self, enable: bool = True) -> None:
+        rc = self.lib.tpc_profile(self._ctx, int(enable))
+        if rc:
+            raise TpcError(rc, self.last_error())
+
+    def stage_stats(self) -> list[dict]:
+        out = []
+        i = 0
+        while True:
+            name = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            calls = ctypes.c_int64()
+            launches = ctypes.c_int64()
+            if self.lib.tpc_stage_stats(self._ctx, i, ctypes.byref(name), ctypes.byref(ms),
+                                        ctypes.byref(calls), ctypes.byref(launches)):
+                break
+            out.append(dict(name=name.value.decode(), ms=ms.value, calls=calls.value,
+                            launches=launches.value))
+            i += 1
+        return out
+
+    def last_launches(self) -> int:
+        return int(self.lib.tpc_last_launches(self._ctx))
 
     def debug(self, name: str) -> np.ndarray:
         nb = ctypes.c_int64(0)
