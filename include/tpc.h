@@ -84,12 +84,15 @@ typedef struct {
   float link_chi2;          /* max squared distance of the middle cluster to the d-u line [cm^2] */
   float seed_c[5];          /* seed covariance diagonal */
   float follow_chi2;        /* cluster pick-up cut of the track following (2 dof) */
-  float max_snp;            /* |sin(phi)| limit of the sector model */
+  float max_snp;            /* |sin(phi)| limit of seeding and following */
+  float fit_max_snp;        /* |sin(phi)| limit of refits, merging and the final fit */
   float score_w;            /* ambiguity score = n_clusters - score_w * chi2/ndf */
   float shared_frac;        /* allowed shared-cluster fraction (paper default 10 %) */
   float merge_chi2, merge_dy, merge_dz; /* merging: 5-dof chi2 cut and position gates */
   float int_chi2;           /* interpolation cut of fit iteration 2, candidate cut (2 dof) */
   float final_chi2;         /* simple chi2 cut of fit iteration 3 */
+  float attach_margin;      /* widening of the Phase II search window [cm] */
+  float edge_margin;        /* following stops at |y| > x*tan(10 deg) + edge_margin [cm] */
   int32_t max_miss;         /* consecutive empty rows ending the following */
   int32_t min_hits;         /* minimum clusters of a tracklet / track */
   int32_t merge_max_gap;    /* max rows between merged segments */

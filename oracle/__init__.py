@@ -32,6 +32,7 @@ class _Opt(ctypes.Structure):
         ("seed_c", ctypes.c_float * 5),
         ("follow_chi2", ctypes.c_float),
         ("max_snp", ctypes.c_float),
+        ("fit_max_snp", ctypes.c_float),
         ("score_w", ctypes.c_float),
         ("shared_frac", ctypes.c_float),
         ("merge_chi2", ctypes.c_float),
@@ -39,6 +40,8 @@ class _Opt(ctypes.Structure):
         ("merge_dz", ctypes.c_float),
         ("int_chi2", ctypes.c_float),
         ("final_chi2", ctypes.c_float),
+        ("attach_margin", ctypes.c_float),
+        ("edge_margin", ctypes.c_float),
         ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32),
         ("merge_max_gap", ctypes.c_int32),
@@ -68,7 +71,14 @@ def _load():
         lib = ctypes.CDLL(_LIB)
         lib.orc_track.restype = ctypes.c_int
         lib.orc_track.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 5 + [
-            ctypes.POINTER(_Opt), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+            ctypes.POINTER(_Opt), ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+            ctypes.POINTER(ctypes.c_void_p)]
+        lib.orc_track_f64.restype = ctypes.c_int
+        lib.orc_track_f64.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 5 + [
+            ctypes.POINTER(_Opt), ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        lib.orc_correct.restype = ctypes.c_int
+        lib.orc_correct.argtypes = [ctypes.POINTER(_Opt), ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]
         lib.orc_info.restype = ctypes.c_long
         lib.orc_info.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p]
         lib.orc_copy.restype = ctypes.c_int
@@ -97,6 +107,20 @@ def _opt(opts: dict) -> _Opt:
     return o
 
 
+class _Map(ctypes.Structure):
+    _fields_ = [("n_phi", ctypes.c_int32), ("n_r", ctypes.c_int32), ("n_z", ctypes.c_int32),
+                ("r_min", ctypes.c_float), ("r_max", ctypes.c_float), ("z_min", ctypes.c_float),
+                ("z_max", ctypes.c_float), ("coeff", ctypes.c_void_p)]
+
+
+def _map(coeff, r_range=(85.0, 245.0), z_range=(-250.0, 250.0)):
+    if coeff is None:
+        return None, None
+    c = np.ascontiguousarray(coeff, dtype=np.float32)
+    nz, nr, nphi = c.shape[1:]
+    return _Map(nphi, nr, nz, r_range[0], r_range[1], z_range[0], z_range[1], c.ctypes.data), c
+
+
 class Result(dict):
     """Named arrays produced by one oracle run."""
 
@@ -116,8 +140,11 @@ def _collect(lib, h) -> Result:
     return res
 
 
-def track(y, z, row, sector, row_x, opts: dict, *, fp64: bool = False) -> Result:
-    """Run the oracle chain on host arrays; ``fp64`` selects the double build."""
+def track(y, z, row, sector, row_x, opts: dict, *, fp64: bool = False, full: bool = False,
+          dist_map=None) -> Result:
+    """Run the oracle chain on host arrays; ``fp64`` selects the double build,
+    ``full`` adds merging, the three-iteration fit and the attachment, with the
+    optional correction map ``dist_map`` ([3][n_z][n_r][n_phi] control points)."""
     lib = _load()
     y = np.ascontiguousarray(y, dtype=np.float32)
     z = np.ascontiguousarray(z, dtype=np.float32)
@@ -125,9 +152,11 @@ def track(y, z, row, sector, row_x, opts: dict, *, fp64: bool = False) -> Result
     sector = np.ascontiguousarray(sector, dtype=np.uint8)
     rx = np.ascontiguousarray(row_x, dtype=np.float64)
     o = _opt(opts)
+    m, _keep = _map(dist_map)
     h = ctypes.c_void_p()
     rc = lib.orc_track(len(y), y.ctypes.data, z.ctypes.data, row.ctypes.data, sector.ctypes.data,
-                       rx.ctypes.data, ctypes.byref(o), int(fp64), ctypes.byref(h))
+                       rx.ctypes.data, ctypes.byref(o), ctypes.byref(m) if m is not None else None,
+                       int(full), int(fp64), ctypes.byref(h))
     if rc:
         raise ValueError(f"oracle rejected the input (code {rc})")
     try:
@@ -175,3 +204,41 @@ def seed(points, row_x, opts, fp64=True):
     io[:9] = np.asarray(points, dtype=np.float64).ravel()
     rc, io = _op(3, io, row_x, opts, fp64)
     return (None if rc else (io[9:14], io[14:29], io[29]))
+
+
+def track_f64(y, z, row, sector, row_x, opts: dict, *, full: bool = True, dist_map=None) -> Result:
+    """FP64 oracle chain with FP64 cluster coordinates (exact-input pins)."""
+    lib = _load()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    row = np.ascontiguousarray(row, dtype=np.uint8)
+    sector = np.ascontiguousarray(sector, dtype=np.uint8)
+    rx = np.ascontiguousarray(row_x, dtype=np.float64)
+    o = _opt(opts)
+    m, _keep = _map(dist_map)
+    h = ctypes.c_void_p()
+    rc = lib.orc_track_f64(len(y), y.ctypes.data, z.ctypes.data, row.ctypes.data,
+                           sector.ctypes.data, rx.ctypes.data, ctypes.byref(o),
+                           ctypes.byref(m) if m is not None else None, int(full), ctypes.byref(h))
+    if rc:
+        raise ValueError(f"oracle rejected the input (code {rc})")
+    try:
+        return _collect(lib, h)
+    finally:
+        lib.orc_free(h)
+
+
+def correct(sector, x, y, z, z0, ref, row_x, opts, dist_map):
+    """FP64 map displacement D and the measurement projected on the row along `ref`."""
+    lib = _load()
+    io = np.zeros(16)
+    io[:5] = (sector, x, y, z, z0)
+    io[5:10] = ref
+    o = _opt(opts)
+    m, _keep = _map(dist_map)
+    rx = np.ascontiguousarray(row_x, dtype=np.float64)
+    rc = lib.orc_correct(ctypes.byref(o), rx.ctypes.data, ctypes.byref(m) if m is not None else None,
+                         io.ctypes.data)
+    if rc:
+        return None
+    return io[10:13].copy(), io[13:15].copy()

@@ -51,11 +51,14 @@ struct orc_options {
   float link_wy, link_wz, link_chi2;
   float seed_c[5];       // diagonal of the seed covariance
   float follow_chi2;
-  float max_snp;
+  float max_snp;         // |sin(phi)| limit of seeding and following
+  float fit_max_snp;     // |sin(phi)| limit of refits, merging and the final fit
   float score_w;
   float shared_frac;
   float merge_chi2, merge_dy, merge_dz;
   float int_chi2, final_chi2;
+  float attach_margin;   // widening of the Phase II search window [cm]
+  float edge_margin;     // following stops |y| > x*tan(10 deg) + edge_margin [cm]
   int32_t max_miss;
   int32_t min_hits;
   int32_t merge_max_gap;
@@ -65,6 +68,13 @@ struct orc_options {
   int32_t n_rows;
   int32_t n_sectors;
 };
+// Correction map of the oracle (host memory): layout [3][n_z][n_r][n_phi].
+struct orc_map {
+  int32_t n_phi, n_r, n_z;
+  float r_min, r_max, z_min, z_max;
+  const float* coeff;
+};
+
 }
 
 namespace orc {
@@ -130,8 +140,9 @@ struct Track {
 template <typename Real>
 struct Params {
   Real kb, tan_half, rot_c, rot_s, link_wy, link_wz, link_chi2;
-  Real seed_c[5], meas_sy2, meas_sz2, ms_theta2, row_pitch_inv, follow_chi2, max_snp, score_w,
-      shared_frac, merge_chi2, merge_dy, merge_dz, int_chi2, final_chi2;
+  Real seed_c[5], meas_sy2, meas_sz2, ms_theta2, row_pitch_inv, follow_chi2, max_snp, fit_max_snp, score_w,
+      shared_frac, merge_chi2, merge_dy, merge_dz, int_chi2, final_chi2, attach_margin,
+      edge_margin, merge_zspan;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors;
   std::vector<Real> row_x;
 };
@@ -151,10 +162,17 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
       (Real)((double)(o.n_rows - 1) / ((double)row_x[o.n_rows - 1] - (double)row_x[0]));
   P.link_wy = o.link_wy; P.link_wz = o.link_wz; P.link_chi2 = o.link_chi2;
   for (int i = 0; i < 5; ++i) P.seed_c[i] = o.seed_c[i];
-  P.follow_chi2 = o.follow_chi2; P.max_snp = o.max_snp; P.score_w = o.score_w;
+  P.follow_chi2 = o.follow_chi2; P.max_snp = o.max_snp; P.fit_max_snp = o.fit_max_snp;
+  P.score_w = o.score_w;
   P.shared_frac = o.shared_frac;
   P.merge_chi2 = o.merge_chi2; P.merge_dy = o.merge_dy; P.merge_dz = o.merge_dz;
   P.int_chi2 = o.int_chi2; P.final_chi2 = o.final_chi2;
+  P.attach_margin = o.attach_margin;
+  P.edge_margin = o.edge_margin;
+  // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
+  P.merge_zspan = (Real)((double)(o.merge_max_gap + 2) *
+                         (((double)row_x[o.n_rows - 1] - (double)row_x[0]) / (double)(o.n_rows - 1)) /
+                         std::sqrt(1.0 - (double)o.max_snp * (double)o.max_snp));
   P.max_miss = o.max_miss; P.min_hits = o.min_hits; P.merge_max_gap = o.merge_max_gap;
   P.inner_rows = o.inner_rows; P.cand_k = o.cand_k; P.brute_force = o.brute_force;
   P.n_rows = o.n_rows; P.n_sectors = o.n_sectors;
@@ -186,11 +204,11 @@ struct Step {
 };
 
 template <typename Real>
-bool helix_step(const Real* p, Real dx, const Params<Real>& P, Step<Real>& st) {
+bool helix_step(const Real* p, Real dx, const Params<Real>& P, Step<Real>& st, Real lim) {
   const Real kappa = p[4] * P.kb;
   const Real s0 = p[2];
   const Real s1 = s0 + kappa * dx;
-  if (!(std::fabs(s1) < P.max_snp)) return false;
+  if (!(std::fabs(s1) < lim)) return false;
   const Real c0 = std::sqrt(Real(1) - s0 * s0);
   const Real c1 = std::sqrt(Real(1) - s1 * s1);
   const Real N = s0 + s1;
@@ -257,10 +275,10 @@ void add_ms(Real* c, const Real* p, Real dx, const Params<Real>& P) {
 
 // Extended-Kalman propagation (Jacobian at the current state) with scattering.
 template <typename Real>
-bool propagate(Track<Real>& t, Real xnew, const Params<Real>& P) {
+bool propagate(Track<Real>& t, Real xnew, const Params<Real>& P, Real lim) {
   const Real dx = xnew - t.x;
   Step<Real> st;
-  if (!helix_step(t.p, dx, P, st)) return false;
+  if (!helix_step(t.p, dx, P, st, lim)) return false;
   for (int i = 0; i < 5; ++i) t.p[i] = st.p[i];
   cov_transport(t.c, st);
   add_ms(t.c, t.p, dx, P);
@@ -315,7 +333,7 @@ void update(Track<Real>& t, const Resid<Real>& R) {
 // Jacobian d(y',z',snp')/d(y,snp): csp/csp', -sin(a) tgl/csp', -sin(a) kappa
 // (a shift along the track turns its direction), csp'/csp.
 template <typename Real>
-bool rotate(Track<Real>& t, int dir, const Params<Real>& P) {
+bool rotate(Track<Real>& t, int dir, const Params<Real>& P, Real lim) {
   const Real ca = P.rot_c;
   const Real sa = dir > 0 ? P.rot_s : -P.rot_s;
   const Real snp = t.p[2];
@@ -324,7 +342,7 @@ bool rotate(Track<Real>& t, int dir, const Params<Real>& P) {
   const Real yn = t.p[0] * ca - t.x * sa;
   const Real sn = snp * ca - csp * sa;
   const Real cn = csp * ca + snp * sa;
-  if (!(cn > Real(0)) || !(std::fabs(sn) < P.max_snp)) return false;
+  if (!(cn > Real(0)) || !(std::fabs(sn) < lim)) return false;
   const Real j00 = csp / cn;
   const Real j10 = -sa * t.p[3] / cn;
   const Real j20 = -sa * (t.p[4] * P.kb);
@@ -541,7 +559,7 @@ Tracklet<Real> construct(const Frame<Real>& F, const Params<Real>& P, const std:
     zs[i] = F.z[sel[i]];
   }
   Track<Real> t;
-  if (!seed3(xs, ys, zs, P, t)) return T;
+  if (!seed3(xs, ys, zs, P, t)) { T.ndf = -1; return T; }
   std::vector<int> have(P.n_rows, -1);
   // upward: along the chain, then row-by-row following
   {
@@ -554,7 +572,7 @@ Tracklet<Real> construct(const Frame<Real>& F, const Params<Real>& P, const std:
   bool alive = true;
   for (size_t i = 1; i < chain.size(); ++i) {
     const int c = chain[i];
-    if (!propagate(t, P.row_x[F.row[c]], P)) { alive = false; break; }
+    if (!propagate(t, P.row_x[F.row[c]], P, P.max_snp)) { alive = false; break; }
     Resid<Real> R = residual(t, F.y[c], F.z[c], P);
     update(t, R);
     have[F.row[c]] = c;
@@ -564,8 +582,8 @@ Tracklet<Real> construct(const Frame<Real>& F, const Params<Real>& P, const std:
   if (alive) {
     int miss = 0;
     for (int r = top + 1; r < P.n_rows; ++r) {
-      if (!propagate(t, P.row_x[r], P)) break;
-      if (std::fabs(t.p[0]) > t.x * P.tan_half) break;
+      if (!propagate(t, P.row_x[r], P, P.max_snp)) break;
+      if (std::fabs(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
       Resid<Real> R;
       const int c = pick(F, P, t, s, r, &R);
       if (c >= 0) {
@@ -597,8 +615,8 @@ Tracklet<Real> construct(const Frame<Real>& F, const Params<Real>& P, const std:
   Track<Real> inner = t;
   int miss = 0;
   for (int r = top - 1; r >= 0; --r) {
-    if (!propagate(t, P.row_x[r], P)) break;
-    if (std::fabs(t.p[0]) > t.x * P.tan_half) break;
+    if (!propagate(t, P.row_x[r], P, P.max_snp)) break;
+    if (std::fabs(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
     if (r >= r0) {
       const int c = have[r];
       if (c < 0) continue;
@@ -623,7 +641,7 @@ Tracklet<Real> construct(const Frame<Real>& F, const Params<Real>& P, const std:
       }
     }
   }
-  if (n < P.min_hits) return T;
+  if (n < P.min_hits) { T.ndf = -100 - n; return T; }
   T.n = n;
   T.t = inner;
   T.chi2 = chi2;
@@ -693,9 +711,735 @@ Selection<Real> select(const Frame<Real>& F, const Params<Real>& P,
   return S;
 }
 
+// ---------------------------------------------------- a8 distortion map
+// Uniform cubic B-spline in (u, r, z): u = sector + 0.5 + 0.5*(y/x)/tan(10 deg)
+// periodic over 18 sectors, control point j at u = (j+0.5)*18/n_phi; r and z
+// clamped to the map range, control point j at j-1 knot spacings.  Weights
+// (1-f)^3/6, (3f^3-6f^2+4)/6, (-3f^3+3f^2+3f+1)/6, f^3/6.
+template <typename Real>
+struct MapR {
+  bool on = false;
+  int nphi = 0, nr = 0, nz = 0;
+  Real rmin = 0, zmin = 0, zmax = 0, phi_scale = 0, r_scale = 0, z_scale = 0;
+  const float* c = nullptr;
+};
+
+template <typename Real>
+void spline_w(Real f, Real* w) {
+  const Real g = Real(1) - f;
+  const Real f2 = f * f, f3 = f2 * f;
+  w[0] = g * g * g / Real(6);
+  w[1] = (Real(3) * f3 - Real(6) * f2 + Real(4)) / Real(6);
+  w[2] = (Real(-3) * f3 + Real(3) * f2 + Real(3) * f + Real(1)) / Real(6);
+  w[3] = f3 / Real(6);
+}
+
+// Clamped span: t in [0, n-3], i <= n-4.
+template <typename Real>
+void spline_span(Real t, int n, int& i, Real& f) {
+  const Real tmax = Real(n - 3);
+  if (t < Real(0)) t = Real(0);
+  if (t > tmax) t = tmax;
+  i = (int)std::floor(t);
+  if (i > n - 4) i = n - 4;
+  f = t - Real(i);
+}
+
+// Spline weights and base indices of one point (shared by evaluation and the
+// gradient scatter).
+template <typename Real>
+struct SplinePoint {
+  int ip, ir, iz;
+  Real wp[4], wr[4], wz[4];
+};
+
+template <typename Real>
+SplinePoint<Real> spline_point(const MapR<Real>& M, const Params<Real>& P, int sector, Real x,
+                               Real y, Real zdrift) {
+  SplinePoint<Real> sp;
+  const int sphi = sector % (P.n_sectors / 2);
+  const Real u = (Real(sphi) + Real(0.5)) + Real(0.5) * (y / x) / P.tan_half;
+  const Real tp = u * M.phi_scale - Real(0.5);
+  sp.ip = (int)std::floor(tp);
+  const Real fp = tp - Real(sp.ip);
+  const Real r = std::sqrt(x * x + y * y);
+  Real fr, fz;
+  spline_span((r - M.rmin) * M.r_scale, M.nr, sp.ir, fr);
+  Real zc = zdrift;
+  if (zc < M.zmin) zc = M.zmin;
+  if (zc > M.zmax) zc = M.zmax;
+  spline_span((zc - M.zmin) * M.z_scale, M.nz, sp.iz, fz);
+  spline_w(fp, sp.wp);
+  spline_w(fr, sp.wr);
+  spline_w(fz, sp.wz);
+  return sp;
+}
+
+inline int phi_index(int ip, int e, int nphi) { return ((ip - 1 + e) % nphi + nphi) % nphi; }
+
+template <typename Real>
+void map_eval(const MapR<Real>& M, const Params<Real>& P, int sector, Real x, Real y, Real zdrift,
+              Real* D) {
+  D[0] = D[1] = D[2] = Real(0);
+  if (!M.on) return;
+  const SplinePoint<Real> sp = spline_point(M, P, sector, x, y, zdrift);
+  for (int comp = 0; comp < 3; ++comp) {
+    Real acc = Real(0);
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        const Real wzr = sp.wz[a] * sp.wr[b];
+        for (int e = 0; e < 4; ++e) {
+          const long idx = (((long)comp * M.nz + (sp.iz + a)) * M.nr + (sp.ir + b)) * M.nphi +
+                           phi_index(sp.ip, e, M.nphi);
+          acc = acc + wzr * sp.wp[e] * (Real)M.c[idx];
+        }
+      }
+    D[comp] = acc;
+  }
+}
+
+// ---------------------------------------------- a7 sector refit and merging
+template <typename Real>
+struct SectorTrack {
+  int key = -1;          // input id of the tracklet's start cluster
+  int sector = 0;
+  int rmin = 0, rmax = 0;
+  std::vector<int> cl;   // kept clusters, innermost first
+  Track<Real> ie{}, oe{};  // states at the innermost / outermost cluster
+};
+
+// Refit of a sector track at the start of merging (Sec. 3, Phase I): outward
+// from the tracklet parameters, then inward, covariance reset before each.
+template <typename Real>
+bool sector_refit(const Frame<Real>& F, const Params<Real>& P, const Track<Real>& start,
+                  SectorTrack<Real>& S) {
+  Track<Real> t = start;
+  reset_cov(t, P);
+  for (size_t i = 0; i < S.cl.size(); ++i) {
+    const int c = S.cl[i];
+    if (!propagate(t, P.row_x[F.row[c]], P, P.fit_max_snp)) return false;
+    update(t, residual(t, F.y[c], F.z[c], P));
+  }
+  S.oe = t;
+  reset_cov(t, P);
+  for (size_t i = S.cl.size(); i-- > 0;) {
+    const int c = S.cl[i];
+    if (!propagate(t, P.row_x[F.row[c]], P, P.fit_max_snp)) return false;
+    update(t, residual(t, F.y[c], F.z[c], P));
+  }
+  S.ie = t;
+  return true;
+}
+
+// d^T C^-1 d for a 5-vector through a Cholesky factorisation; -1 if C is not
+// positive definite.
+template <typename Real>
+Real chi2_5(const Real* d, const Real* c) {
+  Real L[5][5] = {};
+  for (int j = 0; j < 5; ++j) {
+    Real s = c[ci(j, j)];
+    for (int k = 0; k < j; ++k) s = s - L[j][k] * L[j][k];
+    if (!(s > Real(0))) return Real(-1);
+    L[j][j] = std::sqrt(s);
+    for (int i = j + 1; i < 5; ++i) {
+      Real v = c[ci(i, j)];
+      for (int k = 0; k < j; ++k) v = v - L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  Real yv[5];
+  Real chi2 = Real(0);
+  for (int i = 0; i < 5; ++i) {
+    Real v = d[i];
+    for (int k = 0; k < i; ++k) v = v - L[i][k] * yv[k];
+    yv[i] = v / L[i][i];
+    chi2 = chi2 + yv[i] * yv[i];
+  }
+  return chi2;
+}
+
+// Candidate pair for merging the outer end of A with the inner end of B (Sec. 2:
+// merging inside a sector and between adjacent sectors of one TPC half).
+template <typename Real>
+bool merge_test(const Params<Real>& P, const SectorTrack<Real>& A, const SectorTrack<Real>& B,
+                Real& chi2) {
+  const int half = P.n_sectors / 2;
+  if (A.sector / half != B.sector / half) return false;
+  const int ds = ((B.sector % half) - (A.sector % half) + half) % half;
+  if (ds != 0 && ds != 1 && ds != half - 1) return false;
+  const int gap = B.rmin - A.rmax;
+  if (gap < 1 || gap > P.merge_max_gap) return false;
+  const Real zwin = P.merge_dz + std::fabs(A.oe.p[3]) * P.merge_zspan;
+  if (!(std::fabs(B.ie.p[1] - A.oe.p[1]) <= zwin)) return false;
+  Track<Real> t = A.oe;
+  if (ds == 1 && !rotate(t, 1, P, P.fit_max_snp)) return false;
+  if (ds == half - 1 && !rotate(t, -1, P, P.fit_max_snp)) return false;
+  if (!propagate(t, B.ie.x, P, P.fit_max_snp)) return false;
+  Real d[5], c[15];
+  for (int i = 0; i < 5; ++i) d[i] = B.ie.p[i] - t.p[i];
+  if (!(std::fabs(d[0]) <= P.merge_dy) || !(std::fabs(d[1]) <= P.merge_dz)) return false;
+  for (int i = 0; i < 15; ++i) c[i] = t.c[i] + B.ie.c[i];
+  chi2 = chi2_5(d, c);
+  return chi2 >= Real(0) && chi2 < P.merge_chi2;
+}
+
+// ------------------------------------------------- a9/a10 three-iteration fit
+// Linearised Kalman filter: the state is carried as reference + deviation; the
+// reference (the helix of the iteration's start state) is propagated exactly,
+// the deviation with the Jacobian at the reference ("the initial parameters
+// are used for the linearization", Sec. 2).
+template <typename Real>
+struct Lin {
+  Track<Real> t;  // state, covariance, x
+  Real r[5];      // reference at t.x
+  int sector;
+};
+
+template <typename Real>
+void lin_start(Lin<Real>& L, const Track<Real>& s, int sector, const Params<Real>& P) {
+  L.t = s;
+  reset_cov(L.t, P);
+  for (int i = 0; i < 5; ++i) L.r[i] = s.p[i];
+  L.sector = sector;
+}
+
+template <typename Real>
+bool lin_rotate(Lin<Real>& L, int dir, const Params<Real>& P) {
+  const Real ca = P.rot_c;
+  const Real sa = dir > 0 ? P.rot_s : -P.rot_s;
+  const Real snp = L.r[2];
+  const Real csp = std::sqrt(Real(1) - snp * snp);
+  const Real xn = L.t.x * ca + L.r[0] * sa;
+  const Real yn = L.r[0] * ca - L.t.x * sa;
+  const Real sn = snp * ca - csp * sa;
+  const Real cn = csp * ca + snp * sa;
+  if (!(cn > Real(0)) || !(std::fabs(sn) < P.fit_max_snp)) return false;
+  const Real j00 = csp / cn;
+  const Real j10 = -sa * L.r[3] / cn;
+  const Real j20 = -sa * (L.r[4] * P.kb);
+  const Real j22 = cn / csp;
+  const Real d0 = L.t.p[0] - L.r[0], d1 = L.t.p[1] - L.r[1], d2 = L.t.p[2] - L.r[2];
+  // covariance: same transport as the extended filter's rotation
+  Real M[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) M[i][j] = L.t.c[ci(i, j)];
+  Real A[5][5];
+  for (int j = 0; j < 5; ++j) {
+    A[0][j] = j00 * M[0][j];
+    A[1][j] = j10 * M[0][j] + M[1][j];
+    A[2][j] = j20 * M[0][j] + j22 * M[2][j];
+    A[3][j] = M[3][j];
+    A[4][j] = M[4][j];
+  }
+  for (int i = 0; i < 5; ++i) {
+    L.t.c[ci(i, 0)] = A[i][0] * j00;
+    if (i >= 1) L.t.c[ci(i, 1)] = A[i][0] * j10 + A[i][1];
+    if (i >= 2) L.t.c[ci(i, 2)] = A[i][0] * j20 + A[i][2] * j22;
+    if (i >= 3) L.t.c[ci(i, 3)] = A[i][3];
+    if (i >= 4) L.t.c[ci(i, 4)] = A[i][4];
+  }
+  L.r[0] = yn;
+  L.r[2] = sn;
+  L.t.x = xn;
+  L.t.p[0] = L.r[0] + j00 * d0;
+  L.t.p[1] = L.r[1] + (j10 * d0 + d1);
+  L.t.p[2] = L.r[2] + (j20 * d0 + j22 * d2);
+  return true;
+}
+
+template <typename Real>
+bool lin_propagate(Lin<Real>& L, Real xnew, const Params<Real>& P) {
+  const Real dx = xnew - L.t.x;
+  Step<Real> st;
+  if (!helix_step(L.r, dx, P, st, P.fit_max_snp)) return false;
+  const Real d0 = L.t.p[0] - L.r[0], d1 = L.t.p[1] - L.r[1], d2 = L.t.p[2] - L.r[2];
+  const Real d3 = L.t.p[3] - L.r[3], d4 = L.t.p[4] - L.r[4];
+  for (int i = 0; i < 3; ++i) L.r[i] = st.p[i];
+  L.t.p[0] = L.r[0] + (d0 + st.f02 * d2 + st.f04 * d4);
+  L.t.p[1] = L.r[1] + (d1 + st.f12 * d2 + st.f13 * d3 + st.f14 * d4);
+  L.t.p[2] = L.r[2] + (d2 + st.f24 * d4);
+  cov_transport(L.t.c, st);
+  add_ms(L.t.c, L.r, dx, P);
+  L.t.x = xnew;
+  return true;
+}
+
+template <typename Real>
+bool lin_goto(Lin<Real>& L, int sector, Real x, const Params<Real>& P) {
+  if (sector != L.sector) {
+    const int half = P.n_sectors / 2;
+    const int ds = ((sector % half) - (L.sector % half) + half) % half;
+    if (ds == 1) {
+      if (!lin_rotate(L, 1, P)) return false;
+    } else if (ds == half - 1) {
+      if (!lin_rotate(L, -1, P)) return false;
+    } else {
+      return false;
+    }
+    L.sector = sector;
+  }
+  return lin_propagate(L, x, P);
+}
+
+// Distortion-corrected measurement of cluster (y, z) on the pad row at x,
+// projected back onto the row along the reference helix:
+// m = (y + Dy, z + Dz) - [ref(x + Dx) - ref(x)].
+template <typename Real>
+bool corrected(const MapR<Real>& M, const Params<Real>& P, int sector, Real x, Real y, Real z,
+               Real z0, const Real* ref, Real& my, Real& mz) {
+  Real D[3];
+  map_eval(M, P, sector, x, y, z - z0, D);
+  my = y + D[1];
+  mz = z + D[2];
+  if (D[0] != Real(0)) {
+    Step<Real> st;
+    if (!helix_step(ref, D[0], P, st, P.fit_max_snp)) return false;
+    my = my - (st.p[0] - ref[0]);
+    mz = mz - (st.p[1] - ref[1]);
+  }
+  return true;
+}
+
+// 2x2 symmetric inverse.
+template <typename Real>
+void inv2(Real a00, Real a01, Real a11, Real& i00, Real& i01, Real& i11) {
+  const Real idet = Real(1) / (a00 * a11 - a01 * a01);
+  i00 = a11 * idet;
+  i01 = -a01 * idet;
+  i11 = a00 * idet;
+}
+
+// Weighted mean of two (y,z) estimates (two-filter interpolation).
+template <typename Real>
+struct Interp {
+  Real y, z, c00, c01, c11;
+};
+
+template <typename Real>
+Interp<Real> interpolate(const Real* a, const Real* b) {
+  // a, b: y, z, cyy, czy, czz
+  Real wa00, wa01, wa11, wb00, wb01, wb11;
+  inv2(a[2], a[3], a[4], wa00, wa01, wa11);
+  inv2(b[2], b[3], b[4], wb00, wb01, wb11);
+  Interp<Real> I;
+  inv2(wa00 + wb00, wa01 + wb01, wa11 + wb11, I.c00, I.c01, I.c11);
+  const Real v0 = (wa00 * a[0] + wa01 * a[1]) + (wb00 * b[0] + wb01 * b[1]);
+  const Real v1 = (wa01 * a[0] + wa11 * a[1]) + (wb01 * b[0] + wb11 * b[1]);
+  I.y = I.c00 * v0 + I.c01 * v1;
+  I.z = I.c01 * v0 + I.c11 * v1;
+  return I;
+}
+
+template <typename Real>
+Real chi2_interp(const Interp<Real>& I, Real my, Real mz, const Params<Real>& P) {
+  Real w00, w01, w11;
+  inv2(I.c00 + P.meas_sy2, I.c01, I.c11 + P.meas_sz2, w00, w01, w11);
+  const Real r0 = my - I.y, r1 = mz - I.z;
+  return r0 * (w00 * r0 + w01 * r1) + r1 * (w01 * r0 + w11 * r1);
+}
+
+template <typename Real>
+struct Station {
+  int sector, row, cl;  // cl: cluster id or -1 (empty inner row)
+};
+
+template <typename Real>
+struct FitTrack {
+  int key;
+  std::vector<Station<Real>> st;
+  Track<Real> outer;       // start of iteration 1 (state at the last station)
+  Real z0;                 // drift-coordinate offset for the map lookup
+  // results
+  std::vector<int> flag;   // per station: interpolation-rejected (iteration 2)
+  std::vector<int> ncand;
+  std::vector<int> cand;   // [station][cand_k]
+  std::vector<Real> cchi;  // [station][cand_k]
+  std::vector<int> assigned;
+  bool ok = true;
+  int fail_at = -1;        // diagnostics: 100*iteration + station of a failed step
+  Track<Real> out{};
+  int out_sector = 0;
+  Real chi2 = 0;
+  int n = 0;
+  std::vector<int> used;   // clusters of iteration 3, innermost first
+};
+
+// One three-iteration fit (Sec. 3, Phase I, with the Phase II candidate search
+// when `phase2`): iteration 1 inward stores the predicted (y,z) and covariance
+// at every station; iteration 2 outward interpolates with them, flags clusters
+// with chi2 > int_chi2 and (phase2) collects up to cand_k candidates on inner
+// rows; iteration 3 inward uses the surviving / assigned clusters with a
+// simple chi2 cut.  Iteration 3 runs in fit_iteration3 after the second
+// ambiguity solving.
+template <typename Real>
+void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
+                      FitTrack<Real>& T, bool phase2, std::vector<Real>& store,
+                      Track<Real>& it2_end) {
+  const int ns = (int)T.st.size();
+  store.assign((size_t)ns * 5, Real(0));
+  T.flag.assign(ns, 0);
+  T.ncand.assign(ns, 0);
+  T.cand.assign((size_t)ns * P.cand_k, -1);
+  T.cchi.assign((size_t)ns * P.cand_k, Real(0));
+  Lin<Real> L;
+  // iteration 1: inward
+  lin_start(L, T.outer, T.st[ns - 1].sector, P);
+  for (int k = ns - 1; k >= 0; --k) {
+    const Station<Real>& s = T.st[k];
+    if (k != ns - 1 && !lin_goto(L, s.sector, P.row_x[s.row], P)) {
+      T.ok = false;
+      T.fail_at = 1000 + k;
+      return;
+    }
+    Real* sv = &store[(size_t)k * 5];
+    sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
+    if (s.cl >= 0) {
+      Real my, mz;
+      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], T.z0, L.r, my, mz)) {
+        T.ok = false;
+        return;
+      }
+      update(L.t, residual(L.t, my, mz, P));
+    }
+  }
+  // iteration 2: outward
+  const Track<Real> s1 = L.t;
+  lin_start(L, s1, T.st[0].sector, P);
+  for (int k = 0; k < ns; ++k) {
+    const Station<Real>& s = T.st[k];
+    if (k != 0 && !lin_goto(L, s.sector, P.row_x[s.row], P)) {
+      T.ok = false;
+      T.fail_at = 2000 + k;
+      return;
+    }
+    const Real a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
+    const Interp<Real> I = interpolate(a, &store[(size_t)k * 5]);
+    const bool inner = phase2 && s.row < P.inner_rows;
+    if (s.cl >= 0 && !inner) {
+      Real my, mz;
+      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], T.z0, L.r, my, mz)) {
+        T.ok = false;
+        return;
+      }
+      T.flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
+    }
+    if (inner) {
+      // Phase II: every cluster of the row compatible with the interpolation
+      Real cy = I.y, cz = I.z;
+      {
+        Real D[3];
+        map_eval(M, P, s.sector, L.t.x, I.y, I.z - T.z0, D);
+        Real sy = D[1], sz = D[2];
+        if (D[0] != Real(0)) {
+          Step<Real> stp;
+          if (helix_step(L.r, D[0], P, stp, P.fit_max_snp)) {
+            sy = sy - (stp.p[0] - L.r[0]);
+            sz = sz - (stp.p[1] - L.r[1]);
+          }
+        }
+        cy = I.y - sy;
+        cz = I.z - sz;
+      }
+      const Real wy = std::sqrt(P.int_chi2 * (I.c00 + P.meas_sy2)) * Real(1.001) + P.attach_margin;
+      const Real wz = std::sqrt(P.int_chi2 * (I.c11 + P.meas_sz2)) * Real(1.001) + P.attach_margin;
+      std::vector<std::pair<Real, int>> cands;
+      for_row_range(F, P, s.sector, s.row, cz - wz - Real(0.01), cz + wz + Real(0.01), [&](int id) {
+        if (!(std::fabs(F.y[id] - cy) <= wy && std::fabs(F.z[id] - cz) <= wz)) return;
+        Real my, mz;
+        if (!corrected(M, P, s.sector, L.t.x, F.y[id], F.z[id], T.z0, L.r, my, mz)) return;
+        const Real c2 = chi2_interp(I, my, mz, P);
+        if (c2 < P.int_chi2) cands.push_back({c2, id});
+      });
+      std::sort(cands.begin(), cands.end(), [](const auto& u, const auto& v) {
+        return u.first < v.first || (u.first == v.first && u.second < v.second);
+      });
+      const int nc = std::min((int)cands.size(), P.cand_k);
+      T.ncand[k] = nc;
+      for (int j = 0; j < nc; ++j) {
+        T.cand[(size_t)k * P.cand_k + j] = cands[j].second;
+        T.cchi[(size_t)k * P.cand_k + j] = cands[j].first;
+      }
+    }
+    if (s.cl >= 0) {
+      Real my, mz;
+      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], T.z0, L.r, my, mz)) {
+        T.ok = false;
+        return;
+      }
+      update(L.t, residual(L.t, my, mz, P));
+    }
+  }
+  it2_end = L.t;
+}
+
+template <typename Real>
+void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
+                    FitTrack<Real>& T, bool phase2, const Track<Real>& start) {
+  const int ns = (int)T.st.size();
+  Lin<Real> L;
+  lin_start(L, start, T.st[ns - 1].sector, P);
+  T.chi2 = Real(0);
+  T.n = 0;
+  T.used.clear();
+  bool have = false;
+  for (int k = ns - 1; k >= 0; --k) {
+    const Station<Real>& s = T.st[k];
+    if (k != ns - 1 && !lin_goto(L, s.sector, P.row_x[s.row], P)) break;
+    const bool inner = phase2 && s.row < P.inner_rows;
+    const int c = inner ? T.assigned[k] : (T.flag[k] ? -1 : s.cl);
+    if (c < 0) continue;
+    Real my, mz;
+    if (!corrected(M, P, s.sector, L.t.x, F.y[c], F.z[c], T.z0, L.r, my, mz)) continue;
+    const Resid<Real> R = residual(L.t, my, mz, P);
+    if (R.chi2 > P.final_chi2) continue;
+    T.chi2 = T.chi2 + R.chi2;
+    update(L.t, R);
+    ++T.n;
+    T.used.push_back(c);
+    T.out = L.t;
+    T.out_sector = L.sector;
+    have = true;
+  }
+  std::reverse(T.used.begin(), T.used.end());
+  if (!have) T.n = 0;
+}
+
+// Station list of a merged track: every cluster (segments in order, rows
+// increasing) plus the empty rows below inner_rows between two clusters of
+// the same sector.
+template <typename Real>
+std::vector<Station<Real>> make_stations(const Frame<Real>& F, const Params<Real>& P,
+                                         const std::vector<int>& cl, bool phase2) {
+  std::vector<Station<Real>> st;
+  for (size_t i = 0; i < cl.size(); ++i) {
+    const int c = cl[i];
+    if (phase2 && i > 0) {
+      const int pc = cl[i - 1];
+      if (F.sector[pc] == F.sector[c])
+        for (int r = F.row[pc] + 1; r < F.row[c] && r < P.inner_rows; ++r)
+          st.push_back({F.sector[c], r, -1});
+    }
+    st.push_back({F.sector[c], F.row[c], c});
+  }
+  return st;
+}
+
+// Second ambiguity solving (Sec. 3, Phase II): in round k every cluster still
+// free goes to the best (chi2, track key) among the (track, row) pairs still
+// without an assigned cluster that offer it as their k-th candidate.
+template <typename Real>
+void second_ambiguity(std::vector<FitTrack<Real>>& FT, const Params<Real>& P) {
+  std::map<int, uint64_t> bid;
+  std::map<int, bool> taken;
+  for (auto& T : FT) T.assigned.assign(T.st.size(), -1);
+  for (int k = 0; k < P.cand_k; ++k) {
+    bid.clear();
+    for (auto& T : FT) {
+      if (!T.ok) continue;
+      for (size_t s = 0; s < T.st.size(); ++s) {
+        if (T.assigned[s] >= 0 || T.ncand[s] <= k) continue;
+        const int c = T.cand[s * P.cand_k + k];
+        if (taken.count(c)) continue;
+        const uint64_t key = ((uint64_t)ordered_bits((float)T.cchi[s * P.cand_k + k]) << 32) |
+                             (uint64_t)(uint32_t)T.key;
+        auto it = bid.find(c);
+        if (it == bid.end() || key < it->second) bid[c] = key;
+      }
+    }
+    for (auto& T : FT) {
+      if (!T.ok) continue;
+      for (size_t s = 0; s < T.st.size(); ++s) {
+        if (T.assigned[s] >= 0 || T.ncand[s] <= k) continue;
+        const int c = T.cand[s * P.cand_k + k];
+        if (taken.count(c)) continue;
+        const uint64_t key = ((uint64_t)ordered_bits((float)T.cchi[s * P.cand_k + k]) << 32) |
+                             (uint64_t)(uint32_t)T.key;
+        if (bid[c] == key) T.assigned[s] = c;
+      }
+    }
+    for (auto& kv : bid) taken[kv.first] = true;
+  }
+}
+
 // ------------------------------------------------------------- driver
 template <typename Real>
-void run_sector_tracking(const Frame<Real>& F, const Params<Real>& P, Result& res) {
+struct SectorResult {
+  std::vector<Tracklet<Real>> TL;
+  Selection<Real> S;
+};
+
+template <typename Real>
+void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
+                   const SectorResult<Real>& SR, Result& res) {
+  // a7: sector refit of every accepted tracklet
+  std::vector<SectorTrack<Real>> ST;
+  for (size_t i = 0; i < SR.TL.size(); ++i) {
+    if (!SR.S.accepted[i]) continue;
+    SectorTrack<Real> S;
+    S.key = SR.TL[i].start;
+    S.cl.assign(SR.S.kept[i].rbegin(), SR.S.kept[i].rend());
+    S.sector = F.sector[S.cl[0]];
+    S.rmin = F.row[S.cl.front()];
+    S.rmax = F.row[S.cl.back()];
+    if (!sector_refit(F, P, SR.TL[i].t, S)) continue;
+    ST.push_back(S);
+  }
+  std::sort(ST.begin(), ST.end(), [](const auto& a, const auto& b) { return a.key < b.key; });
+  const int nst = (int)ST.size();
+  // a7: candidate pairs by sector, mutual best
+  const int half = P.n_sectors / 2;
+  std::vector<std::vector<int>> by_sector(P.n_sectors);
+  for (int i = 0; i < nst; ++i) by_sector[ST[i].sector].push_back(i);
+  std::vector<int> bestB(nst, -1), bestA(nst, -1);
+  std::vector<Real> chiB(nst, 0), chiA(nst, 0);
+  for (int a = 0; a < nst; ++a) {
+    const int sa = ST[a].sector;
+    const int side = sa / half, ph = sa % half;
+    for (int d : {0, 1, half - 1}) {
+      const int sb = side * half + (ph + d) % half;
+      for (int b : by_sector[sb]) {
+        if (b == a) continue;
+        Real chi2;
+        if (!merge_test(P, ST[a], ST[b], chi2)) continue;
+        if (bestB[a] < 0 || chi2 < chiB[a] || (chi2 == chiB[a] && ST[b].key < ST[bestB[a]].key)) {
+          bestB[a] = b;
+          chiB[a] = chi2;
+        }
+        if (bestA[b] < 0 || chi2 < chiA[b] || (chi2 == chiA[b] && ST[a].key < ST[bestA[b]].key)) {
+          bestA[b] = a;
+          chiA[b] = chi2;
+        }
+      }
+    }
+  }
+  std::vector<int> next(nst, -1), prev(nst, -1);
+  for (int a = 0; a < nst; ++a)
+    if (bestB[a] >= 0 && bestA[bestB[a]] == a) {
+      next[a] = bestB[a];
+      prev[bestB[a]] = a;
+    }
+  std::vector<int> st_key(nst), st_next(nst);
+  std::vector<Real> st_ie(nst * 5), st_oe(nst * 5);
+  for (int i = 0; i < nst; ++i) {
+    st_key[i] = ST[i].key;
+    st_next[i] = next[i] >= 0 ? ST[next[i]].key : -1;
+    for (int k = 0; k < 5; ++k) {
+      st_ie[i * 5 + k] = ST[i].ie.p[k];
+      st_oe[i * 5 + k] = ST[i].oe.p[k];
+    }
+  }
+  res.put("st_key", st_key, "i4");
+  res.put("st_next", st_next, "i4");
+  res.put("st_ie", st_ie, real_name<Real>());
+  res.put("st_oe", st_oe, real_name<Real>());
+  // merged tracks (chains), ordered by the key of their first segment
+  std::vector<FitTrack<Real>> FT;
+  for (int h = 0; h < nst; ++h) {
+    if (prev[h] >= 0) continue;
+    FitTrack<Real> T;
+    T.key = ST[h].key;
+    std::vector<int> cl;
+    int last = h;
+    for (int s = h; s >= 0; s = next[s]) {
+      cl.insert(cl.end(), ST[s].cl.begin(), ST[s].cl.end());
+      last = s;
+    }
+    T.st = make_stations(F, P, cl, true);
+    T.outer = ST[last].oe;
+    const Track<Real>& ie = ST[h].ie;
+    T.z0 = ie.p[1] - ie.p[3] * std::sqrt(ie.x * ie.x + ie.p[0] * ie.p[0]);
+    FT.push_back(std::move(T));
+  }
+  // a9/a10
+  std::vector<Track<Real>> it2_end(FT.size());
+  std::vector<Real> store;
+  for (size_t i = 0; i < FT.size(); ++i) fit_iterations12(F, P, M, FT[i], true, store, it2_end[i]);
+  second_ambiguity(FT, P);
+  for (size_t i = 0; i < FT.size(); ++i)
+    if (FT[i].ok) fit_iteration3(F, P, M, FT[i], true, it2_end[i]);
+  // a11: output tracks with at least min_hits clusters, attachments
+  std::vector<int> key, ncl, offs(1, 0), ids, sect, ndf, flags;
+  std::vector<Real> par, cov, chi2, xs;
+  std::vector<int> attach(F.n, -1);
+  for (auto& T : FT) {
+    if (!T.ok || T.n < P.min_hits) continue;
+    const int t = (int)key.size();
+    key.push_back(T.key);
+    ncl.push_back(T.n);
+    for (int c : T.used) {
+      ids.push_back(c);
+      if (attach[c] < 0) attach[c] = t;
+    }
+    offs.push_back((int)ids.size());
+    sect.push_back(T.out_sector);
+    ndf.push_back(2 * T.n - 5);
+    chi2.push_back(T.chi2);
+    xs.push_back(T.out.x);
+    for (int k = 0; k < 5; ++k) par.push_back(T.out.p[k]);
+    for (int k = 0; k < 15; ++k) cov.push_back(T.out.c[k]);
+  }
+  res.put("trk_key", key, "i4");
+  res.put("trk_ncl", ncl, "i4");
+  res.put("trk_offset", offs, "i4");
+  res.put("trk_ids", ids, "i4");
+  res.put("trk_sector", sect, "i4");
+  res.put("trk_ndf", ndf, "i4");
+  res.put("trk_chi2", chi2, real_name<Real>());
+  res.put("trk_x", xs, real_name<Real>());
+  res.put("trk_param", par, real_name<Real>());
+  res.put("trk_cov", cov, real_name<Real>());
+  res.put("attach", attach, "i4");
+  // per merged track diagnostics (all chains, including rejected ones)
+  std::vector<int> fk, fflag_n, fcand_n, fassigned_n, ffail, fn;
+  for (auto& T : FT) {
+    fk.push_back(T.key);
+    ffail.push_back(T.ok ? -1 : T.fail_at);
+    fn.push_back(T.n);
+    int nf = 0, nc = 0, na = 0;
+    for (size_t s = 0; s < T.st.size(); ++s) {
+      nf += T.flag.empty() ? 0 : T.flag[s];
+      nc += T.ncand.empty() ? 0 : T.ncand[s];
+      na += T.assigned.empty() ? 0 : (T.assigned[s] >= 0);
+    }
+    fflag_n.push_back(nf);
+    fcand_n.push_back(nc);
+    fassigned_n.push_back(na);
+  }
+  res.put("fit_key", fk, "i4");
+  res.put("fit_nflag", fflag_n, "i4");
+  res.put("fit_ncand", fcand_n, "i4");
+  res.put("fit_nassigned", fassigned_n, "i4");
+  res.put("fit_fail", ffail, "i4");
+  res.put("fit_n", fn, "i4");
+  // Phase II candidates and assignments of every inner station
+  std::vector<int> cs_key, cs_row, cs_sector, cs_n, cs_cand, cs_assigned;
+  std::vector<Real> cs_chi;
+  for (auto& T : FT) {
+    if (!T.ok) continue;
+    for (size_t s = 0; s < T.st.size(); ++s) {
+      if (T.st[s].row >= P.inner_rows) continue;
+      cs_key.push_back(T.key);
+      cs_row.push_back(T.st[s].row);
+      cs_sector.push_back(T.st[s].sector);
+      cs_n.push_back(T.ncand[s]);
+      for (int k = 0; k < P.cand_k; ++k) {
+        cs_cand.push_back(T.cand[s * P.cand_k + k]);
+        cs_chi.push_back(T.cchi[s * P.cand_k + k]);
+      }
+      cs_assigned.push_back(T.assigned[s]);
+    }
+  }
+  res.put("cand_key", cs_key, "i4");
+  res.put("cand_row", cs_row, "i4");
+  res.put("cand_sector", cs_sector, "i4");
+  res.put("cand_n", cs_n, "i4");
+  res.put("cand_ids", cs_cand, "i4");
+  res.put("cand_chi2", cs_chi, real_name<Real>());
+  res.put("cand_assigned", cs_assigned, "i4");
+}
+
+template <typename Real>
+SectorResult<Real> run_sector_tracking(const Frame<Real>& F, const Params<Real>& P, Result& res) {
   std::vector<int> up, dn, cu, cd;
   find_links(F, P, up, dn);
   clean_links(up, dn, cu, cd);
@@ -753,10 +1497,14 @@ void run_sector_tracking(const Frame<Real>& F, const Params<Real>& P, Result& re
   res.put("tl_nkept", nk, "i4");
   res.put("tl_kept", kept, "i4");
   res.put("sector_owner", owner, "i4");
+  SectorResult<Real> SR;
+  SR.TL = std::move(TL);
+  SR.S = std::move(S);
+  return SR;
 }
 
-template <typename Real>
-Frame<Real> make_frame(long n, const float* y, const float* z, const uint8_t* row,
+template <typename Real, typename In>
+Frame<Real> make_frame(long n, const In* y, const In* z, const uint8_t* row,
                        const uint8_t* sector, const Params<Real>& P) {
   Frame<Real> F;
   F.n = n;
@@ -768,32 +1516,81 @@ Frame<Real> make_frame(long n, const float* y, const float* z, const uint8_t* ro
   return F;
 }
 
+template <typename Real>
+MapR<Real> make_map(const orc_map* m) {
+  MapR<Real> M;
+  if (!m || !m->coeff) return M;
+  M.on = true;
+  M.nphi = m->n_phi; M.nr = m->n_r; M.nz = m->n_z;
+  M.rmin = m->r_min; M.zmin = m->z_min; M.zmax = m->z_max;
+  M.phi_scale = (Real)((double)m->n_phi / 18.0);
+  M.r_scale = (Real)((double)(m->n_r - 3) / ((double)m->r_max - (double)m->r_min));
+  M.z_scale = (Real)((double)(m->n_z - 3) / ((double)m->z_max - (double)m->z_min));
+  M.c = m->coeff;
+  return M;
+}
+
 }  // namespace orc
 
 struct orc_result {
   orc::Result r;
 };
 
-extern "C" {
-
-int orc_track(long n, const float* y, const float* z, const uint8_t* row, const uint8_t* sector,
-              const double* row_x, const orc_options* opt, int use_double, orc_result** out) {
+template <typename In>
+static int track_impl(long n, const In* y, const In* z, const uint8_t* row, const uint8_t* sector,
+                      const double* row_x, const orc_options* opt, const orc_map* map, int stages,
+                      int use_double, orc_result** out) {
   if (!opt || !row_x || !out || n < 0) return 1;
   for (long i = 0; i < n; ++i)
     if (row[i] >= opt->n_rows || sector[i] >= opt->n_sectors || !std::isfinite(y[i]) ||
         !std::isfinite(z[i]))
       return 2;
   auto* R = new orc_result();
-  if (use_double) {
-    const auto P = orc::make_params<double>(*opt, row_x);
-    const auto F = orc::make_frame<double>(n, y, z, row, sector, P);
-    orc::run_sector_tracking(F, P, R->r);
-  } else {
-    const auto P = orc::make_params<float>(*opt, row_x);
-    const auto F = orc::make_frame<float>(n, y, z, row, sector, P);
-    orc::run_sector_tracking(F, P, R->r);
-  }
+  auto run = [&](auto tag) {
+    using Real = decltype(tag);
+    const auto P = orc::make_params<Real>(*opt, row_x);
+    const auto F = orc::make_frame<Real>(n, y, z, row, sector, P);
+    auto SR = orc::run_sector_tracking(F, P, R->r);
+    if (stages >= 1) orc::run_merge_fit(F, P, orc::make_map<Real>(map), SR, R->r);
+  };
+  if (use_double)
+    run(double{});
+  else
+    run(float{});
   *out = R;
+  return 0;
+}
+
+// stages: 0 = sector tracking only, 1 = full chain (merging, fit, attachment)
+
+extern "C" {
+
+int orc_track(long n, const float* y, const float* z, const uint8_t* row, const uint8_t* sector,
+              const double* row_x, const orc_options* opt, const orc_map* map, int stages,
+              int use_double, orc_result** out) {
+  return track_impl(n, y, z, row, sector, row_x, opt, map, stages, use_double, out);
+}
+
+// The same with FP64 cluster coordinates (precision pins with exact inputs).
+int orc_track_f64(long n, const double* y, const double* z, const uint8_t* row,
+                  const uint8_t* sector, const double* row_x, const orc_options* opt,
+                  const orc_map* map, int stages, orc_result** out) {
+  return track_impl(n, y, z, row, sector, row_x, opt, map, stages, 1, out);
+}
+
+// Correction of one cluster in FP64 (pins): io = {sector, x, y, z, z0, ref[5]} ->
+// io[10..12] = D (map displacement), io[13..14] = projected measurement.
+int orc_correct(const orc_options* opt, const double* row_x, const orc_map* map, double* io) {
+  if (!opt || !io) return 1;
+  const auto P = orc::make_params<double>(*opt, row_x);
+  const auto M = orc::make_map<double>(map);
+  double D[3];
+  orc::map_eval(M, P, (int)io[0], io[1], io[2], io[3] - io[4], D);
+  io[10] = D[0]; io[11] = D[1]; io[12] = D[2];
+  double my, mz;
+  if (!orc::corrected(M, P, (int)io[0], io[1], io[2], io[3], io[4], &io[5], my, mz)) return 2;
+  io[13] = my;
+  io[14] = mz;
   return 0;
 }
 
@@ -842,7 +1639,7 @@ int orc_op(int op, int use_double, const orc_options* opt, const double* row_x, 
     }
     if (op == 0) {
       t.x = (Real)io[20];
-      if (!orc::propagate(t, (Real)io[21], P)) return 1;
+      if (!orc::propagate(t, (Real)io[21], P, P.max_snp)) return 1;
       io[20] = t.x;
     } else if (op == 1) {
       const auto R = orc::residual(t, (Real)io[20], (Real)io[21], P);
@@ -850,7 +1647,7 @@ int orc_op(int op, int use_double, const orc_options* opt, const double* row_x, 
       io[22] = R.chi2;
     } else if (op == 2) {
       t.x = (Real)io[20];
-      if (!orc::rotate(t, io[21] > 0 ? 1 : -1, P)) return 1;
+      if (!orc::rotate(t, io[21] > 0 ? 1 : -1, P, P.max_snp)) return 1;
       io[20] = t.x;
     } else if (op == 3) {
       Real x[3], y[3], z[3];

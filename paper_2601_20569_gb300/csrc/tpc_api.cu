@@ -96,6 +96,7 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   for (int i = 0; i < 5; ++i) P.seed_c[i] = o.seed_c[i];
   P.follow_chi2 = o.follow_chi2;
   P.max_snp = o.max_snp;
+  P.fit_max_snp = o.fit_max_snp;
   P.score_w = o.score_w;
   P.shared_frac = o.shared_frac;
   P.merge_chi2 = o.merge_chi2;
@@ -103,6 +104,12 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.merge_dz = o.merge_dz;
   P.int_chi2 = o.int_chi2;
   P.final_chi2 = o.final_chi2;
+  P.attach_margin = o.attach_margin;
+  P.edge_margin = o.edge_margin;
+  // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
+  P.merge_zspan = (float)((double)(o.merge_max_gap + 2) *
+                          (((double)row_x[nr - 1] - (double)row_x[0]) / (double)(nr - 1)) /
+                          std::sqrt(1.0 - (double)o.max_snp * (double)o.max_snp));
   P.max_miss = o.max_miss;
   P.min_hits = o.min_hits;
   P.merge_max_gap = o.merge_max_gap;

@@ -19,9 +19,9 @@ struct KParams {
   float pitch_inv;   // rows per cm
   float link_wy, link_wz, link_chi2;
   float seed_c[5];
-  float follow_chi2, max_snp, score_w, shared_frac;
-  float merge_chi2, merge_dy, merge_dz;
-  float int_chi2, final_chi2;
+  float follow_chi2, max_snp, fit_max_snp, score_w, shared_frac;
+  float merge_chi2, merge_dy, merge_dz, merge_zspan;
+  float int_chi2, final_chi2, attach_margin, edge_margin;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k;
   int n_rows, n_sectors;
   float grid_dy;     // target y bin size [cm]

@@ -58,11 +58,12 @@ struct StepJ {
 };
 
 // Helix step of p by dx.  Returns false when |sin(phi)| leaves the model domain.
-__device__ __forceinline__ bool helix_step(const float* p, float dx, const KParams& P, StepJ& st) {
+__device__ __forceinline__ bool helix_step(const float* p, float dx, const KParams& P, StepJ& st,
+                                           float lim) {
   const float kappa = p[4] * P.kb;
   const float s0 = p[2];
   const float s1 = s0 + kappa * dx;
-  if (!(fabsf(s1) < P.max_snp)) return false;
+  if (!(fabsf(s1) < lim)) return false;
   const float c0 = sqrtf(1.0f - s0 * s0);
   const float c1 = sqrtf(1.0f - s1 * s1);
   const float N = s0 + s1;
@@ -144,10 +145,10 @@ __device__ __forceinline__ void add_ms(float* c, const float* p, float dx, const
 }
 
 // Extended-Kalman propagation to xnew (Jacobian at the current state).
-__device__ __forceinline__ bool propagate(Trk<float>& t, float xnew, const KParams& P) {
+__device__ __forceinline__ bool propagate(Trk<float>& t, float xnew, const KParams& P, float lim) {
   const float dx = xnew - t.x;
   StepJ st;
-  if (!helix_step(t.p, dx, P, st)) return false;
+  if (!helix_step(t.p, dx, P, st, lim)) return false;
   t.p[0] = st.p0;
   t.p[1] = st.p1;
   t.p[2] = st.p2;
@@ -220,7 +221,7 @@ __device__ __forceinline__ void update(Trk<float>& t, const Resid& R) {
 }
 
 // Frame rotation to the adjacent sector (dir = +1: +20 deg).
-__device__ __forceinline__ bool rotate(Trk<float>& t, int dir, const KParams& P) {
+__device__ __forceinline__ bool rotate(Trk<float>& t, int dir, const KParams& P, float lim) {
   const float ca = P.rot_c;
   const float sa = dir > 0 ? P.rot_s : -P.rot_s;
   const float snp = t.p[2];
@@ -229,7 +230,7 @@ __device__ __forceinline__ bool rotate(Trk<float>& t, int dir, const KParams& P)
   const float yn = t.p[0] * ca - t.x * sa;
   const float sn = snp * ca - csp * sa;
   const float cn = csp * ca + snp * sa;
-  if (!(cn > 0.0f) || !(fabsf(sn) < P.max_snp)) return false;
+  if (!(cn > 0.0f) || !(fabsf(sn) < lim)) return false;
   const float j00 = csp / cn;
   const float j10 = -sa * t.p[3] / cn;
   const float j20 = -sa * (t.p[4] * P.kb);

@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(128) k_tracklets(FrameDev F, KParams P) {
     for (int i = 1; i < L; ++i) {
       c = F.cup[c];
       const int r = F.srow[c] % NR;
-      if (!propagate(t, F.row_x[r], P)) {
+      if (!propagate(t, F.row_x[r], P, P.max_snp)) {
         alive = false;
         break;
       }
@@ -402,8 +402,8 @@ __global__ void __launch_bounds__(128) k_tracklets(FrameDev F, KParams P) {
     if (alive) {
       int miss = 0;
       for (int r = top + 1; r < NR; ++r) {
-        if (!propagate(t, F.row_x[r], P)) break;
-        if (fabsf(t.p[0]) > t.x * P.tan_half) break;
+        if (!propagate(t, F.row_x[r], P, P.max_snp)) break;
+        if (fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
         const int k = pick(F, P, t, sbase + r);
         if (k >= 0) {
           const Resid R = residual(t, F.sy[k], F.sz[k], P);
@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(128) k_tracklets(FrameDev F, KParams P) {
     int rlo = top;
     int miss = 0;
     for (int r = top - 1; r >= 0; --r) {
-      if (!propagate(t, F.row_x[r], P)) break;
-      if (fabsf(t.p[0]) > t.x * P.tan_half) break;
+      if (!propagate(t, F.row_x[r], P, P.max_snp)) break;
+      if (fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
       if (r >= r0) {
         const int k = H[r];
         if (k < 0) continue;

@@ -29,7 +29,8 @@ class TrackerOptions:
     link_chi2: float = 1.0          # max squared distance of the middle cluster to the d-u line [cm^2]
     seed_c: tuple = (1.0, 1.0, 0.25, 0.25, 100.0)  # seed covariance diagonal
     follow_chi2: float = 9.0        # cluster pick-up cut during following (2 dof)
-    max_snp: float = 0.95
+    max_snp: float = 0.95           # |sin(phi)| limit of seeding and following
+    fit_max_snp: float = 0.99       # limit of refits, merging and the final fit
     score_w: float = 2.0            # selector score = n_clusters - score_w * chi2/ndf
     shared_frac: float = 0.10
     merge_chi2: float = 30.0        # 5-dof match at the common x
@@ -37,6 +38,8 @@ class TrackerOptions:
     merge_dz: float = 3.0
     int_chi2: float = 25.0          # interpolation cut / Phase II candidate cut (2 dof)
     final_chi2: float = 16.0        # simple cut of the last fit iteration
+    attach_margin: float = 0.5      # widening of the Phase II search window [cm]
+    edge_margin: float = 1.0        # following stops beyond the sector edge + this [cm]
     max_miss: int = 10              # consecutive empty rows ending the following
     min_hits: int = 10
     merge_max_gap: int = 20         # rows between merged segments
@@ -51,8 +54,8 @@ class TrackerOptions:
 
 
 FLOAT_FIELDS = ("bz", "sigma_y", "sigma_z", "ms_theta", "link_wy", "link_wz", "link_chi2")
-FLOAT_FIELDS2 = ("follow_chi2", "max_snp", "score_w", "shared_frac", "merge_chi2", "merge_dy",
-                 "merge_dz", "int_chi2", "final_chi2")
+FLOAT_FIELDS2 = ("follow_chi2", "max_snp", "fit_max_snp", "score_w", "shared_frac", "merge_chi2", "merge_dy",
+                 "merge_dz", "int_chi2", "final_chi2", "attach_margin", "edge_margin")
 INT_FIELDS = ("max_miss", "min_hits", "merge_max_gap", "inner_rows", "cand_k", "brute_force",
               "n_rows", "n_sectors")
 

@@ -258,7 +258,7 @@ def generate(workload: str = "one_sector", frame: int = 0, *, seed: int | None =
             map=cmap, workload=workload,
         )
         if store_truth:
-            for k in ("ty", "tz", "tsnp", "ttgl", "tqpt"):
+            for k in ("ty", "tz", "tsnp", "ttgl", "tqpt", "tyu", "tzu"):
                 fr.truth[k[1:]] = get(k, np.float64, n)
         for k, dt in (("p_pt", np.float64), ("p_q", np.float64), ("p_tgl", np.float64),
                       ("p_phi", np.float64), ("p_t0", np.float64), ("p_vx", np.float64),

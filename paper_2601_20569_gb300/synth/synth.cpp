@@ -359,6 +359,7 @@ struct synth_result {
   std::vector<uint8_t> row, sector;
   std::vector<int32_t> label;
   std::vector<double> ty, tz, tsnp, ttgl, tqpt;  // truth per cluster (optional)
+  std::vector<double> tyu, tzu;  // undistorted crossing (with the drift shift), truth
   std::vector<double> p_pt, p_q, p_tgl, p_phi, p_t0, p_vx, p_vy;
   std::vector<int32_t> p_secondary, p_ncl_leg0, p_ncl_leg1;
   std::vector<double> sector_thin;
@@ -502,6 +503,7 @@ int synth_generate(const synth_config* cfgp, synth_result** out) {
   if (cfg.store_truth) {
     res->ty.assign(ntot, 0); res->tz.assign(ntot, 0); res->tsnp.assign(ntot, 0);
     res->ttgl.assign(ntot, 0); res->tqpt.assign(ntot, 0);
+    res->tyu.assign(ntot, 0); res->tzu.assign(ntot, 0);
   }
   res->p_pt.resize(np); res->p_q.resize(np); res->p_tgl.resize(np); res->p_phi.resize(np);
   res->p_t0.resize(np); res->p_vx.resize(np); res->p_vy.resize(np);
@@ -547,6 +549,7 @@ int synth_generate(const synth_config* cfgp, synth_result** out) {
       res->label[k] = (int32_t)(2 * i + c.leg);
       if (cfg.store_truth) {
         res->ty[k] = ym; res->tz[k] = zm + zshift;
+        res->tyu[k] = c.y; res->tzu[k] = c.z + zshift;
         res->tsnp[k] = c.snp; res->ttgl[k] = c.tgl; res->tqpt[k] = c.qpt;
       }
       if (c.leg == 0) res->p_ncl_leg0[i]++; else res->p_ncl_leg1[i]++;
@@ -578,6 +581,7 @@ int synth_generate(const synth_config* cfgp, synth_result** out) {
       res->label[k] = -1;
       if (cfg.store_truth) {
         res->ty[k] = yy; res->tz[k] = zz;
+        res->tyu[k] = yy; res->tzu[k] = zz;
       }
     }
   }
@@ -596,7 +600,7 @@ int synth_generate(const synth_config* cfgp, synth_result** out) {
     };
     apply(res->y); apply(res->z); apply(res->q); apply(res->row); apply(res->sector);
     apply(res->label); apply(res->ty); apply(res->tz); apply(res->tsnp); apply(res->ttgl);
-    apply(res->tqpt);
+    apply(res->tqpt); apply(res->tyu); apply(res->tzu);
   }
   *out = res;
   return 0;
@@ -631,6 +635,8 @@ int synth_copy(const synth_result* r, const char* what, void* dst, long cap) {
   if (w == "tsnp") return cp(r->tsnp);
   if (w == "ttgl") return cp(r->ttgl);
   if (w == "tqpt") return cp(r->tqpt);
+  if (w == "tyu") return cp(r->tyu);
+  if (w == "tzu") return cp(r->tzu);
   if (w == "p_pt") return cp(r->p_pt);
   if (w == "p_q") return cp(r->p_q);
   if (w == "p_tgl") return cp(r->p_tgl);

@@ -45,10 +45,12 @@ class Options(ctypes.Structure):
         ("bz", ctypes.c_float), ("sigma_y", ctypes.c_float), ("sigma_z", ctypes.c_float),
         ("ms_theta", ctypes.c_float), ("link_wy", ctypes.c_float), ("link_wz", ctypes.c_float),
         ("link_chi2", ctypes.c_float), ("seed_c", ctypes.c_float * 5),
-        ("follow_chi2", ctypes.c_float), ("max_snp", ctypes.c_float), ("score_w", ctypes.c_float),
+        ("follow_chi2", ctypes.c_float), ("max_snp", ctypes.c_float),
+        ("fit_max_snp", ctypes.c_float), ("score_w", ctypes.c_float),
         ("shared_frac", ctypes.c_float), ("merge_chi2", ctypes.c_float),
         ("merge_dy", ctypes.c_float), ("merge_dz", ctypes.c_float), ("int_chi2", ctypes.c_float),
-        ("final_chi2", ctypes.c_float), ("max_miss", ctypes.c_int32),
+        ("final_chi2", ctypes.c_float), ("attach_margin", ctypes.c_float),
+        ("edge_margin", ctypes.c_float), ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32), ("merge_max_gap", ctypes.c_int32),
         ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
@@ -72,7 +74,7 @@ class Tracks(ctypes.Structure):
 class _DevArray:
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr or 0), True), "version": 2}
+                                         "data": (int(ptr or 0), False), "version": 2}
 
 
 def wrap_device(ptr, shape, typestr):
