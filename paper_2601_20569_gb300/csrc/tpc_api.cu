@@ -29,6 +29,9 @@ const StageDef kStages[] = {
     {"starts", strict::stage_starts, fast::stage_starts},
     {"tracklets", strict::stage_tracklets, fast::stage_tracklets},
     {"select", strict::stage_select, fast::stage_select},
+    {"merge", strict::stage_merge, fast::stage_merge},
+    {"fit", strict::stage_fit, fast::stage_fit},
+    {"output", strict::stage_output, fast::stage_output},
 };
 constexpr int kNumStages = sizeof(kStages) / sizeof(kStages[0]);
 }  // namespace
@@ -119,7 +122,25 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.grid_occ = 1.0f;
 }
 
-#define CK(call)                                                                       \
+// Kernel view of a correction map; scales derived in double, rounded once.
+MapDev make_mapdev(const tpc_map& m) {
+  MapDev M{};
+  if (!m.coeff) return M;
+  M.on = 1;
+  M.nphi = m.n_phi;
+  M.nr = m.n_r;
+  M.nz = m.n_z;
+  M.rmin = m.r_min;
+  M.zmin = m.z_min;
+  M.zmax = m.z_max;
+  M.phi_scale = (float)((double)m.n_phi / 18.0);
+  M.r_scale = (float)((double)(m.n_r - 3) / ((double)m.r_max - (double)m.r_min));
+  M.z_scale = (float)((double)(m.n_z - 3) / ((double)m.z_max - (double)m.z_min));
+  M.c = m.coeff;
+  return M;
+}
+
+#define CK(call)                                                                     \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
     if (e_ != cudaSuccess) return fail(ctx, TPC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
@@ -136,7 +157,14 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   if (geo->n_rows < 4 || geo->n_rows > kMaxRows || geo->n_sectors < 1 || geo->n_sectors > 255 ||
       geo->n_sectors * geo->n_rows > 65535 || opt->cap_clusters < 1 || opt->cand_k < 1 ||
       opt->cand_k > kMaxCand || opt->min_hits < 3 || !(opt->shared_frac >= 0.0f) ||
-      (opt->mode != 0 && opt->mode != 1) || opt->cap_clusters > (1L << 30))
+      (opt->mode != 0 && opt->mode != 1) || opt->cap_clusters > (1L << 30) ||
+      opt->inner_rows < 0 || opt->inner_rows > kMaxInner || opt->merge_max_gap < 1 ||
+      !(opt->fit_max_snp > 0.0f && opt->fit_max_snp < 1.0f) ||
+      !(opt->max_snp > 0.0f && opt->max_snp < 1.0f))
+    return TPC_ERR_INVALID_ARG;
+  if (map && map->coeff &&
+      (map->n_phi < 1 || map->n_r < 4 || map->n_z < 4 || !(map->r_max > map->r_min) ||
+       !(map->z_max > map->z_min)))
     return TPC_ERR_INVALID_ARG;
   for (int r = 1; r < geo->n_rows; ++r)
     if (!(geo->row_x[r] > geo->row_x[r - 1])) return TPC_ERR_INVALID_ARG;
@@ -196,6 +224,67 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.tl_kept, F.cap_tl * kMaxRows);
   ok &= dalloc(ctx, &F.sec_owner, n);
   ok &= dalloc(ctx, &F.cnt, 1);
+  // a7
+  const long T = F.cap_tl;
+  const long nmb = (long)geo->n_sectors * kMergeBins;
+  ok &= dalloc(ctx, &F.st_tl, T);
+  ok &= dalloc(ctx, &F.st_ok, T);
+  ok &= dalloc(ctx, &F.st_key, T);
+  ok &= dalloc(ctx, &F.st_sector, T);
+  ok &= dalloc(ctx, &F.st_rmin, T);
+  ok &= dalloc(ctx, &F.st_rmax, T);
+  ok &= dalloc(ctx, &F.st_ie, T * kStateF);
+  ok &= dalloc(ctx, &F.st_oe, T * kStateF);
+  ok &= dalloc(ctx, &F.st_next, T);
+  ok &= dalloc(ctx, &F.st_hasprev, T);
+  ok &= dalloc(ctx, &F.st_bestB, T);
+  ok &= dalloc(ctx, &F.st_bestchi, T);
+  ok &= dalloc(ctx, &F.st_bestA, T);
+  ok &= dalloc(ctx, &F.ie_cnt, nmb + 1);
+  ok &= dalloc(ctx, &F.ie_first, nmb + 1);
+  ok &= dalloc(ctx, &F.ie_slot, T);
+  ok &= dalloc(ctx, &F.ie_bin, T);
+  ok &= dalloc(ctx, &F.ie_idx, T);
+  ok &= dalloc(ctx, &F.sec_zlo, geo->n_sectors);
+  ok &= dalloc(ctx, &F.sec_zinv, geo->n_sectors);
+  // a9/a10/a11
+  F.cap_ft = opt->cap_tracks > 0 ? opt->cap_tracks : n / 40 + 4096;
+  const long FT = F.cap_ft;
+  ok &= dalloc(ctx, &F.ft_head, FT);
+  ok &= dalloc(ctx, &F.ft_key, FT);
+  ok &= dalloc(ctx, &F.ft_ok, FT);
+  ok &= dalloc(ctx, &F.ft_nst, FT);
+  ok &= dalloc(ctx, &F.ft_z0, FT);
+  ok &= dalloc(ctx, &F.ft_st_cl, FT * kMaxRows);
+  ok &= dalloc(ctx, &F.ft_st_rs, FT * kMaxRows);
+  ok &= dalloc(ctx, &F.ft_store, FT * kMaxRows * 5);
+  ok &= dalloc(ctx, &F.ft_flag, FT * kMaxRows);
+  ok &= dalloc(ctx, &F.ft_end2, FT * kStateF);
+  ok &= dalloc(ctx, &F.ft_ncand, FT * kMaxInner);
+  ok &= dalloc(ctx, &F.ft_cand, FT * kMaxInner * kMaxCand);
+  ok &= dalloc(ctx, &F.ft_cchi, FT * kMaxInner * kMaxCand);
+  ok &= dalloc(ctx, &F.ft_assigned, FT * kMaxInner);
+  ok &= dalloc(ctx, &F.ft_newly, FT * kMaxInner);
+  ok &= dalloc(ctx, &F.bid, n);
+  ok &= dalloc(ctx, &F.taken, n);
+  ok &= dalloc(ctx, &F.ft_n, FT);
+  ok &= dalloc(ctx, &F.ft_chi2, FT);
+  ok &= dalloc(ctx, &F.ft_out, FT * kStateF);
+  ok &= dalloc(ctx, &F.ft_used, FT * kMaxRows);
+  ok &= dalloc(ctx, &F.ft_outidx, FT);
+  ok &= dalloc(ctx, &F.out_par, FT * 5);
+  ok &= dalloc(ctx, &F.out_cov, FT * 15);
+  ok &= dalloc(ctx, &F.out_chi2, FT);
+  ok &= dalloc(ctx, &F.out_x, FT);
+  ok &= dalloc(ctx, &F.out_ndf, FT);
+  ok &= dalloc(ctx, &F.out_sector, FT);
+  ok &= dalloc(ctx, &F.out_ncl, FT);
+  ok &= dalloc(ctx, &F.out_offset, FT + 1);
+  F.cap_refs = n + n / 4 + 4096;
+  ok &= dalloc(ctx, &F.out_ids, F.cap_refs);
+  ok &= dalloc(ctx, &F.out_key, FT);
+  ok &= dalloc(ctx, &F.attach, n);
+  ok &= dalloc(ctx, &F.attach_key, n);
   if (!ok) {
     tpc_destroy(ctx);
     return TPC_ERR_OOM;
@@ -252,7 +341,14 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
   if (n > 0) {
     CK(cudaMemsetAsync(F.owner_key, 0, sizeof(unsigned long long) * n, s));
     CK(cudaMemsetAsync(F.sec_owner, 0xFF, sizeof(int) * n, s));
+    CK(cudaMemsetAsync(F.bid, 0xFF, sizeof(unsigned long long) * n, s));
+    CK(cudaMemsetAsync(F.taken, 0, n, s));
+    CK(cudaMemsetAsync(F.attach, 0xFF, sizeof(int) * n, s));
+    CK(cudaMemsetAsync(F.attach_key, 0x7F, sizeof(int) * n, s));
   }
+  CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * ((long)ctx->n_sectors * kMergeBins + 1), s));
+  CK(cudaMemsetAsync(F.out_offset, 0, sizeof(int), s));
+  F.map = make_mapdev(ctx->map);
   ctx->launches_last = 0;
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
   for (int i = 0; i < kNumStages; ++i) {
@@ -285,7 +381,29 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
     return fail(ctx, TPC_ERR_CAPACITY, "start hits %d exceed tracklet capacity %ld", c.n_starts,
                 F.cap_tl);
   }
-  out->attach = F.sec_owner;
+  if (c.err & kErrCapRefs) {
+    if (needed) *needed = c.n_refs;
+    return fail(ctx, TPC_ERR_CAPACITY, "cluster references %d exceed capacity %ld", c.n_refs,
+                F.cap_refs);
+  }
+  if (c.err & kErrCapTracks) {
+    if (needed) *needed = c.need_tracks;
+    return fail(ctx, TPC_ERR_CAPACITY, "merged tracks %d exceed track capacity %ld", c.n_merged,
+                F.cap_ft);
+  }
+  out->n_tracks = c.n_out;
+  out->n_cluster_refs = c.n_refs;
+  out->params = F.out_par;
+  out->cov = F.out_cov;
+  out->chi2 = F.out_chi2;
+  out->x = F.out_x;
+  out->ndf = F.out_ndf;
+  out->sector = F.out_sector;
+  out->n_clusters = F.out_ncl;
+  out->cl_offset = F.out_offset;
+  out->cl_ids = F.out_ids;
+  out->key = F.out_key;
+  out->attach = F.attach;
   return TPC_OK;
 }
 
@@ -297,6 +415,7 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   const long n = F.n;
   const long nrr = (long)ctx->n_sectors * ctx->n_rows;
   const long nst = c.n_starts < F.cap_tl ? c.n_starts : F.cap_tl;
+  const long nft = c.n_merged < F.cap_ft ? c.n_merged : F.cap_ft;
   const void* src = nullptr;
   long nb = 0;
   const std::string w(name);
@@ -325,6 +444,34 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   else if (w == "tl_nkept") { src = F.tl_nkept; nb = 4 * nst; }
   else if (w == "owner_key") { src = F.owner_key; nb = 8 * n; }
   else if (w == "sec_owner") { src = F.sec_owner; nb = 4 * n; }
+  else if (w == "st_tl") { src = F.st_tl; nb = 4L * c.n_tracks; }
+  else if (w == "st_ok") { src = F.st_ok; nb = 4L * c.n_tracks; }
+  else if (w == "st_key") { src = F.st_key; nb = 4L * c.n_tracks; }
+  else if (w == "st_next") { src = F.st_next; nb = 4L * c.n_tracks; }
+  else if (w == "st_ie") { src = F.st_ie; nb = 4L * kStateF * c.n_tracks; }
+  else if (w == "st_oe") { src = F.st_oe; nb = 4L * kStateF * c.n_tracks; }
+  else if (w == "ft_key") { src = F.ft_key; nb = 4L * nft; }
+  else if (w == "ft_ok") { src = F.ft_ok; nb = 4L * nft; }
+  else if (w == "ft_nst") { src = F.ft_nst; nb = 4L * nft; }
+  else if (w == "ft_st_cl") { src = F.ft_st_cl; nb = 4L * kMaxRows * nft; }
+  else if (w == "ft_st_rs") { src = F.ft_st_rs; nb = 2L * kMaxRows * nft; }
+  else if (w == "ft_flag") { src = F.ft_flag; nb = 1L * kMaxRows * nft; }
+  else if (w == "ft_ncand") { src = F.ft_ncand; nb = 1L * kMaxInner * nft; }
+  else if (w == "ft_cand") { src = F.ft_cand; nb = 4L * kMaxInner * kMaxCand * nft; }
+  else if (w == "ft_cchi") { src = F.ft_cchi; nb = 4L * kMaxInner * kMaxCand * nft; }
+  else if (w == "ft_assigned") { src = F.ft_assigned; nb = 4L * kMaxInner * nft; }
+  else if (w == "ft_n") { src = F.ft_n; nb = 4L * nft; }
+  else if (w == "out_par") { src = F.out_par; nb = 4L * 5 * c.n_out; }
+  else if (w == "out_cov") { src = F.out_cov; nb = 4L * 15 * c.n_out; }
+  else if (w == "out_chi2") { src = F.out_chi2; nb = 4L * c.n_out; }
+  else if (w == "out_x") { src = F.out_x; nb = 4L * c.n_out; }
+  else if (w == "out_ndf") { src = F.out_ndf; nb = 4L * c.n_out; }
+  else if (w == "out_sector") { src = F.out_sector; nb = 4L * c.n_out; }
+  else if (w == "out_ncl") { src = F.out_ncl; nb = 4L * c.n_out; }
+  else if (w == "out_offset") { src = F.out_offset; nb = 4L * (c.n_out + 1); }
+  else if (w == "out_ids") { src = F.out_ids; nb = 4L * c.n_refs; }
+  else if (w == "out_key") { src = F.out_key; nb = 4L * c.n_out; }
+  else if (w == "attach") { src = F.attach; nb = 4 * n; }
   else return fail(ctx, TPC_ERR_INVALID_ARG, "unknown buffer %s", name);
   if (bytes) *bytes = nb;
   if (!host_dst) return TPC_OK;

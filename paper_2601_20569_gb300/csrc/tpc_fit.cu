@@ -1,0 +1,924 @@
+// Track merging and the final fit (Sec. 2 "track merging and track fit",
+// Sec. 3 Phases I and II):
+//   a7  sector refit of every accepted tracklet and mutual-best merging of
+//       track ends inside a sector and between adjacent sectors of one half;
+//   a8  space-charge correction of clusters with a cubic B-spline map;
+//   a9  three-iteration linearised Kalman fit: iteration 1 inward stores the
+//       predicted (y,z) and covariance per station, iteration 2 outward
+//       interpolates and flags outliers, iteration 3 inward refits;
+//   a10 Phase II re-attachment on the inner rows: candidates within the
+//       interpolation cut, second ambiguity solving in cand_k rounds;
+//   a11 output compaction and cluster-to-track attachment.
+// Compiled twice (strict / fast) like the sector kernels.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tpc_kernels.h"
+#include "tpc_model.cuh"
+#include "tpc_util.cuh"
+
+namespace tpc {
+namespace TPC_NS {
+
+namespace {
+
+// ------------------------------------------------------------- state I/O
+__device__ __forceinline__ void put_state(float* dst, const Trk<float>& t, int sector) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dst[i] = t.p[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) dst[5 + i] = t.c[i];
+  dst[20] = t.x;
+  dst[21] = __int_as_float(sector);
+}
+
+__device__ __forceinline__ void get_state(const float* src, Trk<float>& t) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) t.p[i] = src[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) t.c[i] = src[5 + i];
+  t.x = src[20];
+}
+
+// --------------------------------------------------------- a8 distortion map
+__device__ __forceinline__ void spline_w(float f, float* w) {
+  const float g = 1.0f - f;
+  const float f2 = f * f, f3 = f2 * f;
+  w[0] = g * g * g / 6.0f;
+  w[1] = (3.0f * f3 - 6.0f * f2 + 4.0f) / 6.0f;
+  w[2] = (-3.0f * f3 + 3.0f * f2 + 3.0f * f + 1.0f) / 6.0f;
+  w[3] = f3 / 6.0f;
+}
+
+__device__ __forceinline__ void spline_span(float t, int n, int& i, float& f) {
+  const float tmax = (float)(n - 3);
+  if (t < 0.0f) t = 0.0f;
+  if (t > tmax) t = tmax;
+  i = (int)floorf(t);
+  if (i > n - 4) i = n - 4;
+  f = t - (float)i;
+}
+
+struct SplinePt {
+  int ip, ir, iz;
+  float wp[4], wr[4], wz[4];
+};
+
+__device__ __forceinline__ SplinePt spline_point(const MapDev& M, const KParams& P, int sector,
+                                                 float x, float y, float zdrift) {
+  SplinePt sp;
+  const int sphi = sector % (P.n_sectors / 2);
+  const float u = ((float)sphi + 0.5f) + 0.5f * (y / x) / P.tan_half;
+  const float tp = u * M.phi_scale - 0.5f;
+  sp.ip = (int)floorf(tp);
+  const float fp = tp - (float)sp.ip;
+  const float r = sqrtf(x * x + y * y);
+  float fr, fz;
+  spline_span((r - M.rmin) * M.r_scale, M.nr, sp.ir, fr);
+  float zc = zdrift;
+  if (zc < M.zmin) zc = M.zmin;
+  if (zc > M.zmax) zc = M.zmax;
+  spline_span((zc - M.zmin) * M.z_scale, M.nz, sp.iz, fz);
+  spline_w(fp, sp.wp);
+  spline_w(fr, sp.wr);
+  spline_w(fz, sp.wz);
+  return sp;
+}
+
+__device__ __forceinline__ int phi_index(int ip, int e, int nphi) {
+  return ((ip - 1 + e) % nphi + nphi) % nphi;
+}
+
+__device__ __forceinline__ void map_eval(const MapDev& M, const KParams& P, int sector, float x,
+                                         float y, float zdrift, float* D) {
+  D[0] = D[1] = D[2] = 0.0f;
+  if (!M.on) return;
+  const SplinePt sp = spline_point(M, P, sector, x, y, zdrift);
+  int pidx[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) pidx[e] = phi_index(sp.ip, e, M.nphi);
+  for (int comp = 0; comp < 3; ++comp) {
+    float acc = 0.0f;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        const float wzr = sp.wz[a] * sp.wr[b];
+        const float* row = M.c + (((long)comp * M.nz + (sp.iz + a)) * M.nr + (sp.ir + b)) * M.nphi;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc = acc + wzr * sp.wp[e] * __ldg(row + pidx[e]);
+      }
+    D[comp] = acc;
+  }
+}
+
+// Corrected measurement projected back onto the pad row along the reference.
+__device__ __forceinline__ bool corrected(const MapDev& M, const KParams& P, int sector, float x,
+                                          float y, float z, float z0, const float* ref, float& my,
+                                          float& mz) {
+  float D[3];
+  map_eval(M, P, sector, x, y, z - z0, D);
+  my = y + D[1];
+  mz = z + D[2];
+  if (D[0] != 0.0f) {
+    StepJ st;
+    if (!helix_step(ref, D[0], P, st, P.fit_max_snp)) return false;
+    my = my - (st.p0 - ref[0]);
+    mz = mz - (st.p1 - ref[1]);
+  }
+  return true;
+}
+
+// ------------------------------------------------------ a7 sector refit
+__device__ __forceinline__ unsigned long long pack_chi_key(float chi2, int key) {
+  return ((unsigned long long)f2o(chi2) << 32) | (unsigned long long)(unsigned)key;
+}
+
+// Compaction of accepted tracklets into the sector-track list (tracklet order).
+__global__ void k_acc_count(FrameDev F) {
+  __shared__ int sh[32];
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = (!F.cnt->err && i < nst && F.tl_acc[i]) ? 1 : 0;
+  int tot;
+  block_exscan(f, sh, &tot);
+  if (threadIdx.x == 0) F.scan_tmp[blockIdx.x] = tot;
+}
+
+__global__ void k_acc_write(FrameDev F) {
+  __shared__ int sh[32];
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = (!F.cnt->err && i < nst && F.tl_acc[i]) ? 1 : 0;
+  int tot;
+  const int ex = block_exscan(f, sh, &tot);
+  if (f) F.st_tl[F.scan_tmp[blockIdx.x] + ex] = i;
+}
+
+__global__ void __launch_bounds__(128) k_sector_refit(FrameDev F, KParams P) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  const int NR = P.n_rows;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+    const int ti = F.st_tl[i];
+    const int nk = F.tl_nkept[ti];
+    const int* K = F.tl_kept + (long)ti * kMaxRows;  // outermost first
+    const int rs = F.srow[K[nk - 1]];
+    F.st_key[i] = F.sid[F.starts[ti]];
+    F.st_sector[i] = rs / NR;
+    F.st_rmin[i] = rs % NR;
+    F.st_rmax[i] = F.srow[K[0]] % NR;
+    F.st_next[i] = -1;
+    F.st_hasprev[i] = 0;
+    F.st_bestB[i] = -1;
+    F.st_bestA[i] = ~0ull;
+    Trk<float> t;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) t.p[k] = F.tl_par[(long)ti * 5 + k];
+    t.x = F.tl_x[ti];
+    reset_cov(t.c, P);
+    bool ok = true;
+    for (int j = nk - 1; j >= 0 && ok; --j) {
+      const int c = K[j];
+      if (!propagate(t, F.row_x[F.srow[c] % NR], P, P.fit_max_snp)) { ok = false; break; }
+      update(t, residual(t, F.sy[c], F.sz[c], P));
+    }
+    if (ok) {
+      put_state(F.st_oe + (long)i * kStateF, t, rs / NR);
+      reset_cov(t.c, P);
+      for (int j = 0; j < nk; ++j) {
+        const int c = K[j];
+        if (!propagate(t, F.row_x[F.srow[c] % NR], P, P.fit_max_snp)) { ok = false; break; }
+        update(t, residual(t, F.sy[c], F.sz[c], P));
+      }
+      if (ok) put_state(F.st_ie + (long)i * kStateF, t, rs / NR);
+    }
+    F.st_ok[i] = ok ? 1 : 0;
+  }
+}
+
+// z range of each sector (from the row statistics of the grid build).
+__global__ void k_sector_zrange(FrameDev F, KParams P) {
+  const int s = blockIdx.x;
+  __shared__ unsigned lo, hi;
+  if (threadIdx.x == 0) { lo = 0xFFFFFFFFu; hi = 0u; }
+  __syncthreads();
+  for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) {
+    const int rr = s * P.n_rows + r;
+    if (F.row_cnt[rr] > 0) {
+      atomicMin(&lo, F.row_zmin[rr]);
+      atomicMax(&hi, F.row_zmax[rr]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float zl = 0.0f, zh = 1.0f;
+    if (hi >= lo && hi != 0u) { zl = o2f(lo); zh = o2f(hi); }
+    F.sec_zlo[s] = zl;
+    F.sec_zinv[s] = zh > zl ? (float)kMergeBins / (zh - zl) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ int merge_bin(const FrameDev& F, int s, float z) {
+  return s * kMergeBins + clampi((int)floorf((z - F.sec_zlo[s]) * F.sec_zinv[s]), 0, kMergeBins - 1);
+}
+
+__global__ void k_ie_hist(FrameDev F) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+    if (!F.st_ok[i]) { F.ie_bin[i] = -1; continue; }
+    const int b = merge_bin(F, F.st_sector[i], F.st_ie[(long)i * kStateF + 1]);
+    F.ie_bin[i] = b;
+    F.ie_slot[i] = atomicAdd(&F.ie_cnt[b], 1);
+  }
+}
+
+__global__ void k_ie_scatter(FrameDev F) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+    const int b = F.ie_bin[i];
+    if (b >= 0) F.ie_idx[F.ie_first[b] + F.ie_slot[i]] = i;
+  }
+}
+
+// chi2 of a 5-vector difference with a Cholesky factorisation (-1: not PD).
+__device__ __forceinline__ float chi2_5(const float* d, const float* c) {
+  float L[15];  // lower triangle, same indexing as the covariance
+  for (int j = 0; j < 5; ++j) {
+    float s = c[j * (j + 1) / 2 + j];
+    for (int k = 0; k < j; ++k) s = s - L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+    if (!(s > 0.0f)) return -1.0f;
+    L[j * (j + 1) / 2 + j] = sqrtf(s);
+    for (int i = j + 1; i < 5; ++i) {
+      float v = c[i * (i + 1) / 2 + j];
+      for (int k = 0; k < j; ++k) v = v - L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+      L[i * (i + 1) / 2 + j] = v / L[j * (j + 1) / 2 + j];
+    }
+  }
+  float yv[5];
+  float chi2 = 0.0f;
+  for (int i = 0; i < 5; ++i) {
+    float v = d[i];
+    for (int k = 0; k < i; ++k) v = v - L[i * (i + 1) / 2 + k] * yv[k];
+    yv[i] = v / L[i * (i + 1) / 2 + i];
+    chi2 = chi2 + yv[i] * yv[i];
+  }
+  return chi2;
+}
+
+// The pair test of the outer end of A against the inner end of B.
+__device__ __forceinline__ bool merge_test(const FrameDev& F, const KParams& P, int a, int b,
+                                           float& chi2) {
+  const int half = P.n_sectors / 2;
+  const int sa = F.st_sector[a], sb = F.st_sector[b];
+  if (sa / half != sb / half) return false;
+  const int ds = ((sb % half) - (sa % half) + half) % half;
+  if (ds != 0 && ds != 1 && ds != half - 1) return false;
+  const int gap = F.st_rmin[b] - F.st_rmax[a];
+  if (gap < 1 || gap > P.merge_max_gap) return false;
+  const float* oe = F.st_oe + (long)a * kStateF;
+  const float* ie = F.st_ie + (long)b * kStateF;
+  const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
+  if (!(fabsf(ie[1] - oe[1]) <= zwin)) return false;
+  Trk<float> t;
+  get_state(oe, t);
+  if (ds == 1 && !rotate(t, 1, P, P.fit_max_snp)) return false;
+  if (ds == half - 1 && !rotate(t, -1, P, P.fit_max_snp)) return false;
+  if (!propagate(t, ie[20], P, P.fit_max_snp)) return false;
+  float d[5], c[15];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) d[i] = ie[i] - t.p[i];
+  if (!(fabsf(d[0]) <= P.merge_dy) || !(fabsf(d[1]) <= P.merge_dz)) return false;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) c[i] = t.c[i] + ie[5 + i];
+  chi2 = chi2_5(d, c);
+  return chi2 >= 0.0f && chi2 < P.merge_chi2;
+}
+
+template <typename Fn>
+__device__ __forceinline__ void for_merge_candidates(const FrameDev& F, const KParams& P, int a,
+                                                     Fn&& fn) {
+  const int half = P.n_sectors / 2;
+  const int sa = F.st_sector[a];
+  const int side = sa / half, ph = sa % half;
+  const float* oe = F.st_oe + (long)a * kStateF;
+  const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
+  const int dsl[3] = {0, 1, half - 1};
+  for (int q = 0; q < 3; ++q) {
+    const int sb = side * half + (ph + dsl[q]) % half;
+    const float m = 0.01f;
+    const int b0 = merge_bin(F, sb, oe[1] - zwin - m), b1 = merge_bin(F, sb, oe[1] + zwin + m);
+    const int lo = F.ie_first[b0], hi = F.ie_first[b1 + 1];
+    for (int k = lo; k < hi; ++k) {
+      const int b = F.ie_idx[k];
+      if (b != a) fn(b);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_merge_best(FrameDev F, KParams P) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < ns; a += gridDim.x * blockDim.x) {
+    if (!F.st_ok[a]) continue;
+    const int keyA = F.st_key[a];
+    int bb = -1;
+    float bchi = 0.0f;
+    int bkey = 0;
+    for_merge_candidates(F, P, a, [&](int b) {
+      if (!F.st_ok[b]) return;
+      float chi2;
+      if (!merge_test(F, P, a, b, chi2)) return;
+      const int kb = F.st_key[b];
+      if (bb < 0 || chi2 < bchi || (chi2 == bchi && kb < bkey)) {
+        bb = b;
+        bchi = chi2;
+        bkey = kb;
+      }
+      atomicMin(&F.st_bestA[b], pack_chi_key(chi2, keyA));
+    });
+    F.st_bestB[a] = bb;
+    F.st_bestchi[a] = bchi;
+  }
+}
+
+__global__ void k_merge_link(FrameDev F) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < ns; a += gridDim.x * blockDim.x) {
+    const int b = F.st_bestB[a];
+    if (b < 0) continue;
+    if (F.st_bestA[b] == pack_chi_key(F.st_bestchi[a], F.st_key[a])) {
+      F.st_next[a] = b;
+      F.st_hasprev[b] = 1;
+    }
+  }
+}
+
+// Heads of chains -> fit tracks (compaction in sector-track order).
+__device__ __forceinline__ int is_head(const FrameDev& F, int i, int ns) {
+  return (i < ns && F.st_ok[i] && !F.st_hasprev[i]) ? 1 : 0;
+}
+
+__global__ void k_head_count(FrameDev F) {
+  __shared__ int sh[32];
+  const int ns = F.cnt->n_tracks;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = F.cnt->err ? 0 : is_head(F, i, ns);
+  int tot;
+  block_exscan(f, sh, &tot);
+  if (threadIdx.x == 0) F.scan_tmp[blockIdx.x] = tot;
+}
+
+__global__ void k_head_write(FrameDev F) {
+  __shared__ int sh[32];
+  const int ns = F.cnt->n_tracks;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = F.cnt->err ? 0 : is_head(F, i, ns);
+  int tot;
+  const int ex = block_exscan(f, sh, &tot);
+  const int pos = F.scan_tmp[blockIdx.x] + ex;
+  if (f && pos < F.cap_ft) F.ft_head[pos] = i;
+}
+
+__global__ void k_head_check(FrameDev F) {
+  if (F.cnt->n_merged > F.cap_ft) {
+    atomicOr(&F.cnt->err, kErrCapTracks);
+    atomicMax(&F.cnt->need_tracks, F.cnt->n_merged);
+  }
+}
+
+// ------------------------------------------ a9/a10 linearised three-iteration fit
+struct Lin {
+  Trk<float> t;
+  float r[5];
+  int sector;
+};
+
+__device__ __forceinline__ void lin_start(Lin& L, const Trk<float>& s, int sector,
+                                          const KParams& P) {
+  L.t = s;
+  reset_cov(L.t.c, P);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) L.r[i] = s.p[i];
+  L.sector = sector;
+}
+
+__device__ __forceinline__ bool lin_rotate(Lin& L, int dir, const KParams& P) {
+  const float ca = P.rot_c;
+  const float sa = dir > 0 ? P.rot_s : -P.rot_s;
+  const float snp = L.r[2];
+  const float csp = sqrtf(1.0f - snp * snp);
+  const float xn = L.t.x * ca + L.r[0] * sa;
+  const float yn = L.r[0] * ca - L.t.x * sa;
+  const float sn = snp * ca - csp * sa;
+  const float cn = csp * ca + snp * sa;
+  if (!(cn > 0.0f) || !(fabsf(sn) < P.fit_max_snp)) return false;
+  const float j00 = csp / cn;
+  const float j10 = -sa * L.r[3] / cn;
+  const float j20 = -sa * (L.r[4] * P.kb);
+  const float j22 = cn / csp;
+  const float d0 = L.t.p[0] - L.r[0], d1 = L.t.p[1] - L.r[1], d2 = L.t.p[2] - L.r[2];
+  float* c = L.t.c;
+  const float m00 = c[0], m10 = c[1], m11 = c[2], m20 = c[3], m21 = c[4], m22 = c[5];
+  const float m30 = c[6], m31 = c[7], m32 = c[8], m33 = c[9];
+  const float m40 = c[10], m41 = c[11], m42 = c[12], m43 = c[13], m44 = c[14];
+  const float a00 = j00 * m00;
+  const float a10 = j10 * m00 + m10, a11 = j10 * m10 + m11;
+  const float a20 = j20 * m00 + j22 * m20, a21 = j20 * m10 + j22 * m21,
+              a22 = j20 * m20 + j22 * m22;
+  c[0] = a00 * j00;
+  c[1] = a10 * j00;
+  c[2] = a10 * j10 + a11;
+  c[3] = a20 * j00;
+  c[4] = a20 * j10 + a21;
+  c[5] = a20 * j20 + a22 * j22;
+  c[6] = m30 * j00;
+  c[7] = m30 * j10 + m31;
+  c[8] = m30 * j20 + m32 * j22;
+  c[9] = m33;
+  c[10] = m40 * j00;
+  c[11] = m40 * j10 + m41;
+  c[12] = m40 * j20 + m42 * j22;
+  c[13] = m43;
+  c[14] = m44;
+  L.r[0] = yn;
+  L.r[2] = sn;
+  L.t.x = xn;
+  L.t.p[0] = L.r[0] + j00 * d0;
+  L.t.p[1] = L.r[1] + (j10 * d0 + d1);
+  L.t.p[2] = L.r[2] + (j20 * d0 + j22 * d2);
+  return true;
+}
+
+__device__ __forceinline__ bool lin_propagate(Lin& L, float xnew, const KParams& P) {
+  const float dx = xnew - L.t.x;
+  StepJ st;
+  if (!helix_step(L.r, dx, P, st, P.fit_max_snp)) return false;
+  const float d0 = L.t.p[0] - L.r[0], d1 = L.t.p[1] - L.r[1], d2 = L.t.p[2] - L.r[2];
+  const float d3 = L.t.p[3] - L.r[3], d4 = L.t.p[4] - L.r[4];
+  L.r[0] = st.p0;
+  L.r[1] = st.p1;
+  L.r[2] = st.p2;
+  L.t.p[0] = L.r[0] + (d0 + st.f02 * d2 + st.f04 * d4);
+  L.t.p[1] = L.r[1] + (d1 + st.f12 * d2 + st.f13 * d3 + st.f14 * d4);
+  L.t.p[2] = L.r[2] + (d2 + st.f24 * d4);
+  cov_transport(L.t.c, st);
+  add_ms(L.t.c, L.r, dx, P);
+  L.t.x = xnew;
+  return true;
+}
+
+__device__ __forceinline__ bool lin_goto(Lin& L, int sector, float x, const KParams& P) {
+  if (sector != L.sector) {
+    const int half = P.n_sectors / 2;
+    const int ds = ((sector % half) - (L.sector % half) + half) % half;
+    if (ds == 1) {
+      if (!lin_rotate(L, 1, P)) return false;
+    } else if (ds == half - 1) {
+      if (!lin_rotate(L, -1, P)) return false;
+    } else {
+      return false;
+    }
+    L.sector = sector;
+  }
+  return lin_propagate(L, x, P);
+}
+
+__device__ __forceinline__ void inv2(float a00, float a01, float a11, float& i00, float& i01,
+                                     float& i11) {
+  const float idet = 1.0f / (a00 * a11 - a01 * a01);
+  i00 = a11 * idet;
+  i01 = -a01 * idet;
+  i11 = a00 * idet;
+}
+
+struct Interp {
+  float y, z, c00, c01, c11;
+};
+
+__device__ __forceinline__ Interp interpolate(const float* a, const float* b) {
+  float wa00, wa01, wa11, wb00, wb01, wb11;
+  inv2(a[2], a[3], a[4], wa00, wa01, wa11);
+  inv2(b[2], b[3], b[4], wb00, wb01, wb11);
+  Interp I;
+  inv2(wa00 + wb00, wa01 + wb01, wa11 + wb11, I.c00, I.c01, I.c11);
+  const float v0 = (wa00 * a[0] + wa01 * a[1]) + (wb00 * b[0] + wb01 * b[1]);
+  const float v1 = (wa01 * a[0] + wa11 * a[1]) + (wb01 * b[0] + wb11 * b[1]);
+  I.y = I.c00 * v0 + I.c01 * v1;
+  I.z = I.c01 * v0 + I.c11 * v1;
+  return I;
+}
+
+__device__ __forceinline__ float chi2_interp(const Interp& I, float my, float mz,
+                                             const KParams& P) {
+  float w00, w01, w11;
+  inv2(I.c00 + P.sy2, I.c01, I.c11 + P.sz2, w00, w01, w11);
+  const float r0 = my - I.y, r1 = mz - I.z;
+  return r0 * (w00 * r0 + w01 * r1) + r1 * (w01 * r0 + w11 * r1);
+}
+
+// Station list of fit track f: clusters of the chain (rows increasing) plus
+// empty inner rows between two clusters of one sector.
+__device__ int build_stations(FrameDev& F, const KParams& P, int f, int head) {
+  int* SC = F.ft_st_cl + (long)f * kMaxRows;
+  uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
+  const int NR = P.n_rows;
+  int ns = 0, prev = -1;
+  for (int s = head; s >= 0; s = F.st_next[s]) {
+    const int ti = F.st_tl[s];
+    const int nk = F.tl_nkept[ti];
+    const int* K = F.tl_kept + (long)ti * kMaxRows;
+    for (int j = nk - 1; j >= 0; --j) {
+      const int c = K[j];
+      const int rs = F.srow[c];
+      if (prev >= 0 && prev / NR == rs / NR) {
+        for (int r = prev % NR + 1; r < rs % NR && r < P.inner_rows && ns < kMaxRows; ++r) {
+          SC[ns] = -1;
+          SR[ns] = (uint16_t)(rs - rs % NR + r);
+          ++ns;
+        }
+      }
+      if (ns < kMaxRows) {
+        SC[ns] = c;
+        SR[ns] = (uint16_t)rs;
+        ++ns;
+      }
+      prev = rs;
+    }
+  }
+  return ns;
+}
+
+__device__ __forceinline__ float zoff(const float* ie) {
+  return ie[1] - ie[3] * sqrtf(ie[20] * ie[20] + ie[0] * ie[0]);
+}
+
+__global__ void __launch_bounds__(128) k_fit12(FrameDev F, KParams P, MapDev M) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  const int NR = P.n_rows;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const int head = F.ft_head[f];
+    int last = head;
+    while (F.st_next[last] >= 0) last = F.st_next[last];
+    const int ns = build_stations(F, P, f, head);
+    F.ft_nst[f] = ns;
+    F.ft_key[f] = F.st_key[head];
+    const float z0 = zoff(F.st_ie + (long)head * kStateF);
+    F.ft_z0[f] = z0;
+    const int* SC = F.ft_st_cl + (long)f * kMaxRows;
+    const uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
+    float* store = F.ft_store + (long)f * kMaxRows * 5;
+    uint8_t* flag = F.ft_flag + (long)f * kMaxRows;
+    int ok = 1;
+    Lin L;
+    Trk<float> s0;
+    get_state(F.st_oe + (long)last * kStateF, s0);
+    // iteration 1: inward, store predictions
+    lin_start(L, s0, SR[ns - 1] / NR, P);
+    for (int k = ns - 1; k >= 0 && ok; --k) {
+      const int rs = SR[k];
+      if (k != ns - 1 && !lin_goto(L, rs / NR, F.row_x[rs % NR], P)) { ok = 0; break; }
+      float* sv = store + k * 5;
+      sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
+      const int c = SC[k];
+      if (c >= 0) {
+        float my, mz;
+        if (!corrected(M, P, rs / NR, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
+        update(L.t, residual(L.t, my, mz, P));
+      }
+    }
+    // iteration 2: outward, interpolation, flags, inner-row candidates
+    if (ok) {
+      const Trk<float> s1 = L.t;
+      lin_start(L, s1, SR[0] / NR, P);
+      for (int k = 0; k < ns && ok; ++k) {
+        const int rs = SR[k];
+        const int sec = rs / NR, row = rs % NR;
+        if (k != 0 && !lin_goto(L, sec, F.row_x[row], P)) { ok = 0; break; }
+        const float a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
+        const Interp I = interpolate(a, store + k * 5);
+        const bool inner = row < P.inner_rows;
+        const int c = SC[k];
+        flag[k] = 0;
+        if (c >= 0 && !inner) {
+          float my, mz;
+          if (!corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
+          flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
+        }
+        if (inner) {
+          float cy = I.y, cz = I.z;
+          {
+            float D[3];
+            map_eval(M, P, sec, L.t.x, I.y, I.z - z0, D);
+            float sy = D[1], sz = D[2];
+            if (D[0] != 0.0f) {
+              StepJ stp;
+              if (helix_step(L.r, D[0], P, stp, P.fit_max_snp)) {
+                sy = sy - (stp.p0 - L.r[0]);
+                sz = sz - (stp.p1 - L.r[1]);
+              }
+            }
+            cy = I.y - sy;
+            cz = I.z - sz;
+          }
+          const float wy = sqrtf(P.int_chi2 * (I.c00 + P.sy2)) * 1.001f + P.attach_margin;
+          const float wz = sqrtf(P.int_chi2 * (I.c11 + P.sz2)) * 1.001f + P.attach_margin;
+          int* cand = F.ft_cand + ((long)f * kMaxInner + k) * kMaxCand;
+          float* cchi = F.ft_cchi + ((long)f * kMaxInner + k) * kMaxCand;
+          int nc = 0;
+          int cid[kMaxCand];
+          const RowGrid g = F.rows[rs];
+          for_window(F.bin_first, g, cy - wy - 0.01f, cy + wy + 0.01f, cz - wz - 0.01f,
+                     cz + wz + 0.01f, [&](int kk) {
+            const float yk = F.sy[kk], zk = F.sz[kk];
+            if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
+            float my, mz;
+            if (!corrected(M, P, sec, L.t.x, yk, zk, z0, L.r, my, mz)) return;
+            const float c2 = chi2_interp(I, my, mz, P);
+            if (!(c2 < P.int_chi2)) return;
+            const int id = F.sid[kk];
+            // insertion into the sorted top-cand_k list by (chi2, id)
+            int pos = nc;
+            while (pos > 0 && (c2 < cchi[pos - 1] || (c2 == cchi[pos - 1] && id < cid[pos - 1])))
+              --pos;
+            if (pos >= P.cand_k) return;
+            const int lim = nc < P.cand_k ? nc : P.cand_k - 1;
+            for (int j = lim; j > pos; --j) {
+              cand[j] = cand[j - 1];
+              cchi[j] = cchi[j - 1];
+              cid[j] = cid[j - 1];
+            }
+            cand[pos] = kk;
+            cchi[pos] = c2;
+            cid[pos] = id;
+            if (nc < P.cand_k) ++nc;
+          });
+          F.ft_ncand[(long)f * kMaxInner + k] = (uint8_t)nc;
+          F.ft_assigned[(long)f * kMaxInner + k] = -1;
+        }
+        if (c >= 0) {
+          float my, mz;
+          if (!corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
+          update(L.t, residual(L.t, my, mz, P));
+        }
+      }
+      if (ok) put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
+    }
+    F.ft_ok[f] = ok;
+  }
+}
+
+// Second ambiguity solving, round k: bids (chi2, track key) per free cluster.
+__device__ __forceinline__ bool inner_station(const FrameDev& F, const KParams& P, int f, int k) {
+  return k < F.ft_nst[f] && (F.ft_st_rs[(long)f * kMaxRows + k] % P.n_rows) < P.inner_rows;
+}
+
+__global__ void k_amb_bid(FrameDev F, KParams P, int round) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  const long tot = (long)nf * P.inner_rows;
+  for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
+       w += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(w / P.inner_rows), k = (int)(w % P.inner_rows);
+    if (!F.ft_ok[f] || !inner_station(F, P, f, k)) continue;
+    const long sk = (long)f * kMaxInner + k;
+    if (F.ft_assigned[sk] >= 0 || F.ft_ncand[sk] <= round) continue;
+    const int c = F.ft_cand[sk * kMaxCand + round];
+    if (F.taken[c]) continue;
+    atomicMin(&F.bid[c], pack_chi_key(F.ft_cchi[sk * kMaxCand + round], F.ft_key[f]));
+  }
+}
+
+__global__ void k_amb_resolve(FrameDev F, KParams P, int round) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  const long tot = (long)nf * P.inner_rows;
+  for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
+       w += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(w / P.inner_rows), k = (int)(w % P.inner_rows);
+    if (!F.ft_ok[f] || !inner_station(F, P, f, k)) continue;
+    const long sk = (long)f * kMaxInner + k;
+    F.ft_newly[sk] = 0;
+    if (F.ft_assigned[sk] >= 0 || F.ft_ncand[sk] <= round) continue;
+    const int c = F.ft_cand[sk * kMaxCand + round];
+    if (F.taken[c]) continue;
+    if (F.bid[c] == pack_chi_key(F.ft_cchi[sk * kMaxCand + round], F.ft_key[f])) {
+      F.ft_assigned[sk] = c;
+      F.ft_newly[sk] = 1;
+    }
+  }
+}
+
+__global__ void k_amb_mark(FrameDev F, KParams P, int round) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  const long tot = (long)nf * P.inner_rows;
+  for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
+       w += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(w / P.inner_rows), k = (int)(w % P.inner_rows);
+    if (!F.ft_ok[f] || !inner_station(F, P, f, k)) continue;
+    const long sk = (long)f * kMaxInner + k;
+    if (F.ft_ncand[sk] <= round) continue;
+    const int c = F.ft_cand[sk * kMaxCand + round];
+    if (F.ft_newly[sk]) F.taken[c] = 1;
+    F.bid[c] = ~0ull;
+  }
+}
+
+// Iteration 3: inward with the surviving and re-attached clusters, simple cut.
+__global__ void __launch_bounds__(128) k_fit3(FrameDev F, KParams P, MapDev M) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  const int NR = P.n_rows;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    F.ft_n[f] = 0;
+    if (!F.ft_ok[f]) continue;
+    const int ns = F.ft_nst[f];
+    const int* SC = F.ft_st_cl + (long)f * kMaxRows;
+    const uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
+    const uint8_t* flag = F.ft_flag + (long)f * kMaxRows;
+    int* used = F.ft_used + (long)f * kMaxRows;
+    const float z0 = F.ft_z0[f];
+    Trk<float> s2;
+    const float* e2 = F.ft_end2 + (long)f * kStateF;
+    get_state(e2, s2);
+    Lin L;
+    lin_start(L, s2, SR[ns - 1] / NR, P);
+    float chi2 = 0.0f;
+    int n = 0;
+    Trk<float> out = L.t;
+    int out_sec = L.sector;
+    for (int k = ns - 1; k >= 0; --k) {
+      const int rs = SR[k];
+      const int sec = rs / NR, row = rs % NR;
+      if (k != ns - 1 && !lin_goto(L, sec, F.row_x[row], P)) break;
+      const bool inner = row < P.inner_rows;
+      const int c = inner ? F.ft_assigned[(long)f * kMaxInner + k] : (flag[k] ? -1 : SC[k]);
+      if (c < 0) continue;
+      float my, mz;
+      if (!corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) continue;
+      const Resid R = residual(L.t, my, mz, P);
+      if (R.chi2 > P.final_chi2) continue;
+      chi2 = chi2 + R.chi2;
+      update(L.t, R);
+      used[n] = c;
+      ++n;
+      out = L.t;
+      out_sec = L.sector;
+    }
+    F.ft_n[f] = n;
+    F.ft_chi2[f] = chi2;
+    put_state(F.ft_out + (long)f * kStateF, out, out_sec);
+  }
+}
+
+// ------------------------------------------------------------ a11 outputs
+__device__ __forceinline__ int out_flag(const FrameDev& F, const KParams& P, int f, int nf) {
+  return (f < nf && F.ft_ok[f] && F.ft_n[f] >= P.min_hits) ? 1 : 0;
+}
+
+__global__ void k_out_count(FrameDev F, KParams P) {
+  __shared__ int sh[32];
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int fl = F.cnt->err ? 0 : out_flag(F, P, f, nf);
+  const int v = fl ? F.ft_n[f] : 0;
+  int tot_t, tot_r;
+  block_exscan(fl, sh, &tot_t);
+  block_exscan(v, sh, &tot_r);
+  if (threadIdx.x == 0) {
+    F.scan_tmp[2 * blockIdx.x] = tot_t;
+    F.scan_tmp[2 * blockIdx.x + 1] = tot_r;
+  }
+}
+
+// Exclusive scan of the interleaved (tracks, refs) block partials.
+__global__ void k_out_scan(FrameDev F, int nparts) {
+  __shared__ int sh[32];
+  __shared__ int ct, cr;
+  if (threadIdx.x == 0) { ct = 0; cr = 0; }
+  __syncthreads();
+  for (int base = 0; base < nparts; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int vt = i < nparts ? F.scan_tmp[2 * i] : 0;
+    const int vr = i < nparts ? F.scan_tmp[2 * i + 1] : 0;
+    int tt, tr;
+    const int et = block_exscan(vt, sh, &tt);
+    const int er = block_exscan(vr, sh, &tr);
+    if (i < nparts) {
+      F.scan_tmp[2 * i] = ct + et;
+      F.scan_tmp[2 * i + 1] = cr + er;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { ct += tt; cr += tr; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    F.cnt->n_refs = cr;
+    F.cnt->n_out = ct;
+  }
+}
+
+__global__ void k_out_write(FrameDev F, KParams P) {
+  __shared__ int sh[32];
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int fl = F.cnt->err ? 0 : out_flag(F, P, f, nf);
+  const int v = fl ? F.ft_n[f] : 0;
+  int tt, tr;
+  const int et = block_exscan(fl, sh, &tt);
+  const int er = block_exscan(v, sh, &tr);
+  if (!fl) {
+    if (f < nf) F.ft_outidx[f] = -1;
+    return;
+  }
+  const int t = F.scan_tmp[2 * blockIdx.x] + et;
+  const int off = F.scan_tmp[2 * blockIdx.x + 1] + er;
+  F.ft_outidx[f] = t;
+  const float* o = F.ft_out + (long)f * kStateF;
+  for (int i = 0; i < 5; ++i) F.out_par[(long)t * 5 + i] = o[i];
+  for (int i = 0; i < 15; ++i) F.out_cov[(long)t * 15 + i] = o[5 + i];
+  F.out_x[t] = o[20];
+  F.out_sector[t] = __float_as_int(o[21]);
+  F.out_chi2[t] = F.ft_chi2[f];
+  const int n = F.ft_n[f];
+  F.out_ndf[t] = 2 * n - 5;
+  F.out_ncl[t] = n;
+  F.out_key[t] = F.ft_key[f];
+  F.out_offset[t] = off;
+  const int* used = F.ft_used + (long)f * kMaxRows;
+  const bool fits = (long)off + n <= F.cap_refs;
+  if (!fits) atomicOr(&F.cnt->err, kErrCapRefs);
+  for (int j = 0; j < n; ++j) {
+    const int id = F.sid[used[n - 1 - j]];
+    if (fits) F.out_ids[off + j] = id;
+    atomicMin(&F.attach_key[id], F.ft_key[f]);
+  }
+}
+
+__global__ void k_out_attach(FrameDev F, KParams P) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const int t = F.ft_outidx[f];
+    if (t < 0) continue;
+    const int n = F.ft_n[f], key = F.ft_key[f];
+    const int* used = F.ft_used + (long)f * kMaxRows;
+    for (int j = 0; j < n; ++j) {
+      const int id = F.sid[used[j]];
+      if (F.attach_key[id] == key) F.attach[id] = t;
+    }
+    if (t == F.cnt->n_out - 1) F.out_offset[t + 1] = F.cnt->n_refs;
+  }
+}
+
+}  // namespace
+
+int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  const int nb_tl = (int)blocks_for(F.cap_tl, kBlock);
+  k_acc_count<<<nb_tl, kBlock, 0, s>>>(F);
+  k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_tracks);
+  k_acc_write<<<nb_tl, kBlock, 0, s>>>(F);
+  k_sector_refit<<<sms * 16, 128, 0, s>>>(F, P);
+  k_sector_zrange<<<P.n_sectors, 256, 0, s>>>(F, P);
+  k_ie_hist<<<sms * 8, kBlock, 0, s>>>(F);
+  int k = 7;
+  k += scan_exclusive(F.ie_cnt, F.ie_first, (long)P.n_sectors * kMergeBins + 1, F.scan_tmp, s);
+  k_ie_scatter<<<sms * 8, kBlock, 0, s>>>(F);
+  k_merge_best<<<sms * 16, 128, 0, s>>>(F, P);
+  k_merge_link<<<sms * 8, kBlock, 0, s>>>(F);
+  k_head_count<<<nb_tl, kBlock, 0, s>>>(F);
+  k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_merged);
+  k_head_write<<<nb_tl, kBlock, 0, s>>>(F);
+  k_head_check<<<1, 1, 0, s>>>(F);
+  return k + 7;
+}
+
+int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  const MapDev M = F.map;
+  k_fit12<<<sms * 16, 128, 0, s>>>(F, P, M);
+  int k = 1;
+  for (int r = 0; r < P.cand_k; ++r) {
+    k_amb_bid<<<sms * 8, kBlock, 0, s>>>(F, P, r);
+    k_amb_resolve<<<sms * 8, kBlock, 0, s>>>(F, P, r);
+    k_amb_mark<<<sms * 8, kBlock, 0, s>>>(F, P, r);
+    k += 3;
+  }
+  k_fit3<<<sms * 16, 128, 0, s>>>(F, P, M);
+  return k + 1;
+}
+
+int stage_output(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  const int nb = (int)blocks_for(F.cap_ft, kBlock);
+  k_out_count<<<nb, kBlock, 0, s>>>(F, P);
+  k_out_scan<<<1, 1024, 0, s>>>(F, nb);
+  k_out_write<<<nb, kBlock, 0, s>>>(F, P);
+  k_out_attach<<<sms * 8, kBlock, 0, s>>>(F, P);
+  return 4;
+}
+
+}  // namespace TPC_NS
+}  // namespace tpc

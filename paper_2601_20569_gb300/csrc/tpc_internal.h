@@ -48,6 +48,19 @@ enum : int {
   kErrCapCand = 32,
 };
 
+constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
+constexpr int kMergeBins = 2048; // z bins per sector for merge candidates
+constexpr int kMaxInner = 32;    // inner-region rows supported
+
+// Distortion map as seen by the kernels.
+struct MapDev {
+  int on;
+  int nphi, nr, nz;
+  float rmin, zmin, zmax;
+  float phi_scale, r_scale, z_scale;
+  const float* c;
+};
+
 // Small device-side counters read back at the end of a call.
 struct Counters {
   int err;
@@ -59,7 +72,8 @@ struct Counters {
   int n_cand;
   int need_tracklets;
   int need_tracks;
-  int pad[7];
+  int n_out;         // output tracks
+  int pad[6];
 };
 
 // Working set of one frame on the device.
@@ -111,6 +125,68 @@ struct FrameDev {
   int* tl_kept;            // [cap_tl*kMaxRows] outermost first
   int* sec_owner;          // [n] sorted index space: tracklet index or -1
   Counters* cnt;
+
+  // a7 sector tracks (capacity cap_tl)
+  int* st_tl;              // tracklet index of each accepted tracklet
+  int* st_ok;
+  int* st_key;             // input id of the start cluster
+  int* st_sector;
+  int* st_rmin;
+  int* st_rmax;
+  float* st_ie;            // [cap_tl][kStateF] state at the innermost cluster
+  float* st_oe;            // [cap_tl][kStateF] state at the outermost cluster
+  int* st_next;
+  int* st_hasprev;
+  int* st_bestB;
+  float* st_bestchi;
+  unsigned long long* st_bestA;
+  int* ie_cnt;             // [n_sectors*kMergeBins]
+  int* ie_first;           // [n_sectors*kMergeBins + 1]
+  int* ie_slot;            // [cap_tl]
+  int* ie_bin;             // [cap_tl]
+  int* ie_idx;             // [cap_tl] sector tracks sorted by (sector, z bin)
+  float* sec_zlo;          // [n_sectors]
+  float* sec_zinv;         // [n_sectors]
+
+  // a9/a10 fit tracks (capacity cap_ft)
+  long cap_ft;
+  int* ft_head;            // first sector track of the chain
+  int* ft_key;
+  int* ft_ok;
+  int* ft_nst;             // stations
+  float* ft_z0;
+  int* ft_st_cl;           // [cap_ft][kMaxRows] sorted cluster or -1
+  uint16_t* ft_st_rs;      // [cap_ft][kMaxRows] sector*n_rows + row
+  float* ft_store;         // [cap_ft][kMaxRows][5] iteration-1 predictions
+  uint8_t* ft_flag;        // [cap_ft][kMaxRows]
+  float* ft_end2;          // [cap_ft][kStateF] end of iteration 2 (+ sector)
+  uint8_t* ft_ncand;       // [cap_ft][kMaxInner]
+  int* ft_cand;            // [cap_ft][kMaxInner][kMaxCand]
+  float* ft_cchi;          // [cap_ft][kMaxInner][kMaxCand]
+  int* ft_assigned;        // [cap_ft][kMaxInner]
+  uint8_t* ft_newly;       // [cap_ft][kMaxInner]
+  unsigned long long* bid; // [n] per sorted cluster
+  uint8_t* taken;          // [n]
+  int* ft_n;               // iteration 3 results
+  float* ft_chi2;
+  float* ft_out;           // [cap_ft][kStateF]
+  int* ft_used;            // [cap_ft][kMaxRows] sorted clusters, outermost first
+  // a11 outputs
+  int* ft_outidx;          // compaction index of accepted fit tracks
+  float* out_par;
+  float* out_cov;
+  float* out_chi2;
+  float* out_x;
+  int* out_ndf;
+  int* out_sector;
+  int* out_ncl;
+  int* out_offset;
+  int* out_ids;            // [cap_refs] input ids
+  long cap_refs;
+  int* out_key;
+  int* attach;             // [n] input id space
+  int* attach_key;         // [n] input id space
+  MapDev map;              // correction map of this call
 };
 
 }  // namespace tpc

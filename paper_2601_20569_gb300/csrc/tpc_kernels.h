@@ -15,6 +15,9 @@ namespace tpc {
   int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
   int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s);    \
   int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
+  int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s);              \
+  int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s);                \
+  int stage_output(FrameDev& F, const KParams& P, int sms, cudaStream_t s);             \
   int scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s);
 
 namespace strict {

@@ -154,7 +154,17 @@ _DBG_DTYPE = {
     "tl_chi2": np.float32, "tl_x": np.float32, "tl_par": np.float32, "tl_cov": np.float32,
     "tl_hits": np.int32, "tl_kept": np.int32, "tl_acc": np.int32, "tl_nkept": np.int32,
     "owner_key": np.uint64, "sec_owner": np.int32, "counters": np.int32,
+    "st_tl": np.int32, "st_ok": np.int32, "st_key": np.int32, "st_next": np.int32,
+    "st_ie": np.float32, "st_oe": np.float32, "ft_key": np.int32, "ft_ok": np.int32,
+    "ft_nst": np.int32, "ft_st_cl": np.int32, "ft_st_rs": np.uint16, "ft_flag": np.uint8,
+    "ft_ncand": np.uint8, "ft_cand": np.int32, "ft_cchi": np.float32, "ft_assigned": np.int32,
+    "ft_n": np.int32, "out_par": np.float32, "out_cov": np.float32, "out_chi2": np.float32,
+    "out_x": np.float32, "out_ndf": np.int32, "out_sector": np.int32, "out_ncl": np.int32,
+    "out_offset": np.int32, "out_ids": np.int32, "out_key": np.int32, "attach": np.int32,
 }
+STATE_F = 22       # floats per stored state: p[5], c[15], x, sector bits
+MAX_INNER = 32     # inner-row slots per fit track
+MAX_CAND = 8       # candidate slots per inner row
 ROWGRID_DTYPE = np.dtype([("bin0", "<i4"), ("nY", "<i4"), ("nZ", "<i4"), ("cl0", "<i4"),
                           ("ncl", "<i4"), ("y0", "<f4"), ("invDy", "<f4"), ("z0", "<f4"),
                           ("invDz", "<f4")])
@@ -224,6 +234,35 @@ class Tracker:
         """Device tensor view (int32[n_clusters]) of the last call's attachments."""
         out, n = self._last
         return wrap_device(out.attach, (n,), "<i4")
+
+    def result(self) -> dict:
+        """Zero-copy device views of the last call's tracks (valid until the next call)."""
+        out, n = self._last
+        nt, nr = int(out.n_tracks), int(out.n_cluster_refs)
+        f, i = "<f4", "<i4"
+        return {
+            "params": wrap_device(out.params, (nt, 5), f), "cov": wrap_device(out.cov, (nt, 15), f),
+            "chi2": wrap_device(out.chi2, (nt,), f), "x": wrap_device(out.x, (nt,), f),
+            "ndf": wrap_device(out.ndf, (nt,), i), "sector": wrap_device(out.sector, (nt,), i),
+            "n_clusters": wrap_device(out.n_clusters, (nt,), i),
+            "cl_offset": wrap_device(out.cl_offset, (nt + 1,), i),
+            "cl_ids": wrap_device(out.cl_ids, (nr,), i), "key": wrap_device(out.key, (nt,), i),
+            "attach": wrap_device(out.attach, (n,), i),
+        }
+
+    def set_map(self, coeff, r_range=(85.0, 245.0), z_range=(-250.0, 250.0)):
+        """Use a correction map: float32 CUDA tensor [3][n_z][n_r][n_phi] (kept alive here)."""
+        if coeff is None:
+            rc = self.lib.tpc_set_map(self._ctx, None)
+            self._map = None
+        else:
+            nz, nr, nphi = coeff.shape[1:]
+            self._map = coeff
+            m = Map(nphi, nr, nz, r_range[0], r_range[1], z_range[0], z_range[1],
+                    coeff.data_ptr())
+            rc = self.lib.tpc_set_map(self._ctx, ctypes.byref(m))
+        if rc:
+            raise TpcError(rc, self.last_error())
 
     def profile(self, enable: bool = True) -> None:
         rc = self.lib.tpc_profile(self._ctx, int(enable))

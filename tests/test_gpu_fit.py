@@ -1,0 +1,169 @@
+"""GPU merging, distortion-corrected three-iteration fit, Phase II attachment
+and outputs vs the CPU oracle: bit-exact in strict mode; tolerances in fast
+mode (parameters 1e-4 relative, efficiency and fake rate within 0.2 points)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_20569_gb300 import synth
+from paper_2601_20569_gb300.options import TrackerOptions
+from tests.helpers import quality
+
+pytestmark = pytest.mark.gpu
+
+RX = synth.row_x()
+
+
+def run_gpu(f, opts, mode=0, dist_map=None):
+    import torch
+
+    from paper_2601_20569_gb300 import tpc
+
+    tr = tpc.Tracker(RX, opts, mode=mode, cap_clusters=max(f.n, 1024))
+    if dist_map is not None:
+        tr.set_map(torch.as_tensor(dist_map).cuda())
+    tr.track(*tr.to_device(f.y, f.z, f.q, f.row, f.sector))
+    torch.cuda.synchronize()
+    return tr
+
+
+def gpu_tracks(tr):
+    res = {k: v.cpu().numpy() for k, v in tr.result().items()}
+    off, ids = res["cl_offset"], res["cl_ids"]
+    res["hits"] = [ids[off[i]:off[i + 1]] for i in range(len(res["key"]))]
+    return res
+
+
+def ref_tracks(r):
+    off, ids = r["trk_offset"], r["trk_ids"]
+    return [ids[off[i]:off[i + 1]] for i in range(len(r["trk_key"]))]
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+
+
+def compare_full(tr, f, opts, dist_map=None):
+    ref = oracle.track(f.y, f.z, f.row, f.sector, RX, opts, full=True, dist_map=dist_map)
+    sid = tr.debug("sid")
+    # a7: sector tracks, refit states and merge links
+    st_key, st_ok = tr.debug("st_key"), tr.debug("st_ok")
+    ie = tr.debug("st_ie").reshape(-1, 22)
+    oe = tr.debug("st_oe").reshape(-1, 22)
+    nxt = tr.debug("st_next")
+    good = st_ok == 1
+    assert np.array_equal(np.sort(st_key[good]), ref["st_key"])
+    order = np.argsort(st_key[good])
+    gi = np.nonzero(good)[0][order]
+    assert np.array_equal(bits(ie[gi, :5]), bits(ref["st_ie"].reshape(-1, 5)))
+    assert np.array_equal(bits(oe[gi, :5]), bits(ref["st_oe"].reshape(-1, 5)))
+    nkey = np.where(nxt[gi] >= 0, st_key[np.maximum(nxt[gi], 0)], -1)
+    assert np.array_equal(nkey, ref["st_next"])
+    # a10: candidates and assignments per (track, inner row)
+    fk = tr.debug("ft_key")
+    fok = tr.debug("ft_ok")
+    nst = tr.debug("ft_nst")
+    rs = tr.debug("ft_st_rs").reshape(-1, 160)
+    nc = tr.debug("ft_ncand").reshape(-1, 32)
+    cand = tr.debug("ft_cand").reshape(-1, 32, 8)
+    cchi = tr.debug("ft_cchi").reshape(-1, 32, 8)
+    asg = tr.debug("ft_assigned").reshape(-1, 32)
+    K = opts["cand_k"]
+    gpu_c = {}
+    for t in np.nonzero(fok == 1)[0]:
+        for k in range(min(nst[t], 32)):
+            row = rs[t, k] % 152
+            if row >= opts["inner_rows"]:
+                continue
+            ids = sid[cand[t, k, :nc[t, k]]]
+            a = sid[asg[t, k]] if asg[t, k] >= 0 else -1
+            gpu_c[(int(fk[t]), int(row))] = (ids.tolist(), bits(cchi[t, k, :nc[t, k]]).tolist(), a)
+    ref_c = {}
+    rc = ref["cand_ids"].reshape(-1, K)
+    rx = ref["cand_chi2"].reshape(-1, K)
+    for i in range(len(ref["cand_key"])):
+        n = ref["cand_n"][i]
+        ref_c[(int(ref["cand_key"][i]), int(ref["cand_row"][i]))] = (
+            rc[i, :n].tolist(), bits(rx[i, :n]).tolist(), int(ref["cand_assigned"][i]))
+    assert gpu_c == ref_c
+    # a11: output tracks by key, bit-exact
+    g = gpu_tracks(tr)
+    rk = ref["trk_key"]
+    assert np.array_equal(np.sort(g["key"]), rk)
+    o = np.argsort(g["key"])
+    assert np.array_equal(bits(g["params"][o]), bits(ref["trk_param"].reshape(-1, 5)))
+    assert np.array_equal(bits(g["cov"][o]), bits(ref["trk_cov"].reshape(-1, 15)))
+    assert np.array_equal(bits(g["chi2"][o]), bits(ref["trk_chi2"]))
+    assert np.array_equal(bits(g["x"][o]), bits(ref["trk_x"]))
+    assert np.array_equal(g["ndf"][o], ref["trk_ndf"])
+    assert np.array_equal(g["n_clusters"][o], ref["trk_ncl"])
+    assert np.array_equal(g["sector"][o], ref["trk_sector"])
+    rh = ref_tracks(ref)
+    for j, t in enumerate(o):
+        assert np.array_equal(g["hits"][t], rh[j])
+    # attachments: owning track by key
+    ga = g["attach"]
+    gkey = np.where(ga >= 0, g["key"][np.maximum(ga, 0)], -1)
+    ra = ref["attach"]
+    rkey = np.where(ra >= 0, rk[np.maximum(ra, 0)], -1)
+    assert np.array_equal(gkey, rkey)
+    return ref, g
+
+
+@pytest.mark.parametrize("workload,kw", [
+    ("one_sector", {"ms_theta": 0.0}),
+    ("central_event", {"n_primaries": 2500}),
+])
+def test_full_chain_bit_exact(workload, kw):
+    f = synth.generate(workload, **{k: v for k, v in kw.items() if k != "ms_theta"})
+    opts = TrackerOptions().as_dict()
+    opts.update({k: v for k, v in kw.items() if k == "ms_theta"})
+    tr = run_gpu(f, opts)
+    compare_full(tr, f, opts)
+
+
+def test_full_chain_bit_exact_with_distortion_map():
+    """Space-charge distorted clusters corrected with the B-spline map (the
+    differentiation workload's field), strict parity through fit and attachment."""
+    f = synth.generate("central_event", n_primaries=2000, distort=True)
+    opts = TrackerOptions().as_dict()
+    tr = run_gpu(f, opts, dist_map=f.map)
+    compare_full(tr, f, opts, dist_map=f.map)
+
+
+def test_full_central_event_bit_exact():
+    f = synth.generate("central_event")
+    opts = TrackerOptions().as_dict()
+    tr = run_gpu(f, opts)
+    ref, g = compare_full(tr, f, opts)
+    q = quality(f.label, g["hits"], g["attach"])
+    assert q["eff"] > 0.99 and q["fake_rate"] < 0.01, q
+
+
+def test_fast_mode_within_tolerance():
+    """FMA-contracted kernels: efficiency and fake rate within 0.2 points of the
+    strict oracle; tracks with identical clusters agree to 1e-4 relative."""
+    f = synth.generate("central_event", seed=808)
+    opts = TrackerOptions().as_dict()
+    tr = run_gpu(f, opts, mode=1)
+    g = gpu_tracks(tr)
+    ref = oracle.track(f.y, f.z, f.row, f.sector, RX, opts, full=True)
+    rh = ref_tracks(ref)
+    qg = quality(f.label, g["hits"], g["attach"])
+    qr = quality(f.label, rh, ref["attach"])
+    assert abs(qg["eff"] - qr["eff"]) <= 0.002, (qg, qr)
+    assert abs(qg["fake_rate"] - qr["fake_rate"]) <= 0.002, (qg, qr)
+    by_key = {int(k): i for i, k in enumerate(ref["trk_key"])}
+    rpar = ref["trk_param"].reshape(-1, 5)
+    n_same, worst = 0, 0.0
+    for t, k in enumerate(g["key"]):
+        i = by_key.get(int(k))
+        if i is None or not np.array_equal(g["hits"][t], rh[i]):
+            continue
+        n_same += 1
+        d = np.abs(g["params"][t].astype(np.float64) - rpar[i]) / np.maximum(np.abs(rpar[i]), 1.0)
+        worst = max(worst, float(d.max()))
+    assert n_same > 0.9 * len(g["key"])
+    assert worst < 1e-4, worst
