@@ -170,6 +170,36 @@ tpc_status tpc_stage_stats(const tpc_ctx* ctx, int32_t i, const char** name, dou
 /* Kernels launched by the last tracking call. */
 int64_t tpc_last_launches(const tpc_ctx* ctx);
 
+/* Allocation-free cellular-automaton links (this entry point has no
+ * counterpart in the paper; it serves callers that may not allocate device
+ * memory while they run -- code inside an allocator or memory-pool callback,
+ * runtimes that reserve all device memory up front, real-time loops where
+ * allocation is not allowed).
+ *
+ * Computes the same cleaned neighbour links as tpc_track_timeframe in strict
+ * mode (per-row grids, best straight-line pair per cluster, mutual cleaning)
+ * for one frame of at most TPC_NOALLOC_MAX_CLUSTERS clusters, without any
+ * cudaMalloc: its working buffers (about 6.3 MB) are one static device array
+ * that every GPU loading the library holds until the process exits.
+ *   geo, opt: host structs as for tpc_init (opt->bz is the field; capacities
+ *             and mode are ignored).  clusters: device SoA, caller-owned.
+ *   link_up, link_dn: caller-owned device int32[clusters->n], receive the
+ *             input id of the cluster linked on the next / previous pad row
+ *             or -1.
+ * Errors: TPC_ERR_CAPACITY when n exceeds TPC_NOALLOC_MAX_CLUSTERS (nothing
+ * is launched) or the per-row grid would not fit; TPC_ERR_INVALID_INPUT for
+ * NaN/Inf coordinates or out-of-range row/sector; TPC_ERR_INVALID_ARG for bad
+ * pointers or a geometry with more than 36*160 (sector, row) pairs.
+ * The call synchronises the stream.  All calls share the one array, which
+ * keeps the last call's contents; calls whose GPU work overlaps (other
+ * streams or host threads) race on it and must be serialised by the caller.
+ * The first call on a device looks up the array's device address with that
+ * device current; make it before any stream capture. */
+#define TPC_NOALLOC_MAX_CLUSTERS 65536
+tpc_status tpc_links_noalloc(const tpc_geometry* geo, const tpc_options* opt,
+                             const tpc_clusters* clusters, int32_t* link_up, int32_t* link_dn,
+                             void* cuda_stream);
+
 /* Message of the last failed call on this context (never NULL). */
 const char* tpc_last_error(const tpc_ctx* ctx);
 

@@ -81,6 +81,9 @@ bool dalloc(tpc_ctx* c, T** p, long count) {
   return true;
 }
 
+}  // namespace
+
+namespace tpc {
 // Derived constants: computed in double from the physical inputs, rounded once.
 void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>& row_x) {
   const double pi = 3.14159265358979323846;
@@ -121,6 +124,9 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.grid_dy = 2.0f;
   P.grid_occ = 1.0f;
 }
+}  // namespace tpc
+
+namespace {
 
 // Kernel view of a correction map; scales derived in double, rounded once.
 MapDev make_mapdev(const tpc_map& m) {
