@@ -146,6 +146,34 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
 tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_tracks* out,
                                void* cuda_stream, int64_t* needed);
 
+/* Refit of given tracks with fixed cluster lists (the fit of Sec. 2/3 without
+ * the Phase II search) and the data its adjoint needs.  clusters: the frame's
+ * device clusters; in: tracks with cl_offset/cl_ids (innermost first) and
+ * start parameters params/x/sector (e.g. the output of tpc_track_timeframe);
+ * map: correction map (NULL: the context's).  An extended-Kalman pass over
+ * the uncorrected clusters gives the start; iterations 1-3 use the corrected
+ * clusters, linearised about references taken from the previous iteration's
+ * end (Sec. 2: the initial parameters are used for the linearisation).  With
+ * freeze != 0 the references and the discrete decisions (interpolation flags,
+ * the final cut) of the previous refit of the same tracks are reused, making
+ * the chi2 a smooth function of the map (TPC_ERR_STATE otherwise).  out:
+ * chi2, ndf, n_clusters and parameters of every input track (same order);
+ * cl_offset/cl_ids/key/attach are passed through from `in`.  Synchronous.
+ * Not in the paper: the differentiable form serves distortion calibration
+ * (Sec. 2 names the space-charge correction maps as the limiting factor). */
+tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* clusters, const tpc_tracks* in,
+                     const tpc_map* map, int32_t freeze, tpc_tracks* out, void* cuda_stream);
+
+/* Gradient of L = sum_t dL_dchi2[t] * chi2_t of the last tpc_refit with
+ * respect to the map control points, references and decisions held fixed:
+ * a hand-written adjoint sweeping iterations 3, 2, 1 in reverse with the
+ * filter recomputed from checkpoints every 16 stations; per-track work in
+ * FP32, the cross-track reduction in FP64.  dL_dchi2: device float[n_tracks];
+ * dL_dmap: device float[3*n_z*n_r*n_phi] (overwritten).  TPC_ERR_STATE
+ * without a preceding refit that used a map. */
+tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dL_dchi2, float* dL_dmap,
+                              void* cuda_stream);
+
 /* Replace the correction map (device pointer copied by reference; the caller
  * keeps it alive while the context uses it). */
 tpc_status tpc_set_map(tpc_ctx* ctx, const tpc_map* map);

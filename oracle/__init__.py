@@ -242,3 +242,71 @@ def correct(sector, x, y, z, z0, ref, row_x, opts, dist_map):
     if rc:
         return None
     return io[10:13].copy(), io[13:15].copy()
+
+
+class _TracksIn(ctypes.Structure):
+    _fields_ = [("n_tracks", ctypes.c_long), ("offset", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("par", ctypes.c_void_p), ("x", ctypes.c_void_p), ("sector", ctypes.c_void_p)]
+
+
+class _Frozen(ctypes.Structure):
+    _fields_ = [("ref", ctypes.c_void_p), ("flag", ctypes.c_void_p), ("acc", ctypes.c_void_p)]
+
+
+def refit(y, z, row, sector, row_x, opts: dict, tracks: dict, *, dist_map=None, frozen=None,
+          weights=None, mode: str = "f64") -> Result:
+    """Refit tracks with fixed cluster lists (a12).  ``tracks``: offset, ids
+    (innermost first), par [n,5] and x, sector of the start parameters.
+    ``frozen``: the frz_* arrays of a previous call (references and decisions
+    held fixed).  mode: "f32", "f64" or "tape" (FP64 plus the gradient of
+    sum w_t chi2_t with respect to the map coefficients, key "grad")."""
+    lib = _load()
+    if not hasattr(lib, "_refit_typed"):
+        lib.orc_refit.restype = ctypes.c_int
+        lib.orc_refit.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 5 + [
+            ctypes.POINTER(_Opt), ctypes.c_void_p, ctypes.POINTER(_TracksIn), ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        lib._refit_typed = True
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    row = np.ascontiguousarray(row, dtype=np.uint8)
+    sector = np.ascontiguousarray(sector, dtype=np.uint8)
+    rx = np.ascontiguousarray(row_x, dtype=np.float64)
+    off = np.ascontiguousarray(tracks["offset"], dtype=np.int32)
+    ids = np.ascontiguousarray(tracks["ids"], dtype=np.int32)
+    par = np.ascontiguousarray(tracks["par"], dtype=np.float64)
+    tx = np.ascontiguousarray(tracks["x"], dtype=np.float64)
+    ts = np.ascontiguousarray(tracks["sector"], dtype=np.int32)
+    nt = len(off) - 1
+    T = _TracksIn(nt, off.ctypes.data, ids.ctypes.data, par.ctypes.data, tx.ctypes.data,
+                  ts.ctypes.data)
+    w = np.ascontiguousarray(np.ones(nt) if weights is None else weights, dtype=np.float64)
+    keep = []
+    fz = None
+    if frozen is not None:
+        fr = [np.ascontiguousarray(frozen["frz_ref"], dtype=np.float64),
+              np.ascontiguousarray(frozen["frz_flag"], dtype=np.int32),
+              np.ascontiguousarray(frozen["frz_acc"], dtype=np.int32)]
+        keep += fr
+        fz = _Frozen(fr[0].ctypes.data, fr[1].ctypes.data, fr[2].ctypes.data)
+    o = _opt(opts)
+    m, _keep = _map(dist_map)
+    h = ctypes.c_void_p()
+    rc = lib.orc_refit(len(y), y.ctypes.data, z.ctypes.data, row.ctypes.data, sector.ctypes.data,
+                       rx.ctypes.data, ctypes.byref(o), ctypes.byref(m) if m is not None else None,
+                       ctypes.byref(T), ctypes.byref(fz) if fz is not None else None,
+                       w.ctypes.data, {"f32": 0, "f64": 1, "tape": 2}[mode], ctypes.byref(h))
+    if rc:
+        raise ValueError(f"oracle refit rejected the input (code {rc})")
+    try:
+        return _collect(lib, h)
+    finally:
+        lib.orc_free(h)
+
+
+def tracks_for_refit(res: Result, fp64: bool = True) -> dict:
+    """Refit input built from an oracle full-chain result (start = final params)."""
+    n = len(res["trk_key"])
+    return {"offset": res["trk_offset"], "ids": res["trk_ids"],
+            "par": res["trk_param"].reshape(n, 5).astype(np.float64),
+            "x": res["trk_x"].astype(np.float64), "sector": res["trk_sector"]}

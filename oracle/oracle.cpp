@@ -38,6 +38,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 extern "C" {
@@ -79,6 +80,94 @@ struct orc_map {
 
 namespace orc {
 
+// Math entry points of the templated code (overloaded for the FP64 tape type).
+template <class R> inline R o_sqrt(R x) { return std::sqrt(x); }
+template <class R> inline R o_fabs(R x) { return std::fabs(x); }
+template <class R> inline double o_floor(R x) { return std::floor((double)x); }
+template <class R> inline R detach(R x) { return x; }
+
+// ------------------------------------------------ FP64 reverse-mode tape
+// An operator-overloading tape for the refit gradient (independent of the
+// hand-written adjoint of the CUDA library): every arithmetic operation on a
+// Var records its operands and local partial derivatives; a reverse sweep
+// accumulates adjoints.  Values are FP64.
+struct Tape {
+  std::vector<int> a, b;
+  std::vector<double> da, db;
+  int push(int ia, double ga, int ib, double gb) {
+    a.push_back(ia);
+    da.push_back(ga);
+    b.push_back(ib);
+    db.push_back(gb);
+    return (int)a.size() - 1;
+  }
+  void clear() { a.clear(); b.clear(); da.clear(); db.clear(); }
+  // adjoints of every node given the seed on node `out`
+  std::vector<double> reverse(int out) const {
+    std::vector<double> adj(a.size(), 0.0);
+    if (out < 0) return adj;
+    adj[out] = 1.0;
+    for (int i = out; i >= 0; --i) {
+      const double g = adj[i];
+      if (g == 0.0) continue;
+      if (a[i] >= 0) adj[a[i]] += g * da[i];
+      if (b[i] >= 0) adj[b[i]] += g * db[i];
+    }
+    return adj;
+  }
+};
+
+inline Tape& tape() {
+  static Tape t;
+  return t;
+}
+
+struct Var {
+  double v = 0.0;
+  int id = -1;  // -1: constant
+  Var() = default;
+  Var(double x) : v(x), id(-1) {}
+  Var(float x) : v(x), id(-1) {}
+  Var(int x) : v(x), id(-1) {}
+  Var(long x) : v((double)x), id(-1) {}
+  static Var node(double v, int ia, double ga, int ib, double gb) {
+    Var r;
+    r.v = v;
+    r.id = (ia < 0 && ib < 0) ? -1 : tape().push(ia, ga, ib, gb);
+    return r;
+  }
+  static Var leaf(double v) {
+    Var r;
+    r.v = v;
+    r.id = tape().push(-1, 0.0, -1, 0.0);
+    return r;
+  }
+  explicit operator double() const { return v; }
+  explicit operator float() const { return (float)v; }
+  explicit operator int() const { return (int)v; }
+};
+inline Var operator+(Var x, Var y) { return Var::node(x.v + y.v, x.id, 1.0, y.id, 1.0); }
+inline Var operator-(Var x, Var y) { return Var::node(x.v - y.v, x.id, 1.0, y.id, -1.0); }
+inline Var operator*(Var x, Var y) { return Var::node(x.v * y.v, x.id, y.v, y.id, x.v); }
+inline Var operator/(Var x, Var y) {
+  const double q = x.v / y.v;
+  return Var::node(q, x.id, 1.0 / y.v, y.id, -q / y.v);
+}
+inline Var operator-(Var x) { return Var::node(-x.v, x.id, -1.0, -1, 0.0); }
+inline bool operator<(Var x, Var y) { return x.v < y.v; }
+inline bool operator>(Var x, Var y) { return x.v > y.v; }
+inline bool operator<=(Var x, Var y) { return x.v <= y.v; }
+inline bool operator>=(Var x, Var y) { return x.v >= y.v; }
+inline bool operator==(Var x, Var y) { return x.v == y.v; }
+inline bool operator!=(Var x, Var y) { return x.v != y.v; }
+inline Var o_sqrt(Var x) {
+  const double s = std::sqrt(x.v);
+  return Var::node(s, x.id, 0.5 / s, -1, 0.0);
+}
+inline Var o_fabs(Var x) { return Var::node(std::fabs(x.v), x.id, x.v < 0 ? -1.0 : 1.0, -1, 0.0); }
+inline double o_floor(Var x) { return std::floor(x.v); }
+inline Var detach(Var x) { return Var(x.v); }
+
 struct Named {
   std::string dtype;
   std::vector<uint8_t> bytes;
@@ -115,7 +204,7 @@ template <> float asinc<float>(float u) {
 // float (and near 0) the derivative of the series above, 6 terms.
 template <typename Real> Real asinc_deriv(Real u);
 template <> double asinc_deriv<double>(double u) {
-  if (std::fabs(u) > 0.01) return (1.0 / std::sqrt(1.0 - u * u) - std::asin(u) / u) / u;
+  if (o_fabs(u) > 0.01) return (1.0 / o_sqrt(1.0 - u * u) - std::asin(u) / u) / u;
   const double w = u * u;
   return u * (1.0 / 3.0 + w * (3.0 / 10.0 + w * (15.0 / 56.0 + w * (35.0 / 144.0 +
              w * (315.0 / 1408.0 + w * (693.0 / 3328.0))))));
@@ -127,6 +216,15 @@ template <> float asinc_deriv<float>(float u) {
               d6 = (float)(693.0 / 3328.0);
   return u * (d1 + w * (d2 + w * (d3 + w * (d4 + w * (d5 + w * d6)))));
 }
+
+// Tape versions: value and derivative of the FP64 forms.  The derivative of
+// asinc_deriv is not recorded: it only enters Jacobians, which the refit
+// evaluates at its frozen reference (constants on the tape).
+template <> Var asinc<Var>(Var u) {
+  return Var::node(asinc<double>(u.v), u.id, asinc_deriv<double>(u.v), -1, 0.0);
+}
+template <> Var asinc_deriv<Var>(Var u) { return Var(asinc_deriv<double>(u.v)); }
+template <> const char* real_name<Var>() { return "f8"; }
 
 inline int ci(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
 
@@ -172,7 +270,7 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
   // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
   P.merge_zspan = (Real)((double)(o.merge_max_gap + 2) *
                          (((double)row_x[o.n_rows - 1] - (double)row_x[0]) / (double)(o.n_rows - 1)) /
-                         std::sqrt(1.0 - (double)o.max_snp * (double)o.max_snp));
+                         o_sqrt(1.0 - (double)o.max_snp * (double)o.max_snp));
   P.max_miss = o.max_miss; P.min_hits = o.min_hits; P.merge_max_gap = o.merge_max_gap;
   P.inner_rows = o.inner_rows; P.cand_k = o.cand_k; P.brute_force = o.brute_force;
   P.n_rows = o.n_rows; P.n_sectors = o.n_sectors;
@@ -208,17 +306,17 @@ bool helix_step(const Real* p, Real dx, const Params<Real>& P, Step<Real>& st, R
   const Real kappa = p[4] * P.kb;
   const Real s0 = p[2];
   const Real s1 = s0 + kappa * dx;
-  if (!(std::fabs(s1) < lim)) return false;
-  const Real c0 = std::sqrt(Real(1) - s0 * s0);
-  const Real c1 = std::sqrt(Real(1) - s1 * s1);
+  if (!(o_fabs(s1) < lim)) return false;
+  const Real c0 = o_sqrt(Real(1) - s0 * s0);
+  const Real c1 = o_sqrt(Real(1) - s1 * s1);
   const Real N = s0 + s1;
   const Real D = c0 + c1;
   const Real t = N / D;
-  const Real L1 = std::sqrt(Real(1) + t * t);
+  const Real L1 = o_sqrt(Real(1) + t * t);
   const Real chord = dx * L1;
   const Real u = kappa * chord * Real(0.5);
   const Real ds = chord * asinc<Real>(u);
-  const Real B = Real(1) / std::sqrt(Real(1) - u * u);
+  const Real B = Real(1) / o_sqrt(Real(1) - u * u);
   const Real Ap = asinc_deriv<Real>(u);
   st.p[0] = p[0] + dx * t;
   st.p[1] = p[1] + p[3] * ds;
@@ -267,7 +365,7 @@ void cov_transport(Real* c, const Step<Real>& st) {
 // Var(tan lambda) += theta^2 (1 + tan^2 lambda)^2.
 template <typename Real>
 void add_ms(Real* c, const Real* p, Real dx, const Params<Real>& P) {
-  const Real th2 = P.ms_theta2 * (std::fabs(dx) * P.row_pitch_inv);
+  const Real th2 = P.ms_theta2 * (o_fabs(dx) * P.row_pitch_inv);
   const Real a = Real(1) + p[3] * p[3];
   c[5] = c[5] + th2 * (Real(1) - p[2] * p[2]) * a;
   c[9] = c[9] + th2 * a * a;
@@ -337,12 +435,12 @@ bool rotate(Track<Real>& t, int dir, const Params<Real>& P, Real lim) {
   const Real ca = P.rot_c;
   const Real sa = dir > 0 ? P.rot_s : -P.rot_s;
   const Real snp = t.p[2];
-  const Real csp = std::sqrt(Real(1) - snp * snp);
+  const Real csp = o_sqrt(Real(1) - snp * snp);
   const Real xn = t.x * ca + t.p[0] * sa;
   const Real yn = t.p[0] * ca - t.x * sa;
   const Real sn = snp * ca - csp * sa;
   const Real cn = csp * ca + snp * sa;
-  if (!(cn > Real(0)) || !(std::fabs(sn) < lim)) return false;
+  if (!(cn > Real(0)) || !(o_fabs(sn) < lim)) return false;
   const Real j00 = csp / cn;
   const Real j10 = -sa * t.p[3] / cn;
   const Real j20 = -sa * (t.p[4] * P.kb);
@@ -382,16 +480,16 @@ bool seed3(const Real x[3], const Real y[3], const Real z[3], const Params<Real>
   const Real bx = x[2] - x[1], by = y[2] - y[1];
   const Real cx = x[2] - x[0], cy = y[2] - y[0];
   const Real cross = ax * by - ay * bx;
-  const Real la = std::sqrt(ax * ax + ay * ay);
-  const Real lb = std::sqrt(bx * bx + by * by);
-  const Real lc = std::sqrt(cx * cx + cy * cy);
+  const Real la = o_sqrt(ax * ax + ay * ay);
+  const Real lb = o_sqrt(bx * bx + by * by);
+  const Real lc = o_sqrt(cx * cx + cy * cy);
   const Real kappa = Real(2) * cross / (la * lb * lc);
   const Real sh = kappa * lc * Real(0.5);
-  if (!(std::fabs(sh) < Real(1))) return false;
-  const Real ch = std::sqrt(Real(1) - sh * sh);
+  if (!(o_fabs(sh) < Real(1))) return false;
+  const Real ch = o_sqrt(Real(1) - sh * sh);
   const Real snc = cy / lc, csc = cx / lc;
   const Real snp = snc * ch - csc * sh;
-  if (!(std::fabs(snp) < P.max_snp)) return false;
+  if (!(o_fabs(snp) < P.max_snp)) return false;
   const Real arc = lc * asinc<Real>(sh);
   t.x = x[0];
   t.p[0] = y[0];
@@ -457,7 +555,7 @@ void find_links(const Frame<Real>& F, const Params<Real>& P, std::vector<int>& u
     const Real yc = F.y[c], zc = F.z[c];
     std::vector<int> U, D;
     auto inwin = [&](int id) {
-      return std::fabs(F.y[id] - yc) <= P.link_wy && std::fabs(F.z[id] - zc) <= P.link_wz;
+      return o_fabs(F.y[id] - yc) <= P.link_wy && o_fabs(F.z[id] - zc) <= P.link_wz;
     };
     for_row_range(F, P, s, r + 1, zc - P.link_wz - margin, zc + P.link_wz + margin, [&](int id) {
       if (inwin(id)) U.push_back(id);
@@ -521,15 +619,15 @@ struct Tracklet {
 template <typename Real>
 int pick(const Frame<Real>& F, const Params<Real>& P, const Track<Real>& t, int s, int r,
          Resid<Real>* out) {
-  const Real hy = std::sqrt(P.follow_chi2 * (t.c[0] + P.meas_sy2)) * Real(1.001) + Real(0.01);
-  const Real hz = std::sqrt(P.follow_chi2 * (t.c[2] + P.meas_sz2)) * Real(1.001) + Real(0.01);
+  const Real hy = o_sqrt(P.follow_chi2 * (t.c[0] + P.meas_sy2)) * Real(1.001) + Real(0.01);
+  const Real hz = o_sqrt(P.follow_chi2 * (t.c[2] + P.meas_sz2)) * Real(1.001) + Real(0.01);
   int best = -1;
   Resid<Real> bres{};
   const Real ylo = t.p[0] - hy, yhi = t.p[0] + hy;
   const Real margin = Real(0.01);
   for_row_range(F, P, s, r, t.p[1] - hz - margin, t.p[1] + hz + margin, [&](int id) {
     if (!(F.y[id] >= ylo && F.y[id] <= yhi)) return;
-    if (std::fabs(F.z[id] - t.p[1]) > hz) return;
+    if (o_fabs(F.z[id] - t.p[1]) > hz) return;
     const Resid<Real> R = residual(t, F.y[id], F.z[id], P);
     if (!(R.chi2 < P.follow_chi2)) return;
     if (best < 0 || R.chi2 < bres.chi2 || (R.chi2 == bres.chi2 && id < best)) {
@@ -583,7 +681,7 @@ Tracklet<Real> construct(const Frame<Real>& F, const Params<Real>& P, const std:
     int miss = 0;
     for (int r = top + 1; r < P.n_rows; ++r) {
       if (!propagate(t, P.row_x[r], P, P.max_snp)) break;
-      if (std::fabs(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
+      if (o_fabs(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
       Resid<Real> R;
       const int c = pick(F, P, t, s, r, &R);
       if (c >= 0) {
@@ -616,7 +714,7 @@ Tracklet<Real> construct(const Frame<Real>& F, const Params<Real>& P, const std:
   int miss = 0;
   for (int r = top - 1; r >= 0; --r) {
     if (!propagate(t, P.row_x[r], P, P.max_snp)) break;
-    if (std::fabs(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
+    if (o_fabs(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
     if (r >= r0) {
       const int c = have[r];
       if (c < 0) continue;
@@ -722,6 +820,7 @@ struct MapR {
   int nphi = 0, nr = 0, nz = 0;
   Real rmin = 0, zmin = 0, zmax = 0, phi_scale = 0, r_scale = 0, z_scale = 0;
   const float* c = nullptr;
+  const Real* cv = nullptr;  // tape leaves of the coefficients (gradient runs)
 };
 
 template <typename Real>
@@ -740,7 +839,7 @@ void spline_span(Real t, int n, int& i, Real& f) {
   const Real tmax = Real(n - 3);
   if (t < Real(0)) t = Real(0);
   if (t > tmax) t = tmax;
-  i = (int)std::floor(t);
+  i = (int)o_floor(t);
   if (i > n - 4) i = n - 4;
   f = t - Real(i);
 }
@@ -760,9 +859,9 @@ SplinePoint<Real> spline_point(const MapR<Real>& M, const Params<Real>& P, int s
   const int sphi = sector % (P.n_sectors / 2);
   const Real u = (Real(sphi) + Real(0.5)) + Real(0.5) * (y / x) / P.tan_half;
   const Real tp = u * M.phi_scale - Real(0.5);
-  sp.ip = (int)std::floor(tp);
+  sp.ip = (int)o_floor(tp);
   const Real fp = tp - Real(sp.ip);
-  const Real r = std::sqrt(x * x + y * y);
+  const Real r = o_sqrt(x * x + y * y);
   Real fr, fz;
   spline_span((r - M.rmin) * M.r_scale, M.nr, sp.ir, fr);
   Real zc = zdrift;
@@ -791,7 +890,8 @@ void map_eval(const MapR<Real>& M, const Params<Real>& P, int sector, Real x, Re
         for (int e = 0; e < 4; ++e) {
           const long idx = (((long)comp * M.nz + (sp.iz + a)) * M.nr + (sp.ir + b)) * M.nphi +
                            phi_index(sp.ip, e, M.nphi);
-          acc = acc + wzr * sp.wp[e] * (Real)M.c[idx];
+          const Real cval = M.cv ? M.cv[idx] : (Real)M.c[idx];
+          acc = acc + wzr * sp.wp[e] * cval;
         }
       }
     D[comp] = acc;
@@ -840,7 +940,7 @@ Real chi2_5(const Real* d, const Real* c) {
     Real s = c[ci(j, j)];
     for (int k = 0; k < j; ++k) s = s - L[j][k] * L[j][k];
     if (!(s > Real(0))) return Real(-1);
-    L[j][j] = std::sqrt(s);
+    L[j][j] = o_sqrt(s);
     for (int i = j + 1; i < 5; ++i) {
       Real v = c[ci(i, j)];
       for (int k = 0; k < j; ++k) v = v - L[i][k] * L[j][k];
@@ -869,15 +969,15 @@ bool merge_test(const Params<Real>& P, const SectorTrack<Real>& A, const SectorT
   if (ds != 0 && ds != 1 && ds != half - 1) return false;
   const int gap = B.rmin - A.rmax;
   if (gap < 1 || gap > P.merge_max_gap) return false;
-  const Real zwin = P.merge_dz + std::fabs(A.oe.p[3]) * P.merge_zspan;
-  if (!(std::fabs(B.ie.p[1] - A.oe.p[1]) <= zwin)) return false;
+  const Real zwin = P.merge_dz + o_fabs(A.oe.p[3]) * P.merge_zspan;
+  if (!(o_fabs(B.ie.p[1] - A.oe.p[1]) <= zwin)) return false;
   Track<Real> t = A.oe;
   if (ds == 1 && !rotate(t, 1, P, P.fit_max_snp)) return false;
   if (ds == half - 1 && !rotate(t, -1, P, P.fit_max_snp)) return false;
   if (!propagate(t, B.ie.x, P, P.fit_max_snp)) return false;
   Real d[5], c[15];
   for (int i = 0; i < 5; ++i) d[i] = B.ie.p[i] - t.p[i];
-  if (!(std::fabs(d[0]) <= P.merge_dy) || !(std::fabs(d[1]) <= P.merge_dz)) return false;
+  if (!(o_fabs(d[0]) <= P.merge_dy) || !(o_fabs(d[1]) <= P.merge_dz)) return false;
   for (int i = 0; i < 15; ++i) c[i] = t.c[i] + B.ie.c[i];
   chi2 = chi2_5(d, c);
   return chi2 >= Real(0) && chi2 < P.merge_chi2;
@@ -899,7 +999,7 @@ template <typename Real>
 void lin_start(Lin<Real>& L, const Track<Real>& s, int sector, const Params<Real>& P) {
   L.t = s;
   reset_cov(L.t, P);
-  for (int i = 0; i < 5; ++i) L.r[i] = s.p[i];
+  for (int i = 0; i < 5; ++i) L.r[i] = detach(s.p[i]);
   L.sector = sector;
 }
 
@@ -908,12 +1008,12 @@ bool lin_rotate(Lin<Real>& L, int dir, const Params<Real>& P) {
   const Real ca = P.rot_c;
   const Real sa = dir > 0 ? P.rot_s : -P.rot_s;
   const Real snp = L.r[2];
-  const Real csp = std::sqrt(Real(1) - snp * snp);
+  const Real csp = o_sqrt(Real(1) - snp * snp);
   const Real xn = L.t.x * ca + L.r[0] * sa;
   const Real yn = L.r[0] * ca - L.t.x * sa;
   const Real sn = snp * ca - csp * sa;
   const Real cn = csp * ca + snp * sa;
-  if (!(cn > Real(0)) || !(std::fabs(sn) < P.fit_max_snp)) return false;
+  if (!(cn > Real(0)) || !(o_fabs(sn) < P.fit_max_snp)) return false;
   const Real j00 = csp / cn;
   const Real j10 = -sa * L.r[3] / cn;
   const Real j20 = -sa * (L.r[4] * P.kb);
@@ -1140,11 +1240,11 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
         cy = I.y - sy;
         cz = I.z - sz;
       }
-      const Real wy = std::sqrt(P.int_chi2 * (I.c00 + P.meas_sy2)) * Real(1.001) + P.attach_margin;
-      const Real wz = std::sqrt(P.int_chi2 * (I.c11 + P.meas_sz2)) * Real(1.001) + P.attach_margin;
+      const Real wy = o_sqrt(P.int_chi2 * (I.c00 + P.meas_sy2)) * Real(1.001) + P.attach_margin;
+      const Real wz = o_sqrt(P.int_chi2 * (I.c11 + P.meas_sz2)) * Real(1.001) + P.attach_margin;
       std::vector<std::pair<Real, int>> cands;
       for_row_range(F, P, s.sector, s.row, cz - wz - Real(0.01), cz + wz + Real(0.01), [&](int id) {
-        if (!(std::fabs(F.y[id] - cy) <= wy && std::fabs(F.z[id] - cz) <= wz)) return;
+        if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - cz) <= wz)) return;
         Real my, mz;
         if (!corrected(M, P, s.sector, L.t.x, F.y[id], F.z[id], T.z0, L.r, my, mz)) return;
         const Real c2 = chi2_interp(I, my, mz, P);
@@ -1261,6 +1361,126 @@ void second_ambiguity(std::vector<FitTrack<Real>>& FT, const Params<Real>& P) {
   }
 }
 
+// ------------------------------------------- a12 refit with fixed clusters
+// Refit of given tracks whose cluster lists are fixed.  An extended-Kalman
+// pass outward over the uncorrected clusters, from the input parameters,
+// gives the start of iteration 1 (independent of the map); iterations 1-3
+// follow the final fit without the Phase II search.  With `frozen`, the
+// references of iterations 2 and 3 and the discrete decisions (interpolation
+// flags, the iteration-3 cut) are taken from a previous call, so the summed
+// chi2 is a smooth function of the map: the function whose gradient the
+// adjoint computes.
+template <typename Real>
+struct RefitIO {
+  std::vector<Station<Real>> st;  // cluster stations, innermost first
+  Real in_p[5];
+  Real in_x;
+  int in_sector = 0;
+  double ref2[5] = {0, 0, 0, 0, 0}, ref3[5] = {0, 0, 0, 0, 0};
+  std::vector<int> flag, acc;
+  bool ok = false;
+  Real chi2 = Real(0);
+  int n = 0;
+  Track<Real> out{};
+  int out_sector = 0;
+};
+
+template <typename Real>
+void lin_start2(Lin<Real>& L, const Track<Real>& s, const double* ref, int sector,
+                const Params<Real>& P) {
+  L.t = s;
+  reset_cov(L.t, P);
+  for (int i = 0; i < 5; ++i) L.r[i] = Real(ref[i]);
+  L.sector = sector;
+}
+
+template <typename Real>
+void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
+                 RefitIO<Real>& R, bool frozen) {
+  const int ns = (int)R.st.size();
+  R.ok = false;
+  R.chi2 = Real(0);
+  R.n = 0;
+  if (ns < 1) return;
+  const int half = P.n_sectors / 2;
+  const Real z0 = R.in_p[1] - R.in_p[3] * o_sqrt(R.in_x * R.in_x + R.in_p[0] * R.in_p[0]);
+  // start of iteration 1: extended-Kalman pass outward, uncorrected clusters
+  Track<Real> t;
+  for (int i = 0; i < 5; ++i) t.p[i] = R.in_p[i];
+  t.x = R.in_x;
+  reset_cov(t, P);
+  int sec = R.in_sector;
+  for (int k = 0; k < ns; ++k) {
+    const Station<Real>& s = R.st[k];
+    if (s.sector != sec) {
+      const int ds = ((s.sector % half) - (sec % half) + half) % half;
+      if (ds != 1 && ds != half - 1) return;
+      if (!rotate(t, ds == 1 ? 1 : -1, P, P.fit_max_snp)) return;
+      sec = s.sector;
+    }
+    if (!propagate(t, P.row_x[s.row], P, P.fit_max_snp)) return;
+    update(t, residual(t, F.y[s.cl], F.z[s.cl], P));
+  }
+  // iteration 1: inward, predictions stored
+  std::vector<Real> store((size_t)ns * 5);
+  Lin<Real> L;
+  lin_start(L, t, R.st[ns - 1].sector, P);
+  for (int k = ns - 1; k >= 0; --k) {
+    const Station<Real>& s = R.st[k];
+    if (k != ns - 1 && !lin_goto(L, s.sector, P.row_x[s.row], P)) return;
+    Real* sv = &store[(size_t)k * 5];
+    sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
+    Real my, mz;
+    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) return;
+    update(L.t, residual(L.t, my, mz, P));
+  }
+  // iteration 2: outward, interpolation flags
+  {
+    const Track<Real> s1 = L.t;
+    if (!frozen) {
+      for (int i = 0; i < 5; ++i) R.ref2[i] = (double)s1.p[i];
+      R.flag.assign(ns, 0);
+    }
+    lin_start2(L, s1, R.ref2, R.st[0].sector, P);
+  }
+  for (int k = 0; k < ns; ++k) {
+    const Station<Real>& s = R.st[k];
+    if (k != 0 && !lin_goto(L, s.sector, P.row_x[s.row], P)) return;
+    const Real a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
+    const Interp<Real> I = interpolate(a, &store[(size_t)k * 5]);
+    Real my, mz;
+    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) return;
+    if (!frozen) R.flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
+    update(L.t, residual(L.t, my, mz, P));
+  }
+  // iteration 3: inward, simple cut
+  {
+    const Track<Real> s2 = L.t;
+    if (!frozen) {
+      for (int i = 0; i < 5; ++i) R.ref3[i] = (double)s2.p[i];
+      R.acc.assign(ns, 0);
+    }
+    lin_start2(L, s2, R.ref3, R.st[ns - 1].sector, P);
+  }
+  for (int k = ns - 1; k >= 0; --k) {
+    const Station<Real>& s = R.st[k];
+    if (k != ns - 1 && !lin_goto(L, s.sector, P.row_x[s.row], P)) break;
+    if (R.flag[k]) continue;
+    Real my, mz;
+    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) continue;
+    const Resid<Real> Rs = residual(L.t, my, mz, P);
+    const bool accept = frozen ? R.acc[k] != 0 : !(Rs.chi2 > P.final_chi2);
+    if (!frozen) R.acc[k] = accept ? 1 : 0;
+    if (!accept) continue;
+    R.chi2 = R.chi2 + Rs.chi2;
+    update(L.t, Rs);
+    ++R.n;
+    R.out = L.t;
+    R.out_sector = L.sector;
+  }
+  R.ok = R.n > 0;
+}
+
 // ------------------------------------------------------------- driver
 template <typename Real>
 struct SectorResult {
@@ -1347,7 +1567,7 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     T.st = make_stations(F, P, cl, true);
     T.outer = ST[last].oe;
     const Track<Real>& ie = ST[h].ie;
-    T.z0 = ie.p[1] - ie.p[3] * std::sqrt(ie.x * ie.x + ie.p[0] * ie.p[0]);
+    T.z0 = ie.p[1] - ie.p[3] * o_sqrt(ie.x * ie.x + ie.p[0] * ie.p[0]);
     FT.push_back(std::move(T));
   }
   // a9/a10
@@ -1535,6 +1755,120 @@ MapR<Real> make_map(const orc_map* m) {
 struct orc_result {
   orc::Result r;
 };
+
+extern "C" {
+// Tracks handed to the refit: cluster ids innermost first and the start
+// parameters at the innermost cluster (sector frame `sector`, local x).
+struct orc_tracks_in {
+  long n_tracks;
+  const int32_t* offset;  // [n_tracks + 1]
+  const int32_t* ids;
+  const double* par;      // [n_tracks][5]
+  const double* x;
+  const int32_t* sector;
+};
+// Frozen references and decisions of a previous refit (optional).
+struct orc_frozen {
+  const double* ref;   // [n_tracks][10]: iteration-2 and iteration-3 references
+  const int32_t* flag; // per cluster reference
+  const int32_t* acc;  // per cluster reference
+};
+}
+
+// mode: 0 = float, 1 = double, 2 = double with the tape gradient of
+// sum_t w_t chi2_t with respect to the map coefficients.
+template <typename Real>
+static void refit_impl(long n, const float* y, const float* z, const uint8_t* row,
+                       const uint8_t* sector, const double* row_x, const orc_options* opt,
+                       const orc_map* map, const orc_tracks_in* T, const orc_frozen* frz,
+                       const double* w, bool grad, orc::Result& res) {
+  using namespace orc;
+  const auto P = make_params<Real>(*opt, row_x);
+  const auto F = make_frame<Real>(n, y, z, row, sector, P);
+  MapR<Real> M = make_map<Real>(map);
+  const long ncoef = (map && map->coeff) ? 3L * map->n_z * map->n_r * map->n_phi : 0;
+  std::vector<double> gsum(grad ? ncoef : 0, 0.0);
+  const long nt = T->n_tracks;
+  std::vector<double> chi2(nt), par(nt * 5), xs(nt);
+  std::vector<int> nn(nt), ok(nt), sec(nt);
+  std::vector<double> fref(nt * 10, 0.0);
+  std::vector<int> fflag(T->offset[nt], 0), facc(T->offset[nt], 0);
+  for (long t = 0; t < nt; ++t) {
+    RefitIO<Real> R;
+    for (int i = T->offset[t]; i < T->offset[t + 1]; ++i) {
+      const int c = T->ids[i];
+      R.st.push_back({F.sector[c], F.row[c], c});
+    }
+    for (int i = 0; i < 5; ++i) R.in_p[i] = Real(T->par[t * 5 + i]);
+    R.in_x = Real(T->x[t]);
+    R.in_sector = T->sector[t];
+    const bool frozen = frz != nullptr;
+    if (frozen) {
+      for (int i = 0; i < 5; ++i) {
+        R.ref2[i] = frz->ref[t * 10 + i];
+        R.ref3[i] = frz->ref[t * 10 + 5 + i];
+      }
+      R.flag.assign(frz->flag + T->offset[t], frz->flag + T->offset[t + 1]);
+      R.acc.assign(frz->acc + T->offset[t], frz->acc + T->offset[t + 1]);
+    }
+    std::vector<Real> leaves;
+    if (grad && ncoef) {
+      tape().clear();
+      leaves.resize(ncoef);
+      for (long i = 0; i < ncoef; ++i) leaves[i] = Real(Var::leaf((double)map->coeff[i]));
+      M.cv = leaves.data();
+    }
+    refit_track(F, P, M, R, frozen);
+    chi2[t] = (double)R.chi2;
+    nn[t] = R.n;
+    ok[t] = R.ok ? 1 : 0;
+    sec[t] = R.out_sector;
+    xs[t] = (double)R.out.x;
+    for (int i = 0; i < 5; ++i) par[t * 5 + i] = (double)R.out.p[i];
+    for (int i = 0; i < 5; ++i) {
+      fref[t * 10 + i] = R.ref2[i];
+      fref[t * 10 + 5 + i] = R.ref3[i];
+    }
+    for (size_t k = 0; k < R.flag.size(); ++k) fflag[T->offset[t] + k] = R.flag[k];
+    for (size_t k = 0; k < R.acc.size(); ++k) facc[T->offset[t] + k] = R.acc[k];
+    if (grad && ncoef) {
+      if constexpr (std::is_same<Real, Var>::value) {
+        if (R.ok && R.chi2.id >= 0) {
+          const std::vector<double> adj = tape().reverse(R.chi2.id);
+          for (long i = 0; i < ncoef; ++i) gsum[i] += w[t] * adj[leaves[i].id];
+        }
+      }
+      M.cv = nullptr;
+    }
+  }
+  // values of the float mode are exact in double
+  res.put("rf_chi2", chi2, "f8");
+  res.put("rf_n", nn, "i4");
+  res.put("rf_ok", ok, "i4");
+  res.put("rf_par", par, "f8");
+  res.put("rf_x", xs, "f8");
+  res.put("rf_sector", sec, "i4");
+  res.put("frz_ref", fref, "f8");
+  res.put("frz_flag", fflag, "i4");
+  res.put("frz_acc", facc, "i4");
+  if (grad) res.put("grad", gsum, "f8");
+}
+
+extern "C" int orc_refit(long n, const float* y, const float* z, const uint8_t* row,
+                         const uint8_t* sector, const double* row_x, const orc_options* opt,
+                         const orc_map* map, const orc_tracks_in* T, const orc_frozen* frz,
+                         const double* w, int mode, orc_result** out) {
+  if (!opt || !row_x || !out || !T || n < 0) return 1;
+  auto* R = new orc_result();
+  if (mode == 0)
+    refit_impl<float>(n, y, z, row, sector, row_x, opt, map, T, frz, w, false, R->r);
+  else if (mode == 1)
+    refit_impl<double>(n, y, z, row, sector, row_x, opt, map, T, frz, w, false, R->r);
+  else
+    refit_impl<orc::Var>(n, y, z, row, sector, row_x, opt, map, T, frz, w, true, R->r);
+  *out = R;
+  return 0;
+}
 
 template <typename In>
 static int track_impl(long n, const In* y, const In* z, const uint8_t* row, const uint8_t* sector,

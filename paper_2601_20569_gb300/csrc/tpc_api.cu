@@ -53,6 +53,13 @@ struct tpc_ctx {
   tpc_map map{};
   Counters host_cnt{};
   cudaStream_t last_stream = nullptr;
+  // refit and adjoint
+  RefitDev R{};
+  bool refit_alloc = false;
+  bool refit_done = false;
+  long refit_tracks = -1, refit_refs = -1;
+  int* steps3 = nullptr;
+  long gpart_cap = 0;
   std::string err = "ok";
 };
 
@@ -410,6 +417,124 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
   out->cl_ids = F.out_ids;
   out->key = F.out_key;
   out->attach = F.attach;
+  return TPC_OK;
+}
+
+tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* cl, const tpc_tracks* in,
+                     const tpc_map* map, int32_t freeze, tpc_tracks* out, void* cuda_stream) {
+  if (!ctx) return TPC_ERR_INVALID_ARG;
+  if (!cl || !in || !out || in->n_tracks < 0 || in->n_cluster_refs < 0)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "null or negative refit input");
+  if (in->n_tracks > 0 && (!in->cl_offset || !in->cl_ids || !in->params || !in->x ||
+                           !in->sector || !cl->y || !cl->z || !cl->row || !cl->sector))
+    return fail(ctx, TPC_ERR_INVALID_ARG, "null refit array");
+  const tpc_map& mp = map ? *map : ctx->map;
+  if (mp.coeff && (mp.n_phi < 1 || mp.n_r < 4 || mp.n_z < 4 || !(mp.r_max > mp.r_min) ||
+                   !(mp.z_max > mp.z_min)))
+    return fail(ctx, TPC_ERR_INVALID_ARG, "invalid map shape");
+  FrameDev& F = ctx->F;
+  if (in->n_tracks > F.cap_ft || in->n_cluster_refs > F.cap_refs)
+    return fail(ctx, TPC_ERR_CAPACITY, "refit of %lld tracks / %lld clusters exceeds capacity",
+                (long long)in->n_tracks, (long long)in->n_cluster_refs);
+  if (freeze && (!ctx->refit_done || ctx->refit_tracks != in->n_tracks ||
+                 ctx->refit_refs != in->n_cluster_refs))
+    return fail(ctx, TPC_ERR_STATE, "frozen refit needs a previous refit of the same tracks");
+  RefitDev& R = ctx->R;
+  if (!ctx->refit_alloc) {
+    const long T = F.cap_ft, NR = F.cap_refs;
+    bool ok = true;
+    ok &= dalloc(ctx, &R.ref, T * 10);
+    ok &= dalloc(ctx, &R.flag, NR);
+    ok &= dalloc(ctx, &R.acc, NR);
+    ok &= dalloc(ctx, &R.z0, T);
+    ok &= dalloc(ctx, &R.ckpt, T * 3 * kCkptSeg * kCkptF);
+    ok &= dalloc(ctx, &R.store, T * kMaxRows * 5);
+    ok &= dalloc(ctx, &R.ok, T);
+    ok &= dalloc(ctx, &R.nused, T);
+    ok &= dalloc(ctx, &R.chi2, T);
+    ok &= dalloc(ctx, &R.ndf, T);
+    ok &= dalloc(ctx, &R.out_sector, T);
+    ok &= dalloc(ctx, &R.out_par, T * 5);
+    ok &= dalloc(ctx, &R.out_cov, T * 15);
+    ok &= dalloc(ctx, &R.out_x, T);
+    ok &= dalloc(ctx, &R.dD, NR * 3);
+    ok &= dalloc(ctx, &ctx->steps3, T);
+    if (!ok) return fail(ctx, TPC_ERR_OOM, "refit buffers");
+    R.cap = T;
+    R.cap_refs = NR;
+    ctx->refit_alloc = true;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  ctx->last_stream = s;
+  R.n_tracks = in->n_tracks;
+  R.y = cl->y;
+  R.z = cl->z;
+  R.row = cl->row;
+  R.sector = cl->sector;
+  R.offset = in->cl_offset;
+  R.ids = in->cl_ids;
+  R.in_par = in->params;
+  R.in_x = in->x;
+  R.in_sector = in->sector;
+  R.row_x = F.row_x;
+  R.freeze = freeze ? 1 : 0;
+  R.map = make_mapdev(mp);
+  const int k = ctx->opt.mode == 0 ? strict::refit_forward(R, ctx->P, ctx->steps3, ctx->sms, s)
+                                   : fast::refit_forward(R, ctx->P, ctx->steps3, ctx->sms, s);
+  ctx->launches_last = k;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  ctx->refit_done = true;
+  ctx->refit_tracks = in->n_tracks;
+  ctx->refit_refs = in->n_cluster_refs;
+  std::memset(out, 0, sizeof(*out));
+  out->n_tracks = in->n_tracks;
+  out->n_cluster_refs = in->n_cluster_refs;
+  out->params = R.out_par;
+  out->cov = R.out_cov;
+  out->chi2 = R.chi2;
+  out->x = R.out_x;
+  out->ndf = R.ndf;
+  out->sector = R.out_sector;
+  out->n_clusters = R.nused;
+  out->cl_offset = in->cl_offset;
+  out->cl_ids = in->cl_ids;
+  out->key = in->key;
+  out->attach = in->attach;
+  return TPC_OK;
+}
+
+tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* dl_dmap,
+                              void* cuda_stream) {
+  if (!ctx) return TPC_ERR_INVALID_ARG;
+  if (!ctx->refit_done) return fail(ctx, TPC_ERR_STATE, "refit_backward needs a preceding refit");
+  RefitDev& R = ctx->R;
+  if (!R.map.on) return fail(ctx, TPC_ERR_STATE, "the preceding refit used no correction map");
+  if (!dl_dmap || (R.n_tracks > 0 && !dl_dchi2))
+    return fail(ctx, TPC_ERR_INVALID_ARG, "null gradient pointer");
+  const long ncoef = 3L * R.map.nz * R.map.nr * R.map.nphi;
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if ((long)sizeof(double) * ncoef > smem_max)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "map of %ld coefficients exceeds the FP64 block accumulator",
+                ncoef);
+  R.ncoef = (int)ncoef;
+  R.gblocks = ctx->sms;
+  if ((long)R.gblocks * ncoef > ctx->gpart_cap) {
+    if (!dalloc(ctx, &R.gpart, (long)R.gblocks * ncoef)) return fail(ctx, TPC_ERR_OOM, "gradient partials");
+    ctx->gpart_cap = (long)R.gblocks * ncoef;
+  }
+  R.dl_dchi2 = dl_dchi2;
+  R.dl_dmap = dl_dmap;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  ctx->last_stream = s;
+  const int k = ctx->opt.mode == 0
+                    ? strict::refit_backward(R, ctx->P, ctx->steps3, ctx->sms, s)
+                    : fast::refit_backward(R, ctx->P, ctx->steps3, ctx->sms, s);
+  ctx->launches_last = k;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
   return TPC_OK;
 }
 

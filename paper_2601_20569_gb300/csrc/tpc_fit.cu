@@ -405,7 +405,8 @@ __device__ __forceinline__ void lin_start(Lin& L, const Trk<float>& s, int secto
   L.sector = sector;
 }
 
-__device__ __forceinline__ bool lin_rotate(Lin& L, int dir, const KParams& P) {
+__device__ __forceinline__ bool lin_rotate(Lin& L, int dir, const KParams& P,
+                                           float* jrec = nullptr) {
   const float ca = P.rot_c;
   const float sa = dir > 0 ? P.rot_s : -P.rot_s;
   const float snp = L.r[2];
@@ -449,13 +450,21 @@ __device__ __forceinline__ bool lin_rotate(Lin& L, int dir, const KParams& P) {
   L.t.p[0] = L.r[0] + j00 * d0;
   L.t.p[1] = L.r[1] + (j10 * d0 + d1);
   L.t.p[2] = L.r[2] + (j20 * d0 + j22 * d2);
+  if (jrec) {
+    jrec[0] = j00;
+    jrec[1] = j10;
+    jrec[2] = j20;
+    jrec[3] = j22;
+  }
   return true;
 }
 
-__device__ __forceinline__ bool lin_propagate(Lin& L, float xnew, const KParams& P) {
+__device__ __forceinline__ bool lin_propagate(Lin& L, float xnew, const KParams& P,
+                                              StepJ* frec = nullptr) {
   const float dx = xnew - L.t.x;
   StepJ st;
   if (!helix_step(L.r, dx, P, st, P.fit_max_snp)) return false;
+  if (frec) *frec = st;
   const float d0 = L.t.p[0] - L.r[0], d1 = L.t.p[1] - L.r[1], d2 = L.t.p[2] - L.r[2];
   const float d3 = L.t.p[3] - L.r[3], d4 = L.t.p[4] - L.r[4];
   L.r[0] = st.p0;
@@ -470,20 +479,27 @@ __device__ __forceinline__ bool lin_propagate(Lin& L, float xnew, const KParams&
   return true;
 }
 
-__device__ __forceinline__ bool lin_goto(Lin& L, int sector, float x, const KParams& P) {
+// Station change: rotation (when the sector changes) and propagation.  The
+// optional records receive the rotation Jacobian (jrec, *rotated set) and the
+// propagation Jacobian (frec) for the adjoint.
+__device__ __forceinline__ bool lin_goto(Lin& L, int sector, float x, const KParams& P,
+                                         float* jrec = nullptr, bool* rotated = nullptr,
+                                         StepJ* frec = nullptr) {
+  if (rotated) *rotated = false;
   if (sector != L.sector) {
     const int half = P.n_sectors / 2;
     const int ds = ((sector % half) - (L.sector % half) + half) % half;
     if (ds == 1) {
-      if (!lin_rotate(L, 1, P)) return false;
+      if (!lin_rotate(L, 1, P, jrec)) return false;
     } else if (ds == half - 1) {
-      if (!lin_rotate(L, -1, P)) return false;
+      if (!lin_rotate(L, -1, P, jrec)) return false;
     } else {
       return false;
     }
+    if (rotated) *rotated = true;
     L.sector = sector;
   }
-  return lin_propagate(L, x, P);
+  return lin_propagate(L, x, P, frec);
 }
 
 __device__ __forceinline__ void inv2(float a00, float a01, float a11, float& i00, float& i01,
@@ -875,7 +891,341 @@ __global__ void k_out_attach(FrameDev F, KParams P) {
   }
 }
 
+// ------------------------------------------- a12 refit with fixed clusters
+__device__ __forceinline__ void save_ckpt(float* d, const Lin& L) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) d[i] = L.t.p[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) d[5 + i] = L.t.c[i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) d[20 + i] = L.r[i];
+  d[25] = L.t.x;
+  d[26] = __int_as_float(L.sector);
+}
+
+__device__ __forceinline__ void load_ckpt(const float* d, Lin& L) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) L.t.p[i] = d[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) L.t.c[i] = d[5 + i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) L.r[i] = d[20 + i];
+  L.t.x = d[25];
+  L.sector = __float_as_int(d[26]);
+}
+
+__device__ __forceinline__ void lin_start2(Lin& L, const Trk<float>& s, const float* ref,
+                                           int sector, const KParams& P) {
+  L.t = s;
+  reset_cov(L.t.c, P);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) L.r[i] = ref[i];
+  L.sector = sector;
+}
+
+// Forward refit (see the oracle's definition): extended-Kalman start pass on
+// uncorrected clusters, then iterations 1-3 with checkpoints of the filter
+// (state, covariance, reference) every kCkptStride stations.
+__global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps3) {
+  const MapDev M = R.map;
+  const int half = P.n_sectors / 2;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < R.n_tracks;
+       t += gridDim.x * blockDim.x) {
+    R.ok[t] = 0;
+    R.nused[t] = 0;
+    R.chi2[t] = 0.0f;
+    steps3[t] = 0;
+    const int o0 = R.offset[t], ns = R.offset[t + 1] - o0;
+    if (ns < 1 || ns > kMaxRows) continue;
+    const int* ids = R.ids + o0;
+    float ip[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ip[i] = R.in_par[(long)t * 5 + i];
+    const float inx = R.in_x[t];
+    const float z0 = ip[1] - ip[3] * sqrtf(inx * inx + ip[0] * ip[0]);
+    R.z0[t] = z0;
+    Trk<float> t0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t0.p[i] = ip[i];
+    t0.x = inx;
+    reset_cov(t0.c, P);
+    int sec = R.in_sector[t];
+    bool ok = true;
+    for (int k = 0; k < ns && ok; ++k) {
+      const int c = ids[k];
+      const int s = R.sector[c];
+      if (s != sec) {
+        const int ds = ((s % half) - (sec % half) + half) % half;
+        if ((ds != 1 && ds != half - 1) || !rotate(t0, ds == 1 ? 1 : -1, P, P.fit_max_snp)) {
+          ok = false;
+          break;
+        }
+        sec = s;
+      }
+      if (!propagate(t0, R.row_x[R.row[c]], P, P.fit_max_snp)) { ok = false; break; }
+      update(t0, residual(t0, R.y[c], R.z[c], P));
+    }
+    if (!ok) continue;
+    float* store = R.store + (long)t * kMaxRows * 5;
+    float* ck = R.ckpt + (long)t * 3 * kCkptSeg * kCkptF;
+    float* ref = R.ref + (long)t * 10;
+    uint8_t* flag = R.flag + o0;
+    uint8_t* acc = R.acc + o0;
+    Lin L;
+    lin_start(L, t0, R.sector[ids[ns - 1]], P);
+    for (int j = 0; j < ns && ok; ++j) {  // iteration 1: inward
+      const int k = ns - 1 - j, c = ids[k];
+      if (j % kCkptStride == 0) save_ckpt(ck + (0 * kCkptSeg + j / kCkptStride) * kCkptF, L);
+      if (j != 0 && !lin_goto(L, R.sector[c], R.row_x[R.row[c]], P)) { ok = false; break; }
+      float* sv = store + k * 5;
+      sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
+      float my, mz;
+      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) { ok = false; break; }
+      update(L.t, residual(L.t, my, mz, P));
+    }
+    if (!ok) continue;
+    {
+      const Trk<float> s1 = L.t;
+      if (!R.freeze)
+        for (int i = 0; i < 5; ++i) ref[i] = s1.p[i];
+      lin_start2(L, s1, ref, R.sector[ids[0]], P);
+    }
+    for (int j = 0; j < ns && ok; ++j) {  // iteration 2: outward
+      const int k = j, c = ids[k];
+      if (j % kCkptStride == 0) save_ckpt(ck + (1 * kCkptSeg + j / kCkptStride) * kCkptF, L);
+      if (j != 0 && !lin_goto(L, R.sector[c], R.row_x[R.row[c]], P)) { ok = false; break; }
+      const float a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
+      const Interp I = interpolate(a, store + k * 5);
+      float my, mz;
+      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) { ok = false; break; }
+      if (!R.freeze) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
+      update(L.t, residual(L.t, my, mz, P));
+    }
+    if (!ok) continue;
+    {
+      const Trk<float> s2 = L.t;
+      if (!R.freeze)
+        for (int i = 0; i < 5; ++i) ref[5 + i] = s2.p[i];
+      lin_start2(L, s2, ref + 5, R.sector[ids[ns - 1]], P);
+    }
+    float chi2 = 0.0f;
+    int n = 0;
+    Trk<float> out = L.t;
+    int out_sec = L.sector;
+    int j = 0;
+    for (; j < ns; ++j) {  // iteration 3: inward
+      const int k = ns - 1 - j, c = ids[k];
+      if (j % kCkptStride == 0) save_ckpt(ck + (2 * kCkptSeg + j / kCkptStride) * kCkptF, L);
+      if (j != 0 && !lin_goto(L, R.sector[c], R.row_x[R.row[c]], P)) break;
+      if (flag[k]) continue;
+      float my, mz;
+      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) continue;
+      const Resid Rs = residual(L.t, my, mz, P);
+      const bool accept = R.freeze ? acc[k] != 0 : !(Rs.chi2 > P.final_chi2);
+      if (!R.freeze) acc[k] = accept ? 1 : 0;
+      if (!accept) continue;
+      chi2 = chi2 + Rs.chi2;
+      update(L.t, Rs);
+      ++n;
+      out = L.t;
+      out_sec = L.sector;
+    }
+    steps3[t] = j;
+    R.ok[t] = n > 0 ? 1 : 0;
+    R.nused[t] = n;
+    R.chi2[t] = chi2;
+    R.ndf[t] = 2 * n - 5;
+    R.out_sector[t] = out_sec;
+    R.out_x[t] = out.x;
+    for (int i = 0; i < 5; ++i) R.out_par[(long)t * 5 + i] = out.p[i];
+    for (int i = 0; i < 15; ++i) R.out_cov[(long)t * 15 + i] = out.c[i];
+  }
+}
+
+// One recomputed forward step of the refit, kept for the reverse sweep.
+struct StepRec {
+  float j00, j10, j20, j22;
+  StepJ F;
+  float k0[5], k1[5];
+  float w00, w01, w11, r0, r1;
+  float gy, gz;  // d(measurement)/d(Dx)
+  int bits;      // 1 rotated, 2 propagated, 4 updated, 8 counted in chi2
+};
+
+// Replays forward step j of iteration `it` (0: first inward, 1: outward,
+// 2: last inward) from the current filter state, with identical arithmetic,
+// recording the Jacobians, gain and residual.  Returns false when the
+// forward pass stopped at this step.
+__device__ __forceinline__ bool replay_step(const RefitDev& R, const KParams& P, int t, int it,
+                                            int j, int ns, const int* ids, float z0, Lin& L,
+                                            StepRec& S) {
+  const int k = it == 1 ? j : ns - 1 - j;
+  const int c = ids[k];
+  S.bits = 0;
+  if (j != 0) {
+    bool rot = false;
+    float jr[4];
+    if (!lin_goto(L, R.sector[c], R.row_x[R.row[c]], P, jr, &rot, &S.F)) return false;
+    S.bits |= 2;
+    if (rot) {
+      S.bits |= 1;
+      S.j00 = jr[0]; S.j10 = jr[1]; S.j20 = jr[2]; S.j22 = jr[3];
+    }
+  }
+  if (it == 2 && R.flag[R.offset[t] + k]) return true;
+  // measurement with its derivative by the x displacement
+  float D[3];
+  map_eval(R.map, P, R.sector[c], L.t.x, R.y[c], R.z[c] - z0, D);
+  float my = R.y[c] + D[1], mz = R.z[c] + D[2];
+  float snp1 = L.r[2];
+  if (D[0] != 0.0f) {
+    StepJ st;
+    if (!helix_step(L.r, D[0], P, st, P.fit_max_snp)) return it == 2;  // it 2: skipped cluster
+    my = my - (st.p0 - L.r[0]);
+    mz = mz - (st.p1 - L.r[1]);
+    snp1 = st.p2;
+  }
+  const float csp1 = sqrtf(1.0f - snp1 * snp1);
+  S.gy = -snp1 / csp1;
+  S.gz = -L.r[3] / csp1;
+  const Resid Rs = residual(L.t, my, mz, P);
+  if (it == 2) {
+    if (!R.acc[R.offset[t] + k]) return true;
+    S.bits |= 8;
+  }
+  const float h0[5] = {L.t.c[0], L.t.c[1], L.t.c[3], L.t.c[6], L.t.c[10]};
+  const float h1[5] = {L.t.c[1], L.t.c[2], L.t.c[4], L.t.c[7], L.t.c[11]};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    S.k0[i] = h0[i] * Rs.w00 + h1[i] * Rs.w01;
+    S.k1[i] = h0[i] * Rs.w01 + h1[i] * Rs.w11;
+  }
+  S.w00 = Rs.w00; S.w01 = Rs.w01; S.w11 = Rs.w11; S.r0 = Rs.r0; S.r1 = Rs.r1;
+  S.bits |= 4;
+  update(L.t, Rs);
+  return true;
+}
+
+// Adjoint of the refit: d(sum_t w_t chi2_t)/d(map) with references and
+// decisions held fixed.  One thread per track: reverse sweep over iterations
+// 3, 2, 1, each segment of kCkptStride stations recomputed forward from its
+// checkpoint; per-cluster gradients of the (dx, dy, dz) correction are then
+// scattered through the 64 spline weights into an FP64 accumulator of the
+// block (cross-track reduction in FP64), written per block and summed in a
+// fixed order by k_grad_reduce.
+__global__ void __launch_bounds__(256) k_refit_adjoint(RefitDev R, KParams P,
+                                                       const int* steps3) {
+  extern __shared__ double gacc[];
+  for (int i = threadIdx.x; i < R.ncoef; i += blockDim.x) gacc[i] = 0.0;
+  __syncthreads();
+  const MapDev M = R.map;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < R.n_tracks;
+       t += gridDim.x * blockDim.x) {
+    if (!R.ok[t]) continue;
+    const float w = R.dl_dchi2[t];
+    const int o0 = R.offset[t], ns = R.offset[t + 1] - o0;
+    const int* ids = R.ids + o0;
+    const float z0 = R.z0[t];
+    float* dD = R.dD + (long)o0 * 3;
+    for (int i = 0; i < 3 * ns; ++i) dD[i] = 0.0f;
+    const float* ck = R.ckpt + (long)t * 3 * kCkptSeg * kCkptF;
+    float lam[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int it = 2; it >= 0; --it) {
+      const int nsteps = it == 2 ? steps3[t] : ns;
+      const int nseg = (nsteps + kCkptStride - 1) / kCkptStride;
+      for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int j0 = sg * kCkptStride, j1 = min(nsteps, j0 + kCkptStride);
+        StepRec rec[kCkptStride];
+        Lin L;
+        load_ckpt(ck + (it * kCkptSeg + sg) * kCkptF, L);
+        for (int j = j0; j < j1; ++j) replay_step(R, P, t, it, j, ns, ids, z0, L, rec[j - j0]);
+        for (int j = j1 - 1; j >= j0; --j) {
+          const StepRec& S = rec[j - j0];
+          const int k = it == 1 ? j : ns - 1 - j;
+          if (S.bits & 4) {
+            float g0 = 0.0f, g1 = 0.0f;
+            if (S.bits & 8) {
+              g0 = 2.0f * w * (S.w00 * S.r0 + S.w01 * S.r1);
+              g1 = 2.0f * w * (S.w01 * S.r0 + S.w11 * S.r1);
+            }
+            float a0 = g0, a1 = g1;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              a0 += S.k0[i] * lam[i];
+              a1 += S.k1[i] * lam[i];
+            }
+            dD[k * 3 + 0] += S.gy * a0 + S.gz * a1;
+            dD[k * 3 + 1] += a0;
+            dD[k * 3 + 2] += a1;
+            lam[0] -= a0;
+            lam[1] -= a1;
+          }
+          if (S.bits & 2) {
+            const float l0 = lam[0], l1 = lam[1], l2 = lam[2];
+            lam[2] = l2 + S.F.f02 * l0 + S.F.f12 * l1;
+            lam[3] = lam[3] + S.F.f13 * l1;
+            lam[4] = lam[4] + S.F.f04 * l0 + S.F.f14 * l1 + S.F.f24 * l2;
+          }
+          if (S.bits & 1) {
+            const float l0 = lam[0], l1 = lam[1], l2 = lam[2];
+            lam[0] = S.j00 * l0 + S.j10 * l1 + S.j20 * l2;
+            lam[2] = S.j22 * l2;
+          }
+        }
+      }
+    }
+    // scatter d(loss)/d(correction) through the spline weights
+    if (M.on) {
+      for (int k = 0; k < ns; ++k) {
+        const int c = ids[k];
+        const SplinePt sp =
+            spline_point(M, P, R.sector[c], R.row_x[R.row[c]], R.y[c], R.z[c] - z0);
+        int pidx[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pidx[e] = phi_index(sp.ip, e, M.nphi);
+        for (int comp = 0; comp < 3; ++comp) {
+          const double g = (double)dD[k * 3 + comp];
+          if (g == 0.0) continue;
+          for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+              const float wzr = sp.wz[a] * sp.wr[b];
+              const long base = (((long)comp * M.nz + (sp.iz + a)) * M.nr + (sp.ir + b)) * M.nphi;
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                atomicAdd(&gacc[base + pidx[e]], (double)(wzr * sp.wp[e]) * g);
+            }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  double* part = R.gpart + (long)blockIdx.x * R.ncoef;
+  for (int i = threadIdx.x; i < R.ncoef; i += blockDim.x) part[i] = gacc[i];
+}
+
+__global__ void k_grad_reduce(RefitDev R) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R.ncoef; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < R.gblocks; ++b) s += R.gpart[(long)b * R.ncoef + i];
+    R.dl_dmap[i] = (float)s;
+  }
+}
+
 }  // namespace
+
+int refit_forward(RefitDev& R, const KParams& P, int* steps3, int sms, cudaStream_t s) {
+  if (R.n_tracks > 0) k_refit<<<sms * 16, 128, 0, s>>>(R, P, steps3);
+  return R.n_tracks > 0 ? 1 : 0;
+}
+
+int refit_backward(RefitDev& R, const KParams& P, const int* steps3, int sms, cudaStream_t s) {
+  (void)sms;
+  const size_t smem = sizeof(double) * (size_t)R.ncoef;
+  cudaFuncSetAttribute(k_refit_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_refit_adjoint<<<R.gblocks, 256, smem, s>>>(R, P, steps3);
+  k_grad_reduce<<<(R.ncoef + 255) / 256, 256, 0, s>>>(R);
+  return 2;
+}
 
 int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const int nb_tl = (int)blocks_for(F.cap_tl, kBlock);

@@ -189,4 +189,51 @@ struct FrameDev {
   MapDev map;              // correction map of this call
 };
 
+constexpr int kCkptStride = 16;                        // stations per checkpoint segment
+constexpr int kCkptSeg = (kMaxRows + kCkptStride - 1) / kCkptStride;
+constexpr int kCkptF = 27;                             // p[5], c[15], ref[5], x, sector
+
+// Refit of given tracks (fixed clusters) and its adjoint.
+struct RefitDev {
+  long n_tracks;
+  long cap;                // track capacity
+  long cap_refs;
+  // inputs (device, caller-owned)
+  const float* y;
+  const float* z;
+  const uint8_t* row;
+  const uint8_t* sector;
+  const int* offset;       // [n_tracks + 1]
+  const int* ids;          // innermost first
+  const float* in_par;     // [n_tracks][5]
+  const float* in_x;
+  const int* in_sector;
+  const float* row_x;
+  int freeze;
+  // state kept for freezing and for the adjoint
+  float* ref;              // [cap][10]
+  uint8_t* flag;           // [cap_refs]
+  uint8_t* acc;            // [cap_refs]
+  float* z0;               // [cap]
+  float* ckpt;             // [cap][3][kCkptSeg][kCkptF]
+  float* store;            // [cap][kMaxRows][5] iteration-1 predictions
+  int* ok;
+  int* nused;
+  float* chi2;
+  float* out;              // [cap][kStateF]
+  int* ndf;
+  int* out_sector;
+  float* out_par;          // [cap][5]
+  float* out_cov;          // [cap][15]
+  float* out_x;
+  // adjoint
+  const float* dl_dchi2;   // [n_tracks]
+  float* dD;               // [cap_refs][3]
+  double* gpart;           // [blocks][ncoef]
+  float* dl_dmap;          // [ncoef]
+  int ncoef;
+  int gblocks;
+  MapDev map;
+};
+
 }  // namespace tpc

@@ -18,6 +18,9 @@ namespace tpc {
   int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s);              \
   int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s);                \
   int stage_output(FrameDev& F, const KParams& P, int sms, cudaStream_t s);             \
+  int refit_forward(RefitDev& R, const KParams& P, int* steps3, int sms, cudaStream_t s); \
+  int refit_backward(RefitDev& R, const KParams& P, const int* steps3, int sms,          \
+                     cudaStream_t s);                                                    \
   int scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s);
 
 namespace strict {

@@ -250,6 +250,74 @@ class Tracker:
             "attach": wrap_device(out.attach, (n,), i),
         }
 
+    def refit(self, clusters, tracks: dict, coeff=None, *, freeze: bool = False,
+              r_range=(85.0, 245.0), z_range=(-250.0, 250.0), stream=None) -> dict:
+        """Refit tracks with fixed clusters (tpc_refit).  clusters: (y, z, q, row,
+        sector) device tensors; tracks: dict of device tensors cl_offset, cl_ids,
+        params [n,5], x, sector (e.g. ``result()`` of track()); coeff: map tensor or
+        None for the context's map.  Returns zero-copy views of chi2, ndf,
+        n_clusters, params, cov, x, sector (valid until the next call)."""
+        import torch
+
+        lib = self.lib
+        if not getattr(lib, "_refit_typed", False):
+            P = ctypes.POINTER
+            lib.tpc_refit.argtypes = [ctypes.c_void_p, P(Clusters), P(Tracks), P(Map),
+                                      ctypes.c_int32, P(Tracks), ctypes.c_void_p]
+            lib.tpc_refit.restype = ctypes.c_int
+            lib.tpc_refit_backward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p]
+            lib.tpc_refit_backward.restype = ctypes.c_int
+            lib._refit_typed = True
+        y, z, q, row, sector = clusters
+        cl = Clusters(int(y.shape[0]), y.data_ptr(), z.data_ptr(),
+                      q.data_ptr() if q is not None else None, row.data_ptr(), sector.data_ptr())
+        keep = {k: v.contiguous() for k, v in tracks.items() if hasattr(v, "data_ptr")}
+        nt = int(keep["params"].shape[0])
+        tin = Tracks()
+        tin.n_tracks = nt
+        tin.n_cluster_refs = int(keep["cl_ids"].shape[0])
+        tin.params = keep["params"].data_ptr()
+        tin.x = keep["x"].data_ptr()
+        tin.sector = keep["sector"].data_ptr()
+        tin.cl_offset = keep["cl_offset"].data_ptr()
+        tin.cl_ids = keep["cl_ids"].data_ptr()
+        mp = None
+        if coeff is not None:
+            nz, nr, nphi = coeff.shape[1:]
+            mp = Map(nphi, nr, nz, r_range[0], r_range[1], z_range[0], z_range[1],
+                     coeff.data_ptr())
+        out = Tracks()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = lib.tpc_refit(self._ctx, ctypes.byref(cl), ctypes.byref(tin),
+                           ctypes.byref(mp) if mp is not None else None, int(bool(freeze)),
+                           ctypes.byref(out), ctypes.c_void_p(s.cuda_stream))
+        if rc:
+            raise TpcError(rc, self.last_error())
+        self._refit_keep = (keep, coeff, clusters)
+        self._refit_map_shape = tuple(coeff.shape) if coeff is not None else None
+        f, i = "<f4", "<i4"
+        return {"chi2": wrap_device(out.chi2, (nt,), f), "ndf": wrap_device(out.ndf, (nt,), i),
+                "n_clusters": wrap_device(out.n_clusters, (nt,), i),
+                "params": wrap_device(out.params, (nt, 5), f),
+                "cov": wrap_device(out.cov, (nt, 15), f), "x": wrap_device(out.x, (nt,), f),
+                "sector": wrap_device(out.sector, (nt,), i)}
+
+    def refit_backward(self, dl_dchi2, map_shape=None, stream=None):
+        """d(sum dl_dchi2 * chi2)/d(map) of the last refit (tpc_refit_backward)."""
+        import torch
+
+        shape = map_shape or self._refit_map_shape
+        g = torch.empty(shape, dtype=torch.float32, device="cuda")
+        d = dl_dchi2.contiguous().to(torch.float32)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = self.lib.tpc_refit_backward(self._ctx, ctypes.c_void_p(d.data_ptr()),
+                                         ctypes.c_void_p(g.data_ptr()),
+                                         ctypes.c_void_p(s.cuda_stream))
+        if rc:
+            raise TpcError(rc, self.last_error())
+        return g
+
     def set_map(self, coeff, r_range=(85.0, 245.0), z_range=(-250.0, 250.0)):
         """Use a correction map: float32 CUDA tensor [3][n_z][n_r][n_phi] (kept alive here)."""
         if coeff is None:

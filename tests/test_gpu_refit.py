@@ -1,0 +1,190 @@
+"""GPU refit and its hand-written adjoint (d sum w_t chi2_t / d map).
+
+* strict FP32 refit chi2/parameters bit-exact vs the oracle's float refit;
+* adjoint gradient vs the oracle's FP64 reverse-mode tape of the same frozen
+  function (references and decisions of the float refit);
+* adjoint vs central finite differences of the GPU refit with frozen
+  references (h = 1e-2 cm and 1e-3 cm);
+* the torch.autograd bridge returns the adjoint;
+* call-order errors.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_20569_gb300 import synth
+from paper_2601_20569_gb300.options import TrackerOptions
+
+pytestmark = pytest.mark.gpu
+
+RX = synth.row_x()
+
+
+def setup_event(n_primaries=1500, workload="central_event", seed=None):
+    import torch
+
+    from paper_2601_20569_gb300 import tpc
+
+    kw = {"n_primaries": n_primaries} if workload == "central_event" else {}
+    f = synth.generate(workload, distort=True, **kw) if seed is None else \
+        synth.generate(workload, distort=True, seed=seed, **kw)
+    opts = TrackerOptions().as_dict()
+    tr = tpc.Tracker(RX, opts, mode=0, cap_clusters=max(f.n, 1024))
+    coeff = torch.as_tensor(f.map).cuda()
+    tr.set_map(coeff)
+    dev = tr.to_device(f.y, f.z, f.q, f.row, f.sector)
+    tr.track(*dev)
+    res = {k: v.clone() for k, v in tr.result().items()}
+    tracks = {"cl_offset": res["cl_offset"], "cl_ids": res["cl_ids"], "params": res["params"],
+              "x": res["x"], "sector": res["sector"]}
+    return f, opts, tr, dev, coeff, tracks
+
+
+def host_tracks(tracks, sel=None):
+    off = tracks["cl_offset"].cpu().numpy()
+    ids = tracks["cl_ids"].cpu().numpy()
+    par = tracks["params"].cpu().numpy()
+    x = tracks["x"].cpu().numpy()
+    sec = tracks["sector"].cpu().numpy()
+    if sel is None:
+        sel = np.arange(len(par))
+    lists = [ids[off[t]:off[t + 1]] for t in sel]
+    noff = np.concatenate([[0], np.cumsum([len(v) for v in lists])]).astype(np.int32)
+    return {"offset": noff, "ids": np.concatenate(lists).astype(np.int32),
+            "par": par[sel].astype(np.float64), "x": x[sel].astype(np.float64),
+            "sector": sec[sel].astype(np.int32)}
+
+
+def device_tracks(h):
+    import torch
+
+    return {"cl_offset": torch.as_tensor(h["offset"]).cuda(),
+            "cl_ids": torch.as_tensor(h["ids"]).cuda(),
+            "params": torch.as_tensor(h["par"].astype(np.float32)).cuda(),
+            "x": torch.as_tensor(h["x"].astype(np.float32)).cuda(),
+            "sector": torch.as_tensor(h["sector"]).cuda()}
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+
+
+def test_refit_bit_exact_vs_oracle():
+    f, opts, tr, dev, coeff, tracks = setup_event()
+    out = tr.refit(dev, tracks, coeff)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    h = host_tracks(tracks)
+    r = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, h, dist_map=f.map, mode="f32")
+    ok = r["rf_ok"] == 1
+    assert ok.sum() > 0.95 * len(ok)
+    assert np.array_equal(g["n_clusters"], r["rf_n"])
+    assert np.array_equal(bits(g["chi2"][ok]), bits(r["rf_chi2"][ok]))
+    assert np.array_equal(bits(g["params"][ok]), bits(r["rf_par"].reshape(-1, 5)[ok]))
+
+
+def test_adjoint_matches_fp64_tape():
+    import torch
+
+    f, opts, tr, dev, coeff, tracks = setup_event()
+    rng = np.random.default_rng(3)
+    h = host_tracks(tracks)
+    w = rng.uniform(0.5, 1.5, len(h["par"]))
+    tr.refit(dev, tracks, coeff)
+    g = tr.refit_backward(torch.as_tensor(w, dtype=torch.float32).cuda()).cpu().numpy().ravel()
+    # the same frozen function in FP64: references/decisions of the float refit
+    rf = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, h, dist_map=f.map, mode="f32")
+    tape = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, h, dist_map=f.map, frozen=rf,
+                        weights=w, mode="tape")["grad"]
+    err = np.linalg.norm(g - tape) / np.linalg.norm(tape)
+    print(f"adjoint vs FP64 tape: relative L2 error {err:.2e}")
+    assert err < 2e-3, err
+    top = np.argsort(-np.abs(tape))[:100]
+    rel = np.abs(g[top] - tape[top]) / np.abs(tape[top])
+    assert rel.max() < 2e-2, rel.max()
+
+
+@pytest.mark.parametrize("h", [1e-2, 1e-3])
+def test_adjoint_matches_central_differences(h):
+    import torch
+
+    f, opts, tr, dev, coeff, tracks = setup_event()
+    nt = int(tracks["params"].shape[0])
+    w = torch.ones(nt, dtype=torch.float32, device="cuda")
+    base = tr.refit(dev, tracks, coeff)
+    g = tr.refit_backward(w).cpu().numpy().ravel()
+    flat = coeff.clone().reshape(-1)
+    worst = 0.0
+    for i in np.argsort(-np.abs(g))[:12]:
+        cp, cm = flat.clone(), flat.clone()
+        cp[i] += h
+        cm[i] -= h
+        step = float(cp[i].item()) - float(cm[i].item())
+        lp = tr.refit(dev, tracks, cp.reshape(coeff.shape), freeze=True)["chi2"].double().sum()
+        lm = tr.refit(dev, tracks, cm.reshape(coeff.shape), freeze=True)["chi2"].double().sum()
+        fd = float((lp - lm).item()) / step
+        worst = max(worst, abs(fd - g[i]) / abs(g[i]))
+    print(f"adjoint vs central differences (h={h}): worst relative error {worst:.2e}")
+    assert worst < (0.02 if h >= 1e-2 else 0.1), worst
+    del base
+
+
+def test_autograd_bridge_returns_the_adjoint():
+    import torch
+
+    from paper_2601_20569_gb300.autograd import refit_chi2
+
+    f, opts, tr, dev, coeff, tracks = setup_event(n_primaries=600)
+    c = coeff.clone().requires_grad_(True)
+    chi2 = refit_chi2(tr, dev, tracks, c)
+    w = torch.rand(chi2.shape[0], device="cuda")
+    (w * chi2).sum().backward()
+    tr.refit(dev, tracks, coeff)
+    g = tr.refit_backward(w)
+    assert torch.equal(c.grad, g)
+
+
+def test_call_order_errors():
+    import torch
+
+    from paper_2601_20569_gb300 import tpc
+
+    f = synth.generate("one_sector", n_primaries=30)
+    tr = tpc.Tracker(RX, TrackerOptions(), cap_clusters=4096)
+    with pytest.raises(tpc.TpcError) as e:
+        tr.refit_backward(torch.ones(1, device="cuda"), (3, 20, 16, 18))
+    assert e.value.status == 7
+    dev = tr.to_device(f.y, f.z, f.q, f.row, f.sector)
+    tr.track(*dev)
+    res = {k: v.clone() for k, v in tr.result().items()}
+    tracks = {k: res[k] for k in ("cl_offset", "cl_ids", "params", "x", "sector")}
+    with pytest.raises(tpc.TpcError) as e:
+        tr.refit(dev, tracks, None, freeze=True)
+    assert e.value.status == 7
+
+
+def test_full_size_frame_sampled_gradient():
+    """A full 2.8 ms distorted frame (~2e7 clusters): refit and adjoint run on
+    all tracks; for a sample of 150 tracks the adjoint of the sampled subset
+    matches the FP64 tape of the same subset."""
+    import torch
+
+    f, opts, tr, dev, coeff, tracks = setup_event(workload="timeframe_distorted")
+    nt = int(tracks["params"].shape[0])
+    assert nt > 50000
+    out = tr.refit(dev, tracks, coeff)
+    assert int((out["n_clusters"] > 0).sum()) > 0.95 * nt
+    gall = tr.refit_backward(torch.ones(nt, device="cuda"))
+    assert torch.isfinite(gall).all()
+    sel = np.random.default_rng(5).choice(nt, 150, replace=False)
+    h = host_tracks(tracks, sel)
+    dsub = device_tracks(h)
+    tr.refit(dev, dsub, coeff)
+    g = tr.refit_backward(torch.ones(len(sel), device="cuda")).cpu().numpy().ravel()
+    rf = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, h, dist_map=f.map, mode="f32")
+    tape = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, h, dist_map=f.map, frozen=rf,
+                        mode="tape")["grad"]
+    err = np.linalg.norm(g - tape) / np.linalg.norm(tape)
+    print(f"full-size frame, 150 sampled tracks: relative L2 error {err:.2e}")
+    assert err < 2e-3, err
