@@ -93,6 +93,8 @@ typedef struct {
   float final_chi2;         /* simple chi2 cut of fit iteration 3 */
   float attach_margin;      /* widening of the Phase II search window [cm] */
   float edge_margin;        /* following stops at |y| > x*tan(10 deg) + edge_margin [cm] */
+  float looper_qpt;         /* |q/pT| above which the final fit's Kalman update runs in FP64
+                               (low-pT loopers); 0 disables */
   int32_t max_miss;         /* consecutive empty rows ending the following */
   int32_t min_hits;         /* minimum clusters of a tracklet / track */
   int32_t merge_max_gap;    /* max rows between merged segments */

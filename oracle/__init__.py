@@ -41,6 +41,7 @@ class _Opt(ctypes.Structure):
         ("int_chi2", ctypes.c_float),
         ("final_chi2", ctypes.c_float),
         ("attach_margin", ctypes.c_float),
+        ("looper_qpt", ctypes.c_float),
         ("edge_margin", ctypes.c_float),
         ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32),

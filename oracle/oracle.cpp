@@ -59,6 +59,7 @@ struct orc_options {
   float merge_chi2, merge_dy, merge_dz;
   float int_chi2, final_chi2;
   float attach_margin;   // widening of the Phase II search window [cm]
+  float looper_qpt;      // |q/pT| above which the fit's update runs in FP64 (0: never)
   float edge_margin;     // following stops |y| > x*tan(10 deg) + edge_margin [cm]
   int32_t max_miss;
   int32_t min_hits;
@@ -240,7 +241,7 @@ struct Params {
   Real kb, tan_half, rot_c, rot_s, link_wy, link_wz, link_chi2;
   Real seed_c[5], meas_sy2, meas_sz2, ms_theta2, row_pitch_inv, follow_chi2, max_snp, fit_max_snp, score_w,
       shared_frac, merge_chi2, merge_dy, merge_dz, int_chi2, final_chi2, attach_margin,
-      edge_margin, merge_zspan;
+      edge_margin, looper_qpt, merge_zspan;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors;
   std::vector<Real> row_x;
 };
@@ -267,6 +268,7 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
   P.int_chi2 = o.int_chi2; P.final_chi2 = o.final_chi2;
   P.attach_margin = o.attach_margin;
   P.edge_margin = o.edge_margin;
+  P.looper_qpt = o.looper_qpt;
   // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
   P.merge_zspan = (Real)((double)(o.merge_max_gap + 2) *
                          (((double)row_x[o.n_rows - 1] - (double)row_x[0]) / (double)(o.n_rows - 1)) /
@@ -423,6 +425,27 @@ void update(Track<Real>& t, const Resid<Real>& R) {
   for (int i = 0; i < 5; ++i) t.p[i] = t.p[i] + (k0[i] * R.r0 + k1[i] * R.r1);
   for (int i = 0; i < 5; ++i)
     for (int j = 0; j <= i; ++j) t.c[ci(i, j)] = t.c[ci(i, j)] - (k0[i] * h0[j] + k1[i] * h1[j]);
+}
+
+// Kalman update of the final fit and refit: for low-pT loopers
+// (|q/pT| > looper_qpt) the gain and covariance update run in FP64 and are
+// rounded back (the float build; the double build is FP64 throughout).
+template <typename Real>
+void fit_update(Track<Real>& t, const Resid<Real>& R, const Params<Real>& P) {
+  if constexpr (std::is_same<Real, float>::value) {
+    if (P.looper_qpt > 0.0f && std::fabs(t.p[4]) > P.looper_qpt) {
+      Track<double> d;
+      for (int i = 0; i < 5; ++i) d.p[i] = t.p[i];
+      for (int i = 0; i < 15; ++i) d.c[i] = t.c[i];
+      d.x = t.x;
+      const Resid<double> Rd{R.r0, R.r1, R.w00, R.w01, R.w11, R.chi2};
+      update(d, Rd);
+      for (int i = 0; i < 5; ++i) t.p[i] = (float)d.p[i];
+      for (int i = 0; i < 15; ++i) t.c[i] = (float)d.c[i];
+      return;
+    }
+  }
+  update(t, R);
 }
 
 // Rotation of the local frame by +/-20 deg (to an adjacent sector): the
@@ -1199,7 +1222,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
         T.ok = false;
         return;
       }
-      update(L.t, residual(L.t, my, mz, P));
+      fit_update(L.t, residual(L.t, my, mz, P), P);
     }
   }
   // iteration 2: outward
@@ -1266,7 +1289,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
         T.ok = false;
         return;
       }
-      update(L.t, residual(L.t, my, mz, P));
+      fit_update(L.t, residual(L.t, my, mz, P), P);
     }
   }
   it2_end = L.t;
@@ -1293,7 +1316,7 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
     const Resid<Real> R = residual(L.t, my, mz, P);
     if (R.chi2 > P.final_chi2) continue;
     T.chi2 = T.chi2 + R.chi2;
-    update(L.t, R);
+    fit_update(L.t, R, P);
     ++T.n;
     T.used.push_back(c);
     T.out = L.t;
@@ -1432,7 +1455,7 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
     sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
     Real my, mz;
     if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) return;
-    update(L.t, residual(L.t, my, mz, P));
+    fit_update(L.t, residual(L.t, my, mz, P), P);
   }
   // iteration 2: outward, interpolation flags
   {
@@ -1451,7 +1474,7 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
     Real my, mz;
     if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) return;
     if (!frozen) R.flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
-    update(L.t, residual(L.t, my, mz, P));
+    fit_update(L.t, residual(L.t, my, mz, P), P);
   }
   // iteration 3: inward, simple cut
   {
@@ -1473,7 +1496,7 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
     if (!frozen) R.acc[k] = accept ? 1 : 0;
     if (!accept) continue;
     R.chi2 = R.chi2 + Rs.chi2;
-    update(L.t, Rs);
+    fit_update(L.t, Rs, P);
     ++R.n;
     R.out = L.t;
     R.out_sector = L.sector;

@@ -119,6 +119,7 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.final_chi2 = o.final_chi2;
   P.attach_margin = o.attach_margin;
   P.edge_margin = o.edge_margin;
+  P.looper_qpt = o.looper_qpt;
   // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
   P.merge_zspan = (float)((double)(o.merge_max_gap + 2) *
                           (((double)row_x[nr - 1] - (double)row_x[0]) / (double)(nr - 1)) /

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(128) k_fit12(FrameDev F, KParams P, MapDev M) 
       if (c >= 0) {
         float my, mz;
         if (!corrected(M, P, rs / NR, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
-        update(L.t, residual(L.t, my, mz, P));
+        fit_update(L.t, residual(L.t, my, mz, P), P);
       }
     }
     // iteration 2: outward, interpolation, flags, inner-row candidates
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(128) k_fit12(FrameDev F, KParams P, MapDev M) 
         if (c >= 0) {
           float my, mz;
           if (!corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
-          update(L.t, residual(L.t, my, mz, P));
+          fit_update(L.t, residual(L.t, my, mz, P), P);
         }
       }
       if (ok) put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(128) k_fit3(FrameDev F, KParams P, MapDev M) {
       const Resid R = residual(L.t, my, mz, P);
       if (R.chi2 > P.final_chi2) continue;
       chi2 = chi2 + R.chi2;
-      update(L.t, R);
+      fit_update(L.t, R, P);
       used[n] = c;
       ++n;
       out = L.t;
@@ -981,7 +981,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
       sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
       float my, mz;
       if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) { ok = false; break; }
-      update(L.t, residual(L.t, my, mz, P));
+      fit_update(L.t, residual(L.t, my, mz, P), P);
     }
     if (!ok) continue;
     {
@@ -999,7 +999,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
       float my, mz;
       if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) { ok = false; break; }
       if (!R.freeze) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
-      update(L.t, residual(L.t, my, mz, P));
+      fit_update(L.t, residual(L.t, my, mz, P), P);
     }
     if (!ok) continue;
     {
@@ -1025,7 +1025,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
       if (!R.freeze) acc[k] = accept ? 1 : 0;
       if (!accept) continue;
       chi2 = chi2 + Rs.chi2;
-      update(L.t, Rs);
+      fit_update(L.t, Rs, P);
       ++n;
       out = L.t;
       out_sec = L.sector;
@@ -1102,7 +1102,7 @@ __device__ __forceinline__ bool replay_step(const RefitDev& R, const KParams& P,
   }
   S.w00 = Rs.w00; S.w01 = Rs.w01; S.w11 = Rs.w11; S.r0 = Rs.r0; S.r1 = Rs.r1;
   S.bits |= 4;
-  update(L.t, Rs);
+  fit_update(L.t, Rs, P);
   return true;
 }
 

@@ -21,7 +21,7 @@ struct KParams {
   float seed_c[5];
   float follow_chi2, max_snp, fit_max_snp, score_w, shared_frac;
   float merge_chi2, merge_dy, merge_dz, merge_zspan;
-  float int_chi2, final_chi2, attach_margin, edge_margin;
+  float int_chi2, final_chi2, attach_margin, edge_margin, looper_qpt;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k;
   int n_rows, n_sectors;
   float grid_dy;     // target y bin size [cm]

@@ -220,6 +220,39 @@ __device__ __forceinline__ void update(Trk<float>& t, const Resid& R) {
   }
 }
 
+// The same update with the gain and covariance arithmetic in FP64, rounded
+// back to FP32 (the final fit's update of low-pT loopers).
+__device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
+  const double w00 = R.w00, w01 = R.w01, w11 = R.w11, r0 = R.r0, r1 = R.r1;
+  const double h0[5] = {t.c[0], t.c[1], t.c[3], t.c[6], t.c[10]};
+  const double h1[5] = {t.c[1], t.c[2], t.c[4], t.c[7], t.c[11]};
+  double k0[5], k1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    k0[i] = h0[i] * w00 + h1[i] * w01;
+    k1[i] = h0[i] * w01 + h1[i] * w11;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) t.p[i] = (float)((double)t.p[i] + (k0[i] * r0 + k1[i] * r1));
+  int idx = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      t.c[idx] = (float)((double)t.c[idx] - (k0[i] * h0[j] + k1[i] * h1[j]));
+      ++idx;
+    }
+  }
+}
+
+// Update of the final fit and refit: FP64 for loopers (|q/pT| > looper_qpt).
+__device__ __forceinline__ void fit_update(Trk<float>& t, const Resid& R, const KParams& P) {
+  if (P.looper_qpt > 0.0f && fabsf(t.p[4]) > P.looper_qpt)
+    update_fp64(t, R);
+  else
+    update(t, R);
+}
+
 // Frame rotation to the adjacent sector (dir = +1: +20 deg).
 __device__ __forceinline__ bool rotate(Trk<float>& t, int dir, const KParams& P, float lim) {
   const float ca = P.rot_c;

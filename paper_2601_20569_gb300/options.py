@@ -39,6 +39,7 @@ class TrackerOptions:
     int_chi2: float = 25.0          # interpolation cut / Phase II candidate cut (2 dof)
     final_chi2: float = 16.0        # simple cut of the last fit iteration
     attach_margin: float = 0.5      # widening of the Phase II search window [cm]
+    looper_qpt: float = 1.0 / 0.15  # |q/pT| above which the fit update runs in FP64
     edge_margin: float = 1.0        # following stops beyond the sector edge + this [cm]
     max_miss: int = 10              # consecutive empty rows ending the following
     min_hits: int = 10
@@ -55,7 +56,7 @@ class TrackerOptions:
 
 FLOAT_FIELDS = ("bz", "sigma_y", "sigma_z", "ms_theta", "link_wy", "link_wz", "link_chi2")
 FLOAT_FIELDS2 = ("follow_chi2", "max_snp", "fit_max_snp", "score_w", "shared_frac", "merge_chi2", "merge_dy",
-                 "merge_dz", "int_chi2", "final_chi2", "attach_margin", "edge_margin")
+                 "merge_dz", "int_chi2", "final_chi2", "attach_margin", "looper_qpt", "edge_margin")
 INT_FIELDS = ("max_miss", "min_hits", "merge_max_gap", "inner_rows", "cand_k", "brute_force",
               "n_rows", "n_sectors")
 

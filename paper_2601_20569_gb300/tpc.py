@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
         ("shared_frac", ctypes.c_float), ("merge_chi2", ctypes.c_float),
         ("merge_dy", ctypes.c_float), ("merge_dz", ctypes.c_float), ("int_chi2", ctypes.c_float),
         ("final_chi2", ctypes.c_float), ("attach_margin", ctypes.c_float),
-        ("edge_margin", ctypes.c_float), ("max_miss", ctypes.c_int32),
+        ("edge_margin", ctypes.c_float), ("looper_qpt", ctypes.c_float),
+        ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32), ("merge_max_gap", ctypes.c_int32),
         ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
