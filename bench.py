@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--mode", default="fast", choices=["fast", "strict"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up plus one step and exit (for ncu launch lists)")
     return ap.parse_args()
@@ -134,21 +135,21 @@ def cpu_baseline(frames, seconds):
 
     f = frames[0]
     opts = TrackerOptions().as_dict()
-    order = np.argsort(f.sector, kind="stable")
-    bounds = np.searchsorted(f.sector[order], np.arange(37))
-    n_done, t_done, sectors = 0, 0.0, 0
-    for s in range(36):
-        idx = order[bounds[s]:bounds[s + 1]]
+    n_done, t_done, groups = 0, 0.0, 0
+    for g in range(12):  # groups of three adjacent sectors, the whole chain on each
+        idx = np.nonzero((f.sector // 3) == g)[0]
         t0 = time.perf_counter()
-        oracle.track(f.y[idx], f.z[idx], f.row[idx], f.sector[idx], synth.row_x(), opts)
+        oracle.track(f.y[idx], f.z[idx], f.row[idx], f.sector[idx], synth.row_x(), opts,
+                     full=True)
         t_done += time.perf_counter() - t0
         n_done += len(idx)
-        sectors += 1
+        groups += 1
         if t_done >= seconds:
             break
     return {"value": n_done / t_done, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sectors} of 36 sectors of frame 0 ({n_done} clusters, "
-                      f"{t_done:.1f} s), strict FP32 oracle, single thread"}
+            "sample": f"{3 * groups} of 36 sectors of frame 0 in groups of 3 adjacent sectors "
+                      f"({n_done} clusters, {t_done:.1f} s), full chain, strict FP32 oracle, "
+                      f"single thread"}
 
 
 def run_reference(args):
@@ -163,7 +164,8 @@ def run_reference(args):
     opts = TrackerOptions().as_dict()
     # one step = a bounded sample: the clusters of two sectors of frame 0
     sel = np.nonzero(f.sector < 2)[0]
-    run = lambda: oracle.track(f.y[sel], f.z[sel], f.row[sel], f.sector[sel], synth.row_x(), opts)
+    run = lambda: oracle.track(f.y[sel], f.z[sel], f.row[sel], f.sector[sel], synth.row_x(), opts,
+                               full=True)
     for _ in range(args.warmup):
         run()
     t0 = time.perf_counter()
@@ -184,18 +186,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# Algorithmic bytes per unit of each stage (the minimum the stage must move).
-def stage_bytes(name: str, n_clusters: int, tl_hits: int, n_tracklets: int) -> float:
+# Algorithmic bytes of each stage (the minimum it must move), from the counts
+# of one call: clusters, tracklet hits, tracklets, sector-track hits, sector
+# tracks, fitted-track stations, fitted tracks.
+def stage_bytes(name: str, c: dict) -> float:
+    n, th, nt = c["clusters"], c["tl_hits"], c["tracklets"]
+    sh, ns, fh, nf = c["st_hits"], c["sector_tracks"], c["fit_hits"], c["fit_tracks"]
     if name == "grid":       # read y,z,row,sector; write sorted y,z,id,row
-        return n_clusters * (10 + 14)
-    if name == "links":      # read sorted y,z,id once; write 2 links; cleaner: read+write links
-        return n_clusters * (12 + 8 + 8 + 8)
-    if name == "starts":     # read cleaned links; write start list
-        return n_clusters * 8 + n_tracklets * 4
-    if name == "tracklets":  # two passes reading y,z,id of each used cluster, hit writes, state
-        return tl_hits * (2 * 12 + 4) + n_tracklets * 4 * 24
-    if name == "select":     # owner max and walk: hits read twice, owner key read/written
-        return tl_hits * (4 * 2 + 8 * 2) + n_tracklets * 16
+        return n * (10 + 14)
+    if name == "links":      # read sorted y,z,id; write links; cleaner reads/writes links
+        return n * (12 + 8 + 8 + 8)
+    if name == "starts":     # read cleaned links; write the start list
+        return n * 8 + nt * 4
+    if name == "tracklets":  # y,z,id of each hit read twice (up, down), hit written, state out
+        return th * (2 * 12 + 4) + nt * 96
+    if name == "select":     # hits read twice, owner keys read and written
+        return th * (4 * 2 + 8 * 2) + nt * 16
+    if name == "merge":      # kept hits read twice with y,z,row; two end states per track
+        return sh * 2 * (4 + 10) + ns * 2 * 88
+    if name == "fit":        # station lists, 3 passes over y,z, stored predictions, state out
+        return fh * (6 + 3 * 10 + 2 * 20 + 1) + nf * 88 * 3
+    if name == "output":     # used clusters and state per output track
+        return fh * 12 + nf * 100
     return 0.0
 
 
@@ -221,18 +233,16 @@ def main():
     libbuild.build()
     frames = make_frames(args, rank)
     n_per_step = sum(f.n for f in frames)
-    cap = max(f.n for f in frames)
     mode = MODE_FAST if args.mode == "fast" else MODE_STRICT
-    tr = tpc.Tracker(synth.row_x(), TrackerOptions(), mode=mode, cap_clusters=cap)
+    tr = tpc.Tracker(synth.row_x(), TrackerOptions(), mode=mode, cap_clusters=n_per_step,
+                     max_frames=len(frames), use_graphs=True)
     dev = [tr.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
     stream = torch.cuda.current_stream()
+    tuned = tr.autotune(dev) if not args.no_autotune else tr.launch_config()
 
     def step():
-        launches = 0
-        for d in dev:
-            tr.track(*d, stream=stream)
-            launches += tr.last_launches()
-        return launches
+        tr.track_batch(dev, stream=stream)
+        return tr.last_launches()
 
     for _ in range(args.warmup):
         step()
@@ -268,6 +278,22 @@ def main():
         ms = float(t.item())
     value = n_per_step * world * args.steps / (ms / 1e3)
 
+    # the plain form on the same inputs: one call (one launch per stage) per frame
+    plain = tpc.Tracker(synth.row_x(), TrackerOptions(), mode=mode,
+                        cap_clusters=max(f.n for f in frames))
+    for d in dev:
+        plain.track(*d, stream=stream)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        for d in dev:
+            plain.track(*d, stream=stream)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_value = n_per_step * world * args.steps / (p0.elapsed_time(p1) / 1e3)
+    plain.close()
+
     # per-stage device times (CUDA events on the launching stream), a separate pass
     tr.profile(True)
     for _ in range(args.steps):
@@ -275,45 +301,43 @@ def main():
     torch.cuda.synchronize()
     stages = tr.stage_stats()
     tr.profile(False)
-    tl_n = tr.debug("tl_n")
-    tl_hits_last = int(tl_n.sum())
-    n_tl_last = int(tl_n.size)
-    # scale per-frame counts of the last frame to the whole step by cluster share
-    scale = n_per_step / frames[-1].n
+    counts = {
+        "clusters": n_per_step, "tl_hits": int(tr.debug("tl_n").sum()),
+        "tracklets": int(tr.debug("tl_n").size), "st_hits": int(tr.debug("tl_nkept").sum()),
+        "sector_tracks": int(tr.debug("st_key").size), "fit_hits": int(tr.debug("ft_n").sum()),
+        "fit_tracks": int(tr.debug("ft_n").size),
+    }
     hbm, peak_kind = peaks()
     dom = max(stages, key=lambda s: s["ms"])
-    launches_per_call = max(1, dom["launches"] // max(1, dom["calls"]))
-    per_launch_ms = dom["ms"] / max(1, dom["calls"])  # one stage call per frame
-    bytes_call = stage_bytes(dom["name"], n_per_step / len(frames), tl_hits_last * scale / len(frames),
-                             n_tl_last * scale / len(frames))
-    achieved = bytes_call / (per_launch_ms / 1e3) / 1e9
+    per_call_ms = dom["ms"] / max(1, dom["calls"])
+    achieved = stage_bytes(dom["name"], counts) / (per_call_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None,
-            "kernel": f"stage '{dom['name']}' ({launches_per_call} kernels per frame)",
-            "peak_source": f"{peak_kind} hbm_gbs"}
+            "kernel": f"stage '{dom['name']}' ({dom['launches'] // max(1, dom['calls'])} kernels "
+                      f"per batch call)", "peak_source": f"{peak_kind} hbm_gbs",
+            "stage_bytes_per_call": stage_bytes(dom["name"], counts)}
 
-    # end to end through the public API: pinned host clusters in, tracks out
+    # end to end through the public API: pinned host clusters in, attachments out
     host = []
     for f in frames:
         host.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
                           (f.y, f.z, f.q.view(np.int16), f.row, f.sector)))
     dbuf = [tuple(torch.empty_like(h, device="cuda") for h in hs) for hs in host]
-    attach_host = torch.empty(cap, dtype=torch.int32).pin_memory()
+    attach_host = torch.empty(n_per_step, dtype=torch.int32).pin_memory()
     h2d = sum(sum(h.numel() * h.element_size() for h in hs) for hs in host)
-    d2h = 0
+    tr.track_batch(dbuf, stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        for hs, ds, f in zip(host, dbuf, frames):
+        for hs, ds in zip(host, dbuf):
             for h, d in zip(hs, ds):
                 d.copy_(h, non_blocking=True)
-            tr.track(ds[0], ds[1], ds[2], ds[3], ds[4], stream=stream)
-            own = tr.result_attach()
-            attach_host[:f.n].copy_(own, non_blocking=True)
+        tr.track_batch(dbuf, stream=stream)
+        attach_host.copy_(tr.result_attach(), non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    d2h = sum(4 * f.n for f in frames)
+    d2h = 4 * n_per_step
     e2e_ms = e0.elapsed_time(e1)
     e2e = {"value": n_per_step * world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
@@ -323,15 +347,18 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {args.frames} x 2.8 ms frames, 50 kHz Pb-Pb, "
-                               f"{n_per_step} clusters per step", "frames": args.frames,
+                               f"{n_per_step} clusters per step, one batched pass", "frames": args.frames,
                    "clusters_per_step": n_per_step, "mode": args.mode,
                    "l2": "inputs larger than L2 (each frame > 129 MB resident)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "launch": "batched + CUDA graph"},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "stages_ms_per_frame": {s["name"]: s["ms"] / max(1, s["calls"]) for s in stages},
+        "plain_per_frame": {"value": plain_value, "unit": UNIT,
+                            "form": "one call per frame (one launch per stage per frame)"},
+        "stages_ms_per_batch": {s_["name"]: s_["ms"] / max(1, s_["calls"]) for s_ in stages},
+        "launch_config": tuned,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(frames, args.cpu_seconds)

@@ -101,7 +101,10 @@ typedef struct {
   int32_t inner_rows;       /* rows of the inner region (Phase II re-attachment) */
   int32_t cand_k;           /* candidates kept per (track, row), <= 8 */
   int32_t mode;             /* 0 = strict FP32 (no FMA), 1 = fast FP32 (FMA) */
-  int64_t cap_clusters;     /* max clusters per frame */
+  int32_t max_frames;       /* frames per tpc_track_batch call (<= 64; 0 or 1: single frames) */
+  int32_t use_graphs;       /* 1: replay each call's chain from a captured CUDA graph */
+  int32_t reserved;
+  int64_t cap_clusters;     /* max clusters per call (all frames of a batch) */
   int64_t cap_tracklets;    /* max tracklets per frame (0: n/16 + 4096) */
   int64_t cap_tracks;       /* max tracks per frame (0: cap_tracklets) */
 } tpc_options;
@@ -175,6 +178,30 @@ tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* clusters, const tpc_track
  * without a preceding refit that used a map. */
 tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dL_dchi2, float* dL_dmap,
                               void* cuda_stream);
+
+/* Track several time frames in one pass: the frames are concatenated (frame
+ * f's sector s becomes batch sector f*n_sectors + s, its cluster i batch id
+ * sum_{g<f} n_g + i) and every stage runs once over all of them, the heavy
+ * kernels as persistent grids pulling tracks from device-side work queues so
+ * that sectors and frames of very uneven occupancy balance.  Results are
+ * those of tracking each frame alone; tracks report batch sectors and batch
+ * cluster ids.  n_frames <= opt->max_frames of tpc_init.  (Not in the paper,
+ * which processes one time frame at a time: Sec. 1.) */
+tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_frames,
+                           tpc_tracks* out, void* cuda_stream, int64_t* needed);
+
+/* Autotuner: times the heavy kernels (tracklet construction, sector refit,
+ * merging, fit iterations) over block sizes {64, 128, 256} x {4, 8, 16}
+ * blocks per SM on the given frames (tracked as one batch) and keeps the
+ * fastest shape per kernel for later calls (the analogue of the paper's
+ * automatic tuning of threads and blocks per GPU, Sec. 5). */
+tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_frames,
+                        void* cuda_stream);
+
+/* Launch shape chosen for heavy kernel `slot` (0..4): kernel name, block
+ * size, blocks per SM.  TPC_ERR_INVALID_ARG past the last slot. */
+tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
+                             int32_t* block, int32_t* blocks_per_sm);
 
 /* Replace the correction map (device pointer copied by reference; the caller
  * keeps it alive while the context uses it). */

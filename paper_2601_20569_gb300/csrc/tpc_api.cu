@@ -36,8 +36,39 @@ const StageDef kStages[] = {
 constexpr int kNumStages = sizeof(kStages) / sizeof(kStages[0]);
 }  // namespace
 
+// Identity of a captured chain: same buffers, sizes, map and launch shapes.
+struct GraphKey {
+  const void* y;
+  const void* z;
+  const void* row;
+  const void* sector;
+  long n;
+  long nf;
+  const void* map;
+  long lc_version;
+  GraphKey() { std::memset(this, 0, sizeof *this); }
+  GraphKey(const void* a, const void* b, const void* c, const void* d, long n_, int nf_,
+           const void* m, long v) {
+    std::memset(this, 0, sizeof *this);
+    y = a; z = b; row = c; sector = d; n = n_; nf = nf_; map = m; lc_version = v;
+  }
+};
+
 struct tpc_ctx {
   tpc_options opt{};
+  int max_frames = 1;
+  // batch input (concatenated frames)
+  float* by = nullptr;
+  float* bz = nullptr;
+  uint8_t* brow = nullptr;
+  uint8_t* bsec = nullptr;
+  // graph replay
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  GraphKey graph_key;
+  long graph_launches = 0;
+  long lc_version = 0;
   bool prof = false;
   cudaEvent_t ev[kNumStages + 1] = {};
   double stage_ms[kNumStages] = {};
@@ -173,6 +204,8 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
       opt->cand_k > kMaxCand || opt->min_hits < 3 || !(opt->shared_frac >= 0.0f) ||
       (opt->mode != 0 && opt->mode != 1) || opt->cap_clusters > (1L << 30) ||
       opt->inner_rows < 0 || opt->inner_rows > kMaxInner || opt->merge_max_gap < 1 ||
+      opt->max_frames < 0 || opt->max_frames > 64 ||
+      (long)geo->n_sectors * (opt->max_frames > 1 ? opt->max_frames : 1) * geo->n_rows > 65535 ||
       !(opt->fit_max_snp > 0.0f && opt->fit_max_snp < 1.0f) ||
       !(opt->max_snp > 0.0f && opt->max_snp < 1.0f))
     return TPC_ERR_INVALID_ARG;
@@ -189,8 +222,10 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ctx->n_sectors = geo->n_sectors;
   std::vector<float> rx(geo->row_x, geo->row_x + geo->n_rows);
   derive(ctx->P, *opt, bz_tesla, rx);
+  ctx->max_frames = opt->max_frames > 1 ? opt->max_frames : 1;
   ctx->P.n_rows = geo->n_rows;
-  ctx->P.n_sectors = geo->n_sectors;
+  ctx->P.n_sectors = geo->n_sectors * ctx->max_frames;
+  ctx->P.n_phi = geo->n_sectors / 2 > 0 ? geo->n_sectors / 2 : 1;
   if (map) ctx->map = *map;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -199,8 +234,13 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
 
   const long n = opt->cap_clusters;
   ctx->cap_n = n;
-  const long nrr = (long)geo->n_sectors * geo->n_rows;
+  const long nsec_all = (long)geo->n_sectors * ctx->max_frames;
+  const long nrr = nsec_all * geo->n_rows;
   FrameDev& F = ctx->F;
+  for (int i = 0; i < kLNum; ++i) {
+    F.lc.block[i] = 128;
+    F.lc.per_sm[i] = 8;
+  }
   F.cap_bins = (long)((double)n / ctx->P.grid_occ) + nrr * 65;
   F.cap_tl = opt->cap_tracklets > 0 ? opt->cap_tracklets : n / 10 + 4096;
   bool ok = true;
@@ -240,7 +280,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.cnt, 1);
   // a7
   const long T = F.cap_tl;
-  const long nmb = (long)geo->n_sectors * kMergeBins;
+  const long nmb = nsec_all * kMergeBins;
   ok &= dalloc(ctx, &F.st_tl, T);
   ok &= dalloc(ctx, &F.st_ok, T);
   ok &= dalloc(ctx, &F.st_key, T);
@@ -259,8 +299,19 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ie_slot, T);
   ok &= dalloc(ctx, &F.ie_bin, T);
   ok &= dalloc(ctx, &F.ie_idx, T);
-  ok &= dalloc(ctx, &F.sec_zlo, geo->n_sectors);
-  ok &= dalloc(ctx, &F.sec_zinv, geo->n_sectors);
+  ok &= dalloc(ctx, &F.sec_zlo, nsec_all);
+  ok &= dalloc(ctx, &F.sec_zinv, nsec_all);
+  if (ctx->max_frames > 1) {
+    ok &= dalloc(ctx, &ctx->by, n);
+    ok &= dalloc(ctx, &ctx->bz, n);
+    ok &= dalloc(ctx, &ctx->brow, n);
+    ok &= dalloc(ctx, &ctx->bsec, n);
+  }
+  if (opt->use_graphs) {
+    ok &= cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) == cudaSuccess;
+    ok &= cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  }
   // a9/a10/a11
   F.cap_ft = opt->cap_tracks > 0 ? opt->cap_tracks : n / 40 + 4096;
   const long FT = F.cap_ft;
@@ -325,27 +376,15 @@ tpc_status tpc_set_map(tpc_ctx* ctx, const tpc_map* map) {
   return TPC_OK;
 }
 
-tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks* out,
-                               void* cuda_stream, int64_t* needed) {
-  if (!ctx) return TPC_ERR_INVALID_ARG;
-  if (!cl || !out) return fail(ctx, TPC_ERR_INVALID_ARG, "null clusters or output");
-  if (cl->n < 0) return fail(ctx, TPC_ERR_INVALID_ARG, "negative cluster count");
-  if (cl->n > 0 && (!cl->y || !cl->z || !cl->row || !cl->sector))
-    return fail(ctx, TPC_ERR_INVALID_ARG, "null cluster array");
-  if (cl->n > ctx->cap_n) {
-    if (needed) *needed = cl->n;
-    return fail(ctx, TPC_ERR_CAPACITY, "frame has %lld clusters, capacity %ld", (long long)cl->n,
-                ctx->cap_n);
-  }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  ctx->last_stream = s;
-  FrameDev& F = ctx->F;
-  F.y = cl->y;
-  F.z = cl->z;
-  F.row = cl->row;
-  F.sector = cl->sector;
-  F.n = cl->n;
-  const long nrr = (long)ctx->n_sectors * ctx->n_rows;
+}  // extern "C"
+
+namespace {
+
+// Enqueue the whole chain (buffer resets and all stages) for F with the
+// per-call parameters Pc; returns the number of kernels.  No host sync.
+tpc_status enqueue_chain(tpc_ctx* ctx, FrameDev& F, const KParams& Pc, cudaStream_t s,
+                         bool events, long* launches) {
+  const long nrr = (long)Pc.n_sectors * ctx->n_rows;
   const long n = F.n;
   CK(cudaMemsetAsync(F.cnt, 0, sizeof(Counters), s));
   CK(cudaMemsetAsync(F.row_cnt, 0, sizeof(int) * nrr, s));
@@ -360,29 +399,77 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
     CK(cudaMemsetAsync(F.attach, 0xFF, sizeof(int) * n, s));
     CK(cudaMemsetAsync(F.attach_key, 0x7F, sizeof(int) * n, s));
   }
-  CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * ((long)ctx->n_sectors * kMergeBins + 1), s));
+  CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * ((long)Pc.n_sectors * kMergeBins + 1), s));
   CK(cudaMemsetAsync(F.out_offset, 0, sizeof(int), s));
-  F.map = make_mapdev(ctx->map);
-  ctx->launches_last = 0;
-  if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
+  long k = 0;
+  if (events) CK(cudaEventRecord(ctx->ev[0], s));
   for (int i = 0; i < kNumStages; ++i) {
     const StageFn fn = ctx->opt.mode == 0 ? kStages[i].strict_fn : kStages[i].fast_fn;
-    const int k = fn(F, ctx->P, ctx->sms, s);
-    ctx->launches_last += k;
-    ctx->stage_launches[i] += k;
-    if (ctx->prof) CK(cudaEventRecord(ctx->ev[i + 1], s));
+    const int ki = fn(F, Pc, ctx->sms, s);
+    k += ki;
+    ctx->stage_launches[i] += ki;
+    if (events) CK(cudaEventRecord(ctx->ev[i + 1], s));
   }
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(&ctx->host_cnt, F.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (ctx->prof) {
-    for (int i = 0; i < kNumStages; ++i) {
-      float ms = 0.0f;
-      CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
-      ctx->stage_ms[i] += ms;
-      ctx->stage_calls[i] += 1;
+  *launches = k;
+  return TPC_OK;
+}
+
+// Runs the chain on the frame view F (single frame or concatenated batch of
+// nf frames), through a cached CUDA graph unless profiling, then reads the
+// counters back and fills `out`.
+tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_tracks* out,
+                     int64_t* needed) {
+  KParams Pc = ctx->P;
+  Pc.n_sectors = ctx->n_sectors * nf;
+  F.map = make_mapdev(ctx->map);
+  ctx->last_stream = s;
+  long launches = 0;
+  const bool graph = ctx->opt.use_graphs && !ctx->prof;
+  if (graph) {
+    GraphKey key{F.y, F.z, F.row, F.sector, F.n, nf, F.map.c, ctx->lc_version};
+    if (!ctx->graph_exec || std::memcmp(&key, &ctx->graph_key, sizeof key) != 0) {
+      if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+      const tpc_status st = enqueue_chain(ctx, F, Pc, ctx->gstream, false, &launches);
+      const cudaError_t e = cudaStreamEndCapture(ctx->gstream, &g);
+      if (st != TPC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(ctx, TPC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+      CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+      cudaGraphDestroy(g);
+      ctx->graph_key = key;
+      ctx->graph_launches = launches;
+    }
+    launches = ctx->graph_launches;
+    // order the graph after the caller's stream, and the caller after it
+    CK(cudaEventRecord(ctx->ev_in, s));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+    CK(cudaGraphLaunch(ctx->graph_exec, ctx->gstream));
+    CK(cudaMemcpyAsync(&ctx->host_cnt, F.cnt, sizeof(Counters), cudaMemcpyDeviceToHost,
+                       ctx->gstream));
+    CK(cudaEventRecord(ctx->ev_out, ctx->gstream));
+    CK(cudaStreamWaitEvent(s, ctx->ev_out, 0));
+    CK(cudaStreamSynchronize(ctx->gstream));
+  } else {
+    const tpc_status st = enqueue_chain(ctx, F, Pc, s, ctx->prof, &launches);
+    if (st != TPC_OK) return st;
+    CK(cudaMemcpyAsync(&ctx->host_cnt, F.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->prof) {
+      for (int i = 0; i < kNumStages; ++i) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+        ctx->stage_ms[i] += ms;
+        ctx->stage_calls[i] += 1;
+      }
     }
   }
+  ctx->launches_last = launches;
   const Counters& c = ctx->host_cnt;
   std::memset(out, 0, sizeof(*out));
   if (c.err & kErrInput) return fail(ctx, TPC_ERR_INVALID_INPUT, "invalid cluster (NaN/Inf, row or sector out of range)");
@@ -418,6 +505,138 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
   out->cl_ids = F.out_ids;
   out->key = F.out_key;
   out->attach = F.attach;
+  return TPC_OK;
+}
+
+__global__ void k_sector_offset(const uint8_t* in, uint8_t* out, long n, int add) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (uint8_t)min(255, (int)in[i] + add);
+}
+
+}  // namespace
+
+extern "C" {
+
+tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks* out,
+                               void* cuda_stream, int64_t* needed) {
+  if (!ctx) return TPC_ERR_INVALID_ARG;
+  if (!cl || !out) return fail(ctx, TPC_ERR_INVALID_ARG, "null clusters or output");
+  if (cl->n < 0) return fail(ctx, TPC_ERR_INVALID_ARG, "negative cluster count");
+  if (cl->n > 0 && (!cl->y || !cl->z || !cl->row || !cl->sector))
+    return fail(ctx, TPC_ERR_INVALID_ARG, "null cluster array");
+  if (cl->n > ctx->cap_n) {
+    if (needed) *needed = cl->n;
+    return fail(ctx, TPC_ERR_CAPACITY, "frame has %lld clusters, capacity %ld", (long long)cl->n,
+                ctx->cap_n);
+  }
+  FrameDev& F = ctx->F;
+  F.y = cl->y;
+  F.z = cl->z;
+  F.row = cl->row;
+  F.sector = cl->sector;
+  F.n = cl->n;
+  return run_chain(ctx, F, 1, (cudaStream_t)cuda_stream, out, needed);
+}
+
+tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_frames,
+                           tpc_tracks* out, void* cuda_stream, int64_t* needed) {
+  if (!ctx) return TPC_ERR_INVALID_ARG;
+  if (!frames || !out || n_frames < 1)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "null frames/output or no frame");
+  if (n_frames > ctx->max_frames)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "%d frames exceed the context's max_frames %d", n_frames,
+                ctx->max_frames);
+  long total = 0;
+  for (int f = 0; f < n_frames; ++f) {
+    if (frames[f].n < 0 || (frames[f].n > 0 && (!frames[f].y || !frames[f].z || !frames[f].row ||
+                                                 !frames[f].sector)))
+      return fail(ctx, TPC_ERR_INVALID_ARG, "invalid frame %d", f);
+    total += frames[f].n;
+  }
+  if (total > ctx->cap_n) {
+    if (needed) *needed = total;
+    return fail(ctx, TPC_ERR_CAPACITY, "batch has %ld clusters, capacity %ld", total, ctx->cap_n);
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  FrameDev& F = ctx->F;
+  // concatenate: frame f's sector s becomes batch sector f * n_sectors + s
+  long off = 0;
+  for (int f = 0; f < n_frames; ++f) {
+    const long n = frames[f].n;
+    if (n == 0) continue;
+    CK(cudaMemcpyAsync(ctx->by + off, frames[f].y, 4 * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ctx->bz + off, frames[f].z, 4 * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ctx->brow + off, frames[f].row, n, cudaMemcpyDeviceToDevice, s));
+    k_sector_offset<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(frames[f].sector, ctx->bsec + off,
+                                                                n, f * ctx->n_sectors);
+    off += n;
+  }
+  CK(cudaGetLastError());
+  F.y = ctx->by;
+  F.z = ctx->bz;
+  F.row = ctx->brow;
+  F.sector = ctx->bsec;
+  F.n = total;
+  return run_chain(ctx, F, n_frames, s, out, needed);
+}
+
+tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_frames,
+                        void* cuda_stream) {
+  if (!ctx || !frames || n_frames < 1) return TPC_ERR_INVALID_ARG;
+  static const char* slot_stage[kLNum] = {"tracklets", "merge", "merge", "fit", "fit"};
+  static const int blocks[] = {64, 128, 256};
+  static const int per_sm[] = {4, 8, 16};
+  const bool prof_was = ctx->prof;
+  if (!ctx->ev[0])
+    for (auto& e : ctx->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(ctx, TPC_ERR_CUDA, "event create");
+  ctx->prof = true;
+  tpc_tracks out;
+  int64_t need = 0;
+  for (int slot = 0; slot < kLNum; ++slot) {
+    int st = 0;
+    while (st < kNumStages && std::strcmp(kStages[st].name, slot_stage[slot]) != 0) ++st;
+    double best = 1e30;
+    LaunchCfg best_lc = ctx->F.lc;
+    for (int b : blocks)
+      for (int q : per_sm) {
+        ctx->F.lc.block[slot] = b;
+        ctx->F.lc.per_sm[slot] = q;
+        double t = 0.0;
+        for (int rep = 0; rep < 2; ++rep) {
+          const double before = ctx->stage_ms[st];
+          const tpc_status rc = tpc_track_batch(ctx, frames, n_frames, &out, cuda_stream, &need);
+          if (rc != TPC_OK) {
+            ctx->prof = prof_was;
+            return rc;
+          }
+          if (rep == 1) t = ctx->stage_ms[st] - before;  // second run: warm
+        }
+        if (t < best) {
+          best = t;
+          best_lc = ctx->F.lc;
+        }
+      }
+    ctx->F.lc = best_lc;
+  }
+  ctx->prof = prof_was;
+  ++ctx->lc_version;
+  for (int i = 0; i < kNumStages; ++i) {
+    ctx->stage_ms[i] = 0.0;
+    ctx->stage_calls[i] = 0;
+    ctx->stage_launches[i] = 0;
+  }
+  return TPC_OK;
+}
+
+tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
+                             int32_t* block, int32_t* blocks_per_sm) {
+  static const char* names[kLNum] = {"k_tracklets", "k_sector_refit", "k_merge_best", "k_fit12",
+                                     "k_fit3"};
+  if (!ctx || slot < 0 || slot >= kLNum) return TPC_ERR_INVALID_ARG;
+  if (kernel) *kernel = names[slot];
+  if (block) *block = ctx->F.lc.block[slot];
+  if (blocks_per_sm) *blocks_per_sm = ctx->F.lc.per_sm[slot];
   return TPC_OK;
 }
 
@@ -650,6 +869,10 @@ void tpc_destroy(tpc_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   delete ctx;
 }
 

@@ -68,7 +68,7 @@ struct SplinePt {
 __device__ __forceinline__ SplinePt spline_point(const MapDev& M, const KParams& P, int sector,
                                                  float x, float y, float zdrift) {
   SplinePt sp;
-  const int sphi = sector % (P.n_sectors / 2);
+  const int sphi = sector % P.n_phi;
   const float u = ((float)sphi + 0.5f) + 0.5f * (y / x) / P.tan_half;
   const float tp = u * M.phi_scale - 0.5f;
   sp.ip = (int)floorf(tp);
@@ -154,11 +154,12 @@ __global__ void k_acc_write(FrameDev F) {
   if (f) F.st_tl[F.scan_tmp[blockIdx.x] + ex] = i;
 }
 
-__global__ void __launch_bounds__(128) k_sector_refit(FrameDev F, KParams P) {
+__global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+  for (int i = queue_next(&F.cnt->queue[kQSectorRefit]); i < ns;
+       i = queue_next(&F.cnt->queue[kQSectorRefit])) {
     const int ti = F.st_tl[i];
     const int nk = F.tl_nkept[ti];
     const int* K = F.tl_kept + (long)ti * kMaxRows;  // outermost first
@@ -270,7 +271,7 @@ __device__ __forceinline__ float chi2_5(const float* d, const float* c) {
 // The pair test of the outer end of A against the inner end of B.
 __device__ __forceinline__ bool merge_test(const FrameDev& F, const KParams& P, int a, int b,
                                            float& chi2) {
-  const int half = P.n_sectors / 2;
+  const int half = P.n_phi;
   const int sa = F.st_sector[a], sb = F.st_sector[b];
   if (sa / half != sb / half) return false;
   const int ds = ((sb % half) - (sa % half) + half) % half;
@@ -299,7 +300,7 @@ __device__ __forceinline__ bool merge_test(const FrameDev& F, const KParams& P, 
 template <typename Fn>
 __device__ __forceinline__ void for_merge_candidates(const FrameDev& F, const KParams& P, int a,
                                                      Fn&& fn) {
-  const int half = P.n_sectors / 2;
+  const int half = P.n_phi;
   const int sa = F.st_sector[a];
   const int side = sa / half, ph = sa % half;
   const float* oe = F.st_oe + (long)a * kStateF;
@@ -317,10 +318,10 @@ __device__ __forceinline__ void for_merge_candidates(const FrameDev& F, const KP
   }
 }
 
-__global__ void __launch_bounds__(128) k_merge_best(FrameDev F, KParams P) {
+__global__ void __launch_bounds__(256) k_merge_best(FrameDev F, KParams P) {
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < ns; a += gridDim.x * blockDim.x) {
+  for (int a = queue_next(&F.cnt->queue[kQMerge]); a < ns; a = queue_next(&F.cnt->queue[kQMerge])) {
     if (!F.st_ok[a]) continue;
     const int keyA = F.st_key[a];
     int bb = -1;
@@ -487,7 +488,7 @@ __device__ __forceinline__ bool lin_goto(Lin& L, int sector, float x, const KPar
                                          StepJ* frec = nullptr) {
   if (rotated) *rotated = false;
   if (sector != L.sector) {
-    const int half = P.n_sectors / 2;
+    const int half = P.n_phi;
     const int ds = ((sector % half) - (L.sector % half) + half) % half;
     if (ds == 1) {
       if (!lin_rotate(L, 1, P, jrec)) return false;
@@ -571,11 +572,11 @@ __device__ __forceinline__ float zoff(const float* ie) {
   return ie[1] - ie[3] * sqrtf(ie[20] * ie[20] + ie[0] * ie[0]);
 }
 
-__global__ void __launch_bounds__(128) k_fit12(FrameDev F, KParams P, MapDev M) {
+__global__ void __launch_bounds__(256) k_fit12(FrameDev F, KParams P, MapDev M) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+  for (int f = queue_next(&F.cnt->queue[kQFit12]); f < nf; f = queue_next(&F.cnt->queue[kQFit12])) {
     const int head = F.ft_head[f];
     int last = head;
     while (F.st_next[last] >= 0) last = F.st_next[last];
@@ -745,11 +746,11 @@ __global__ void k_amb_mark(FrameDev F, KParams P, int round) {
 }
 
 // Iteration 3: inward with the surviving and re-attached clusters, simple cut.
-__global__ void __launch_bounds__(128) k_fit3(FrameDev F, KParams P, MapDev M) {
+__global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+  for (int f = queue_next(&F.cnt->queue[kQFit3]); f < nf; f = queue_next(&F.cnt->queue[kQFit3])) {
     F.ft_n[f] = 0;
     if (!F.ft_ok[f]) continue;
     const int ns = F.ft_nst[f];
@@ -928,7 +929,7 @@ __device__ __forceinline__ void lin_start2(Lin& L, const Trk<float>& s, const fl
 // (state, covariance, reference) every kCkptStride stations.
 __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps3) {
   const MapDev M = R.map;
-  const int half = P.n_sectors / 2;
+  const int half = P.n_phi;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < R.n_tracks;
        t += gridDim.x * blockDim.x) {
     R.ok[t] = 0;
@@ -1232,13 +1233,13 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_acc_count<<<nb_tl, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_tracks);
   k_acc_write<<<nb_tl, kBlock, 0, s>>>(F);
-  k_sector_refit<<<sms * 16, 128, 0, s>>>(F, P);
+  k_sector_refit<<<persistent_grid(F.lc, kLSectorRefit, sms), F.lc.block[kLSectorRefit], 0, s>>>(F, P);
   k_sector_zrange<<<P.n_sectors, 256, 0, s>>>(F, P);
   k_ie_hist<<<sms * 8, kBlock, 0, s>>>(F);
   int k = 7;
   k += scan_exclusive(F.ie_cnt, F.ie_first, (long)P.n_sectors * kMergeBins + 1, F.scan_tmp, s);
   k_ie_scatter<<<sms * 8, kBlock, 0, s>>>(F);
-  k_merge_best<<<sms * 16, 128, 0, s>>>(F, P);
+  k_merge_best<<<persistent_grid(F.lc, kLMerge, sms), F.lc.block[kLMerge], 0, s>>>(F, P);
   k_merge_link<<<sms * 8, kBlock, 0, s>>>(F);
   k_head_count<<<nb_tl, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_merged);
@@ -1249,7 +1250,7 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 
 int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const MapDev M = F.map;
-  k_fit12<<<sms * 16, 128, 0, s>>>(F, P, M);
+  k_fit12<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, M);
   int k = 1;
   for (int r = 0; r < P.cand_k; ++r) {
     k_amb_bid<<<sms * 8, kBlock, 0, s>>>(F, P, r);
@@ -1257,7 +1258,7 @@ int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
     k_amb_mark<<<sms * 8, kBlock, 0, s>>>(F, P, r);
     k += 3;
   }
-  k_fit3<<<sms * 16, 128, 0, s>>>(F, P, M);
+  k_fit3<<<persistent_grid(F.lc, kLFit3, sms), F.lc.block[kLFit3], 0, s>>>(F, P, M);
   return k + 1;
 }
 

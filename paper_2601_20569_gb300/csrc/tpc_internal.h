@@ -23,10 +23,22 @@ struct KParams {
   float merge_chi2, merge_dy, merge_dz, merge_zspan;
   float int_chi2, final_chi2, attach_margin, edge_margin, looper_qpt;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k;
-  int n_rows, n_sectors;
+  int n_rows, n_sectors;  // n_sectors: all sectors of the call (frames x sectors)
+  int n_phi;         // azimuthal sectors of one TPC half (sector % n_phi, side = sector / n_phi)
   float grid_dy;     // target y bin size [cm]
   float grid_occ;    // target clusters per bin
 };
+
+// Launch shape of the heavy per-item kernels (block size, blocks per SM),
+// chosen by the autotuner.
+enum LaunchSlot : int { kLTracklets = 0, kLSectorRefit, kLMerge, kLFit12, kLFit3, kLNum };
+struct LaunchCfg {
+  int block[kLNum];
+  int per_sm[kLNum];
+};
+
+// Work queues: counters of the dynamic item fetching (zeroed per call).
+enum QueueSlot : int { kQTracklets = 0, kQSectorRefit, kQMerge, kQFit12, kQFit3, kQNum };
 
 // Search grid of one (sector, row): bins iz*nY + iy, clusters of a bin are
 // contiguous in the sorted arrays.
@@ -73,7 +85,8 @@ struct Counters {
   int need_tracklets;
   int need_tracks;
   int n_out;         // output tracks
-  int pad[6];
+  int queue[kQNum];  // work-queue heads
+  int pad[1];
 };
 
 // Working set of one frame on the device.
@@ -187,6 +200,7 @@ struct FrameDev {
   int* attach;             // [n] input id space
   int* attach_key;         // [n] input id space
   MapDev map;              // correction map of this call
+  LaunchCfg lc;            // launch shapes of the heavy kernels
 };
 
 constexpr int kCkptStride = 16;                        // stations per checkpoint segment

@@ -119,10 +119,15 @@ extern "C" tpc_status tpc_links_noalloc(const tpc_geometry* geo, const tpc_optio
   derive(P, *opt, opt->bz, rx);
   P.n_rows = geo->n_rows;
   P.n_sectors = geo->n_sectors;
+  P.n_phi = geo->n_sectors / 2 > 0 ? geo->n_sectors / 2 : 1;
 
   const long n = cl->n;
   const long nrr = (long)geo->n_sectors * geo->n_rows;
   FrameDev F{};
+  for (int i = 0; i < kLNum; ++i) {
+    F.lc.block[i] = 128;
+    F.lc.per_sm[i] = 8;
+  }
   F.y = cl->y;
   F.z = cl->z;
   F.row = cl->row;

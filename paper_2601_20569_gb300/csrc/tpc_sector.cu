@@ -270,11 +270,12 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
   return best;
 }
 
-__global__ void __launch_bounds__(128) k_tracklets(FrameDev F, KParams P) {
+__global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+  for (int ti = queue_next(&F.cnt->queue[kQTracklets]); ti < nst;
+       ti = queue_next(&F.cnt->queue[kQTracklets])) {
     const int start = F.starts[ti];
     int* H = F.tl_hits + (long)ti * kMaxRows;
     // chain length and seed points (first, middle, last)
@@ -493,7 +494,7 @@ int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 }
 
 int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
-  k_tracklets<<<sms * 16, 128, 0, s>>>(F, P);
+  k_tracklets<<<persistent_grid(F.lc, kLTracklets, sms), F.lc.block[kLTracklets], 0, s>>>(F, P);
   return 1;
 }
 

@@ -86,9 +86,28 @@ __global__ void k_scan_partials(int* part, int nparts, int* total) {
   if (threadIdx.x == 0) *total = carry;
 }
 
+// Device-side work queue: each call hands the calling lanes the next item
+// indices of the queue (one atomic per warp), so uneven items (tracklets of
+// 3..150 rows, sectors of 10x different occupancy) balance dynamically across
+// a persistent grid.
+__device__ __forceinline__ int queue_next(int* q) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(q, __popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
 }  // namespace
 
 inline unsigned blocks_for(long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Persistent grid of a heavy kernel for launch slot `slot`.
+inline unsigned persistent_grid(const LaunchCfg& lc, int slot, int sms) {
+  return (unsigned)(sms * lc.per_sm[slot]);
+}
 
 }  // namespace TPC_NS
 }  // namespace tpc

@@ -54,6 +54,8 @@ class Options(ctypes.Structure):
         ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32), ("merge_max_gap", ctypes.c_int32),
         ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
+        ("max_frames", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
         ("cap_tracks", ctypes.c_int64),
     ]
@@ -124,7 +126,7 @@ def load():
 
 def make_options(opts: dict | TrackerOptions | None = None, *, mode: int = 0,
                  cap_clusters: int = 1 << 20, cap_tracklets: int = 0,
-                 cap_tracks: int = 0) -> Options:
+                 cap_tracks: int = 0, max_frames: int = 1, use_graphs: bool = False) -> Options:
     if opts is None:
         opts = TrackerOptions()
     d = opts.as_dict() if isinstance(opts, TrackerOptions) else dict(opts)
@@ -141,6 +143,12 @@ def make_options(opts: dict | TrackerOptions | None = None, *, mode: int = 0,
             o.cap_tracklets = int(cap_tracklets)
         elif name == "cap_tracks":
             o.cap_tracks = int(cap_tracks)
+        elif name == "max_frames":
+            o.max_frames = int(max_frames)
+        elif name == "use_graphs":
+            o.use_graphs = int(bool(use_graphs))
+        elif name == "reserved":
+            o.reserved = 0
         elif typ is ctypes.c_float:
             setattr(o, name, float(d[name]))
         else:
@@ -176,14 +184,15 @@ class Tracker:
 
     def __init__(self, row_x, opts: dict | TrackerOptions | None = None, *, mode: int = 0,
                  cap_clusters: int = 1 << 20, cap_tracklets: int = 0, cap_tracks: int = 0,
-                 bz: float | None = None):
+                 bz: float | None = None, max_frames: int = 1, use_graphs: bool = False):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("the tracker needs a CUDA device")
         self.lib = load()
         self.opts = make_options(opts, mode=mode, cap_clusters=cap_clusters,
-                                 cap_tracklets=cap_tracklets, cap_tracks=cap_tracks)
+                                 cap_tracklets=cap_tracklets, cap_tracks=cap_tracks,
+                                 max_frames=max_frames, use_graphs=use_graphs)
         self._row_x = np.ascontiguousarray(row_x, dtype=np.float32)
         geo = Geometry(36, len(self._row_x), self._row_x.ctypes.data)
         self._ctx = ctypes.c_void_p()
@@ -229,6 +238,71 @@ class Tracker:
         if rc:
             raise TpcError(rc, self.last_error(), needed.value)
         self._last = (out, n)
+        return out
+
+    def track_batch(self, frames, stream=None) -> Tracks:
+        """Track several frames in one pass; frames: list of (y, z, q, row, sector)
+        device tensors.  Tracks carry batch sectors (frame * 36 + sector) and batch
+        cluster ids (offset of the frame + id)."""
+        import torch
+
+        lib = self.lib
+        if not getattr(lib, "_batch_typed", False):
+            P = ctypes.POINTER
+            lib.tpc_track_batch.argtypes = [ctypes.c_void_p, P(Clusters), ctypes.c_int32,
+                                            P(Tracks), ctypes.c_void_p, P(ctypes.c_int64)]
+            lib.tpc_track_batch.restype = ctypes.c_int
+            lib.tpc_autotune.argtypes = [ctypes.c_void_p, P(Clusters), ctypes.c_int32,
+                                         ctypes.c_void_p]
+            lib.tpc_autotune.restype = ctypes.c_int
+            lib.tpc_launch_config.argtypes = [ctypes.c_void_p, ctypes.c_int32,
+                                              P(ctypes.c_char_p), P(ctypes.c_int32),
+                                              P(ctypes.c_int32)]
+            lib.tpc_launch_config.restype = ctypes.c_int
+            lib._batch_typed = True
+        arr = (Clusters * len(frames))()
+        n = 0
+        for i, (y, z, q, row, sector) in enumerate(frames):
+            arr[i] = Clusters(int(y.shape[0]), y.data_ptr(), z.data_ptr(),
+                              q.data_ptr() if q is not None else None, row.data_ptr(),
+                              sector.data_ptr())
+            n += int(y.shape[0])
+        out = Tracks()
+        needed = ctypes.c_int64(0)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = lib.tpc_track_batch(self._ctx, arr, len(frames), ctypes.byref(out),
+                                 ctypes.c_void_p(s.cuda_stream), ctypes.byref(needed))
+        if rc:
+            raise TpcError(rc, self.last_error(), needed.value)
+        self._last = (out, n)
+        return out
+
+    def autotune(self, frames, stream=None) -> list[dict]:
+        """Pick block size / blocks per SM of the heavy kernels on these frames."""
+        import torch
+
+        self.track_batch(frames[:1], stream)  # binds the argtypes
+        arr = (Clusters * len(frames))()
+        for i, (y, z, q, row, sector) in enumerate(frames):
+            arr[i] = Clusters(int(y.shape[0]), y.data_ptr(), z.data_ptr(),
+                              q.data_ptr() if q is not None else None, row.data_ptr(),
+                              sector.data_ptr())
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = self.lib.tpc_autotune(self._ctx, arr, len(frames), ctypes.c_void_p(s.cuda_stream))
+        if rc:
+            raise TpcError(rc, self.last_error())
+        return self.launch_config()
+
+    def launch_config(self) -> list[dict]:
+        out = []
+        for slot in range(16):
+            name = ctypes.c_char_p()
+            b = ctypes.c_int32()
+            q = ctypes.c_int32()
+            if self.lib.tpc_launch_config(self._ctx, slot, ctypes.byref(name), ctypes.byref(b),
+                                          ctypes.byref(q)):
+                break
+            out.append({"kernel": name.value.decode(), "block": b.value, "blocks_per_sm": q.value})
         return out
 
     def result_attach(self):
