@@ -1531,8 +1531,10 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   const int nst = (int)ST.size();
   // a7: candidate pairs by sector, mutual best
   const int half = P.n_sectors / 2;
-  std::vector<std::vector<int>> by_sector(P.n_sectors);
-  for (int i = 0; i < nst; ++i) by_sector[ST[i].sector].push_back(i);
+  // candidate lists by (sector, innermost row); the pair test requires
+  // 1 <= rmin(B) - rmax(A) <= merge_max_gap, so only those rows are visited
+  std::vector<std::vector<int>> by_sector((size_t)P.n_sectors * P.n_rows);
+  for (int i = 0; i < nst; ++i) by_sector[(size_t)ST[i].sector * P.n_rows + ST[i].rmin].push_back(i);
   std::vector<int> bestB(nst, -1), bestA(nst, -1);
   std::vector<Real> chiB(nst, 0), chiA(nst, 0);
   for (int a = 0; a < nst; ++a) {
@@ -1540,7 +1542,8 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     const int side = sa / half, ph = sa % half;
     for (int d : {0, 1, half - 1}) {
       const int sb = side * half + (ph + d) % half;
-      for (int b : by_sector[sb]) {
+      for (int rb = ST[a].rmax + 1; rb <= ST[a].rmax + P.merge_max_gap && rb < P.n_rows; ++rb)
+      for (int b : by_sector[(size_t)sb * P.n_rows + rb]) {
         if (b == a) continue;
         Real chi2;
         if (!merge_test(P, ST[a], ST[b], chi2)) continue;

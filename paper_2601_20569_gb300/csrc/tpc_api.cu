@@ -280,7 +280,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.cnt, 1);
   // a7
   const long T = F.cap_tl;
-  const long nmb = nsec_all * kMergeBins;
+  const long nmb = nrr * kMergeZ;
   ok &= dalloc(ctx, &F.st_tl, T);
   ok &= dalloc(ctx, &F.st_ok, T);
   ok &= dalloc(ctx, &F.st_key, T);
@@ -399,7 +399,7 @@ tpc_status enqueue_chain(tpc_ctx* ctx, FrameDev& F, const KParams& Pc, cudaStrea
     CK(cudaMemsetAsync(F.attach, 0xFF, sizeof(int) * n, s));
     CK(cudaMemsetAsync(F.attach_key, 0x7F, sizeof(int) * n, s));
   }
-  CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * ((long)Pc.n_sectors * kMergeBins + 1), s));
+  CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * (nrr * kMergeZ + 1), s));
   CK(cudaMemsetAsync(F.out_offset, 0, sizeof(int), s));
   long k = 0;
   if (events) CK(cudaEventRecord(ctx->ev[0], s));

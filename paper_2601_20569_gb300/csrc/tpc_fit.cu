@@ -215,20 +215,23 @@ __global__ void k_sector_zrange(FrameDev F, KParams P) {
     float zl = 0.0f, zh = 1.0f;
     if (hi >= lo && hi != 0u) { zl = o2f(lo); zh = o2f(hi); }
     F.sec_zlo[s] = zl;
-    F.sec_zinv[s] = zh > zl ? (float)kMergeBins / (zh - zl) : 0.0f;
+    F.sec_zinv[s] = zh > zl ? (float)kMergeZ / (zh - zl) : 0.0f;
   }
 }
 
-__device__ __forceinline__ int merge_bin(const FrameDev& F, int s, float z) {
-  return s * kMergeBins + clampi((int)floorf((z - F.sec_zlo[s]) * F.sec_zinv[s]), 0, kMergeBins - 1);
+// Merge candidate index: inner ends binned by (sector, innermost row, z).
+__device__ __forceinline__ int merge_bin(const FrameDev& F, int nrows, int s, int r, float z) {
+  return (s * nrows + r) * kMergeZ +
+         clampi((int)floorf((z - F.sec_zlo[s]) * F.sec_zinv[s]), 0, kMergeZ - 1);
 }
 
-__global__ void k_ie_hist(FrameDev F) {
+__global__ void k_ie_hist(FrameDev F, KParams P) {
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
     if (!F.st_ok[i]) { F.ie_bin[i] = -1; continue; }
-    const int b = merge_bin(F, F.st_sector[i], F.st_ie[(long)i * kStateF + 1]);
+    const int b = merge_bin(F, P.n_rows, F.st_sector[i], F.st_rmin[i],
+                            F.st_ie[(long)i * kStateF + 1]);
     F.ie_bin[i] = b;
     F.ie_slot[i] = atomicAdd(&F.ie_cnt[b], 1);
   }
@@ -306,14 +309,21 @@ __device__ __forceinline__ void for_merge_candidates(const FrameDev& F, const KP
   const float* oe = F.st_oe + (long)a * kStateF;
   const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
   const int dsl[3] = {0, 1, half - 1};
+  // the pair test needs 1 <= rmin(B) - rmax(A) <= merge_max_gap: only those
+  // rows of the index are visited
+  const int r0 = F.st_rmax[a] + 1;
+  const int r1 = min(F.st_rmax[a] + P.merge_max_gap, P.n_rows - 1);
+  const float m = 0.01f;
   for (int q = 0; q < 3; ++q) {
     const int sb = side * half + (ph + dsl[q]) % half;
-    const float m = 0.01f;
-    const int b0 = merge_bin(F, sb, oe[1] - zwin - m), b1 = merge_bin(F, sb, oe[1] + zwin + m);
-    const int lo = F.ie_first[b0], hi = F.ie_first[b1 + 1];
-    for (int k = lo; k < hi; ++k) {
-      const int b = F.ie_idx[k];
-      if (b != a) fn(b);
+    for (int rb = r0; rb <= r1; ++rb) {
+      const int b0 = merge_bin(F, P.n_rows, sb, rb, oe[1] - zwin - m);
+      const int b1 = merge_bin(F, P.n_rows, sb, rb, oe[1] + zwin + m);
+      const int lo = F.ie_first[b0], hi = F.ie_first[b1 + 1];
+      for (int k = lo; k < hi; ++k) {
+        const int b = F.ie_idx[k];
+        if (b != a) fn(b);
+      }
     }
   }
 }
@@ -1235,9 +1245,10 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_acc_write<<<nb_tl, kBlock, 0, s>>>(F);
   k_sector_refit<<<persistent_grid(F.lc, kLSectorRefit, sms), F.lc.block[kLSectorRefit], 0, s>>>(F, P);
   k_sector_zrange<<<P.n_sectors, 256, 0, s>>>(F, P);
-  k_ie_hist<<<sms * 8, kBlock, 0, s>>>(F);
+  k_ie_hist<<<sms * 8, kBlock, 0, s>>>(F, P);
   int k = 7;
-  k += scan_exclusive(F.ie_cnt, F.ie_first, (long)P.n_sectors * kMergeBins + 1, F.scan_tmp, s);
+  k += scan_exclusive(F.ie_cnt, F.ie_first, (long)P.n_sectors * P.n_rows * kMergeZ + 1,
+                      F.scan_tmp, s);
   k_ie_scatter<<<sms * 8, kBlock, 0, s>>>(F);
   k_merge_best<<<persistent_grid(F.lc, kLMerge, sms), F.lc.block[kLMerge], 0, s>>>(F, P);
   k_merge_link<<<sms * 8, kBlock, 0, s>>>(F);

@@ -61,7 +61,7 @@ enum : int {
 };
 
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
-constexpr int kMergeBins = 2048; // z bins per sector for merge candidates
+constexpr int kMergeZ = 64;      // z bins per (sector, row) of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 
 // Distortion map as seen by the kernels.
@@ -153,8 +153,8 @@ struct FrameDev {
   int* st_bestB;
   float* st_bestchi;
   unsigned long long* st_bestA;
-  int* ie_cnt;             // [n_sectors*kMergeBins]
-  int* ie_first;           // [n_sectors*kMergeBins + 1]
+  int* ie_cnt;             // [n_sectors*n_rows*kMergeZ]
+  int* ie_first;           // [n_sectors*n_rows*kMergeZ + 1]
   int* ie_slot;            // [cap_tl]
   int* ie_bin;             // [cap_tl]
   int* ie_idx;             // [cap_tl] sector tracks sorted by (sector, z bin)
