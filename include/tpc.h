@@ -43,7 +43,9 @@ extern "C" {
 typedef enum {
   TPC_OK = 0,
   TPC_ERR_INVALID_ARG = 1,   /* null pointer, bad size or option */
-  TPC_ERR_INVALID_INPUT = 2, /* NaN/Inf coordinate, row >= n_rows, sector >= n_sectors */
+  TPC_ERR_INVALID_INPUT = 2, /* NaN/Inf coordinate, row >= n_rows, sector >= n_sectors,
+                                or more than 1024 clusters in one search-grid bin (many
+                                clusters at one point of a row) */
   TPC_ERR_CAPACITY = 3,      /* an internal buffer is too small; *needed reports the size */
   TPC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
   TPC_ERR_OOM = 5,           /* device allocation failed */

@@ -61,7 +61,7 @@ struct tpc_ctx {
   float* by = nullptr;
   float* bz = nullptr;
   uint8_t* brow = nullptr;
-  uint8_t* bsec = nullptr;
+  uint16_t* bsec = nullptr;
   // graph replay
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -427,7 +427,8 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   long launches = 0;
   const bool graph = ctx->opt.use_graphs && !ctx->prof;
   if (graph) {
-    GraphKey key{F.y, F.z, F.row, F.sector, F.n, nf, F.map.c, ctx->lc_version};
+    GraphKey key{F.y, F.z, F.row, F.bsector ? (const void*)F.bsector : (const void*)F.sector, F.n,
+                 nf, F.map.c, ctx->lc_version};
     if (!ctx->graph_exec || std::memcmp(&key, &ctx->graph_key, sizeof key) != 0) {
       if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
       ctx->graph_exec = nullptr;
@@ -473,6 +474,8 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   const Counters& c = ctx->host_cnt;
   std::memset(out, 0, sizeof(*out));
   if (c.err & kErrInput) return fail(ctx, TPC_ERR_INVALID_INPUT, "invalid cluster (NaN/Inf, row or sector out of range)");
+  if (c.err & kErrDense)
+    return fail(ctx, TPC_ERR_INVALID_INPUT, "more than %d clusters in one search bin", kMaxBinOcc);
   if (c.err & kErrCapBins) {
     if (needed) *needed = c.n_bins;
     return fail(ctx, TPC_ERR_CAPACITY, "grid bins %d exceed capacity %ld", c.n_bins, F.cap_bins);
@@ -508,9 +511,11 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   return TPC_OK;
 }
 
-__global__ void k_sector_offset(const uint8_t* in, uint8_t* out, long n, int add) {
+// Batch sector of each cluster of one frame; a sector outside the frame's
+// range maps to 0xFFFF so that the grid build reports the bad input.
+__global__ void k_sector_offset(const uint8_t* in, uint16_t* out, long n, int nsec, int add) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (uint8_t)min(255, (int)in[i] + add);
+  if (i < n) out[i] = in[i] < nsec ? (uint16_t)(in[i] + add) : (uint16_t)0xFFFF;
 }
 
 }  // namespace
@@ -534,6 +539,7 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
   F.z = cl->z;
   F.row = cl->row;
   F.sector = cl->sector;
+  F.bsector = nullptr;
   F.n = cl->n;
   return run_chain(ctx, F, 1, (cudaStream_t)cuda_stream, out, needed);
 }
@@ -567,15 +573,16 @@ tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_f
     CK(cudaMemcpyAsync(ctx->by + off, frames[f].y, 4 * n, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(ctx->bz + off, frames[f].z, 4 * n, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(ctx->brow + off, frames[f].row, n, cudaMemcpyDeviceToDevice, s));
-    k_sector_offset<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(frames[f].sector, ctx->bsec + off,
-                                                                n, f * ctx->n_sectors);
+    k_sector_offset<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        frames[f].sector, ctx->bsec + off, n, ctx->n_sectors, f * ctx->n_sectors);
     off += n;
   }
   CK(cudaGetLastError());
   F.y = ctx->by;
   F.z = ctx->bz;
   F.row = ctx->brow;
-  F.sector = ctx->bsec;
+  F.sector = nullptr;
+  F.bsector = ctx->bsec;
   F.n = total;
   return run_chain(ctx, F, n_frames, s, out, needed);
 }

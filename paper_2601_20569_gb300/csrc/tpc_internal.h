@@ -58,7 +58,14 @@ enum : int {
   kErrCapTracks = 8,
   kErrCapRefs = 16,
   kErrCapCand = 32,
+  kErrDense = 64,    // a search bin holds more than kMaxBinOcc clusters
 };
+
+// Largest number of clusters one search bin may hold.  Bins are sized for a
+// few clusters each; a frame that piles more than this into one bin (many
+// clusters at one point of a row) is rejected as invalid input, which keeps
+// the per-bin ordering and the window searches bounded.
+constexpr int kMaxBinOcc = 1024;
 
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kMergeZ = 64;      // z bins per (sector, row) of the merge candidate index
@@ -96,6 +103,7 @@ struct FrameDev {
   const float* z;
   const uint8_t* row;
   const uint8_t* sector;
+  const uint16_t* bsector; // batch calls: frame * sectors per frame + sector (else null)
   long n;
   const float* row_x;  // [n_rows]
   // a1 grid

@@ -180,7 +180,7 @@ extern "C" tpc_status tpc_links_noalloc(const tpc_geometry* geo, const tpc_optio
   if (cudaMemcpyAsync(&hc, F.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return TPC_ERR_CUDA;
-  if (hc.err & kErrInput) return TPC_ERR_INVALID_INPUT;
+  if (hc.err & (kErrInput | kErrDense)) return TPC_ERR_INVALID_INPUT;
   if (hc.err & kErrCapBins) return TPC_ERR_CAPACITY;
   return TPC_OK;
 }

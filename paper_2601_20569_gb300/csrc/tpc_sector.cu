@@ -18,10 +18,15 @@ namespace TPC_NS {
 namespace {
 
 // ------------------------------------------------------------------ a1 grid
+// Sector of input cluster i (batch sector in a multi-frame call).
+__device__ __forceinline__ int sector_of(const FrameDev& F, long i) {
+  return F.bsector ? (int)F.bsector[i] : (int)F.sector[i];
+}
+
 __global__ void k_row_stats(FrameDev F, KParams P) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n) return;
-  const int r = F.row[i], s = F.sector[i];
+  const int r = F.row[i], s = sector_of(F, i);
   const float y = F.y[i], z = F.z[i];
   if (r >= P.n_rows || s >= P.n_sectors || !isfinite(y) || !isfinite(z)) {
     atomicOr(&F.cnt->err, kErrInput);
@@ -91,7 +96,7 @@ __global__ void k_row_grid(FrameDev F, KParams P) {
 __global__ void k_bin_hist(FrameDev F, KParams P) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n || F.cnt->err) return;
-  const int rr = F.sector[i] * P.n_rows + F.row[i];
+  const int rr = sector_of(F, i) * P.n_rows + F.row[i];
   const RowGrid g = F.rows[rr];
   const int iy = bin_of(F.y[i], g.y0, g.invDy, g.nY);
   const int iz = bin_of(F.z[i], g.z0, g.invDz, g.nZ);
@@ -107,7 +112,7 @@ __global__ void k_scatter(FrameDev F, KParams P) {
   F.sy[pos] = F.y[i];
   F.sz[pos] = F.z[i];
   F.sid[pos] = (int)i;
-  F.srow[pos] = (uint16_t)(F.sector[i] * P.n_rows + F.row[i]);
+  F.srow[pos] = (uint16_t)(sector_of(F, i) * P.n_rows + F.row[i]);
 }
 
 // Order the clusters of each bin by input id (deterministic layout).
@@ -116,6 +121,10 @@ __global__ void k_bin_sort(FrameDev F) {
   if (F.cnt->err) return;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     const int lo = F.bin_first[b], hi = F.bin_first[b + 1];
+    if (hi - lo > kMaxBinOcc) {
+      atomicOr(&F.cnt->err, kErrDense);
+      continue;
+    }
     for (int k = lo + 1; k < hi; ++k) {
       const int id = F.sid[k];
       const float y = F.sy[k], z = F.sz[k];

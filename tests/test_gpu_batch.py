@@ -100,6 +100,10 @@ def test_full_size_frames_sampled_sector_parity():
     dev = [tb.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
     out = tb.track_batch(dev)
     assert out.n_tracks > 100000
+    # real frames stay far below the 1024-cluster limit of one search bin
+    occ = np.diff(tb.debug("bin_first"))
+    print(f"search-bin occupancy: mean {occ.mean():.2f}, max {occ.max()}")
+    assert occ.max() < 256
     sid = tb.debug("sid")
     starts = tb.debug("starts")
     tl_n = tb.debug("tl_n")
@@ -113,7 +117,8 @@ def test_full_size_frames_sampled_sector_parity():
         # GPU tracklets of these sectors, keyed by frame-local start id
         gid = sid[starts] - offsets[fi]
         mine = (gid >= 0) & (gid < f.n)
-        mine &= np.isin(np.where(mine, f.sector[np.clip(gid, 0, f.n - 1)], -1), sectors)
+        sec = f.sector[np.clip(gid, 0, f.n - 1)].astype(np.int64)
+        mine &= np.isin(np.where(mine, sec, -1), sectors)
         g = {int(gid[i]): i for i in np.nonzero(mine)[0]}
         r = {int(sel[s]): j for j, s in enumerate(ref["tl_start"])}
         assert set(g) == set(r)
@@ -124,3 +129,41 @@ def test_full_size_frames_sampled_sector_parity():
             assert acc[i] == ref["tl_accept"][j]
             if tl_n[i]:
                 assert np.array_equal(par[i].view(np.uint32), rpar[j].view(np.uint32))
+
+
+def test_nine_frames_batch_sectors_beyond_255():
+    """Nine frames: batch sectors reach 9 * 36 - 1 = 323, past an 8-bit id;
+    every frame's tracks equal those of the frame tracked alone."""
+    from paper_2601_20569_gb300 import tpc
+
+    frames = [synth.generate("central_event", n_primaries=120, seed=40 + k) for k in range(9)]
+    ntot = sum(f.n for f in frames)
+    opts = TrackerOptions().as_dict()
+    tb = tpc.Tracker(RX, opts, mode=0, cap_clusters=ntot, max_frames=9)
+    dev = [tb.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
+    tb.track_batch(dev)
+    res = host(tb)
+    assert int(res["sector"].max()) >= 8 * 36
+    offsets = np.concatenate([[0], np.cumsum([f.n for f in frames])])
+    batch = tracks_by_frame(res, offsets)
+    ts = tpc.Tracker(RX, opts, mode=0, cap_clusters=max(f.n for f in frames))
+    for i in range(len(frames)):
+        ts.track(*dev[i])
+        assert batch.get(i, {}) == single_tracks(host(ts)), i
+
+
+def test_batch_rejects_sector_outside_frame():
+    """A sector id >= 36 in one frame must not alias a sector of the next
+    frame: the batch call reports invalid input."""
+    from paper_2601_20569_gb300 import tpc
+
+    frames = [synth.generate("one_sector", n_primaries=20, seed=s) for s in (1, 2)]
+    sec = frames[0].sector.copy()
+    sec[7] = 40
+    tb = tpc.Tracker(RX, TrackerOptions(), mode=0, cap_clusters=sum(f.n for f in frames),
+                     max_frames=2)
+    dev = [tb.to_device(frames[0].y, frames[0].z, frames[0].q, frames[0].row, sec),
+           tb.to_device(frames[1].y, frames[1].z, frames[1].q, frames[1].row, frames[1].sector)]
+    with pytest.raises(tpc.TpcError) as e:
+        tb.track_batch(dev)
+    assert e.value.status == 2

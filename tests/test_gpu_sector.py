@@ -183,3 +183,20 @@ def test_capacity_errors_report_needed_size():
     with pytest.raises(tpc.TpcError) as e:
         tr2.track(*tr2.to_device(f.y, f.z, f.q, f.row, f.sector))
     assert e.value.status == 3 and e.value.needed > 5
+
+
+def test_clusters_piled_on_one_point_rejected():
+    """Thousands of clusters at one point of a row cannot come from the
+    detector; the grid build rejects the frame instead of ordering one huge
+    bin."""
+    from paper_2601_20569_gb300 import tpc
+
+    f = synth.generate("one_sector", n_primaries=20)
+    n = 5000
+    y = np.concatenate([f.y, np.full(n, 1.5, np.float32)])
+    z = np.concatenate([f.z, np.full(n, 10.0, np.float32)])
+    row = np.concatenate([f.row, np.full(n, 30, np.uint8)])
+    sec = np.concatenate([f.sector, np.full(n, f.sector[0], np.uint8)])
+    with pytest.raises(tpc.TpcError) as e:
+        _run(y, z, row, sec)
+    assert e.value.status == 2
