@@ -316,6 +316,10 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   F.cap_ft = opt->cap_tracks > 0 ? opt->cap_tracks : n / 40 + 4096;
   const long FT = F.cap_ft;
   ok &= dalloc(ctx, &F.ft_head, FT);
+  ok &= dalloc(ctx, &F.ft_order, FT);
+  ok &= dalloc(ctx, &F.ft_obucket, FT);
+  ok &= dalloc(ctx, &F.ft_oslot, FT);
+  ok &= dalloc(ctx, &F.ord_cnt, kOrdBuckets);
   ok &= dalloc(ctx, &F.ft_key, FT);
   ok &= dalloc(ctx, &F.ft_ok, FT);
   ok &= dalloc(ctx, &F.ft_nst, FT);
@@ -400,6 +404,7 @@ tpc_status enqueue_chain(tpc_ctx* ctx, FrameDev& F, const KParams& Pc, cudaStrea
     CK(cudaMemsetAsync(F.attach_key, 0x7F, sizeof(int) * n, s));
   }
   CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * (nrr * kMergeZ + 1), s));
+  CK(cudaMemsetAsync(F.ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
   CK(cudaMemsetAsync(F.out_offset, 0, sizeof(int), s));
   long k = 0;
   if (events) CK(cudaEventRecord(ctx->ev[0], s));
@@ -552,6 +557,8 @@ tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_f
   if (n_frames > ctx->max_frames)
     return fail(ctx, TPC_ERR_INVALID_ARG, "%d frames exceed the context's max_frames %d", n_frames,
                 ctx->max_frames);
+  // one frame: batch sectors equal the frame's own, no concatenation needed
+  if (n_frames == 1) return tpc_track_timeframe(ctx, frames, out, cuda_stream, needed);
   long total = 0;
   for (int f = 0; f < n_frames; ++f) {
     if (frames[f].n < 0 || (frames[f].n > 0 && (!frames[f].y || !frames[f].z || !frames[f].row ||

@@ -382,7 +382,10 @@ __global__ void k_head_count(FrameDev F) {
   if (threadIdx.x == 0) F.scan_tmp[blockIdx.x] = tot;
 }
 
-__global__ void k_head_write(FrameDev F) {
+// Head list plus the scheduling bucket of each chain: whether its fit
+// updates run in FP64 (|q/pT| at the inner end above looper_qpt) and its
+// cluster count.  The bucket only orders the work; no result depends on it.
+__global__ void k_head_write(FrameDev F, KParams P) {
   __shared__ int sh[32];
   const int ns = F.cnt->n_tracks;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -390,7 +393,34 @@ __global__ void k_head_write(FrameDev F) {
   int tot;
   const int ex = block_exscan(f, sh, &tot);
   const int pos = F.scan_tmp[blockIdx.x] + ex;
-  if (f && pos < F.cap_ft) F.ft_head[pos] = i;
+  if (f && pos < F.cap_ft) {
+    F.ft_head[pos] = i;
+    int len = 0;
+    for (int c = i; c >= 0; c = F.st_next[c]) len += F.tl_nkept[F.st_tl[c]];
+    const float q = fabsf(F.st_ie[(long)i * kStateF + 4]);
+    const int looper = (P.looper_qpt > 0.0f && q > P.looper_qpt) ? 1 : 0;
+    const int b = (1 - looper) * kOrdLen + (kOrdLen - 1 - min(kOrdLen - 1, len >> 2));
+    F.ft_obucket[pos] = b;
+    F.ft_oslot[pos] = atomicAdd(&F.ord_cnt[b], 1);
+  }
+}
+
+// ft_order: fit tracks grouped by bucket (bucket starts from a scan of the
+// per-bucket counts, done by every block in shared memory).
+__global__ void k_order_write(FrameDev F) {
+  __shared__ int base[kOrdBuckets];
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < kOrdBuckets; ++b) {
+      base[b] = acc;
+      acc += F.ord_cnt[b];
+    }
+  }
+  __syncthreads();
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x)
+    F.ft_order[base[F.ft_obucket[f]] + F.ft_oslot[f]] = f;
 }
 
 __global__ void k_head_check(FrameDev F) {
@@ -586,7 +616,8 @@ __global__ void __launch_bounds__(256) k_fit12(FrameDev F, KParams P, MapDev M) 
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int f = queue_next(&F.cnt->queue[kQFit12]); f < nf; f = queue_next(&F.cnt->queue[kQFit12])) {
+  for (int q = queue_next(&F.cnt->queue[kQFit12]); q < nf; q = queue_next(&F.cnt->queue[kQFit12])) {
+    const int f = F.ft_order[q];
     const int head = F.ft_head[f];
     int last = head;
     while (F.st_next[last] >= 0) last = F.st_next[last];
@@ -760,7 +791,8 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int f = queue_next(&F.cnt->queue[kQFit3]); f < nf; f = queue_next(&F.cnt->queue[kQFit3])) {
+  for (int q = queue_next(&F.cnt->queue[kQFit3]); q < nf; q = queue_next(&F.cnt->queue[kQFit3])) {
+    const int f = F.ft_order[q];
     F.ft_n[f] = 0;
     if (!F.ft_ok[f]) continue;
     const int ns = F.ft_nst[f];
@@ -1254,9 +1286,10 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_merge_link<<<sms * 8, kBlock, 0, s>>>(F);
   k_head_count<<<nb_tl, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_merged);
-  k_head_write<<<nb_tl, kBlock, 0, s>>>(F);
+  k_head_write<<<nb_tl, kBlock, 0, s>>>(F, P);
   k_head_check<<<1, 1, 0, s>>>(F);
-  return k + 7;
+  k_order_write<<<sms * 4, kBlock, 0, s>>>(F);
+  return k + 8;
 }
 
 int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

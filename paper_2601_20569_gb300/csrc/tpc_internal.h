@@ -70,6 +70,11 @@ constexpr int kMaxBinOcc = 1024;
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kMergeZ = 64;      // z bins per (sector, row) of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
+// Scheduling buckets of the fit kernels: loopers (FP64 updates) first, then
+// the rest, each from the longest chain to the shortest, so that the tracks
+// of one warp take the same update path and run about as long.
+constexpr int kOrdLen = 64;
+constexpr int kOrdBuckets = 2 * kOrdLen;
 
 // Distortion map as seen by the kernels.
 struct MapDev {
@@ -172,6 +177,10 @@ struct FrameDev {
   // a9/a10 fit tracks (capacity cap_ft)
   long cap_ft;
   int* ft_head;            // first sector track of the chain
+  int* ft_order;           // [cap_ft] order in which the fit kernels take the tracks
+  int* ft_obucket;         // [cap_ft] scheduling bucket of each fit track
+  int* ft_oslot;           // [cap_ft] place within the bucket
+  int* ord_cnt;            // [kOrdBuckets] tracks per scheduling bucket
   int* ft_key;
   int* ft_ok;
   int* ft_nst;             // stations
