@@ -270,6 +270,13 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.tl_chi2, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_n, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_rlo, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_len, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_mid, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_end, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_order, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_obucket, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_oslot, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_ord_cnt, kOrdBuckets);
   ok &= dalloc(ctx, &F.tl_rhi, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_hits, F.cap_tl * kMaxRows);
   ok &= dalloc(ctx, &F.owner_key, n);
@@ -282,6 +289,10 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   const long T = F.cap_tl;
   const long nmb = nrr * kMergeZ;
   ok &= dalloc(ctx, &F.st_tl, T);
+  ok &= dalloc(ctx, &F.st_order, T);
+  ok &= dalloc(ctx, &F.st_obucket, T);
+  ok &= dalloc(ctx, &F.st_oslot, T);
+  ok &= dalloc(ctx, &F.st_ord_cnt, kOrdBuckets);
   ok &= dalloc(ctx, &F.st_ok, T);
   ok &= dalloc(ctx, &F.st_key, T);
   ok &= dalloc(ctx, &F.st_sector, T);
@@ -405,6 +416,8 @@ tpc_status enqueue_chain(tpc_ctx* ctx, FrameDev& F, const KParams& Pc, cudaStrea
   }
   CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * (nrr * kMergeZ + 1), s));
   CK(cudaMemsetAsync(F.ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
+  CK(cudaMemsetAsync(F.tl_ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
+  CK(cudaMemsetAsync(F.st_ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
   CK(cudaMemsetAsync(F.out_offset, 0, sizeof(int), s));
   long k = 0;
   if (events) CK(cudaEventRecord(ctx->ev[0], s));

@@ -151,15 +151,23 @@ __global__ void k_acc_write(FrameDev F) {
   const int f = (!F.cnt->err && i < nst && F.tl_acc[i]) ? 1 : 0;
   int tot;
   const int ex = block_exscan(f, sh, &tot);
-  if (f) F.st_tl[F.scan_tmp[blockIdx.x] + ex] = i;
+  if (f) {
+    const int j = F.scan_tmp[blockIdx.x] + ex;
+    F.st_tl[j] = i;
+    // scheduling bucket of the sector refit: most clusters first
+    const int b = kOrdBuckets - 1 - min(kOrdBuckets - 1, F.tl_nkept[i]);
+    F.st_obucket[j] = b;
+    F.st_oslot[j] = atomicAdd(&F.st_ord_cnt[b], 1);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int i = queue_next(&F.cnt->queue[kQSectorRefit]); i < ns;
-       i = queue_next(&F.cnt->queue[kQSectorRefit])) {
+  for (int q = queue_next(&F.cnt->queue[kQSectorRefit]); q < ns;
+       q = queue_next(&F.cnt->queue[kQSectorRefit])) {
+    const int i = F.st_order[q];
     const int ti = F.st_tl[i];
     const int nk = F.tl_nkept[ti];
     const int* K = F.tl_kept + (long)ti * kMaxRows;  // outermost first
@@ -403,24 +411,6 @@ __global__ void k_head_write(FrameDev F, KParams P) {
     F.ft_obucket[pos] = b;
     F.ft_oslot[pos] = atomicAdd(&F.ord_cnt[b], 1);
   }
-}
-
-// ft_order: fit tracks grouped by bucket (bucket starts from a scan of the
-// per-bucket counts, done by every block in shared memory).
-__global__ void k_order_write(FrameDev F) {
-  __shared__ int base[kOrdBuckets];
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int b = 0; b < kOrdBuckets; ++b) {
-      base[b] = acc;
-      acc += F.ord_cnt[b];
-    }
-  }
-  __syncthreads();
-  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
-  if (F.cnt->err) return;
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x)
-    F.ft_order[base[F.ft_obucket[f]] + F.ft_oslot[f]] = f;
 }
 
 __global__ void k_head_check(FrameDev F) {
@@ -1275,6 +1265,8 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_acc_count<<<nb_tl, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_tracks);
   k_acc_write<<<nb_tl, kBlock, 0, s>>>(F);
+  k_order_scatter<<<sms * 4, kBlock, 0, s>>>(F.st_obucket, F.st_oslot, F.st_ord_cnt,
+                                             &F.cnt->n_tracks, F.cap_tl, &F.cnt->err, F.st_order);
   k_sector_refit<<<persistent_grid(F.lc, kLSectorRefit, sms), F.lc.block[kLSectorRefit], 0, s>>>(F, P);
   k_sector_zrange<<<P.n_sectors, 256, 0, s>>>(F, P);
   k_ie_hist<<<sms * 8, kBlock, 0, s>>>(F, P);
@@ -1288,8 +1280,9 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_merged);
   k_head_write<<<nb_tl, kBlock, 0, s>>>(F, P);
   k_head_check<<<1, 1, 0, s>>>(F);
-  k_order_write<<<sms * 4, kBlock, 0, s>>>(F);
-  return k + 8;
+  k_order_scatter<<<sms * 4, kBlock, 0, s>>>(F.ft_obucket, F.ft_oslot, F.ord_cnt, &F.cnt->n_merged,
+                                             F.cap_ft, &F.cnt->err, F.ft_order);
+  return k + 9;
 }
 
 int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

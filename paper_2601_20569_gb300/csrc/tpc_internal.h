@@ -144,6 +144,13 @@ struct FrameDev {
   int* tl_rlo;
   int* tl_rhi;
   int* tl_hits;            // [cap_tl*kMaxRows] row-indexed sorted cluster or -1
+  int* tl_len;             // [cap_tl] CA chain length from the start hit
+  int* tl_mid;             // [cap_tl] middle chain cluster (seed point)
+  int* tl_end;             // [cap_tl] last chain cluster (seed point)
+  int* tl_order;           // [cap_tl] order in which the constructor takes the tracklets
+  int* tl_obucket;         // [cap_tl] scheduling bucket
+  int* tl_oslot;           // [cap_tl] place within the bucket
+  int* tl_ord_cnt;         // [kOrdBuckets]
   // a6
   unsigned long long* owner_key;  // [n] sorted index space
   int* tl_acc;
@@ -154,6 +161,10 @@ struct FrameDev {
 
   // a7 sector tracks (capacity cap_tl)
   int* st_tl;              // tracklet index of each accepted tracklet
+  int* st_order;           // order in which the sector refit takes the tracks
+  int* st_obucket;         // scheduling bucket
+  int* st_oslot;           // place within the bucket
+  int* st_ord_cnt;         // [kOrdBuckets]
   int* st_ok;
   int* st_key;             // input id of the start cluster
   int* st_sector;

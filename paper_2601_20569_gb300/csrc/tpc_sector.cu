@@ -279,22 +279,41 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
   return best;
 }
 
+// CA chain of each start hit: length and the seed points (middle cluster =
+// the (L-1)/2-th up-link, last cluster), plus the constructor's scheduling
+// bucket (longest chains first, so the tracklets of one warp run about as
+// long).
+__global__ void k_chain_info(FrameDev F) {
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  if (F.cnt->err) return;
+  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+    const int start = F.starts[ti];
+    int L = 1, last = start, mid = start;
+    while (F.cup[last] >= 0) {
+      last = F.cup[last];
+      ++L;
+      if (L & 1) mid = F.cup[mid];
+    }
+    F.tl_len[ti] = L;
+    F.tl_mid[ti] = mid;
+    F.tl_end[ti] = last;
+    const int b = kOrdBuckets - 1 - min(kOrdBuckets - 1, L);
+    F.tl_obucket[ti] = b;
+    F.tl_oslot[ti] = atomicAdd(&F.tl_ord_cnt[b], 1);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int ti = queue_next(&F.cnt->queue[kQTracklets]); ti < nst;
-       ti = queue_next(&F.cnt->queue[kQTracklets])) {
+  for (int q = queue_next(&F.cnt->queue[kQTracklets]); q < nst;
+       q = queue_next(&F.cnt->queue[kQTracklets])) {
+    const int ti = F.tl_order[q];
     const int start = F.starts[ti];
     int* H = F.tl_hits + (long)ti * kMaxRows;
     // chain length and seed points (first, middle, last)
-    int L = 1, last_c = start;
-    while (F.cup[last_c] >= 0) {
-      last_c = F.cup[last_c];
-      ++L;
-    }
-    int mid = start;
-    for (int i = 0; i < (L - 1) / 2; ++i) mid = F.cup[mid];
+    const int L = F.tl_len[ti], mid = F.tl_mid[ti], last_c = F.tl_end[ti];
     const int rr0 = F.srow[start];
     const int r0 = rr0 % NR;
     const int sbase = rr0 - r0;  // sector * n_rows
@@ -503,8 +522,11 @@ int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 }
 
 int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  k_chain_info<<<sms * 8, kBlock, 0, s>>>(F);
+  k_order_scatter<<<sms * 4, kBlock, 0, s>>>(F.tl_obucket, F.tl_oslot, F.tl_ord_cnt,
+                                             &F.cnt->n_starts, F.cap_tl, &F.cnt->err, F.tl_order);
   k_tracklets<<<persistent_grid(F.lc, kLTracklets, sms), F.lc.block[kLTracklets], 0, s>>>(F, P);
-  return 1;
+  return 3;
 }
 
 int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

@@ -100,6 +100,28 @@ __device__ __forceinline__ int queue_next(int* q) {
   return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// Scheduling order from per-item buckets: order[start of bucket b + slot] = i
+// for the first min(*n, cap) items.  Every block scans the kOrdBuckets counts
+// in shared memory.  The order only decides which item a thread takes next;
+// no result depends on it (slots within a bucket follow atomic arrival).
+__global__ void k_order_scatter(const int* __restrict__ bucket, const int* __restrict__ slot,
+                                const int* __restrict__ cnt, const int* n, long cap,
+                                const int* err, int* __restrict__ order) {
+  __shared__ int base[kOrdBuckets];
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < kOrdBuckets; ++b) {
+      base[b] = acc;
+      acc += cnt[b];
+    }
+  }
+  __syncthreads();
+  if (*err) return;
+  const int m = (int)min((long)*n, cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    order[base[bucket[i]] + slot[i]] = i;
+}
+
 }  // namespace
 
 inline unsigned blocks_for(long n, int b) { return (unsigned)((n + b - 1) / b); }
