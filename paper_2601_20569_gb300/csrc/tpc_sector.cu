@@ -303,128 +303,153 @@ __global__ void k_chain_info(FrameDev F) {
   }
 }
 
+// Tracklet constructor as a per-lane state machine: every loop iteration is
+// one row step (propagate, choose the row's cluster, update) of the lane's
+// current tracklet, and a lane whose tracklet ends takes the next one from the
+// work queue in the same loop.  The lanes of a warp therefore stay busy on
+// row steps however unequal their tracklets are.  Per tracklet the sequence
+// of operations is that of the constructor (Sec. 2.2): seed from the chain's
+// first, middle and last clusters; follow the CA chain upwards; extend
+// upwards by the best cluster of each row until max_miss rows in a row have
+// none; restart from the top with reset covariance, refit downwards over the
+// found clusters and extend below the start the same way.
+enum : int { kTlIdle = 0, kTlChain, kTlUp, kTlDown };
+
 __global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int q = queue_next(&F.cnt->queue[kQTracklets]); q < nst;
-       q = queue_next(&F.cnt->queue[kQTracklets])) {
-    const int ti = F.tl_order[q];
-    const int start = F.starts[ti];
-    int* H = F.tl_hits + (long)ti * kMaxRows;
-    // chain length and seed points (first, middle, last)
-    const int L = F.tl_len[ti], mid = F.tl_mid[ti], last_c = F.tl_end[ti];
-    const int rr0 = F.srow[start];
-    const int r0 = rr0 % NR;
-    const int sbase = rr0 - r0;  // sector * n_rows
-    float xs[3], ys[3], zs[3];
-    {
-      const int sel[3] = {start, mid, last_c};
+  int phase = kTlIdle;
+  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, c = 0, left = 0, miss = 0, n = 0, rlo = 0;
+  int* H = nullptr;
+  float chi2 = 0.0f, last_x = 0.0f;
+  float last_p[5];
+  Trk<float> t, inner;
+  for (;;) {
+    if (phase == kTlIdle) {
+      // take the next tracklet and seed it
+      const int q = queue_next(&F.cnt->queue[kQTracklets]);
+      if (q >= nst) break;
+      ti = F.tl_order[q];
+      const int start = F.starts[ti];
+      H = F.tl_hits + (long)ti * kMaxRows;
+      const int L = F.tl_len[ti], mid = F.tl_mid[ti], last_c = F.tl_end[ti];
+      const int rr0 = F.srow[start];
+      r0 = rr0 % NR;
+      sbase = rr0 - r0;  // sector * n_rows
+      float xs[3], ys[3], zs[3];
+      {
+        const int sel[3] = {start, mid, last_c};
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        xs[i] = F.row_x[F.srow[sel[i]] % NR];
-        ys[i] = F.sy[sel[i]];
-        zs[i] = F.sz[sel[i]];
-      }
-    }
-    Trk<float> t;
-    F.tl_n[ti] = 0;
-    if (!seed3(xs, ys, zs, P, t)) continue;
-    {
-      const Resid R = residual(t, F.sy[start], F.sz[start], P);
-      update(t, R);
-      H[r0] = start;
-    }
-    Trk<float> last = t;
-    int top = r0;
-    bool alive = true;
-    int c = start;
-    for (int i = 1; i < L; ++i) {
-      c = F.cup[c];
-      const int r = F.srow[c] % NR;
-      if (!propagate(t, F.row_x[r], P, P.max_snp)) {
-        alive = false;
-        break;
-      }
-      const Resid R = residual(t, F.sy[c], F.sz[c], P);
-      update(t, R);
-      H[r] = c;
-      last = t;
-      top = r;
-    }
-    if (alive) {
-      int miss = 0;
-      for (int r = top + 1; r < NR; ++r) {
-        if (!propagate(t, F.row_x[r], P, P.max_snp)) break;
-        if (fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
-        const int k = pick(F, P, t, sbase + r);
-        if (k >= 0) {
-          const Resid R = residual(t, F.sy[k], F.sz[k], P);
-          update(t, R);
-          H[r] = k;
-          last = t;
-          top = r;
-          miss = 0;
-        } else {
-          H[r] = -1;
-          if (++miss >= P.max_miss) break;
+        for (int i = 0; i < 3; ++i) {
+          xs[i] = F.row_x[F.srow[sel[i]] % NR];
+          ys[i] = F.sy[sel[i]];
+          zs[i] = F.sz[sel[i]];
         }
       }
+      F.tl_n[ti] = 0;
+      if (!seed3(xs, ys, zs, P, t)) continue;
+      update(t, residual(t, F.sy[start], F.sz[start], P));
+      H[r0] = start;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) last_p[i] = t.p[i];
+      last_x = t.x;
+      top = r0;
+      rcur = r0;
+      c = start;
+      left = L - 1;  // chain steps still to take
+      miss = 0;
+      phase = left > 0 ? kTlChain : kTlUp;
+      continue;
     }
-    // downward pass: reset covariance at the top, refit, extend below the start
-    t = last;
-    reset_cov(t.c, P);
-    float chi2 = 0.0f;
-    int n = 0;
-    {
-      const int k = H[top];
-      const Resid R = residual(t, F.sy[k], F.sz[k], P);
-      chi2 = chi2 + R.chi2;
-      update(t, R);
-      ++n;
+    // ---- one row step
+    int r, k = -1;
+    bool stop;
+    if (phase == kTlChain) {
+      k = F.cup[c];
+      c = k;
+      r = F.srow[k] % NR;
+      stop = false;
+    } else if (phase == kTlUp) {
+      r = rcur + 1;
+      stop = r >= NR;
+    } else {
+      r = rcur - 1;
+      stop = r < 0;
     }
-    Trk<float> inner = t;
-    int rlo = top;
-    int miss = 0;
-    for (int r = top - 1; r >= 0; --r) {
-      if (!propagate(t, F.row_x[r], P, P.max_snp)) break;
-      if (fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
-      if (r >= r0) {
-        const int k = H[r];
-        if (k < 0) continue;
+    if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);
+    if (!stop && phase != kTlChain) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
+    bool miss_out = false;
+    if (!stop) {
+      if (phase == kTlDown && r >= r0)
+        k = H[r];
+      else if (phase != kTlChain)
+        k = pick(F, P, t, sbase + r);
+      if (k >= 0) {
         const Resid R = residual(t, F.sy[k], F.sz[k], P);
-        chi2 = chi2 + R.chi2;
+        if (phase == kTlDown) chi2 = chi2 + R.chi2;
         update(t, R);
-        ++n;
-        inner = t;
-        rlo = r;
-      } else {
-        const int k = pick(F, P, t, sbase + r);
-        if (k >= 0) {
-          const Resid R = residual(t, F.sy[k], F.sz[k], P);
-          chi2 = chi2 + R.chi2;
-          update(t, R);
-          H[r] = k;
+        if (phase == kTlDown) {
+          if (r < r0) {
+            H[r] = k;
+            miss = 0;
+          }
           ++n;
           inner = t;
           rlo = r;
-          miss = 0;
         } else {
-          H[r] = -1;
-          if (++miss >= P.max_miss) break;
+          H[r] = k;
+#pragma unroll
+          for (int i = 0; i < 5; ++i) last_p[i] = t.p[i];
+          last_x = t.x;
+          top = r;
+          miss = 0;
         }
+      } else if (phase != kTlDown || r < r0) {
+        H[r] = -1;
+        miss_out = ++miss >= P.max_miss;
+      }
+      rcur = r;
+      if (phase == kTlChain && --left == 0) {
+        phase = kTlUp;
+        miss = 0;
       }
     }
-    if (n < P.min_hits) continue;
-    F.tl_n[ti] = n;
-    F.tl_rlo[ti] = rlo;
-    F.tl_rhi[ti] = top;
-    F.tl_chi2[ti] = chi2;
-    F.tl_x[ti] = inner.x;
+    if (phase == kTlDown) {
+      if (!(stop || miss_out)) continue;
+      // tracklet done
+      phase = kTlIdle;
+      if (n < P.min_hits) continue;
+      F.tl_n[ti] = n;
+      F.tl_rlo[ti] = rlo;
+      F.tl_rhi[ti] = top;
+      F.tl_chi2[ti] = chi2;
+      F.tl_x[ti] = inner.x;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = inner.p[i];
+      for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = inner.p[i];
 #pragma unroll
-    for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = inner.c[i];
+      for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = inner.c[i];
+      continue;
+    }
+    if (!(stop || miss_out)) continue;
+    // upward part done (chain broken, no more rows, edge or max_miss misses):
+    // restart at the top with reset covariance and refit downwards
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t.p[i] = last_p[i];
+    t.x = last_x;
+    reset_cov(t.c, P);
+    {
+      const int kt = H[top];
+      const Resid R = residual(t, F.sy[kt], F.sz[kt], P);
+      chi2 = R.chi2;
+      update(t, R);
+    }
+    n = 1;
+    inner = t;
+    rlo = top;
+    rcur = top;
+    miss = 0;
+    phase = kTlDown;
   }
 }
 
