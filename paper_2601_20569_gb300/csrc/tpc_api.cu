@@ -273,10 +273,6 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.tl_len, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_mid, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_end, F.cap_tl);
-  ok &= dalloc(ctx, &F.tl_order, F.cap_tl);
-  ok &= dalloc(ctx, &F.tl_obucket, F.cap_tl);
-  ok &= dalloc(ctx, &F.tl_oslot, F.cap_tl);
-  ok &= dalloc(ctx, &F.tl_ord_cnt, kOrdBuckets);
   ok &= dalloc(ctx, &F.tl_rhi, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_hits, F.cap_tl * kMaxRows);
   ok &= dalloc(ctx, &F.owner_key, n);
@@ -328,9 +324,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   const long FT = F.cap_ft;
   ok &= dalloc(ctx, &F.ft_head, FT);
   ok &= dalloc(ctx, &F.ft_order, FT);
-  ok &= dalloc(ctx, &F.ft_obucket, FT);
-  ok &= dalloc(ctx, &F.ft_oslot, FT);
-  ok &= dalloc(ctx, &F.ord_cnt, kOrdBuckets);
+  ok &= dalloc(ctx, &F.ft_looper, FT);
   ok &= dalloc(ctx, &F.ft_key, FT);
   ok &= dalloc(ctx, &F.ft_ok, FT);
   ok &= dalloc(ctx, &F.ft_nst, FT);
@@ -415,8 +409,6 @@ tpc_status enqueue_chain(tpc_ctx* ctx, FrameDev& F, const KParams& Pc, cudaStrea
     CK(cudaMemsetAsync(F.attach_key, 0x7F, sizeof(int) * n, s));
   }
   CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * (nrr * kMergeZ + 1), s));
-  CK(cudaMemsetAsync(F.ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
-  CK(cudaMemsetAsync(F.tl_ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
   CK(cudaMemsetAsync(F.st_ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
   CK(cudaMemsetAsync(F.out_offset, 0, sizeof(int), s));
   long k = 0;

@@ -390,9 +390,8 @@ __global__ void k_head_count(FrameDev F) {
   if (threadIdx.x == 0) F.scan_tmp[blockIdx.x] = tot;
 }
 
-// Head list plus the scheduling bucket of each chain: whether its fit
-// updates run in FP64 (|q/pT| at the inner end above looper_qpt) and its
-// cluster count.  The bucket only orders the work; no result depends on it.
+// Head list, plus whether the chain's fit updates run in FP64 (|q/pT| at
+// its inner end above looper_qpt).
 __global__ void k_head_write(FrameDev F, KParams P) {
   __shared__ int sh[32];
   const int ns = F.cnt->n_tracks;
@@ -403,14 +402,38 @@ __global__ void k_head_write(FrameDev F, KParams P) {
   const int pos = F.scan_tmp[blockIdx.x] + ex;
   if (f && pos < F.cap_ft) {
     F.ft_head[pos] = i;
-    int len = 0;
-    for (int c = i; c >= 0; c = F.st_next[c]) len += F.tl_nkept[F.st_tl[c]];
     const float q = fabsf(F.st_ie[(long)i * kStateF + 4]);
-    const int looper = (P.looper_qpt > 0.0f && q > P.looper_qpt) ? 1 : 0;
-    const int b = (1 - looper) * kOrdLen + (kOrdLen - 1 - min(kOrdLen - 1, len >> 2));
-    F.ft_obucket[pos] = b;
-    F.ft_oslot[pos] = atomicAdd(&F.ord_cnt[b], 1);
+    F.ft_looper[pos] = (P.looper_qpt > 0.0f && q > P.looper_qpt) ? 1 : 0;
   }
+}
+
+// Processing order of the fit kernels: a stable partition of the fit tracks,
+// loopers first.  On this GPU an FP64 update costs the whole warp the FP64
+// pipe's time even when only one lane needs it, so loopers share warps; each
+// part keeps list order (sector-major), which keeps the cluster accesses of a
+// warp close together.  No result depends on the order.
+__device__ __forceinline__ int looper_flag(const FrameDev& F, int f) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  return (!F.cnt->err && f < nf) ? F.ft_looper[f] : 0;
+}
+
+__global__ void k_looper_count(FrameDev F) {
+  __shared__ int sh[32];
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  int tot;
+  block_exscan(looper_flag(F, f), sh, &tot);
+  if (threadIdx.x == 0) F.scan_tmp[blockIdx.x] = tot;
+}
+
+__global__ void k_looper_write(FrameDev F) {
+  __shared__ int sh[32];
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int fl = looper_flag(F, f);
+  int tot;
+  const int lr = F.scan_tmp[blockIdx.x] + block_exscan(fl, sh, &tot);  // loopers before f
+  if (F.cnt->err || f >= nf) return;
+  F.ft_order[fl ? lr : F.cnt->n_loopers + (f - lr)] = f;
 }
 
 __global__ void k_head_check(FrameDev F) {
@@ -602,120 +625,162 @@ __device__ __forceinline__ float zoff(const float* ie) {
   return ie[1] - ie[3] * sqrtf(ie[20] * ie[20] + ie[0] * ie[0]);
 }
 
-__global__ void __launch_bounds__(256) k_fit12(FrameDev F, KParams P, MapDev M) {
+// Iterations 1 and 2 of the final fit as a per-lane state machine: every loop
+// iteration is one station (station change, then the iteration's own work,
+// then the update) of the lane's current track, and a lane whose track ends
+// takes the next one from the work queue.  The lanes of a warp thus issue the
+// update (FP64 for loopers) together however unequal their tracks are.
+// Iteration 1 runs inward storing the predictions; iteration 2 runs outward,
+// interpolates with them, flags outliers and collects the inner-row
+// candidates (Sec. 3).
+enum : int { kFitIdle = 0, kFitIn, kFitOut };
+
+__device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, const MapDev& M,
+                                                 int f, int k, int rs, const Lin& L,
+                                                 const Interp& I, float z0) {
+  const int sec = rs / P.n_rows;
+  float cy = I.y, cz = I.z;
+  {
+    float D[3];
+    map_eval(M, P, sec, L.t.x, I.y, I.z - z0, D);
+    float sy = D[1], sz = D[2];
+    if (D[0] != 0.0f) {
+      StepJ stp;
+      if (helix_step(L.r, D[0], P, stp, P.fit_max_snp)) {
+        sy = sy - (stp.p0 - L.r[0]);
+        sz = sz - (stp.p1 - L.r[1]);
+      }
+    }
+    cy = I.y - sy;
+    cz = I.z - sz;
+  }
+  const float wy = sqrtf(P.int_chi2 * (I.c00 + P.sy2)) * 1.001f + P.attach_margin;
+  const float wz = sqrtf(P.int_chi2 * (I.c11 + P.sz2)) * 1.001f + P.attach_margin;
+  int* cand = F.ft_cand + ((long)f * kMaxInner + k) * kMaxCand;
+  float* cchi = F.ft_cchi + ((long)f * kMaxInner + k) * kMaxCand;
+  int nc = 0;
+  int cid[kMaxCand];
+  const RowGrid g = F.rows[rs];
+  for_window(F.bin_first, g, cy - wy - 0.01f, cy + wy + 0.01f, cz - wz - 0.01f, cz + wz + 0.01f,
+             [&](int kk) {
+    const float yk = F.sy[kk], zk = F.sz[kk];
+    if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
+    float my, mz;
+    if (!corrected(M, P, sec, L.t.x, yk, zk, z0, L.r, my, mz)) return;
+    const float c2 = chi2_interp(I, my, mz, P);
+    if (!(c2 < P.int_chi2)) return;
+    const int id = F.sid[kk];
+    // insertion into the sorted top-cand_k list by (chi2, id)
+    int pos = nc;
+    while (pos > 0 && (c2 < cchi[pos - 1] || (c2 == cchi[pos - 1] && id < cid[pos - 1]))) --pos;
+    if (pos >= P.cand_k) return;
+    const int lim = nc < P.cand_k ? nc : P.cand_k - 1;
+    for (int j = lim; j > pos; --j) {
+      cand[j] = cand[j - 1];
+      cchi[j] = cchi[j - 1];
+      cid[j] = cid[j - 1];
+    }
+    cand[pos] = kk;
+    cchi[pos] = c2;
+    cid[pos] = id;
+    if (nc < P.cand_k) ++nc;
+  });
+  F.ft_ncand[(long)f * kMaxInner + k] = (uint8_t)nc;
+  F.ft_assigned[(long)f * kMaxInner + k] = -1;
+}
+
+__global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev M) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int q = queue_next(&F.cnt->queue[kQFit12]); q < nf; q = queue_next(&F.cnt->queue[kQFit12])) {
-    const int f = F.ft_order[q];
-    const int head = F.ft_head[f];
-    int last = head;
-    while (F.st_next[last] >= 0) last = F.st_next[last];
-    const int ns = build_stations(F, P, f, head);
-    F.ft_nst[f] = ns;
-    F.ft_key[f] = F.st_key[head];
-    const float z0 = zoff(F.st_ie + (long)head * kStateF);
-    F.ft_z0[f] = z0;
-    const int* SC = F.ft_st_cl + (long)f * kMaxRows;
-    const uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
-    float* store = F.ft_store + (long)f * kMaxRows * 5;
-    uint8_t* flag = F.ft_flag + (long)f * kMaxRows;
-    int ok = 1;
-    Lin L;
-    Trk<float> s0;
-    get_state(F.st_oe + (long)last * kStateF, s0);
-    // iteration 1: inward, store predictions
-    lin_start(L, s0, SR[ns - 1] / NR, P);
-    for (int k = ns - 1; k >= 0 && ok; --k) {
-      const int rs = SR[k];
-      if (k != ns - 1 && !lin_goto(L, rs / NR, F.row_x[rs % NR], P)) { ok = 0; break; }
-      float* sv = store + k * 5;
-      sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
-      const int c = SC[k];
-      if (c >= 0) {
-        float my, mz;
-        if (!corrected(M, P, rs / NR, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
-        fit_update(L.t, residual(L.t, my, mz, P), P);
+  int phase = kFitIdle;
+  int f = 0, ns = 0, k = 0;
+  float z0 = 0.0f;
+  const int* SC = nullptr;
+  const uint16_t* SR = nullptr;
+  float* store = nullptr;
+  uint8_t* flag = nullptr;
+  Lin L;
+  for (;;) {
+    if (phase == kFitIdle) {
+      const int q = queue_next(&F.cnt->queue[kQFit12]);
+      if (q >= nf) break;
+      f = F.ft_order[q];
+      const int head = F.ft_head[f];
+      int last = head;
+      while (F.st_next[last] >= 0) last = F.st_next[last];
+      ns = build_stations(F, P, f, head);
+      F.ft_nst[f] = ns;
+      F.ft_key[f] = F.st_key[head];
+      if (ns == 0) {  // not reached: every chain holds clusters
+        F.ft_ok[f] = 0;
+        continue;
       }
+      z0 = zoff(F.st_ie + (long)head * kStateF);
+      F.ft_z0[f] = z0;
+      SC = F.ft_st_cl + (long)f * kMaxRows;
+      SR = F.ft_st_rs + (long)f * kMaxRows;
+      store = F.ft_store + (long)f * kMaxRows * 5;
+      flag = F.ft_flag + (long)f * kMaxRows;
+      Trk<float> s0;
+      get_state(F.st_oe + (long)last * kStateF, s0);
+      lin_start(L, s0, SR[ns - 1] / NR, P);
+      k = ns - 1;
+      phase = kFitIn;
+      continue;
     }
-    // iteration 2: outward, interpolation, flags, inner-row candidates
+    // ---- one station
+    const bool out = phase == kFitOut;
+    const int rs = SR[k];
+    const int sec = rs / NR, row = rs % NR;
+    bool ok = true;
+    if (k != (out ? 0 : ns - 1)) ok = lin_goto(L, sec, F.row_x[row], P);
+    const int c = SC[k];
+    const bool inner = out && row < P.inner_rows;
+    bool have = false;
+    float my = 0.0f, mz = 0.0f;
+    Interp I;
     if (ok) {
-      const Trk<float> s1 = L.t;
-      lin_start(L, s1, SR[0] / NR, P);
-      for (int k = 0; k < ns && ok; ++k) {
-        const int rs = SR[k];
-        const int sec = rs / NR, row = rs % NR;
-        if (k != 0 && !lin_goto(L, sec, F.row_x[row], P)) { ok = 0; break; }
+      if (!out) {
+        float* sv = store + k * 5;
+        sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
+      } else {
         const float a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
-        const Interp I = interpolate(a, store + k * 5);
-        const bool inner = row < P.inner_rows;
-        const int c = SC[k];
+        I = interpolate(a, store + k * 5);
         flag[k] = 0;
-        if (c >= 0 && !inner) {
-          float my, mz;
-          if (!corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
-          flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
-        }
-        if (inner) {
-          float cy = I.y, cz = I.z;
-          {
-            float D[3];
-            map_eval(M, P, sec, L.t.x, I.y, I.z - z0, D);
-            float sy = D[1], sz = D[2];
-            if (D[0] != 0.0f) {
-              StepJ stp;
-              if (helix_step(L.r, D[0], P, stp, P.fit_max_snp)) {
-                sy = sy - (stp.p0 - L.r[0]);
-                sz = sz - (stp.p1 - L.r[1]);
-              }
-            }
-            cy = I.y - sy;
-            cz = I.z - sz;
-          }
-          const float wy = sqrtf(P.int_chi2 * (I.c00 + P.sy2)) * 1.001f + P.attach_margin;
-          const float wz = sqrtf(P.int_chi2 * (I.c11 + P.sz2)) * 1.001f + P.attach_margin;
-          int* cand = F.ft_cand + ((long)f * kMaxInner + k) * kMaxCand;
-          float* cchi = F.ft_cchi + ((long)f * kMaxInner + k) * kMaxCand;
-          int nc = 0;
-          int cid[kMaxCand];
-          const RowGrid g = F.rows[rs];
-          for_window(F.bin_first, g, cy - wy - 0.01f, cy + wy + 0.01f, cz - wz - 0.01f,
-                     cz + wz + 0.01f, [&](int kk) {
-            const float yk = F.sy[kk], zk = F.sz[kk];
-            if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
-            float my, mz;
-            if (!corrected(M, P, sec, L.t.x, yk, zk, z0, L.r, my, mz)) return;
-            const float c2 = chi2_interp(I, my, mz, P);
-            if (!(c2 < P.int_chi2)) return;
-            const int id = F.sid[kk];
-            // insertion into the sorted top-cand_k list by (chi2, id)
-            int pos = nc;
-            while (pos > 0 && (c2 < cchi[pos - 1] || (c2 == cchi[pos - 1] && id < cid[pos - 1])))
-              --pos;
-            if (pos >= P.cand_k) return;
-            const int lim = nc < P.cand_k ? nc : P.cand_k - 1;
-            for (int j = lim; j > pos; --j) {
-              cand[j] = cand[j - 1];
-              cchi[j] = cchi[j - 1];
-              cid[j] = cid[j - 1];
-            }
-            cand[pos] = kk;
-            cchi[pos] = c2;
-            cid[pos] = id;
-            if (nc < P.cand_k) ++nc;
-          });
-          F.ft_ncand[(long)f * kMaxInner + k] = (uint8_t)nc;
-          F.ft_assigned[(long)f * kMaxInner + k] = -1;
-        }
+      }
+      if (c >= 0 && !inner) {
+        ok = corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz);
+        have = ok;
+        if (ok && out) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
+      }
+      if (ok && inner) {
+        inner_candidates(F, P, M, f, k, rs, L, I, z0);
         if (c >= 0) {
-          float my, mz;
-          if (!corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) { ok = 0; break; }
-          fit_update(L.t, residual(L.t, my, mz, P), P);
+          ok = corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz);
+          have = ok;
         }
       }
-      if (ok) put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
     }
-    F.ft_ok[f] = ok;
+    if (have) fit_update(L.t, residual(L.t, my, mz, P), P);
+    if (!ok) {
+      F.ft_ok[f] = 0;
+      phase = kFitIdle;
+      continue;
+    }
+    if (!out) {
+      if (--k < 0) {
+        // iteration 2 starts from the inner end of iteration 1
+        const Trk<float> s1 = L.t;
+        lin_start(L, s1, SR[0] / NR, P);
+        k = 0;
+        phase = kFitOut;
+      }
+    } else if (++k == ns) {
+      put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
+      F.ft_ok[f] = 1;
+      phase = kFitIdle;
+    }
   }
 }
 
@@ -1280,9 +1345,11 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_merged);
   k_head_write<<<nb_tl, kBlock, 0, s>>>(F, P);
   k_head_check<<<1, 1, 0, s>>>(F);
-  k_order_scatter<<<sms * 4, kBlock, 0, s>>>(F.ft_obucket, F.ft_oslot, F.ord_cnt, &F.cnt->n_merged,
-                                             F.cap_ft, &F.cnt->err, F.ft_order);
-  return k + 9;
+  const int nb_ft = (int)blocks_for(F.cap_ft, kBlock);
+  k_looper_count<<<nb_ft, kBlock, 0, s>>>(F);
+  k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_ft, &F.cnt->n_loopers);
+  k_looper_write<<<nb_ft, kBlock, 0, s>>>(F);
+  return k + 11;
 }
 
 int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

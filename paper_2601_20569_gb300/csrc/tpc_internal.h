@@ -70,11 +70,8 @@ constexpr int kMaxBinOcc = 1024;
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kMergeZ = 64;      // z bins per (sector, row) of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
-// Scheduling buckets of the fit kernels: loopers (FP64 updates) first, then
-// the rest, each from the longest chain to the shortest, so that the tracks
-// of one warp take the same update path and run about as long.
-constexpr int kOrdLen = 64;
-constexpr int kOrdBuckets = 2 * kOrdLen;
+// Scheduling buckets of the sector refit (most clusters first).
+constexpr int kOrdBuckets = 128;
 
 // Distortion map as seen by the kernels.
 struct MapDev {
@@ -98,7 +95,7 @@ struct Counters {
   int need_tracks;
   int n_out;         // output tracks
   int queue[kQNum];  // work-queue heads
-  int pad[1];
+  int n_loopers;     // fit tracks whose updates run in FP64
 };
 
 // Working set of one frame on the device.
@@ -147,10 +144,6 @@ struct FrameDev {
   int* tl_len;             // [cap_tl] CA chain length from the start hit
   int* tl_mid;             // [cap_tl] middle chain cluster (seed point)
   int* tl_end;             // [cap_tl] last chain cluster (seed point)
-  int* tl_order;           // [cap_tl] order in which the constructor takes the tracklets
-  int* tl_obucket;         // [cap_tl] scheduling bucket
-  int* tl_oslot;           // [cap_tl] place within the bucket
-  int* tl_ord_cnt;         // [kOrdBuckets]
   // a6
   unsigned long long* owner_key;  // [n] sorted index space
   int* tl_acc;
@@ -188,10 +181,9 @@ struct FrameDev {
   // a9/a10 fit tracks (capacity cap_ft)
   long cap_ft;
   int* ft_head;            // first sector track of the chain
-  int* ft_order;           // [cap_ft] order in which the fit kernels take the tracks
-  int* ft_obucket;         // [cap_ft] scheduling bucket of each fit track
-  int* ft_oslot;           // [cap_ft] place within the bucket
-  int* ord_cnt;            // [kOrdBuckets] tracks per scheduling bucket
+  int* ft_order;           // [cap_ft] order in which the fit kernels take the tracks:
+                           // FP64-update loopers first, then the rest, each in list order
+  int* ft_looper;          // [cap_ft] 1: |q/pT| of the chain's inner end above looper_qpt
   int* ft_key;
   int* ft_ok;
   int* ft_nst;             // stations

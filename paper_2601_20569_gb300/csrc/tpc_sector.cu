@@ -280,9 +280,7 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
 }
 
 // CA chain of each start hit: length and the seed points (middle cluster =
-// the (L-1)/2-th up-link, last cluster), plus the constructor's scheduling
-// bucket (longest chains first, so the tracklets of one warp run about as
-// long).
+// the (L-1)/2-th up-link, last cluster).
 __global__ void k_chain_info(FrameDev F) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
@@ -297,9 +295,6 @@ __global__ void k_chain_info(FrameDev F) {
     F.tl_len[ti] = L;
     F.tl_mid[ti] = mid;
     F.tl_end[ti] = last;
-    const int b = kOrdBuckets - 1 - min(kOrdBuckets - 1, L);
-    F.tl_obucket[ti] = b;
-    F.tl_oslot[ti] = atomicAdd(&F.tl_ord_cnt[b], 1);
   }
 }
 
@@ -328,9 +323,8 @@ __global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
   for (;;) {
     if (phase == kTlIdle) {
       // take the next tracklet and seed it
-      const int q = queue_next(&F.cnt->queue[kQTracklets]);
-      if (q >= nst) break;
-      ti = F.tl_order[q];
+      ti = queue_next(&F.cnt->queue[kQTracklets]);
+      if (ti >= nst) break;
       const int start = F.starts[ti];
       H = F.tl_hits + (long)ti * kMaxRows;
       const int L = F.tl_len[ti], mid = F.tl_mid[ti], last_c = F.tl_end[ti];
@@ -548,10 +542,8 @@ int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 
 int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_chain_info<<<sms * 8, kBlock, 0, s>>>(F);
-  k_order_scatter<<<sms * 4, kBlock, 0, s>>>(F.tl_obucket, F.tl_oslot, F.tl_ord_cnt,
-                                             &F.cnt->n_starts, F.cap_tl, &F.cnt->err, F.tl_order);
   k_tracklets<<<persistent_grid(F.lc, kLTracklets, sms), F.lc.block[kLTracklets], 0, s>>>(F, P);
-  return 3;
+  return 2;
 }
 
 int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
