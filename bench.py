@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch", default="",
+                    help="fixed launch shapes instead of autotuning, e.g. "
+                         "256x4,128x4,256x16,64x8,256x8 (block x blocks per SM, slot order)")
+    ap.add_argument("--collisions", type=float, default=0.0,
+                    help="mean collisions per frame instead of the workload's (small "
+                         "profiling cases)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up plus one step and exit (for ncu launch lists)")
     return ap.parse_args()
@@ -128,7 +134,8 @@ def make_frames(args, rank):
 
     frames = []
     for k in range(args.frames):
-        frames.append(synth.generate(args.workload, frame=rank * args.frames + k))
+        kw = {"mean_collisions": args.collisions} if args.collisions > 0 else {}
+        frames.append(synth.generate(args.workload, frame=rank * args.frames + k, **kw))
     return frames
 
 
@@ -250,7 +257,12 @@ def main():
     stream = torch.cuda.current_stream()
     note("inputs resident")
     # launch shapes tuned on two frames of the batch (the frames are alike)
-    tuned = tr.autotune(dev[:2]) if not args.no_autotune else tr.launch_config()
+    if args.launch:
+        tr.set_launch_config([{"block": int(b), "blocks_per_sm": int(q)} for b, q in
+                              (x.split("x") for x in args.launch.split(","))])
+        tuned = tr.launch_config()
+    else:
+        tuned = tr.autotune(dev[:2]) if not args.no_autotune else tr.launch_config()
     note("launch shapes chosen")
 
     def step():

@@ -205,6 +205,14 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
 tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
                              int32_t* block, int32_t* blocks_per_sm);
 
+/* Set the launch shape of heavy kernel `slot` (0..4, as tpc_launch_config
+ * numbers them), e.g. to reapply a shape the autotuner chose earlier on the
+ * same GPU.  block: multiple of 32 in [32, 1024]; blocks_per_sm in [1, 32].
+ * The shape changes only scheduling: results are identical for every shape.
+ * TPC_ERR_INVALID_ARG for any other value. */
+tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
+                                 int32_t blocks_per_sm);
+
 /* Replace the correction map (device pointer copied by reference; the caller
  * keeps it alive while the context uses it). */
 tpc_status tpc_set_map(tpc_ctx* ctx, const tpc_map* map);

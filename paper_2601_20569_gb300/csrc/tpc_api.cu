@@ -659,6 +659,19 @@ tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kern
   return TPC_OK;
 }
 
+tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
+                                 int32_t blocks_per_sm) {
+  if (!ctx) return TPC_ERR_INVALID_ARG;
+  if (slot < 0 || slot >= kLNum || block < 32 || block > 1024 || block % 32 != 0 ||
+      blocks_per_sm < 1 || blocks_per_sm > 32)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "launch shape slot %d: block %d, %d per SM", slot, block,
+                blocks_per_sm);
+  ctx->F.lc.block[slot] = block;
+  ctx->F.lc.per_sm[slot] = blocks_per_sm;
+  ++ctx->lc_version;
+  return TPC_OK;
+}
+
 tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* cl, const tpc_tracks* in,
                      const tpc_map* map, int32_t freeze, tpc_tracks* out, void* cuda_stream) {
   if (!ctx) return TPC_ERR_INVALID_ARG;

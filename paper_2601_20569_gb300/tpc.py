@@ -305,6 +305,17 @@ class Tracker:
             out.append({"kernel": name.value.decode(), "block": b.value, "blocks_per_sm": q.value})
         return out
 
+    def set_launch_config(self, shapes) -> None:
+        """Apply launch shapes, e.g. the list launch_config() returned earlier
+        (dicts with "block" and "blocks_per_sm", in slot order)."""
+        fn = self.lib.tpc_set_launch_config
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        fn.restype = ctypes.c_int
+        for slot, sh in enumerate(shapes):
+            rc = fn(self._ctx, slot, int(sh["block"]), int(sh["blocks_per_sm"]))
+            if rc:
+                raise TpcError(rc, self.last_error())
+
     def result_attach(self):
         """Device tensor view (int32[n_clusters]) of the last call's attachments."""
         out, n = self._last
