@@ -161,7 +161,45 @@ __global__ void k_acc_write(FrameDev F) {
   }
 }
 
+// Position of sorted cluster c: pad-row x (from the shared-memory copy of the
+// row radii), y, z.
+struct ClPt {
+  float x, y, z;
+};
+__device__ __forceinline__ ClPt cl_point(const FrameDev& F, const float* rx, int NR, int c) {
+  ClPt p;
+  p.x = rx[F.srow[c] % NR];
+  p.y = F.sy[c];
+  p.z = F.sz[c];
+  return p;
+}
+
+// Sector refit of one track over its kept clusters K[j], j = j0, j0+dj, ...
+// (nsteps steps).  Loads run one step ahead of the filter (the index two
+// steps ahead), so the gather of the next cluster overlaps the arithmetic of
+// the current one.
+__device__ __forceinline__ bool refit_pass(const FrameDev& F, const KParams& P, const float* rx,
+                                           const int* K, int j0, int dj, int nsteps,
+                                           Trk<float>& t) {
+  const int NR = P.n_rows;
+  ClPt nxt = cl_point(F, rx, NR, K[j0]);
+  int cnext = nsteps > 1 ? K[j0 + dj] : 0;
+  for (int s = 0; s < nsteps; ++s) {
+    const ClPt cur = nxt;
+    if (s + 1 < nsteps) {
+      nxt = cl_point(F, rx, NR, cnext);
+      if (s + 2 < nsteps) cnext = K[j0 + (s + 2) * dj];
+    }
+    if (!propagate(t, cur.x, P, P.fit_max_snp)) return false;
+    update(t, residual(t, cur.y, cur.z, P));
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
+  __shared__ float rx[kMaxRows];
+  for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
+  __syncthreads();
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
   const int NR = P.n_rows;
@@ -185,20 +223,12 @@ __global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
     for (int k = 0; k < 5; ++k) t.p[k] = F.tl_par[(long)ti * 5 + k];
     t.x = F.tl_x[ti];
     reset_cov(t.c, P);
-    bool ok = true;
-    for (int j = nk - 1; j >= 0 && ok; --j) {
-      const int c = K[j];
-      if (!propagate(t, F.row_x[F.srow[c] % NR], P, P.fit_max_snp)) { ok = false; break; }
-      update(t, residual(t, F.sy[c], F.sz[c], P));
-    }
+    // outward over the kept clusters (innermost first), then inward
+    bool ok = refit_pass(F, P, rx, K, nk - 1, -1, nk, t);
     if (ok) {
       put_state(F.st_oe + (long)i * kStateF, t, rs / NR);
       reset_cov(t.c, P);
-      for (int j = 0; j < nk; ++j) {
-        const int c = K[j];
-        if (!propagate(t, F.row_x[F.srow[c] % NR], P, P.fit_max_snp)) { ok = false; break; }
-        update(t, residual(t, F.sy[c], F.sz[c], P));
-      }
+      ok = refit_pass(F, P, rx, K, 0, 1, nk, t);
       if (ok) put_state(F.st_ie + (long)i * kStateF, t, rs / NR);
     }
     F.st_ok[i] = ok ? 1 : 0;
@@ -227,10 +257,13 @@ __global__ void k_sector_zrange(FrameDev F, KParams P) {
   }
 }
 
-// Merge candidate index: inner ends binned by (sector, innermost row, z).
+// Merge candidate index: inner ends binned by (sector, z, innermost row), so
+// that the rows a pair test accepts form one contiguous range per z bin.
+__device__ __forceinline__ int merge_zbin(const FrameDev& F, int s, float z) {
+  return clampi((int)floorf((z - F.sec_zlo[s]) * F.sec_zinv[s]), 0, kMergeZ - 1);
+}
 __device__ __forceinline__ int merge_bin(const FrameDev& F, int nrows, int s, int r, float z) {
-  return (s * nrows + r) * kMergeZ +
-         clampi((int)floorf((z - F.sec_zlo[s]) * F.sec_zinv[s]), 0, kMergeZ - 1);
+  return (s * kMergeZ + merge_zbin(F, s, z)) * nrows + r;
 }
 
 __global__ void k_ie_hist(FrameDev F, KParams P) {
@@ -322,12 +355,14 @@ __device__ __forceinline__ void for_merge_candidates(const FrameDev& F, const KP
   const int r0 = F.st_rmax[a] + 1;
   const int r1 = min(F.st_rmax[a] + P.merge_max_gap, P.n_rows - 1);
   const float m = 0.01f;
+  if (r0 > r1) return;
   for (int q = 0; q < 3; ++q) {
     const int sb = side * half + (ph + dsl[q]) % half;
-    for (int rb = r0; rb <= r1; ++rb) {
-      const int b0 = merge_bin(F, P.n_rows, sb, rb, oe[1] - zwin - m);
-      const int b1 = merge_bin(F, P.n_rows, sb, rb, oe[1] + zwin + m);
-      const int lo = F.ie_first[b0], hi = F.ie_first[b1 + 1];
+    const int z0 = merge_zbin(F, sb, oe[1] - zwin - m);
+    const int z1 = merge_zbin(F, sb, oe[1] + zwin + m);
+    for (int zb = z0; zb <= z1; ++zb) {
+      const int base = (sb * kMergeZ + zb) * P.n_rows;
+      const int lo = F.ie_first[base + r0], hi = F.ie_first[base + r1 + 1];
       for (int k = lo; k < hi; ++k) {
         const int b = F.ie_idx[k];
         if (b != a) fn(b);
@@ -411,7 +446,8 @@ __global__ void k_head_write(FrameDev F, KParams P) {
 // loopers first.  On this GPU an FP64 update costs the whole warp the FP64
 // pipe's time even when only one lane needs it, so loopers share warps; each
 // part keeps list order (sector-major), which keeps the cluster accesses of a
-// warp close together.  No result depends on the order.
+// warp close together.  The two parts are served by two work queues (see
+// fit_next).  No result depends on the order.
 __device__ __forceinline__ int looper_flag(const FrameDev& F, int f) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   return (!F.cnt->err && f < nf) ? F.ft_looper[f] : 0;
@@ -441,6 +477,29 @@ __global__ void k_head_check(FrameDev F) {
     atomicOr(&F.cnt->err, kErrCapTracks);
     atomicMax(&F.cnt->need_tracks, F.cnt->n_merged);
   }
+}
+
+// Next fit track for the calling lane from the two queues of a fit kernel:
+// loopers hold ft_order[0, nL), the other tracks ft_order[nL, nf).  About a
+// quarter of the warps (spread pseudo-randomly over the grid) serve the
+// looper queue first, the rest the other queue first; each turns to the other
+// queue when its own is empty.  So while loopers remain, every SM runs some
+// warps whose updates keep the (narrow) FP64 pipe busy beside warps issuing
+// FP32 work, instead of one kind after the other.  Returns nf when both
+// queues are empty.
+__device__ __forceinline__ int fit_next(Counters* cnt, int qL, int qN, int nL, int nf) {
+  const unsigned gw = (unsigned)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const bool looper_home = nL > 0 && ((gw * 2654435761u) >> 30) == 0u;
+  if (looper_home) {
+    const int q = queue_next(&cnt->queue[qL]);
+    if (q < nL) return q;
+    const int r = nL + queue_next(&cnt->queue[qN]);
+    return r < nf ? r : nf;
+  }
+  const int r = nL + queue_next(&cnt->queue[qN]);
+  if (r < nf) return r;
+  const int q = nL > 0 ? queue_next(&cnt->queue[qL]) : nL;
+  return q < nL ? q : nf;
 }
 
 // ------------------------------------------ a9/a10 linearised three-iteration fit
@@ -692,6 +751,7 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
 __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev M) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
+  const int nL = min(F.cnt->n_loopers, nf);
   const int NR = P.n_rows;
   int phase = kFitIdle;
   int f = 0, ns = 0, k = 0;
@@ -703,7 +763,7 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
   Lin L;
   for (;;) {
     if (phase == kFitIdle) {
-      const int q = queue_next(&F.cnt->queue[kQFit12]);
+      const int q = fit_next(F.cnt, kQFit12, kQFit12N, nL, nf);
       if (q >= nf) break;
       f = F.ft_order[q];
       const int head = F.ft_head[f];
@@ -846,7 +906,9 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int q = queue_next(&F.cnt->queue[kQFit3]); q < nf; q = queue_next(&F.cnt->queue[kQFit3])) {
+  const int nL = min(F.cnt->n_loopers, nf);
+  for (int q = fit_next(F.cnt, kQFit3, kQFit3N, nL, nf); q < nf;
+       q = fit_next(F.cnt, kQFit3, kQFit3N, nL, nf)) {
     const int f = F.ft_order[q];
     F.ft_n[f] = 0;
     if (!F.ft_ok[f]) continue;

@@ -38,7 +38,11 @@ struct LaunchCfg {
 };
 
 // Work queues: counters of the dynamic item fetching (zeroed per call).
-enum QueueSlot : int { kQTracklets = 0, kQSectorRefit, kQMerge, kQFit12, kQFit3, kQNum };
+// The fit kernels keep two queues each: FP64-update loopers (kQFit12, kQFit3)
+// and the other tracks (kQFit12N, kQFit3N).
+enum QueueSlot : int {
+  kQTracklets = 0, kQSectorRefit, kQMerge, kQFit12, kQFit3, kQFit12N, kQFit3N, kQNum
+};
 
 // Search grid of one (sector, row): bins iz*nY + iy, clusters of a bin are
 // contiguous in the sorted arrays.
@@ -68,7 +72,7 @@ enum : int {
 constexpr int kMaxBinOcc = 1024;
 
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
-constexpr int kMergeZ = 64;      // z bins per (sector, row) of the merge candidate index
+constexpr int kMergeZ = 64;      // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 // Scheduling buckets of the sector refit (most clusters first).
 constexpr int kOrdBuckets = 128;
@@ -170,8 +174,8 @@ struct FrameDev {
   int* st_bestB;
   float* st_bestchi;
   unsigned long long* st_bestA;
-  int* ie_cnt;             // [n_sectors*n_rows*kMergeZ]
-  int* ie_first;           // [n_sectors*n_rows*kMergeZ + 1]
+  int* ie_cnt;             // [n_sectors*kMergeZ*n_rows]
+  int* ie_first;           // [n_sectors*kMergeZ*n_rows + 1]
   int* ie_slot;            // [cap_tl]
   int* ie_bin;             // [cap_tl]
   int* ie_idx;             // [cap_tl] sector tracks sorted by (sector, z bin)

@@ -143,6 +143,15 @@ __global__ void k_bin_sort(FrameDev F) {
 }
 
 // ------------------------------------------------------------- a2 neighbours
+// Clusters of the row below inside the window are listed once (up to
+// kLinkList of them; a denser window falls back to rescanning the grid for
+// every upper candidate), then every upper candidate inside the window is
+// paired with the list.  The best pair minimises the distance of the middle
+// cluster to the straight line through the pair; ties go to the smaller
+// input id of the upper, then of the lower cluster, so the result does not
+// depend on the visiting order.
+constexpr int kLinkList = 8;
+
 __global__ void k_links(FrameDev F, KParams P) {
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= F.n || F.cnt->err) return;
@@ -157,30 +166,50 @@ __global__ void k_links(FrameDev F, KParams P) {
     const float m = 0.01f;
     const float ylo = yc - P.link_wy - m, yhi = yc + P.link_wy + m;
     const float zlo = zc - P.link_wz - m, zhi = zc + P.link_wz + m;
+    int dl[kLinkList];
+    int nd = 0;
+    bool dense = false;
+    for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
+      const float yd = F.sy[d], zd = F.sz[d];
+      if (!(fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)) return;
+      if (nd < kLinkList)
+        dl[nd++] = d;
+      else
+        dense = true;
+    });
     float best = 0.0f;
     int buid = 0, bdid = 0;
-    for_window(F.bin_first, gu, ylo, yhi, zlo, zhi, [&](int u) {
-      const float yu = F.sy[u], zu = F.sz[u];
-      if (!(fabsf(yu - yc) <= P.link_wy && fabsf(zu - zc) <= P.link_wz)) return;
-      const int uid = F.sid[u];
-      for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
-        const float yd = F.sy[d], zd = F.sz[d];
-        if (!(fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)) return;
-        const float yp = yd + (yu - yd) * f;
-        const float zp = zd + (zu - zd) * f;
-        const float ey = yp - yc, ez = zp - zc;
-        const float d2 = ey * ey + ez * ez;
-        if (!(d2 < P.link_chi2)) return;
-        const int did = F.sid[d];
-        if (bu < 0 || d2 < best || (d2 == best && (uid < buid || (uid == buid && did < bdid)))) {
-          best = d2;
-          bu = u;
-          bd = d;
-          buid = uid;
-          bdid = did;
+    auto pair = [&](int u, float yu, float zu, int uid, int d) {
+      const float yd = F.sy[d], zd = F.sz[d];
+      const float yp = yd + (yu - yd) * f;
+      const float zp = zd + (zu - zd) * f;
+      const float ey = yp - yc, ez = zp - zc;
+      const float d2 = ey * ey + ez * ez;
+      if (!(d2 < P.link_chi2)) return;
+      const int did = F.sid[d];
+      if (bu < 0 || d2 < best || (d2 == best && (uid < buid || (uid == buid && did < bdid)))) {
+        best = d2;
+        bu = u;
+        bd = d;
+        buid = uid;
+        bdid = did;
+      }
+    };
+    if (nd > 0)
+      for_window(F.bin_first, gu, ylo, yhi, zlo, zhi, [&](int u) {
+        const float yu = F.sy[u], zu = F.sz[u];
+        if (!(fabsf(yu - yc) <= P.link_wy && fabsf(zu - zc) <= P.link_wz)) return;
+        const int uid = F.sid[u];
+        if (!dense) {
+          for (int j = 0; j < nd; ++j) pair(u, yu, zu, uid, dl[j]);
+        } else {
+          for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
+            const float yd = F.sy[d], zd = F.sz[d];
+            if (fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)
+              pair(u, yu, zu, uid, d);
+          });
         }
       });
-    });
   }
   F.lup[k] = bu;
   F.ldn[k] = bd;
