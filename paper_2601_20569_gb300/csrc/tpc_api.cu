@@ -271,8 +271,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.tl_n, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_rlo, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_len, F.cap_tl);
-  ok &= dalloc(ctx, &F.tl_mid, F.cap_tl);
-  ok &= dalloc(ctx, &F.tl_end, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_seed, F.cap_tl * kSeedF);
   ok &= dalloc(ctx, &F.tl_rhi, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_hits, F.cap_tl * kMaxRows);
   ok &= dalloc(ctx, &F.owner_key, n);
@@ -323,6 +322,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   F.cap_ft = opt->cap_tracks > 0 ? opt->cap_tracks : n / 40 + 4096;
   const long FT = F.cap_ft;
   ok &= dalloc(ctx, &F.ft_head, FT);
+  ok &= dalloc(ctx, &F.ft_last, FT);
   ok &= dalloc(ctx, &F.ft_order, FT);
   ok &= dalloc(ctx, &F.ft_looper, FT);
   ok &= dalloc(ctx, &F.ft_key, FT);

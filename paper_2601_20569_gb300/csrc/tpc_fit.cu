@@ -480,16 +480,15 @@ __global__ void k_head_check(FrameDev F) {
 }
 
 // Next fit track for the calling lane from the two queues of a fit kernel:
-// loopers hold ft_order[0, nL), the other tracks ft_order[nL, nf).  About a
-// quarter of the warps (spread pseudo-randomly over the grid) serve the
-// looper queue first, the rest the other queue first; each turns to the other
-// queue when its own is empty.  So while loopers remain, every SM runs some
-// warps whose updates keep the (narrow) FP64 pipe busy beside warps issuing
-// FP32 work, instead of one kind after the other.  Returns nf when both
-// queues are empty.
+// loopers hold ft_order[0, nL), the other tracks ft_order[nL, nf).  Half of
+// the warps (chosen pseudo-randomly over the grid) serve the looper queue
+// first, the rest the other queue first; each turns to the other queue when
+// its own is empty, so that the (narrow) FP64 pipe is in use while the other
+// tracks are fitted rather than only at one end of the kernel.  Returns nf
+// when both queues are empty.
 __device__ __forceinline__ int fit_next(Counters* cnt, int qL, int qN, int nL, int nf) {
   const unsigned gw = (unsigned)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const bool looper_home = nL > 0 && ((gw * 2654435761u) >> 30) == 0u;
+  const bool looper_home = nL > 0 && ((gw * 2654435761u) >> 31) == 0u;
   if (looper_home) {
     const int q = queue_next(&cnt->queue[qL]);
     if (q < nL) return q;
@@ -684,6 +683,25 @@ __device__ __forceinline__ float zoff(const float* ie) {
   return ie[1] - ie[3] * sqrtf(ie[20] * ie[20] + ie[0] * ie[0]);
 }
 
+// Per fit track, ahead of the fit: the station list, the chain's last
+// segment (whose outer end starts iteration 1), the identity key and the
+// drift-time z offset.  A separate pass with one thread per track, so that
+// the fit's state machine does not stall a whole warp while one lane walks
+// a chain.
+__global__ void k_fit_stations(FrameDev F, KParams P) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const int head = F.ft_head[f];
+    int last = head;
+    while (F.st_next[last] >= 0) last = F.st_next[last];
+    F.ft_nst[f] = build_stations(F, P, f, head);
+    F.ft_key[f] = F.st_key[head];
+    F.ft_last[f] = last;
+    F.ft_z0[f] = zoff(F.st_ie + (long)head * kStateF);
+  }
+}
+
 // Iterations 1 and 2 of the final fit as a per-lane state machine: every loop
 // iteration is one station (station change, then the iteration's own work,
 // then the update) of the lane's current track, and a lane whose track ends
@@ -749,6 +767,9 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
 }
 
 __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev M) {
+  __shared__ float rx[kMaxRows];
+  for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
+  __syncthreads();
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int nL = min(F.cnt->n_loopers, nf);
@@ -766,58 +787,64 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
       const int q = fit_next(F.cnt, kQFit12, kQFit12N, nL, nf);
       if (q >= nf) break;
       f = F.ft_order[q];
-      const int head = F.ft_head[f];
-      int last = head;
-      while (F.st_next[last] >= 0) last = F.st_next[last];
-      ns = build_stations(F, P, f, head);
-      F.ft_nst[f] = ns;
-      F.ft_key[f] = F.st_key[head];
+      ns = F.ft_nst[f];
       if (ns == 0) {  // not reached: every chain holds clusters
         F.ft_ok[f] = 0;
         continue;
       }
-      z0 = zoff(F.st_ie + (long)head * kStateF);
-      F.ft_z0[f] = z0;
+      z0 = F.ft_z0[f];
       SC = F.ft_st_cl + (long)f * kMaxRows;
       SR = F.ft_st_rs + (long)f * kMaxRows;
       store = F.ft_store + (long)f * kMaxRows * 5;
       flag = F.ft_flag + (long)f * kMaxRows;
       Trk<float> s0;
-      get_state(F.st_oe + (long)last * kStateF, s0);
+      get_state(F.st_oe + (long)F.ft_last[f] * kStateF, s0);
       lin_start(L, s0, SR[ns - 1] / NR, P);
       k = ns - 1;
       phase = kFitIn;
       continue;
     }
-    // ---- one station
+    // ---- one station.  The cluster and, outward, the stored prediction do
+    // not depend on the state: they are requested before the station change
+    // so that their latency overlaps its arithmetic.
     const bool out = phase == kFitOut;
     const int rs = SR[k];
-    const int sec = rs / NR, row = rs % NR;
-    bool ok = true;
-    if (k != (out ? 0 : ns - 1)) ok = lin_goto(L, sec, F.row_x[row], P);
     const int c = SC[k];
+    const int sec = rs / NR, row = rs % NR;
+    float cy = 0.0f, cz = 0.0f;
+    if (c >= 0) {
+      cy = F.sy[c];
+      cz = F.sz[c];
+    }
+    float sv[5];
+    if (out) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) sv[i] = store[k * 5 + i];
+    }
+    bool ok = true;
+    if (k != (out ? 0 : ns - 1)) ok = lin_goto(L, sec, rx[row], P);
     const bool inner = out && row < P.inner_rows;
     bool have = false;
     float my = 0.0f, mz = 0.0f;
     Interp I;
     if (ok) {
       if (!out) {
-        float* sv = store + k * 5;
-        sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
+        float* st = store + k * 5;
+        st[0] = L.t.p[0]; st[1] = L.t.p[1]; st[2] = L.t.c[0]; st[3] = L.t.c[1]; st[4] = L.t.c[2];
       } else {
         const float a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
-        I = interpolate(a, store + k * 5);
+        I = interpolate(a, sv);
         flag[k] = 0;
       }
       if (c >= 0 && !inner) {
-        ok = corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz);
+        ok = corrected(M, P, sec, L.t.x, cy, cz, z0, L.r, my, mz);
         have = ok;
         if (ok && out) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
       }
       if (ok && inner) {
         inner_candidates(F, P, M, f, k, rs, L, I, z0);
         if (c >= 0) {
-          ok = corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz);
+          ok = corrected(M, P, sec, L.t.x, cy, cz, z0, L.r, my, mz);
           have = ok;
         }
       }
@@ -903,6 +930,9 @@ __global__ void k_amb_mark(FrameDev F, KParams P, int round) {
 
 // Iteration 3: inward with the surviving and re-attached clusters, simple cut.
 __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
+  __shared__ float rx[kMaxRows];
+  for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
+  __syncthreads();
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
@@ -928,14 +958,22 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
     Trk<float> out = L.t;
     int out_sec = L.sector;
     for (int k = ns - 1; k >= 0; --k) {
+      // the station's cluster is requested before the station change (it
+      // does not depend on the state); inner stations hold at most
+      // inner_rows <= kMaxInner entries, as rows increase along a track
       const int rs = SR[k];
       const int sec = rs / NR, row = rs % NR;
-      if (k != ns - 1 && !lin_goto(L, sec, F.row_x[row], P)) break;
       const bool inner = row < P.inner_rows;
       const int c = inner ? F.ft_assigned[(long)f * kMaxInner + k] : (flag[k] ? -1 : SC[k]);
+      float cy = 0.0f, cz = 0.0f;
+      if (c >= 0) {
+        cy = F.sy[c];
+        cz = F.sz[c];
+      }
+      if (k != ns - 1 && !lin_goto(L, sec, rx[row], P)) break;
       if (c < 0) continue;
       float my, mz;
-      if (!corrected(M, P, sec, L.t.x, F.sy[c], F.sz[c], z0, L.r, my, mz)) continue;
+      if (!corrected(M, P, sec, L.t.x, cy, cz, z0, L.r, my, mz)) continue;
       const Resid R = residual(L.t, my, mz, P);
       if (R.chi2 > P.final_chi2) continue;
       chi2 = chi2 + R.chi2;
@@ -1416,8 +1454,9 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 
 int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const MapDev M = F.map;
+  k_fit_stations<<<sms * 8, kBlock, 0, s>>>(F, P);
   k_fit12<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, M);
-  int k = 1;
+  int k = 2;
   for (int r = 0; r < P.cand_k; ++r) {
     k_amb_bid<<<sms * 8, kBlock, 0, s>>>(F, P, r);
     k_amb_resolve<<<sms * 8, kBlock, 0, s>>>(F, P, r);

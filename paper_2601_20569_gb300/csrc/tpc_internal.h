@@ -72,6 +72,7 @@ enum : int {
 constexpr int kMaxBinOcc = 1024;
 
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
+constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
 constexpr int kMergeZ = 64;      // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 // Scheduling buckets of the sector refit (most clusters first).
@@ -146,8 +147,7 @@ struct FrameDev {
   int* tl_rhi;
   int* tl_hits;            // [cap_tl*kMaxRows] row-indexed sorted cluster or -1
   int* tl_len;             // [cap_tl] CA chain length from the start hit
-  int* tl_mid;             // [cap_tl] middle chain cluster (seed point)
-  int* tl_end;             // [cap_tl] last chain cluster (seed point)
+  float* tl_seed;          // [cap_tl][kSeedF] seed state, start (sector, row), valid flag
   // a6
   unsigned long long* owner_key;  // [n] sorted index space
   int* tl_acc;
@@ -185,6 +185,7 @@ struct FrameDev {
   // a9/a10 fit tracks (capacity cap_ft)
   long cap_ft;
   int* ft_head;            // first sector track of the chain
+  int* ft_last;            // last sector track of the chain
   int* ft_order;           // [cap_ft] order in which the fit kernels take the tracks:
                            // FP64-update loopers first, then the rest, each in list order
   int* ft_looper;          // [cap_ft] 1: |q/pT| of the chain's inner end above looper_qpt

@@ -284,12 +284,11 @@ struct Pick {
 // Best cluster of row (s, r) with chi2 < follow_chi2 (ties: smaller input id);
 // the y/z box is the widened 2x2 Mahalanobis bound of the cut.
 __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const Trk<float>& t,
-                                    int rr) {
+                                    const RowGrid& g) {
   const float hy = sqrtf(P.follow_chi2 * (t.c[0] + P.sy2)) * 1.001f + 0.01f;
   const float hz = sqrtf(P.follow_chi2 * (t.c[2] + P.sz2)) * 1.001f + 0.01f;
   const float ylo = t.p[0] - hy, yhi = t.p[0] + hy;
   const float zlo = t.p[1] - hz, zhi = t.p[1] + hz;
-  const RowGrid g = F.rows[rr];
   int best = -1, bid = 0;
   float bchi = 0.0f;
   for_window(F.bin_first, g, ylo, yhi, zlo, zhi, [&](int k) {
@@ -308,11 +307,14 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
   return best;
 }
 
-// CA chain of each start hit: length and the seed points (middle cluster =
-// the (L-1)/2-th up-link, last cluster).
-__global__ void k_chain_info(FrameDev F) {
+// CA chain of each start hit: its length and the seed through the chain's
+// first, middle (the (L-1)/2-th up-link) and last cluster, computed here for
+// all tracklets at once so that the constructor's state machine only loads
+// it.  tl_seed: p[5], x, (sector, row) of the start, 1 / 0 = seed valid.
+__global__ void k_chain_info(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
+  const int NR = P.n_rows;
   for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
     const int start = F.starts[ti];
     int L = 1, last = start, mid = start;
@@ -322,8 +324,25 @@ __global__ void k_chain_info(FrameDev F) {
       if (L & 1) mid = F.cup[mid];
     }
     F.tl_len[ti] = L;
-    F.tl_mid[ti] = mid;
-    F.tl_end[ti] = last;
+    float xs[3], ys[3], zs[3];
+    const int sel[3] = {start, mid, last};
+    int rr0 = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int rs = F.srow[sel[i]];
+      if (i == 0) rr0 = rs;
+      xs[i] = F.row_x[rs % NR];
+      ys[i] = F.sy[sel[i]];
+      zs[i] = F.sz[sel[i]];
+    }
+    Trk<float> t;
+    const bool ok = seed3(xs, ys, zs, P, t);
+    float* sd = F.tl_seed + (long)ti * kSeedF;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) sd[i] = t.p[i];
+    sd[5] = t.x;
+    sd[6] = __int_as_float(rr0);
+    sd[7] = __int_as_float(ok ? 1 : 0);
   }
 }
 
@@ -332,19 +351,20 @@ __global__ void k_chain_info(FrameDev F) {
 // current tracklet, and a lane whose tracklet ends takes the next one from the
 // work queue in the same loop.  The lanes of a warp therefore stay busy on
 // row steps however unequal their tracklets are.  Per tracklet the sequence
-// of operations is that of the constructor (Sec. 2.2): seed from the chain's
+// of operations is that of the constructor (Sec. 2): seed from the chain's
 // first, middle and last clusters; follow the CA chain upwards; extend
 // upwards by the best cluster of each row until max_miss rows in a row have
 // none; restart from the top with reset covariance, refit downwards over the
 // found clusters and extend below the start the same way.
 enum : int { kTlIdle = 0, kTlChain, kTlUp, kTlDown };
 
-__global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
+__global__ void __launch_bounds__(256, 2) k_tracklets(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
   int phase = kTlIdle;
-  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, c = 0, left = 0, miss = 0, n = 0, rlo = 0;
+  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, c = 0, cn = 0, left = 0, miss = 0, n = 0,
+      rlo = 0;
   int* H = nullptr;
   float chi2 = 0.0f, last_x = 0.0f;
   float last_p[5];
@@ -356,24 +376,25 @@ __global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
       if (ti >= nst) break;
       const int start = F.starts[ti];
       H = F.tl_hits + (long)ti * kMaxRows;
-      const int L = F.tl_len[ti], mid = F.tl_mid[ti], last_c = F.tl_end[ti];
-      const int rr0 = F.srow[start];
+      const int L = F.tl_len[ti];
+      const float* sd = F.tl_seed + (long)ti * kSeedF;
+      float sv[kSeedF];
+#pragma unroll
+      for (int i = 0; i < kSeedF; ++i) sv[i] = sd[i];
+      F.tl_n[ti] = 0;
+      if (__float_as_int(sv[7]) == 0) continue;  // no seed
+      const int rr0 = __float_as_int(sv[6]);
       r0 = rr0 % NR;
       sbase = rr0 - r0;  // sector * n_rows
-      float xs[3], ys[3], zs[3];
-      {
-        const int sel[3] = {start, mid, last_c};
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          xs[i] = F.row_x[F.srow[sel[i]] % NR];
-          ys[i] = F.sy[sel[i]];
-          zs[i] = F.sz[sel[i]];
-        }
-      }
-      F.tl_n[ti] = 0;
-      if (!seed3(xs, ys, zs, P, t)) continue;
-      update(t, residual(t, F.sy[start], F.sz[start], P));
+      for (int i = 0; i < 5; ++i) t.p[i] = sv[i];
+      t.x = sv[5];
+      reset_cov(t.c, P);
+      // the seed passes through the start cluster: its measurement is (y, z)
+      // of the seed itself
+      update(t, residual(t, t.p[0], t.p[1], P));
       H[r0] = start;
+      if (L > 1) cn = F.cup[start];
 #pragma unroll
       for (int i = 0; i < 5; ++i) last_p[i] = t.p[i];
       last_x = t.x;
@@ -385,13 +406,19 @@ __global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
       phase = left > 0 ? kTlChain : kTlUp;
       continue;
     }
-    // ---- one row step
+    // ---- one row step.  Everything the step reads that does not depend on
+    // the propagated state (the next chain cluster, the row's grid record,
+    // the stored hit of a row already visited) is requested before the
+    // propagation, so its latency overlaps the arithmetic.  A CA link always
+    // joins adjacent pad rows of one sector, so the chain's next row is known.
     int r, k = -1;
     bool stop;
     if (phase == kTlChain) {
-      k = F.cup[c];
+      // the next link was requested one step earlier
+      k = cn;
       c = k;
-      r = F.srow[k] % NR;
+      if (left > 1) cn = F.cup[k];
+      r = rcur + 1;
       stop = false;
     } else if (phase == kTlUp) {
       r = rcur + 1;
@@ -400,14 +427,19 @@ __global__ void __launch_bounds__(256) k_tracklets(FrameDev F, KParams P) {
       r = rcur - 1;
       stop = r < 0;
     }
+    const bool stored = phase == kTlDown && r >= r0;
+    RowGrid g;
+    if (!stop && phase != kTlChain) {
+      if (stored)
+        k = H[r];
+      else
+        g = F.rows[sbase + r];
+    }
     if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);
     if (!stop && phase != kTlChain) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
     bool miss_out = false;
     if (!stop) {
-      if (phase == kTlDown && r >= r0)
-        k = H[r];
-      else if (phase != kTlChain)
-        k = pick(F, P, t, sbase + r);
+      if (phase != kTlChain && !stored) k = pick(F, P, t, g);
       if (k >= 0) {
         const Resid R = residual(t, F.sy[k], F.sz[k], P);
         if (phase == kTlDown) chi2 = chi2 + R.chi2;
@@ -570,7 +602,7 @@ int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 }
 
 int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
-  k_chain_info<<<sms * 8, kBlock, 0, s>>>(F);
+  k_chain_info<<<sms * 8, kBlock, 0, s>>>(F, P);
   k_tracklets<<<persistent_grid(F.lc, kLTracklets, sms), F.lc.block[kLTracklets], 0, s>>>(F, P);
   return 2;
 }
