@@ -15,6 +15,7 @@
 #pragma once
 
 #include "tpc_internal.h"
+#include "tpc_fp64.cuh"
 
 namespace tpc {
 
@@ -223,9 +224,13 @@ __device__ __forceinline__ void update(Trk<float>& t, const Resid& R) {
 // The same update with the gain and covariance arithmetic in FP64, rounded
 // back to FP32 (the final fit's update of low-pT loopers).
 __device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
-  const double w00 = R.w00, w01 = R.w01, w11 = R.w11, r0 = R.r0, r1 = R.r1;
-  const double h0[5] = {t.c[0], t.c[1], t.c[3], t.c[6], t.c[10]};
-  const double h1[5] = {t.c[1], t.c[2], t.c[4], t.c[7], t.c[11]};
+  const double w00 = widen(R.w00), w01 = widen(R.w01), w11 = widen(R.w11), r0 = widen(R.r0),
+               r1 = widen(R.r1);
+  double cd[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) cd[i] = widen(t.c[i]);
+  const double h0[5] = {cd[0], cd[1], cd[3], cd[6], cd[10]};
+  const double h1[5] = {cd[1], cd[2], cd[4], cd[7], cd[11]};
   double k0[5], k1[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
@@ -233,13 +238,13 @@ __device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
     k1[i] = h0[i] * w01 + h1[i] * w11;
   }
 #pragma unroll
-  for (int i = 0; i < 5; ++i) t.p[i] = (float)((double)t.p[i] + (k0[i] * r0 + k1[i] * r1));
+  for (int i = 0; i < 5; ++i) t.p[i] = narrow(widen(t.p[i]) + (k0[i] * r0 + k1[i] * r1));
   int idx = 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
-      t.c[idx] = (float)((double)t.c[idx] - (k0[i] * h0[j] + k1[i] * h1[j]));
+      t.c[idx] = narrow(cd[idx] - (k0[i] * h0[j] + k1[i] * h1[j]));
       ++idx;
     }
   }
