@@ -201,29 +201,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# Algorithmic bytes of each stage (the minimum it must move), from the counts
-# of one call: clusters, tracklet hits, tracklets, sector-track hits, sector
-# tracks, fitted-track stations, fitted tracks.
+# Algorithmic bytes of each stage: the minimum it must move, from the counts
+# of one call (clusters n, tracklet hits th, tracklets nt, sector-track hits
+# sh, sector tracks ns, fit stations fst, fitted hits fh, fit tracks nf).
 def stage_bytes(name: str, c: dict) -> float:
     n, th, nt = c["clusters"], c["tl_hits"], c["tracklets"]
     sh, ns, fh, nf = c["st_hits"], c["sector_tracks"], c["fit_hits"], c["fit_tracks"]
-    if name == "grid":       # read y,z,row,sector; write sorted y,z,id,row
-        return n * (10 + 14)
-    if name == "links":      # read sorted y,z,id; write links; cleaner reads/writes links
-        return n * (12 + 8 + 8 + 8)
-    if name == "starts":     # read cleaned links; write the start list
-        return n * 8 + nt * 4
-    if name == "tracklets":  # y,z,id of each hit read twice (up, down), hit written, state out
-        return th * (2 * 12 + 4) + nt * 96
-    if name == "select":     # hits read twice, owner keys read and written
-        return th * (4 * 2 + 8 * 2) + nt * 16
-    if name == "merge":      # kept hits read twice with y,z,row; two end states per track
-        return sh * 2 * (4 + 10) + ns * 2 * 88
-    if name == "fit":        # station lists, 3 passes over y,z, stored predictions, state out
-        return fh * (6 + 3 * 10 + 2 * 20 + 1) + nf * 88 * 3
-    if name == "output":     # used clusters and state per output track
-        return fh * 12 + nf * 100
-    return 0.0
+    fst = c["fit_stations"]
+    table = {
+        # read y, z, row, sector; write sorted y, z, id, sector-row
+        "grid": n * (10 + 14),
+        # read sorted y, z, id; write links; cleaner reads/writes links
+        "links": n * (12 + 8 + 8 + 8),
+        # read cleaned links, write the start list
+        "starts": n * 8 + nt * 4,
+        # per hit: y, z, id read on the way up and down, hit written; state out
+        "tracklets": th * (2 * 12 + 4) + nt * 96,
+        # per hit: index and owner key read twice, key written; per tracklet
+        "select": th * (4 * 2 + 8 * 2) + nt * 16,
+        # per kept hit and pass: index, y, z, row; per track: start, two end states
+        "sector_refit": sh * 2 * (4 + 8 + 2) + ns * (24 + 2 * 88),
+        # both end states of every sector track, index and link words
+        "merge": ns * (2 * 88 + 16),
+        # per station: list entry, y, z and the stored prediction written
+        # (iteration 1), read back with the flag written (iteration 2); states
+        "fit12": fst * (6 + 8 + 20 + 6 + 8 + 20 + 1) + nf * 2 * 88,
+        # per inner station and round: candidate, chi2, bid word
+        "ambiguity2": nf * 20 * 4 * (4 + 4 + 8),
+        # per station: list entry, flag, y, z, used index; states
+        "fit3": fst * (6 + 1 + 8 + 4) + nf * 2 * 88,
+        # used clusters and state per output track
+        "output": fh * 12 + nf * 100,
+    }
+    return float(table.get(name, 0.0))
 
 
 def main():
@@ -333,7 +343,7 @@ def main():
         "clusters": n_per_step, "tl_hits": int(tr.debug("tl_n").sum()),
         "tracklets": int(tr.debug("tl_n").size), "st_hits": int(tr.debug("tl_nkept").sum()),
         "sector_tracks": int(tr.debug("st_key").size), "fit_hits": int(tr.debug("ft_n").sum()),
-        "fit_tracks": int(tr.debug("ft_n").size),
+        "fit_tracks": int(tr.debug("ft_n").size), "fit_stations": int(tr.debug("ft_nst").sum()),
     }
     hbm, peak_kind = peaks()
     dom = max(stages, key=lambda s: s["ms"])

@@ -2,7 +2,7 @@
 
 The sector/fit kernels are compiled twice: ``--fmad=false`` into namespace
 ``tpc::strict`` (bit-identical to a strict CPU evaluation) and with FMA
-contraction into ``tpc::fast``.
+contraction and hardware reciprocals (``TPC_FAST_ARITH``) into ``tpc::fast``.
 """
 from __future__ import annotations
 
@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if not os.path.exists(os.path.join(CSRC, tu)):
             continue
         base = os.path.splitext(tu)[0]
-        for ns, flags in (("strict", ["--fmad=false"]), ("fast", ["--fmad=true"])):
+        for ns, flags in (("strict", ["--fmad=false"]), ("fast", ["--fmad=true", "-DTPC_FAST_ARITH"])):
             obj = os.path.join(BUILD_DIR, f"{base}_{ns}.o")
             cmd = [nvcc] + COMMON + flags + [f"-DTPC_NS={ns}", "-c", os.path.join(CSRC, tu),
                                              "-o", obj]

@@ -29,8 +29,11 @@ const StageDef kStages[] = {
     {"starts", strict::stage_starts, fast::stage_starts},
     {"tracklets", strict::stage_tracklets, fast::stage_tracklets},
     {"select", strict::stage_select, fast::stage_select},
+    {"sector_refit", strict::stage_sector_refit, fast::stage_sector_refit},
     {"merge", strict::stage_merge, fast::stage_merge},
-    {"fit", strict::stage_fit, fast::stage_fit},
+    {"fit12", strict::stage_fit12, fast::stage_fit12},
+    {"ambiguity2", strict::stage_ambiguity2, fast::stage_ambiguity2},
+    {"fit3", strict::stage_fit3, fast::stage_fit3},
     {"output", strict::stage_output, fast::stage_output},
 };
 constexpr int kNumStages = sizeof(kStages) / sizeof(kStages[0]);
@@ -602,7 +605,7 @@ tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_f
 tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_frames,
                         void* cuda_stream) {
   if (!ctx || !frames || n_frames < 1) return TPC_ERR_INVALID_ARG;
-  static const char* slot_stage[kLNum] = {"tracklets", "merge", "merge", "fit", "fit"};
+  static const char* slot_stage[kLNum] = {"tracklets", "sector_refit", "merge", "fit12", "fit3"};
   static const int blocks[] = {64, 128, 256};
   static const int per_sm[] = {4, 8, 16};
   const bool prof_was = ctx->prof;

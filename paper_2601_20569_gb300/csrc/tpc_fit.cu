@@ -616,7 +616,7 @@ __device__ __forceinline__ bool lin_goto(Lin& L, int sector, float x, const KPar
 
 __device__ __forceinline__ void inv2(float a00, float a01, float a11, float& i00, float& i01,
                                      float& i11) {
-  const float idet = 1.0f / (a00 * a11 - a01 * a01);
+  const float idet = frcp(a00 * a11 - a01 * a01);
   i00 = a11 * idet;
   i01 = -a01 * idet;
   i11 = a00 * idet;
@@ -1425,7 +1425,7 @@ int refit_backward(RefitDev& R, const KParams& P, const int* steps3, int sms, cu
   return 2;
 }
 
-int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+int stage_sector_refit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const int nb_tl = (int)blocks_for(F.cap_tl, kBlock);
   k_acc_count<<<nb_tl, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_tracks);
@@ -1433,9 +1433,14 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_order_scatter<<<sms * 4, kBlock, 0, s>>>(F.st_obucket, F.st_oslot, F.st_ord_cnt,
                                              &F.cnt->n_tracks, F.cap_tl, &F.cnt->err, F.st_order);
   k_sector_refit<<<persistent_grid(F.lc, kLSectorRefit, sms), F.lc.block[kLSectorRefit], 0, s>>>(F, P);
+  return 5;
+}
+
+int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  const int nb_tl = (int)blocks_for(F.cap_tl, kBlock);
   k_sector_zrange<<<P.n_sectors, 256, 0, s>>>(F, P);
   k_ie_hist<<<sms * 8, kBlock, 0, s>>>(F, P);
-  int k = 7;
+  int k = 2;
   k += scan_exclusive(F.ie_cnt, F.ie_first, (long)P.n_sectors * P.n_rows * kMergeZ + 1,
                       F.scan_tmp, s);
   k_ie_scatter<<<sms * 8, kBlock, 0, s>>>(F);
@@ -1452,19 +1457,26 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   return k + 11;
 }
 
-int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
-  const MapDev M = F.map;
+int stage_fit12(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_fit_stations<<<sms * 8, kBlock, 0, s>>>(F, P);
-  k_fit12<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, M);
-  int k = 2;
+  k_fit12<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, F.map);
+  return 2;
+}
+
+int stage_ambiguity2(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  int k = 0;
   for (int r = 0; r < P.cand_k; ++r) {
     k_amb_bid<<<sms * 8, kBlock, 0, s>>>(F, P, r);
     k_amb_resolve<<<sms * 8, kBlock, 0, s>>>(F, P, r);
     k_amb_mark<<<sms * 8, kBlock, 0, s>>>(F, P, r);
     k += 3;
   }
-  k_fit3<<<persistent_grid(F.lc, kLFit3, sms), F.lc.block[kLFit3], 0, s>>>(F, P, M);
-  return k + 1;
+  return k;
+}
+
+int stage_fit3(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  k_fit3<<<persistent_grid(F.lc, kLFit3, sms), F.lc.block[kLFit3], 0, s>>>(F, P, F.map);
+  return 1;
 }
 
 int stage_output(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

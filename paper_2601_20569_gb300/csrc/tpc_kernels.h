@@ -15,8 +15,11 @@ namespace tpc {
   int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
   int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s);    \
   int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
+  int stage_sector_refit(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
   int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s);              \
-  int stage_fit(FrameDev& F, const KParams& P, int sms, cudaStream_t s);                \
+  int stage_fit12(FrameDev& F, const KParams& P, int sms, cudaStream_t s);              \
+  int stage_ambiguity2(FrameDev& F, const KParams& P, int sms, cudaStream_t s);         \
+  int stage_fit3(FrameDev& F, const KParams& P, int sms, cudaStream_t s);               \
   int stage_output(FrameDev& F, const KParams& P, int sms, cudaStream_t s);             \
   int refit_forward(RefitDev& R, const KParams& P, int* steps3, int sms, cudaStream_t s); \
   int refit_backward(RefitDev& R, const KParams& P, const int* steps3, int sms,          \

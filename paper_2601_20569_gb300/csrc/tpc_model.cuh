@@ -25,6 +25,16 @@ template <typename R> struct Trk {
   R x;
 };
 
+// 1/x: correctly rounded in strict mode; the hardware approximation (about
+// one ulp) in fast mode.
+__device__ __forceinline__ float frcp(float x) {
+#ifdef TPC_FAST_ARITH
+  return __fdividef(1.0f, x);
+#else
+  return 1.0f / x;
+#endif
+}
+
 // asin(u)/u as an 8-term series in u^2 (coefficients (2n)!/(4^n (n!)^2 (2n+1))).
 __device__ __forceinline__ float asinc_f(float u) {
   const float w = u * u;
@@ -65,6 +75,34 @@ __device__ __forceinline__ bool helix_step(const float* p, float dx, const KPara
   const float s0 = p[2];
   const float s1 = s0 + kappa * dx;
   if (!(fabsf(s1) < lim)) return false;
+#ifdef TPC_FAST_ARITH
+  // fast mode: hardware reciprocal and reciprocal square root (a few ulp)
+  // instead of the correctly rounded divide and square root
+  const float a0 = 1.0f - s0 * s0, a1 = 1.0f - s1 * s1;
+  const float rc0 = rsqrtf(a0), rc1 = rsqrtf(a1);
+  const float c0 = a0 * rc0;
+  const float c1 = a1 * rc1;
+  const float N = s0 + s1;
+  const float D = c0 + c1;
+  const float iD = frcp(D);
+  const float t = N * iD;
+  const float tt = 1.0f + t * t;
+  const float rL = rsqrtf(tt);
+  const float L1 = tt * rL;
+  const float chord = dx * L1;
+  const float u = kappa * chord * 0.5f;
+  const float ds = chord * asinc_f(u);
+  const float B = rsqrtf(1.0f - u * u);
+  const float Ap = asinc_deriv_f(u);
+  st.p0 = p[0] + dx * t;
+  st.p1 = p[1] + p[3] * ds;
+  st.p2 = s1;
+  const float iD2 = iD * iD;
+  const float q0 = s0 * rc0, q1 = s1 * rc1;
+  const float dt_ds0 = (2.0f * D + N * (q0 + q1)) * iD2;
+  const float dt_dk = dx * (D + N * q1) * iD2;
+  const float g = dx * t * rL;
+#else
   const float c0 = sqrtf(1.0f - s0 * s0);
   const float c1 = sqrtf(1.0f - s1 * s1);
   const float N = s0 + s1;
@@ -84,6 +122,7 @@ __device__ __forceinline__ bool helix_step(const float* p, float dx, const KPara
   const float dt_ds0 = (2.0f * D + N * (q0 + q1)) * iD2;
   const float dt_dk = dx * (D + N * q1) * iD2;
   const float g = dx * t / L1;
+#endif
   st.f02 = dx * dt_ds0;
   st.f04 = dx * dt_dk * P.kb;
   st.f12 = p[3] * g * dt_ds0 * B;
@@ -171,7 +210,7 @@ __device__ __forceinline__ Resid residual(const Trk<float>& t, float my, float m
   const float s00 = t.c[0] + P.sy2;
   const float s01 = t.c[1];
   const float s11 = t.c[2] + P.sz2;
-  const float idet = 1.0f / (s00 * s11 - s01 * s01);
+  const float idet = frcp(s00 * s11 - s01 * s01);
   R.w00 = s11 * idet;
   R.w01 = -s01 * idet;
   R.w11 = s00 * idet;
@@ -189,7 +228,7 @@ __device__ __forceinline__ float chi2_of(const Trk<float>& t, float my, float mz
   const float s00 = t.c[0] + P.sy2;
   const float s01 = t.c[1];
   const float s11 = t.c[2] + P.sz2;
-  const float idet = 1.0f / (s00 * s11 - s01 * s01);
+  const float idet = frcp(s00 * s11 - s01 * s01);
   const float w00 = s11 * idet;
   const float w01 = -s01 * idet;
   const float w11 = s00 * idet;
@@ -226,17 +265,30 @@ __device__ __forceinline__ void update(Trk<float>& t, const Resid& R) {
 __device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
   const double w00 = widen(R.w00), w01 = widen(R.w01), w11 = widen(R.w11), r0 = widen(R.r0),
                r1 = widen(R.r1);
-  double cd[15];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) cd[i] = widen(t.c[i]);
-  const double h0[5] = {cd[0], cd[1], cd[3], cd[6], cd[10]};
-  const double h1[5] = {cd[1], cd[2], cd[4], cd[7], cd[11]};
+  const double h0[5] = {widen(t.c[0]), widen(t.c[1]), widen(t.c[3]), widen(t.c[6]),
+                        widen(t.c[10])};
+  const double h1[5] = {h0[1], widen(t.c[2]), widen(t.c[4]), widen(t.c[7]), widen(t.c[11])};
   double k0[5], k1[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     k0[i] = h0[i] * w00 + h1[i] * w01;
     k1[i] = h0[i] * w01 + h1[i] * w11;
   }
+#ifdef TPC_FAST_ARITH
+  // fast mode: each correction accumulated into the entry by two FMAs (a
+  // different FP64 rounding order, one FP64 operation fewer per entry)
+#pragma unroll
+  for (int i = 0; i < 5; ++i) t.p[i] = narrow(fma(k1[i], r1, fma(k0[i], r0, widen(t.p[i]))));
+  int idx = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      t.c[idx] = narrow(fma(-k1[i], h1[j], fma(-k0[i], h0[j], widen(t.c[idx]))));
+      ++idx;
+    }
+  }
+#else
 #pragma unroll
   for (int i = 0; i < 5; ++i) t.p[i] = narrow(widen(t.p[i]) + (k0[i] * r0 + k1[i] * r1));
   int idx = 0;
@@ -244,10 +296,11 @@ __device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
   for (int i = 0; i < 5; ++i) {
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
-      t.c[idx] = narrow(cd[idx] - (k0[i] * h0[j] + k1[i] * h1[j]));
+      t.c[idx] = narrow(widen(t.c[idx]) - (k0[i] * h0[j] + k1[i] * h1[j]));
       ++idx;
     }
   }
+#endif
 }
 
 // Update of the final fit and refit: FP64 for loopers (|q/pT| > looper_qpt).

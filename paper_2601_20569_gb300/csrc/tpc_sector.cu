@@ -284,7 +284,7 @@ struct Pick {
 // Best cluster of row (s, r) with chi2 < follow_chi2 (ties: smaller input id);
 // the y/z box is the widened 2x2 Mahalanobis bound of the cut.
 __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const Trk<float>& t,
-                                    const RowGrid& g) {
+                                    const RowGrid& g, float& by, float& bz) {
   const float hy = sqrtf(P.follow_chi2 * (t.c[0] + P.sy2)) * 1.001f + 0.01f;
   const float hz = sqrtf(P.follow_chi2 * (t.c[2] + P.sz2)) * 1.001f + 0.01f;
   const float ylo = t.p[0] - hy, yhi = t.p[0] + hy;
@@ -302,6 +302,8 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
       best = k;
       bchi = chi2;
       bid = id;
+      by = yk;
+      bz = zk;
     }
   });
   return best;
@@ -358,17 +360,40 @@ __global__ void k_chain_info(FrameDev F, KParams P) {
 // found clusters and extend below the start the same way.
 enum : int { kTlIdle = 0, kTlChain, kTlUp, kTlDown };
 
-__global__ void __launch_bounds__(256, 2) k_tracklets(FrameDev F, KParams P) {
+// The state the constructor only saves and restores -- the state at the
+// innermost hit of the downward pass, and the state and position at the top
+// hit of the upward pass -- lives in shared memory (kTlShared floats per
+// thread, field-major so that a warp's accesses hit distinct banks), which
+// keeps the register count low enough for three 256-thread blocks per SM.
+constexpr int kTlShared = 29;  // inner p[5], c[15], x; top p[5], x, y_hit, z_hit
+
+__global__ void __launch_bounds__(256, 3) k_tracklets(FrameDev F, KParams P) {
+  extern __shared__ float tl_sh[];
+  float* const S = tl_sh + threadIdx.x;
+  const int BS = blockDim.x;
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
   int phase = kTlIdle;
-  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, c = 0, cn = 0, left = 0, miss = 0, n = 0,
-      rlo = 0;
+  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, c = 0, cn = 0, hn = -1, left = 0, miss = 0,
+      n = 0, rlo = 0;
   int* H = nullptr;
-  float chi2 = 0.0f, last_x = 0.0f;
-  float last_p[5];
-  Trk<float> t, inner;
+  float chi2 = 0.0f;
+  Trk<float> t;
+  auto save_inner = [&]() {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[i * BS] = t.p[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) S[(5 + i) * BS] = t.c[i];
+    S[20 * BS] = t.x;
+  };
+  auto save_top = [&](float y, float z) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[(21 + i) * BS] = t.p[i];
+    S[26 * BS] = t.x;
+    S[27 * BS] = y;
+    S[28 * BS] = z;
+  };
   for (;;) {
     if (phase == kTlIdle) {
       // take the next tracklet and seed it
@@ -392,12 +417,11 @@ __global__ void __launch_bounds__(256, 2) k_tracklets(FrameDev F, KParams P) {
       reset_cov(t.c, P);
       // the seed passes through the start cluster: its measurement is (y, z)
       // of the seed itself
-      update(t, residual(t, t.p[0], t.p[1], P));
+      const float y0 = t.p[0], z0 = t.p[1];
+      update(t, residual(t, y0, z0, P));
       H[r0] = start;
       if (L > 1) cn = F.cup[start];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) last_p[i] = t.p[i];
-      last_x = t.x;
+      save_top(y0, z0);
       top = r0;
       rcur = r0;
       c = start;
@@ -407,14 +431,14 @@ __global__ void __launch_bounds__(256, 2) k_tracklets(FrameDev F, KParams P) {
       continue;
     }
     // ---- one row step.  Everything the step reads that does not depend on
-    // the propagated state (the next chain cluster, the row's grid record,
-    // the stored hit of a row already visited) is requested before the
-    // propagation, so its latency overlaps the arithmetic.  A CA link always
+    // the propagated state is requested before the propagation so that its
+    // latency overlaps the arithmetic: the next chain link and the next
+    // stored hit (both one step ahead), the position of a cluster already
+    // known (chain, stored hit), the row's grid record.  A CA link always
     // joins adjacent pad rows of one sector, so the chain's next row is known.
     int r, k = -1;
     bool stop;
     if (phase == kTlChain) {
-      // the next link was requested one step earlier
       k = cn;
       c = k;
       if (left > 1) cn = F.cup[k];
@@ -429,19 +453,26 @@ __global__ void __launch_bounds__(256, 2) k_tracklets(FrameDev F, KParams P) {
     }
     const bool stored = phase == kTlDown && r >= r0;
     RowGrid g;
-    if (!stop && phase != kTlChain) {
-      if (stored)
-        k = H[r];
-      else
+    float ky = 0.0f, kz = 0.0f;
+    if (!stop) {
+      if (stored) {
+        k = hn;
+        hn = r - 1 >= r0 ? H[r - 1] : -1;
+      } else if (phase != kTlChain) {
         g = F.rows[sbase + r];
+      }
+      if (k >= 0) {
+        ky = F.sy[k];
+        kz = F.sz[k];
+      }
     }
     if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);
     if (!stop && phase != kTlChain) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
     bool miss_out = false;
     if (!stop) {
-      if (phase != kTlChain && !stored) k = pick(F, P, t, g);
+      if (phase != kTlChain && !stored) k = pick(F, P, t, g, ky, kz);
       if (k >= 0) {
-        const Resid R = residual(t, F.sy[k], F.sz[k], P);
+        const Resid R = residual(t, ky, kz, P);
         if (phase == kTlDown) chi2 = chi2 + R.chi2;
         update(t, R);
         if (phase == kTlDown) {
@@ -450,13 +481,11 @@ __global__ void __launch_bounds__(256, 2) k_tracklets(FrameDev F, KParams P) {
             miss = 0;
           }
           ++n;
-          inner = t;
+          save_inner();
           rlo = r;
         } else {
           H[r] = k;
-#pragma unroll
-          for (int i = 0; i < 5; ++i) last_p[i] = t.p[i];
-          last_x = t.x;
+          save_top(ky, kz);
           top = r;
           miss = 0;
         }
@@ -479,28 +508,28 @@ __global__ void __launch_bounds__(256, 2) k_tracklets(FrameDev F, KParams P) {
       F.tl_rlo[ti] = rlo;
       F.tl_rhi[ti] = top;
       F.tl_chi2[ti] = chi2;
-      F.tl_x[ti] = inner.x;
+      F.tl_x[ti] = S[20 * BS];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = inner.p[i];
+      for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = S[i * BS];
 #pragma unroll
-      for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = inner.c[i];
+      for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = S[(5 + i) * BS];
       continue;
     }
     if (!(stop || miss_out)) continue;
     // upward part done (chain broken, no more rows, edge or max_miss misses):
     // restart at the top with reset covariance and refit downwards
 #pragma unroll
-    for (int i = 0; i < 5; ++i) t.p[i] = last_p[i];
-    t.x = last_x;
+    for (int i = 0; i < 5; ++i) t.p[i] = S[(21 + i) * BS];
+    t.x = S[26 * BS];
     reset_cov(t.c, P);
     {
-      const int kt = H[top];
-      const Resid R = residual(t, F.sy[kt], F.sz[kt], P);
+      const Resid R = residual(t, S[27 * BS], S[28 * BS], P);
       chi2 = R.chi2;
       update(t, R);
     }
+    hn = top - 1 >= r0 ? H[top - 1] : -1;
     n = 1;
-    inner = t;
+    save_inner();
     rlo = top;
     rcur = top;
     miss = 0;
@@ -531,6 +560,11 @@ __global__ void k_sel_owner(FrameDev F, KParams P) {
   }
 }
 
+// Outer-to-inner walk of every tracklet's hits.  The rows are taken in
+// groups of kWalkGroup: their hit indices, then those hits' owner keys, are
+// requested together before the (sequential) keep decisions of the group.
+constexpr int kWalkGroup = 8;
+
 __global__ void k_sel_walk(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
@@ -541,24 +575,34 @@ __global__ void k_sel_walk(FrameDev F, KParams P) {
     const unsigned long long key = tracklet_key(F, P, ti);
     const int* H = F.tl_hits + (long)ti * kMaxRows;
     int* K = F.tl_kept + (long)ti * kMaxRows;
+    const int rlo = F.tl_rlo[ti], rhi = F.tl_rhi[ti];
     int kept = 0, shared = 0;
-    for (int r = F.tl_rhi[ti]; r >= F.tl_rlo[ti]; --r) {
-      const int k = H[r];
-      if (k < 0) continue;
-      if (F.owner_key[k] == key) {
-        K[kept++] = k;
-      } else if ((float)(shared + 1) <= P.shared_frac * (float)(kept + 1)) {
-        K[kept++] = k;
-        ++shared;
+    unsigned owned[(kMaxRows + 31) / 32] = {};  // bit j: K[j] is owned
+    for (int rg = rhi; rg >= rlo; rg -= kWalkGroup) {
+      int h[kWalkGroup];
+      unsigned long long ok[kWalkGroup];
+#pragma unroll
+      for (int j = 0; j < kWalkGroup; ++j) h[j] = rg - j >= rlo ? H[rg - j] : -1;
+#pragma unroll
+      for (int j = 0; j < kWalkGroup; ++j) ok[j] = h[j] >= 0 ? F.owner_key[h[j]] : 0ull;
+#pragma unroll
+      for (int j = 0; j < kWalkGroup; ++j) {
+        const int k = h[j];
+        if (k < 0) continue;
+        if (ok[j] == key) {
+          owned[kept >> 5] |= 1u << (kept & 31);
+          K[kept++] = k;
+        } else if ((float)(shared + 1) <= P.shared_frac * (float)(kept + 1)) {
+          K[kept++] = k;
+          ++shared;
+        }
       }
     }
     if (kept >= P.min_hits) {
       F.tl_nkept[ti] = kept;
       F.tl_acc[ti] = 1;
-      for (int r = F.tl_rhi[ti]; r >= F.tl_rlo[ti]; --r) {
-        const int k = H[r];
-        if (k >= 0 && F.owner_key[k] == key) F.sec_owner[k] = ti;
-      }
+      for (int j = 0; j < kept; ++j)
+        if (owned[j >> 5] & (1u << (j & 31))) F.sec_owner[K[j]] = ti;
     }
   }
 }
@@ -603,7 +647,9 @@ int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 
 int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_chain_info<<<sms * 8, kBlock, 0, s>>>(F, P);
-  k_tracklets<<<persistent_grid(F.lc, kLTracklets, sms), F.lc.block[kLTracklets], 0, s>>>(F, P);
+  const int tb = F.lc.block[kLTracklets];
+  k_tracklets<<<persistent_grid(F.lc, kLTracklets, sms), tb, sizeof(float) * kTlShared * tb, s>>>(
+      F, P);
   return 2;
 }
 
