@@ -73,7 +73,7 @@ constexpr int kMaxBinOcc = 1024;
 
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
-constexpr int kMergeZ = 64;      // z bins per sector of the merge candidate index
+constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 // Scheduling buckets of the sector refit (most clusters first).
 constexpr int kOrdBuckets = 128;
