@@ -287,6 +287,9 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   const long T = F.cap_tl;
   const long nmb = nrr * kMergeZ;
   ok &= dalloc(ctx, &F.st_tl, T);
+  ok &= dalloc(ctx, &F.st_off, T);
+  F.cap_pos = n + n / 4 + 4096;
+  ok &= dalloc(ctx, &F.st_pos, F.cap_pos);
   ok &= dalloc(ctx, &F.st_order, T);
   ok &= dalloc(ctx, &F.st_obucket, T);
   ok &= dalloc(ctx, &F.st_oslot, T);
@@ -502,6 +505,11 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
     if (needed) *needed = c.n_refs;
     return fail(ctx, TPC_ERR_CAPACITY, "cluster references %d exceed capacity %ld", c.n_refs,
                 F.cap_refs);
+  }
+  if (c.err & kErrCapPos) {
+    if (needed) *needed = c.n_pos;
+    return fail(ctx, TPC_ERR_CAPACITY, "kept sector-track clusters %d exceed capacity %ld",
+                c.n_pos, F.cap_pos);
   }
   if (c.err & kErrCapTracks) {
     if (needed) *needed = c.need_tracks;

@@ -151,45 +151,63 @@ __global__ void k_acc_write(FrameDev F) {
   const int f = (!F.cnt->err && i < nst && F.tl_acc[i]) ? 1 : 0;
   int tot;
   const int ex = block_exscan(f, sh, &tot);
+  // room for the track's kept-cluster positions: one atomic per warp (the
+  // layout of the position array is arbitrary; every track reads its own range)
+  const int nk = f ? F.tl_nkept[i] : 0;
+  const int lane = threadIdx.x & 31;
+  int incl = nk;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int base = 0;
+  if (lane == 31 && incl > 0) base = atomicAdd(&F.cnt->n_pos, incl);
+  base = __shfl_sync(0xffffffffu, base, 31);
   if (f) {
     const int j = F.scan_tmp[blockIdx.x] + ex;
     F.st_tl[j] = i;
+    F.st_off[j] = base + incl - nk;
     // scheduling bucket of the sector refit: most clusters first
-    const int b = kOrdBuckets - 1 - min(kOrdBuckets - 1, F.tl_nkept[i]);
+    const int b = kOrdBuckets - 1 - min(kOrdBuckets - 1, nk);
     F.st_obucket[j] = b;
     F.st_oslot[j] = atomicAdd(&F.st_ord_cnt[b], 1);
   }
 }
 
-// Position of sorted cluster c: pad-row x (from the shared-memory copy of the
-// row radii), y, z.
-struct ClPt {
-  float x, y, z;
-};
-__device__ __forceinline__ ClPt cl_point(const FrameDev& F, const float* rx, int NR, int c) {
-  ClPt p;
-  p.x = rx[F.srow[c] % NR];
-  p.y = F.sy[c];
-  p.z = F.sz[c];
-  return p;
+// Positions (pad-row x, y, z) of every sector track's kept clusters, in
+// kept order, gathered once so that the two passes of the sector refit read
+// each track's clusters as one contiguous run.
+__global__ void k_st_gather(FrameDev F, KParams P) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  if (F.cnt->n_pos > F.cap_pos) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&F.cnt->err, kErrCapPos);
+    return;
+  }
+  const int NR = P.n_rows;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x) {
+    const int ti = F.st_tl[j];
+    const int nk = F.tl_nkept[ti];
+    const int* K = F.tl_kept + (long)ti * kMaxRows;
+    float4* out = F.st_pos + F.st_off[j];
+#pragma unroll 4
+    for (int m = 0; m < nk; ++m) {
+      const int c = K[m];
+      out[m] = make_float4(F.row_x[F.srow[c] % NR], F.sy[c], F.sz[c], 0.0f);
+    }
+  }
 }
 
-// Sector refit of one track over its kept clusters K[j], j = j0, j0+dj, ...
-// (nsteps steps).  Loads run one step ahead of the filter (the index two
-// steps ahead), so the gather of the next cluster overlaps the arithmetic of
-// the current one.
-__device__ __forceinline__ bool refit_pass(const FrameDev& F, const KParams& P, const float* rx,
-                                           const int* K, int j0, int dj, int nsteps,
-                                           Trk<float>& t) {
-  const int NR = P.n_rows;
-  ClPt nxt = cl_point(F, rx, NR, K[j0]);
-  int cnext = nsteps > 1 ? K[j0 + dj] : 0;
+// Sector refit of one track over its kept clusters' positions PS[j], j = j0,
+// j0+dj, ... (nsteps steps).  Each position is loaded one step ahead of the
+// filter, so the load overlaps the arithmetic of the current step.
+__device__ __forceinline__ bool refit_pass(const KParams& P, const float4* PS, int j0, int dj,
+                                           int nsteps, Trk<float>& t) {
+  float4 nxt = PS[j0];
   for (int s = 0; s < nsteps; ++s) {
-    const ClPt cur = nxt;
-    if (s + 1 < nsteps) {
-      nxt = cl_point(F, rx, NR, cnext);
-      if (s + 2 < nsteps) cnext = K[j0 + (s + 2) * dj];
-    }
+    const float4 cur = nxt;
+    if (s + 1 < nsteps) nxt = PS[j0 + (s + 1) * dj];
     if (!propagate(t, cur.x, P, P.fit_max_snp)) return false;
     update(t, residual(t, cur.y, cur.z, P));
   }
@@ -197,9 +215,6 @@ __device__ __forceinline__ bool refit_pass(const FrameDev& F, const KParams& P, 
 }
 
 __global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
-  __shared__ float rx[kMaxRows];
-  for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
-  __syncthreads();
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
   const int NR = P.n_rows;
@@ -209,6 +224,7 @@ __global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
     const int ti = F.st_tl[i];
     const int nk = F.tl_nkept[ti];
     const int* K = F.tl_kept + (long)ti * kMaxRows;  // outermost first
+    const float4* PS = F.st_pos + F.st_off[i];       // same order
     const int rs = F.srow[K[nk - 1]];
     F.st_key[i] = F.sid[F.starts[ti]];
     F.st_sector[i] = rs / NR;
@@ -224,11 +240,11 @@ __global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
     t.x = F.tl_x[ti];
     reset_cov(t.c, P);
     // outward over the kept clusters (innermost first), then inward
-    bool ok = refit_pass(F, P, rx, K, nk - 1, -1, nk, t);
+    bool ok = refit_pass(P, PS, nk - 1, -1, nk, t);
     if (ok) {
       put_state(F.st_oe + (long)i * kStateF, t, rs / NR);
       reset_cov(t.c, P);
-      ok = refit_pass(F, P, rx, K, 0, 1, nk, t);
+      ok = refit_pass(P, PS, 0, 1, nk, t);
       if (ok) put_state(F.st_ie + (long)i * kStateF, t, rs / NR);
     }
     F.st_ok[i] = ok ? 1 : 0;
@@ -1432,8 +1448,9 @@ int stage_sector_refit(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_acc_write<<<nb_tl, kBlock, 0, s>>>(F);
   k_order_scatter<<<sms * 4, kBlock, 0, s>>>(F.st_obucket, F.st_oslot, F.st_ord_cnt,
                                              &F.cnt->n_tracks, F.cap_tl, &F.cnt->err, F.st_order);
+  k_st_gather<<<sms * 8, kBlock, 0, s>>>(F, P);
   k_sector_refit<<<persistent_grid(F.lc, kLSectorRefit, sms), F.lc.block[kLSectorRefit], 0, s>>>(F, P);
-  return 5;
+  return 6;
 }
 
 int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

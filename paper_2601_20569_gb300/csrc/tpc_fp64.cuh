@@ -5,8 +5,9 @@
 // of its FP64 issue on conversions.  widen() is exact for every finite float;
 // narrow() rounds to nearest even exactly as the hardware conversion does.
 // Values outside the normal float range (widen: denormals, infinities, NaN;
-// narrow: results below the smallest normal float or above the largest float
-// exponent) take the hardware conversion.  Host-compilable so that a CPU test
+// narrow: non-zero results below the smallest normal float or above the
+// largest float exponent) take the hardware conversion; zeros do not (fresh
+// covariances have many exact zeros).  Host-compilable so that a CPU test
 // can check both against the host's IEEE conversions.
 #pragma once
 
@@ -82,6 +83,7 @@ TPC_HD float narrow(double d) {
   uint32_t hi, lo;
   dbits(d, hi, lo);
   const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (((hi & 0x7fffffffu) | lo) == 0u) return bitsf(hi & 0x80000000u);  // signed zero
   if (e < 897u || e > 1150u) return (float)d;
   const uint32_t m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
   const uint32_t rest = lo & 0x1fffffffu;

@@ -4,6 +4,8 @@
 
 #include <cstdint>
 
+#include <vector_types.h>
+
 namespace tpc {
 
 constexpr int kMaxRows = 160;      // pad rows supported by the per-tracklet row arrays
@@ -63,6 +65,7 @@ enum : int {
   kErrCapRefs = 16,
   kErrCapCand = 32,
   kErrDense = 64,    // a search bin holds more than kMaxBinOcc clusters
+  kErrCapPos = 128,  // kept-cluster positions of the sector tracks
 };
 
 // Largest number of clusters one search bin may hold.  Bins are sized for a
@@ -101,6 +104,7 @@ struct Counters {
   int n_out;         // output tracks
   int queue[kQNum];  // work-queue heads
   int n_loopers;     // fit tracks whose updates run in FP64
+  int n_pos;         // kept-cluster positions of the sector tracks
 };
 
 // Working set of one frame on the device.
@@ -158,6 +162,9 @@ struct FrameDev {
 
   // a7 sector tracks (capacity cap_tl)
   int* st_tl;              // tracklet index of each accepted tracklet
+  int* st_off;             // first entry of the track's kept-cluster positions
+  float4* st_pos;          // [cap_pos] (x, y, z, -) of kept clusters, outermost first per track
+  long cap_pos;
   int* st_order;           // order in which the sector refit takes the tracks
   int* st_obucket;         // scheduling bucket
   int* st_oslot;           // place within the bucket
