@@ -256,8 +256,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.bin_first, F.cap_bins + 1);
   ok &= dalloc(ctx, &F.cl_bin, n);
   ok &= dalloc(ctx, &F.cl_slot, n);
-  ok &= dalloc(ctx, &F.sy, n);
-  ok &= dalloc(ctx, &F.sz, n);
+  ok &= dalloc(ctx, &F.syz, n);
   ok &= dalloc(ctx, &F.sid, n);
   ok &= dalloc(ctx, &F.srow, n);
   ok &= dalloc(ctx, &F.lup, n);
@@ -816,8 +815,7 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   if (w == "counters") { src = F.cnt; nb = sizeof(Counters); }
   else if (w == "rows") { src = F.rows; nb = sizeof(RowGrid) * nrr; }
   else if (w == "bin_first") { src = F.bin_first; nb = sizeof(int) * ((long)c.n_bins + 1); }
-  else if (w == "sy") { src = F.sy; nb = 4 * n; }
-  else if (w == "sz") { src = F.sz; nb = 4 * n; }
+  else if (w == "syz") { src = F.syz; nb = 8 * n; }
   else if (w == "sid") { src = F.sid; nb = 4 * n; }
   else if (w == "srow") { src = F.srow; nb = 2 * n; }
   else if (w == "lup") { src = F.lup; nb = 4 * n; }

@@ -194,7 +194,8 @@ __global__ void k_st_gather(FrameDev F, KParams P) {
 #pragma unroll 4
     for (int m = 0; m < nk; ++m) {
       const int c = K[m];
-      out[m] = make_float4(F.row_x[F.srow[c] % NR], F.sy[c], F.sz[c], 0.0f);
+      const float2 yz = F.syz[c];
+      out[m] = make_float4(F.row_x[F.srow[c] % NR], yz.x, yz.y, 0.0f);
     }
   }
 }
@@ -756,7 +757,8 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
   const RowGrid g = F.rows[rs];
   for_window(F.bin_first, g, cy - wy - 0.01f, cy + wy + 0.01f, cz - wz - 0.01f, cz + wz + 0.01f,
              [&](int kk) {
-    const float yk = F.sy[kk], zk = F.sz[kk];
+    const float2 pk = F.syz[kk];
+    const float yk = pk.x, zk = pk.y;
     if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
     float my, mz;
     if (!corrected(M, P, sec, L.t.x, yk, zk, z0, L.r, my, mz)) return;
@@ -829,8 +831,9 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
     const int sec = rs / NR, row = rs % NR;
     float cy = 0.0f, cz = 0.0f;
     if (c >= 0) {
-      cy = F.sy[c];
-      cz = F.sz[c];
+      const float2 pc = F.syz[c];
+      cy = pc.x;
+      cz = pc.y;
     }
     float sv[5];
     if (out) {
@@ -983,8 +986,9 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
       const int c = inner ? F.ft_assigned[(long)f * kMaxInner + k] : (flag[k] ? -1 : SC[k]);
       float cy = 0.0f, cz = 0.0f;
       if (c >= 0) {
-        cy = F.sy[c];
-        cz = F.sz[c];
+        const float2 pc = F.syz[c];
+        cy = pc.x;
+        cz = pc.y;
       }
       if (k != ns - 1 && !lin_goto(L, sec, rx[row], P)) break;
       if (c < 0) continue;

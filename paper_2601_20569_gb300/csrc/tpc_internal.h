@@ -127,8 +127,7 @@ struct FrameDev {
   int* cl_bin;             // [n] per input cluster
   int* cl_slot;            // [n]
   long cap_bins;
-  float* sy;               // [n] sorted
-  float* sz;
+  float2* syz;             // [n] sorted (y, z)
   int* sid;                // sorted -> input id
   uint16_t* srow;          // sorted -> sector*n_rows + row
   // a2/a3

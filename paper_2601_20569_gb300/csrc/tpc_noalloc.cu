@@ -54,11 +54,13 @@ constexpr long kOffBinFirst = kOffBinCnt + align256(sizeof(int) * (kNoAllocBins 
 constexpr long kOffScanTmp = kOffBinFirst + align256(sizeof(int) * (kNoAllocBins + 1));
 constexpr long kScanTmpInts = kNoAllocBins / 256 + 4096;
 constexpr long kOffPerCl = kOffScanTmp + align256(sizeof(int) * kScanTmpInts);
-constexpr long kPerClInts = 9;  // cl_bin, cl_slot, sy, sz, sid, lup, ldn, cup, cdn
+constexpr long kPerClInts = 9;  // cl_bin, cl_slot, (y, z) [two slots], sid, lup, ldn, cup, cdn
 constexpr long kOffSrow = kOffPerCl + kPerClInts * align256(4 * kNoAllocMaxClusters);
 constexpr long kScratchBytes = kOffSrow + align256(2 * kNoAllocMaxClusters);
 
 static_assert(kScratchBytes < (16L << 20), "no-allocation scratch must stay modest");
+static_assert(align256(4 * kNoAllocMaxClusters) == 4 * kNoAllocMaxClusters,
+              "the (y, z) pairs span two consecutive per-cluster slots");
 
 // The scratch.  Host code must never use the symbol's host-side address: the
 // device address is looked up per device below.
@@ -148,8 +150,7 @@ extern "C" tpc_status tpc_links_noalloc(const tpc_geometry* geo, const tpc_optio
     per[i] = (int*)(b + kOffPerCl + i * align256(4 * kNoAllocMaxClusters));
   F.cl_bin = per[0];
   F.cl_slot = per[1];
-  F.sy = (float*)per[2];
-  F.sz = (float*)per[3];
+  F.syz = (float2*)per[2];  // spans slots 2 and 3 (8 bytes per cluster)
   F.sid = per[4];
   F.lup = per[5];
   F.ldn = per[6];

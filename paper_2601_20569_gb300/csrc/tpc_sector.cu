@@ -109,8 +109,7 @@ __global__ void k_scatter(FrameDev F, KParams P) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n || F.cnt->err) return;
   const int pos = F.bin_first[F.cl_bin[i]] + F.cl_slot[i];
-  F.sy[pos] = F.y[i];
-  F.sz[pos] = F.z[i];
+  F.syz[pos] = make_float2(F.y[i], F.z[i]);
   F.sid[pos] = (int)i;
   F.srow[pos] = (uint16_t)(sector_of(F, i) * P.n_rows + F.row[i]);
 }
@@ -127,17 +126,15 @@ __global__ void k_bin_sort(FrameDev F) {
     }
     for (int k = lo + 1; k < hi; ++k) {
       const int id = F.sid[k];
-      const float y = F.sy[k], z = F.sz[k];
+      const float2 yz = F.syz[k];
       int j = k - 1;
       while (j >= lo && F.sid[j] > id) {
         F.sid[j + 1] = F.sid[j];
-        F.sy[j + 1] = F.sy[j];
-        F.sz[j + 1] = F.sz[j];
+        F.syz[j + 1] = F.syz[j];
         --j;
       }
       F.sid[j + 1] = id;
-      F.sy[j + 1] = y;
-      F.sz[j + 1] = z;
+      F.syz[j + 1] = yz;
     }
   }
 }
@@ -159,7 +156,8 @@ __global__ void k_links(FrameDev F, KParams P) {
   const int r = rr % P.n_rows;
   int bu = -1, bd = -1;
   if (r >= 1 && r <= P.n_rows - 2) {
-    const float yc = F.sy[k], zc = F.sz[k];
+    const float2 pc = F.syz[k];
+    const float yc = pc.x, zc = pc.y;
     const float xd = F.row_x[r - 1], xc = F.row_x[r], xu = F.row_x[r + 1];
     const float f = (xc - xd) / (xu - xd);
     const RowGrid gu = F.rows[rr + 1], gd = F.rows[rr - 1];
@@ -170,7 +168,8 @@ __global__ void k_links(FrameDev F, KParams P) {
     int nd = 0;
     bool dense = false;
     for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
-      const float yd = F.sy[d], zd = F.sz[d];
+      const float2 pd = F.syz[d];
+      const float yd = pd.x, zd = pd.y;
       if (!(fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)) return;
       if (nd < kLinkList)
         dl[nd++] = d;
@@ -180,7 +179,8 @@ __global__ void k_links(FrameDev F, KParams P) {
     float best = 0.0f;
     int buid = 0, bdid = 0;
     auto pair = [&](int u, float yu, float zu, int uid, int d) {
-      const float yd = F.sy[d], zd = F.sz[d];
+      const float2 pd = F.syz[d];
+      const float yd = pd.x, zd = pd.y;
       const float yp = yd + (yu - yd) * f;
       const float zp = zd + (zu - zd) * f;
       const float ey = yp - yc, ez = zp - zc;
@@ -197,14 +197,16 @@ __global__ void k_links(FrameDev F, KParams P) {
     };
     if (nd > 0)
       for_window(F.bin_first, gu, ylo, yhi, zlo, zhi, [&](int u) {
-        const float yu = F.sy[u], zu = F.sz[u];
+        const float2 pu = F.syz[u];
+        const float yu = pu.x, zu = pu.y;
         if (!(fabsf(yu - yc) <= P.link_wy && fabsf(zu - zc) <= P.link_wz)) return;
         const int uid = F.sid[u];
         if (!dense) {
           for (int j = 0; j < nd; ++j) pair(u, yu, zu, uid, dl[j]);
         } else {
           for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
-            const float yd = F.sy[d], zd = F.sz[d];
+            const float2 pd = F.syz[d];
+      const float yd = pd.x, zd = pd.y;
             if (fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)
               pair(u, yu, zu, uid, d);
           });
@@ -292,7 +294,8 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
   int best = -1, bid = 0;
   float bchi = 0.0f;
   for_window(F.bin_first, g, ylo, yhi, zlo, zhi, [&](int k) {
-    const float yk = F.sy[k], zk = F.sz[k];
+    const float2 pk = F.syz[k];
+    const float yk = pk.x, zk = pk.y;
     if (!(yk >= ylo && yk <= yhi)) return;
     if (fabsf(zk - t.p[1]) > hz) return;
     const float chi2 = chi2_of(t, yk, zk, P);
@@ -334,8 +337,9 @@ __global__ void k_chain_info(FrameDev F, KParams P) {
       const int rs = F.srow[sel[i]];
       if (i == 0) rr0 = rs;
       xs[i] = F.row_x[rs % NR];
-      ys[i] = F.sy[sel[i]];
-      zs[i] = F.sz[sel[i]];
+      const float2 ps = F.syz[sel[i]];
+      ys[i] = ps.x;
+      zs[i] = ps.y;
     }
     Trk<float> t;
     const bool ok = seed3(xs, ys, zs, P, t);
@@ -462,8 +466,9 @@ __global__ void __launch_bounds__(256, 3) k_tracklets(FrameDev F, KParams P) {
         g = F.rows[sbase + r];
       }
       if (k >= 0) {
-        ky = F.sy[k];
-        kz = F.sz[k];
+        const float2 pk = F.syz[k];
+        ky = pk.x;
+        kz = pk.y;
       }
     }
     if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);

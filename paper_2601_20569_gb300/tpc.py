@@ -157,7 +157,7 @@ def make_options(opts: dict | TrackerOptions | None = None, *, mode: int = 0,
 
 
 _DBG_DTYPE = {
-    "rows": None, "bin_first": np.int32, "sy": np.float32, "sz": np.float32, "sid": np.int32,
+    "rows": None, "bin_first": np.int32, "syz": np.float32, "sid": np.int32,
     "srow": np.uint16, "lup": np.int32, "ldn": np.int32, "cup": np.int32, "cdn": np.int32,
     "starts": np.int32, "tl_n": np.int32, "tl_rlo": np.int32, "tl_rhi": np.int32,
     "tl_chi2": np.float32, "tl_x": np.float32, "tl_par": np.float32, "tl_cov": np.float32,

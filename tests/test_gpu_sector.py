@@ -52,7 +52,8 @@ def compare_sector(tr, y, z, row, sec, opts, R=152):
     assert np.all(np.diff(srow) >= 0)
     rows = tr.debug("rows")
     bf = tr.debug("bin_first")
-    sy, sz = tr.debug("sy"), tr.debug("sz")
+    syz = tr.debug("syz")
+    sy, sz = syz[0::2], syz[1::2]
     assert np.array_equal(sy, y[sid]) and np.array_equal(sz, z[sid])
     for rr in np.nonzero(rows["ncl"])[0][:400]:
         g = rows[rr]
