@@ -97,6 +97,7 @@ typedef struct {
   float edge_margin;        /* following stops at |y| > x*tan(10 deg) + edge_margin [cm] */
   float looper_qpt;         /* |q/pT| above which the final fit's Kalman update runs in FP64
                                (low-pT loopers); 0 disables */
+  float ext_chi2;           /* Phase III: candidate cut of the inward extrapolation (2 dof) */
   int32_t max_miss;         /* consecutive empty rows ending the following */
   int32_t min_hits;         /* minimum clusters of a tracklet / track */
   int32_t merge_max_gap;    /* max rows between merged segments */
@@ -105,7 +106,8 @@ typedef struct {
   int32_t mode;             /* 0 = strict FP32 (no FMA), 1 = fast FP32 (FMA) */
   int32_t max_frames;       /* frames per tpc_track_batch call (<= 64; 0 or 1: single frames) */
   int32_t use_graphs;       /* 1: replay each call's chain from a captured CUDA graph */
-  int32_t reserved;
+  int32_t ext_rows;         /* Phase III (Sec. 3): rows below a track's innermost cluster searched
+                               by inward extrapolation, 0..32 (0: off) */
   int64_t cap_clusters;     /* max clusters per call (all frames of a batch) */
   int64_t cap_tracklets;    /* max tracklets per frame (0: n/16 + 4096) */
   int64_t cap_tracks;       /* max tracks per frame (0: cap_tracklets) */

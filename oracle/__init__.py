@@ -43,6 +43,7 @@ class _Opt(ctypes.Structure):
         ("attach_margin", ctypes.c_float),
         ("looper_qpt", ctypes.c_float),
         ("edge_margin", ctypes.c_float),
+        ("ext_chi2", ctypes.c_float),
         ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32),
         ("merge_max_gap", ctypes.c_int32),
@@ -51,6 +52,7 @@ class _Opt(ctypes.Structure):
         ("brute_force", ctypes.c_int32),
         ("n_rows", ctypes.c_int32),
         ("n_sectors", ctypes.c_int32),
+        ("ext_rows", ctypes.c_int32),
     ]
 
 

@@ -61,6 +61,7 @@ struct orc_options {
   float attach_margin;   // widening of the Phase II search window [cm]
   float looper_qpt;      // |q/pT| above which the fit's update runs in FP64 (0: never)
   float edge_margin;     // following stops |y| > x*tan(10 deg) + edge_margin [cm]
+  float ext_chi2;        // Phase III: candidate cut of the inward extrapolation (2 dof)
   int32_t max_miss;
   int32_t min_hits;
   int32_t merge_max_gap;
@@ -69,6 +70,7 @@ struct orc_options {
   int32_t brute_force;  // 1: candidate search scans whole rows (self-check)
   int32_t n_rows;
   int32_t n_sectors;
+  int32_t ext_rows;     // Phase III: rows searched below a track's innermost cluster (0: off)
 };
 // Correction map of the oracle (host memory): layout [3][n_z][n_r][n_phi].
 struct orc_map {
@@ -241,8 +243,9 @@ struct Params {
   Real kb, tan_half, rot_c, rot_s, link_wy, link_wz, link_chi2;
   Real seed_c[5], meas_sy2, meas_sz2, ms_theta2, row_pitch_inv, follow_chi2, max_snp, fit_max_snp, score_w,
       shared_frac, merge_chi2, merge_dy, merge_dz, int_chi2, final_chi2, attach_margin,
-      edge_margin, looper_qpt, merge_zspan;
-  int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors;
+      edge_margin, looper_qpt, merge_zspan, ext_chi2;
+  int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors,
+      ext_rows;
   std::vector<Real> row_x;
 };
 
@@ -276,6 +279,7 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
   P.max_miss = o.max_miss; P.min_hits = o.min_hits; P.merge_max_gap = o.merge_max_gap;
   P.inner_rows = o.inner_rows; P.cand_k = o.cand_k; P.brute_force = o.brute_force;
   P.n_rows = o.n_rows; P.n_sectors = o.n_sectors;
+  P.ext_chi2 = o.ext_chi2; P.ext_rows = o.ext_rows;
   P.row_x.resize(o.n_rows);
   for (int r = 0; r < o.n_rows; ++r) P.row_x[r] = (Real)row_x[r];
   return P;
@@ -1178,6 +1182,8 @@ struct FitTrack {
   std::vector<int> cand;   // [station][cand_k]
   std::vector<Real> cchi;  // [station][cand_k]
   std::vector<int> assigned;
+  int n_ext = 0;           // Phase III: rows extrapolated below the innermost station;
+                           // their candidate slots follow the stations' in ncand/cand/cchi
   bool ok = true;
   int fail_at = -1;        // diagnostics: 100*iteration + station of a failed step
   Track<Real> out{};
@@ -1194,16 +1200,76 @@ struct FitTrack {
 // rows; iteration 3 inward uses the surviving / assigned clusters with a
 // simple chi2 cut.  Iteration 3 runs in fit_iteration3 after the second
 // ambiguity solving.
+// Phase III (Sec. 3): from the state at the innermost station after
+// iteration 1, the track is extrapolated inward row by row over at most
+// ext_rows rows of the same sector (stopping where the propagation fails or
+// the track leaves the sector), and every cluster of a row whose chi2 to the
+// prediction is below ext_chi2 -- the stricter cut of the extrapolation --
+// becomes a candidate, except clusters already held by a station outside the
+// inner region of some track (`fixed`).  The candidates join the second
+// ambiguity solving; iteration 3 continues over the extrapolated rows.
+template <typename Real>
+void extrapolate_inward(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
+                        const std::vector<char>& fixed, FitTrack<Real>& T, Lin<Real> E) {
+  const int ns = (int)T.st.size();
+  const int sec = T.st[0].sector, r_first = T.st[0].row;
+  T.n_ext = 0;
+  for (int e = 0; e < P.ext_rows && r_first - 1 - e >= 0; ++e) {
+    const int r = r_first - 1 - e;
+    if (!lin_goto(E, sec, P.row_x[r], P)) break;
+    if (o_fabs(E.t.p[0]) > E.t.x * P.tan_half + P.edge_margin) break;
+    // window centre: the prediction moved back by the map's shift there
+    Real cy, cz;
+    {
+      Real D[3];
+      map_eval(M, P, sec, E.t.x, E.t.p[0], E.t.p[1] - T.z0, D);
+      Real sy = D[1], sz = D[2];
+      if (D[0] != Real(0)) {
+        Step<Real> stp;
+        if (helix_step(E.r, D[0], P, stp, P.fit_max_snp)) {
+          sy = sy - (stp.p[0] - E.r[0]);
+          sz = sz - (stp.p[1] - E.r[1]);
+        }
+      }
+      cy = E.t.p[0] - sy;
+      cz = E.t.p[1] - sz;
+    }
+    const Real wy = o_sqrt(P.ext_chi2 * (E.t.c[0] + P.meas_sy2)) * Real(1.001) + P.attach_margin;
+    const Real wz = o_sqrt(P.ext_chi2 * (E.t.c[2] + P.meas_sz2)) * Real(1.001) + P.attach_margin;
+    std::vector<std::pair<Real, int>> cands;
+    for_row_range(F, P, sec, r, cz - wz - Real(0.01), cz + wz + Real(0.01), [&](int id) {
+      if (fixed[id]) return;
+      if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - cz) <= wz)) return;
+      Real my, mz;
+      if (!corrected(M, P, sec, E.t.x, F.y[id], F.z[id], T.z0, E.r, my, mz)) return;
+      const Real c2 = residual(E.t, my, mz, P).chi2;
+      if (c2 < P.ext_chi2) cands.push_back({c2, id});
+    });
+    std::sort(cands.begin(), cands.end(), [](const auto& u, const auto& v) {
+      return u.first < v.first || (u.first == v.first && u.second < v.second);
+    });
+    const int nc = std::min((int)cands.size(), P.cand_k);
+    const size_t slot = (size_t)ns + e;
+    T.ncand[slot] = nc;
+    for (int j = 0; j < nc; ++j) {
+      T.cand[slot * P.cand_k + j] = cands[j].second;
+      T.cchi[slot * P.cand_k + j] = cands[j].first;
+    }
+    T.n_ext = e + 1;
+  }
+}
+
 template <typename Real>
 void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
-                      FitTrack<Real>& T, bool phase2, std::vector<Real>& store,
-                      Track<Real>& it2_end) {
+                      const std::vector<char>& fixed, FitTrack<Real>& T, bool phase2,
+                      std::vector<Real>& store, Track<Real>& it2_end) {
   const int ns = (int)T.st.size();
+  const int nslot = ns + (phase2 ? P.ext_rows : 0);
   store.assign((size_t)ns * 5, Real(0));
   T.flag.assign(ns, 0);
-  T.ncand.assign(ns, 0);
-  T.cand.assign((size_t)ns * P.cand_k, -1);
-  T.cchi.assign((size_t)ns * P.cand_k, Real(0));
+  T.ncand.assign(nslot, 0);
+  T.cand.assign((size_t)nslot * P.cand_k, -1);
+  T.cchi.assign((size_t)nslot * P.cand_k, Real(0));
   Lin<Real> L;
   // iteration 1: inward
   lin_start(L, T.outer, T.st[ns - 1].sector, P);
@@ -1225,6 +1291,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
       fit_update(L.t, residual(L.t, my, mz, P), P);
     }
   }
+  if (phase2 && P.ext_rows > 0) extrapolate_inward(F, P, M, fixed, T, L);
   // iteration 2: outward
   const Track<Real> s1 = L.t;
   lin_start(L, s1, T.st[0].sector, P);
@@ -1304,15 +1371,28 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
   T.chi2 = Real(0);
   T.n = 0;
   T.used.clear();
-  bool have = false;
-  for (int k = ns - 1; k >= 0; --k) {
-    const Station<Real>& s = T.st[k];
-    if (k != ns - 1 && !lin_goto(L, s.sector, P.row_x[s.row], P)) break;
-    const bool inner = phase2 && s.row < P.inner_rows;
-    const int c = inner ? T.assigned[k] : (T.flag[k] ? -1 : s.cl);
+  bool have = false, reached = true;
+  // the stations inward, then the rows extrapolated below the innermost one
+  for (int k = ns - 1; k >= -T.n_ext; --k) {
+    int sector, row, c;
+    if (k >= 0) {
+      const Station<Real>& s = T.st[k];
+      sector = s.sector;
+      row = s.row;
+      const bool inner = phase2 && s.row < P.inner_rows;
+      c = inner ? T.assigned[k] : (T.flag[k] ? -1 : s.cl);
+    } else {
+      sector = T.st[0].sector;
+      row = T.st[0].row + k;
+      c = T.assigned[ns - 1 - k];
+    }
+    if (k != ns - 1 && !lin_goto(L, sector, P.row_x[row], P)) {
+      reached = false;
+      break;
+    }
     if (c < 0) continue;
     Real my, mz;
-    if (!corrected(M, P, s.sector, L.t.x, F.y[c], F.z[c], T.z0, L.r, my, mz)) continue;
+    if (!corrected(M, P, sector, L.t.x, F.y[c], F.z[c], T.z0, L.r, my, mz)) continue;
     const Resid<Real> R = residual(L.t, my, mz, P);
     if (R.chi2 > P.final_chi2) continue;
     T.chi2 = T.chi2 + R.chi2;
@@ -1323,6 +1403,7 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
     T.out_sector = L.sector;
     have = true;
   }
+  (void)reached;
   std::reverse(T.used.begin(), T.used.end());
   if (!have) T.n = 0;
 }
@@ -1354,12 +1435,12 @@ template <typename Real>
 void second_ambiguity(std::vector<FitTrack<Real>>& FT, const Params<Real>& P) {
   std::map<int, uint64_t> bid;
   std::map<int, bool> taken;
-  for (auto& T : FT) T.assigned.assign(T.st.size(), -1);
+  for (auto& T : FT) T.assigned.assign(T.ncand.size(), -1);
   for (int k = 0; k < P.cand_k; ++k) {
     bid.clear();
     for (auto& T : FT) {
       if (!T.ok) continue;
-      for (size_t s = 0; s < T.st.size(); ++s) {
+      for (size_t s = 0; s < T.ncand.size(); ++s) {
         if (T.assigned[s] >= 0 || T.ncand[s] <= k) continue;
         const int c = T.cand[s * P.cand_k + k];
         if (taken.count(c)) continue;
@@ -1371,7 +1452,7 @@ void second_ambiguity(std::vector<FitTrack<Real>>& FT, const Params<Real>& P) {
     }
     for (auto& T : FT) {
       if (!T.ok) continue;
-      for (size_t s = 0; s < T.st.size(); ++s) {
+      for (size_t s = 0; s < T.ncand.size(); ++s) {
         if (T.assigned[s] >= 0 || T.ncand[s] <= k) continue;
         const int c = T.cand[s * P.cand_k + k];
         if (taken.count(c)) continue;
@@ -1596,10 +1677,17 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     T.z0 = ie.p[1] - ie.p[3] * o_sqrt(ie.x * ie.x + ie.p[0] * ie.p[0]);
     FT.push_back(std::move(T));
   }
-  // a9/a10
+  // a9/a10 (+ Phase III): clusters held by a station outside the inner
+  // region of any track are not extrapolation candidates
+  std::vector<char> fixed(F.n, 0);
+  if (P.ext_rows > 0)
+    for (const auto& T : FT)
+      for (const auto& s : T.st)
+        if (s.cl >= 0 && s.row >= P.inner_rows) fixed[s.cl] = 1;
   std::vector<Track<Real>> it2_end(FT.size());
   std::vector<Real> store;
-  for (size_t i = 0; i < FT.size(); ++i) fit_iterations12(F, P, M, FT[i], true, store, it2_end[i]);
+  for (size_t i = 0; i < FT.size(); ++i)
+    fit_iterations12(F, P, M, fixed, FT[i], true, store, it2_end[i]);
   second_ambiguity(FT, P);
   for (size_t i = 0; i < FT.size(); ++i)
     if (FT[i].ok) fit_iteration3(F, P, M, FT[i], true, it2_end[i]);
@@ -1682,6 +1770,31 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   res.put("cand_ids", cs_cand, "i4");
   res.put("cand_chi2", cs_chi, real_name<Real>());
   res.put("cand_assigned", cs_assigned, "i4");
+  // Phase III candidates and assignments of every extrapolated row
+  std::vector<int> ex_key, ex_row, ex_n, ex_cand, ex_assigned, fit_next;
+  std::vector<Real> ex_chi;
+  for (auto& T : FT) {
+    fit_next.push_back(T.ok ? T.n_ext : 0);
+    if (!T.ok) continue;
+    const size_t ns = T.st.size();
+    for (int e = 0; e < T.n_ext; ++e) {
+      ex_key.push_back(T.key);
+      ex_row.push_back(T.st[0].row - 1 - e);
+      ex_n.push_back(T.ncand[ns + e]);
+      for (int k = 0; k < P.cand_k; ++k) {
+        ex_cand.push_back(T.cand[(ns + e) * P.cand_k + k]);
+        ex_chi.push_back(T.cchi[(ns + e) * P.cand_k + k]);
+      }
+      ex_assigned.push_back(T.assigned[ns + e]);
+    }
+  }
+  res.put("fit_next", fit_next, "i4");
+  res.put("ext_key", ex_key, "i4");
+  res.put("ext_row", ex_row, "i4");
+  res.put("ext_n", ex_n, "i4");
+  res.put("ext_ids", ex_cand, "i4");
+  res.put("ext_chi2", ex_chi, real_name<Real>());
+  res.put("ext_assigned", ex_assigned, "i4");
 }
 
 template <typename Real>

@@ -154,6 +154,8 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.attach_margin = o.attach_margin;
   P.edge_margin = o.edge_margin;
   P.looper_qpt = o.looper_qpt;
+  P.ext_chi2 = o.ext_chi2;
+  P.ext_rows = o.ext_rows;
   // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
   P.merge_zspan = (float)((double)(o.merge_max_gap + 2) *
                           (((double)row_x[nr - 1] - (double)row_x[0]) / (double)(nr - 1)) /
@@ -207,6 +209,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
       opt->cand_k > kMaxCand || opt->min_hits < 3 || !(opt->shared_frac >= 0.0f) ||
       (opt->mode != 0 && opt->mode != 1) || opt->cap_clusters > (1L << 30) ||
       opt->inner_rows < 0 || opt->inner_rows > kMaxInner || opt->merge_max_gap < 1 ||
+      opt->ext_rows < 0 || opt->ext_rows > kMaxExt || !(opt->ext_chi2 > 0.0f) ||
       opt->max_frames < 0 || opt->max_frames > 64 ||
       (long)geo->n_sectors * (opt->max_frames > 1 ? opt->max_frames : 1) * geo->n_rows > 65535 ||
       !(opt->fit_max_snp > 0.0f && opt->fit_max_snp < 1.0f) ||
@@ -339,11 +342,15 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ft_store, FT * kMaxRows * 5);
   ok &= dalloc(ctx, &F.ft_flag, FT * kMaxRows);
   ok &= dalloc(ctx, &F.ft_end2, FT * kStateF);
-  ok &= dalloc(ctx, &F.ft_ncand, FT * kMaxInner);
-  ok &= dalloc(ctx, &F.ft_cand, FT * kMaxInner * kMaxCand);
-  ok &= dalloc(ctx, &F.ft_cchi, FT * kMaxInner * kMaxCand);
-  ok &= dalloc(ctx, &F.ft_assigned, FT * kMaxInner);
-  ok &= dalloc(ctx, &F.ft_newly, FT * kMaxInner);
+  F.nslot = kMaxInner + opt->ext_rows;
+  const long NS = F.nslot;
+  ok &= dalloc(ctx, &F.ft_ncand, FT * NS);
+  ok &= dalloc(ctx, &F.ft_cand, FT * NS * kMaxCand);
+  ok &= dalloc(ctx, &F.ft_cchi, FT * NS * kMaxCand);
+  ok &= dalloc(ctx, &F.ft_assigned, FT * NS);
+  ok &= dalloc(ctx, &F.ft_newly, FT * NS);
+  ok &= dalloc(ctx, &F.ft_next, FT);
+  ok &= dalloc(ctx, &F.ft_fixed, n);
   ok &= dalloc(ctx, &F.bid, n);
   ok &= dalloc(ctx, &F.taken, n);
   ok &= dalloc(ctx, &F.ft_n, FT);
@@ -412,6 +419,7 @@ tpc_status enqueue_chain(tpc_ctx* ctx, FrameDev& F, const KParams& Pc, cudaStrea
     CK(cudaMemsetAsync(F.taken, 0, n, s));
     CK(cudaMemsetAsync(F.attach, 0xFF, sizeof(int) * n, s));
     CK(cudaMemsetAsync(F.attach_key, 0x7F, sizeof(int) * n, s));
+    if (Pc.ext_rows > 0) CK(cudaMemsetAsync(F.ft_fixed, 0, n, s));
   }
   CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * (nrr * kMergeZ + 1), s));
   CK(cudaMemsetAsync(F.st_ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
@@ -848,10 +856,11 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   else if (w == "ft_st_cl") { src = F.ft_st_cl; nb = 4L * kMaxRows * nft; }
   else if (w == "ft_st_rs") { src = F.ft_st_rs; nb = 2L * kMaxRows * nft; }
   else if (w == "ft_flag") { src = F.ft_flag; nb = 1L * kMaxRows * nft; }
-  else if (w == "ft_ncand") { src = F.ft_ncand; nb = 1L * kMaxInner * nft; }
-  else if (w == "ft_cand") { src = F.ft_cand; nb = 4L * kMaxInner * kMaxCand * nft; }
-  else if (w == "ft_cchi") { src = F.ft_cchi; nb = 4L * kMaxInner * kMaxCand * nft; }
-  else if (w == "ft_assigned") { src = F.ft_assigned; nb = 4L * kMaxInner * nft; }
+  else if (w == "ft_ncand") { src = F.ft_ncand; nb = 1L * F.nslot * nft; }
+  else if (w == "ft_cand") { src = F.ft_cand; nb = 4L * F.nslot * kMaxCand * nft; }
+  else if (w == "ft_cchi") { src = F.ft_cchi; nb = 4L * F.nslot * kMaxCand * nft; }
+  else if (w == "ft_assigned") { src = F.ft_assigned; nb = 4L * F.nslot * nft; }
+  else if (w == "ft_next") { src = F.ft_next; nb = 4L * nft; }
   else if (w == "ft_n") { src = F.ft_n; nb = 4L * nft; }
   else if (w == "out_par") { src = F.out_par; nb = 4L * 5 * c.n_out; }
   else if (w == "out_cov") { src = F.out_cov; nb = 4L * 15 * c.n_out; }

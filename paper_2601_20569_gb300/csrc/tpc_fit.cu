@@ -712,10 +712,20 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
     const int head = F.ft_head[f];
     int last = head;
     while (F.st_next[last] >= 0) last = F.st_next[last];
-    F.ft_nst[f] = build_stations(F, P, f, head);
+    const int ns = build_stations(F, P, f, head);
+    F.ft_nst[f] = ns;
     F.ft_key[f] = F.st_key[head];
     F.ft_last[f] = last;
     F.ft_z0[f] = zoff(F.st_ie + (long)head * kStateF);
+    F.ft_next[f] = 0;
+    if (P.ext_rows > 0) {
+      // Phase III: clusters held by a station outside the inner region are
+      // not extrapolation candidates of any track
+      const int* SC = F.ft_st_cl + (long)f * kMaxRows;
+      const uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
+      for (int k = 0; k < ns; ++k)
+        if (SC[k] >= 0 && SR[k] % P.n_rows >= P.inner_rows) F.ft_fixed[SC[k]] = 1;
+    }
   }
 }
 
@@ -727,7 +737,7 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
 // Iteration 1 runs inward storing the predictions; iteration 2 runs outward,
 // interpolates with them, flags outliers and collects the inner-row
 // candidates (Sec. 3).
-enum : int { kFitIdle = 0, kFitIn, kFitOut };
+enum : int { kFitIdle = 0, kFitIn, kFitOut, kFitExt };
 
 __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, const MapDev& M,
                                                  int f, int k, int rs, const Lin& L,
@@ -750,8 +760,8 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
   }
   const float wy = sqrtf(P.int_chi2 * (I.c00 + P.sy2)) * 1.001f + P.attach_margin;
   const float wz = sqrtf(P.int_chi2 * (I.c11 + P.sz2)) * 1.001f + P.attach_margin;
-  int* cand = F.ft_cand + ((long)f * kMaxInner + k) * kMaxCand;
-  float* cchi = F.ft_cchi + ((long)f * kMaxInner + k) * kMaxCand;
+  int* cand = F.ft_cand + ((long)f * F.nslot + k) * kMaxCand;
+  float* cchi = F.ft_cchi + ((long)f * F.nslot + k) * kMaxCand;
   int nc = 0;
   int cid[kMaxCand];
   const RowGrid g = F.rows[rs];
@@ -780,8 +790,67 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
     cid[pos] = id;
     if (nc < P.cand_k) ++nc;
   });
-  F.ft_ncand[(long)f * kMaxInner + k] = (uint8_t)nc;
-  F.ft_assigned[(long)f * kMaxInner + k] = -1;
+  F.ft_ncand[(long)f * F.nslot + k] = (uint8_t)nc;
+  F.ft_assigned[(long)f * F.nslot + k] = -1;
+}
+
+// Phase III (Sec. 3): candidates of extrapolated row slot e (sorted (sector,
+// row) rr) -- every cluster not held by a station outside the inner region
+// whose chi2 to the prediction is below ext_chi2, the best cand_k by
+// (chi2, id), for the second ambiguity solving.
+__device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, const MapDev& M, int f,
+                                            int e, int rr, const Lin& L, float z0) {
+  const int sec = rr / P.n_rows;
+  float cy, cz;
+  {
+    float D[3];
+    map_eval(M, P, sec, L.t.x, L.t.p[0], L.t.p[1] - z0, D);
+    float sy = D[1], sz = D[2];
+    if (D[0] != 0.0f) {
+      StepJ stp;
+      if (helix_step(L.r, D[0], P, stp, P.fit_max_snp)) {
+        sy = sy - (stp.p0 - L.r[0]);
+        sz = sz - (stp.p1 - L.r[1]);
+      }
+    }
+    cy = L.t.p[0] - sy;
+    cz = L.t.p[1] - sz;
+  }
+  const float wy = sqrtf(P.ext_chi2 * (L.t.c[0] + P.sy2)) * 1.001f + P.attach_margin;
+  const float wz = sqrtf(P.ext_chi2 * (L.t.c[2] + P.sz2)) * 1.001f + P.attach_margin;
+  const long slot = (long)f * F.nslot + kMaxInner + e;
+  int* cand = F.ft_cand + slot * kMaxCand;
+  float* cchi = F.ft_cchi + slot * kMaxCand;
+  int nc = 0;
+  int cid[kMaxCand];
+  const RowGrid g = F.rows[rr];
+  for_window(F.bin_first, g, cy - wy - 0.01f, cy + wy + 0.01f, cz - wz - 0.01f, cz + wz + 0.01f,
+             [&](int kk) {
+    if (F.ft_fixed[kk]) return;
+    const float2 pk = F.syz[kk];
+    const float yk = pk.x, zk = pk.y;
+    if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
+    float my, mz;
+    if (!corrected(M, P, sec, L.t.x, yk, zk, z0, L.r, my, mz)) return;
+    const float c2 = chi2_of(L.t, my, mz, P);
+    if (!(c2 < P.ext_chi2)) return;
+    const int id = F.sid[kk];
+    int pos = nc;
+    while (pos > 0 && (c2 < cchi[pos - 1] || (c2 == cchi[pos - 1] && id < cid[pos - 1]))) --pos;
+    if (pos >= P.cand_k) return;
+    const int lim = nc < P.cand_k ? nc : P.cand_k - 1;
+    for (int j = lim; j > pos; --j) {
+      cand[j] = cand[j - 1];
+      cchi[j] = cchi[j - 1];
+      cid[j] = cid[j - 1];
+    }
+    cand[pos] = kk;
+    cchi[pos] = c2;
+    cid[pos] = id;
+    if (nc < P.cand_k) ++nc;
+  });
+  F.ft_ncand[slot] = (uint8_t)nc;
+  F.ft_assigned[slot] = -1;
 }
 
 __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev M) {
@@ -820,6 +889,28 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
       lin_start(L, s0, SR[ns - 1] / NR, P);
       k = ns - 1;
       phase = kFitIn;
+      continue;
+    }
+    if (phase == kFitExt) {
+      // Phase III: one row of the inward extrapolation below the innermost
+      // station (k counts the rows done); at its end iteration 2 starts from
+      // the state iteration 1 ended with
+      const int rs0 = SR[0];
+      const int r = rs0 % NR - 1 - k;
+      bool go = k < P.ext_rows && r >= 0;
+      if (go) go = lin_goto(L, rs0 / NR, rx[r], P);
+      if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
+      if (go) {
+        ext_candidates(F, P, M, f, k, rs0 - rs0 % NR + r, L, z0);
+        ++k;
+      } else {
+        F.ft_next[f] = k;
+        Trk<float> s1;
+        get_state(F.ft_end2 + (long)f * kStateF, s1);
+        lin_start(L, s1, rs0 / NR, P);
+        k = 0;
+        phase = kFitOut;
+      }
       continue;
     }
     // ---- one station.  The cluster and, outward, the stored prediction do
@@ -876,11 +967,18 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
     }
     if (!out) {
       if (--k < 0) {
-        // iteration 2 starts from the inner end of iteration 1
-        const Trk<float> s1 = L.t;
-        lin_start(L, s1, SR[0] / NR, P);
-        k = 0;
-        phase = kFitOut;
+        if (P.ext_rows > 0) {
+          // keep the end of iteration 1 for iteration 2; extrapolate first
+          put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
+          k = 0;
+          phase = kFitExt;
+        } else {
+          // iteration 2 starts from the inner end of iteration 1
+          const Trk<float> s1 = L.t;
+          lin_start(L, s1, SR[0] / NR, P);
+          k = 0;
+          phase = kFitOut;
+        }
       }
     } else if (++k == ns) {
       put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
@@ -895,15 +993,28 @@ __device__ __forceinline__ bool inner_station(const FrameDev& F, const KParams& 
   return k < F.ft_nst[f] && (F.ft_st_rs[(long)f * kMaxRows + k] % P.n_rows) < P.inner_rows;
 }
 
+// Work item w of the second ambiguity: (fit track, candidate slot).  Slots
+// 0..inner_rows-1 are the inner stations, the next ext_rows slots the rows
+// extrapolated below the track (Phase III); returns -1 for an unused slot.
+__device__ __forceinline__ long amb_slot(const FrameDev& F, const KParams& P, long w, int& f) {
+  const int per = P.inner_rows + P.ext_rows;
+  f = (int)(w / per);
+  const int k = (int)(w % per);
+  if (!F.ft_ok[f]) return -1;
+  if (k < P.inner_rows) return inner_station(F, P, f, k) ? (long)f * F.nslot + k : -1;
+  const int e = k - P.inner_rows;
+  return e < F.ft_next[f] ? (long)f * F.nslot + kMaxInner + e : -1;
+}
+
 __global__ void k_amb_bid(FrameDev F, KParams P, int round) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  const long tot = (long)nf * P.inner_rows;
+  const long tot = (long)nf * (P.inner_rows + P.ext_rows);
   for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
        w += (long)gridDim.x * blockDim.x) {
-    const int f = (int)(w / P.inner_rows), k = (int)(w % P.inner_rows);
-    if (!F.ft_ok[f] || !inner_station(F, P, f, k)) continue;
-    const long sk = (long)f * kMaxInner + k;
+    int f;
+    const long sk = amb_slot(F, P, w, f);
+    if (sk < 0) continue;
     if (F.ft_assigned[sk] >= 0 || F.ft_ncand[sk] <= round) continue;
     const int c = F.ft_cand[sk * kMaxCand + round];
     if (F.taken[c]) continue;
@@ -914,12 +1025,12 @@ __global__ void k_amb_bid(FrameDev F, KParams P, int round) {
 __global__ void k_amb_resolve(FrameDev F, KParams P, int round) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  const long tot = (long)nf * P.inner_rows;
+  const long tot = (long)nf * (P.inner_rows + P.ext_rows);
   for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
        w += (long)gridDim.x * blockDim.x) {
-    const int f = (int)(w / P.inner_rows), k = (int)(w % P.inner_rows);
-    if (!F.ft_ok[f] || !inner_station(F, P, f, k)) continue;
-    const long sk = (long)f * kMaxInner + k;
+    int f;
+    const long sk = amb_slot(F, P, w, f);
+    if (sk < 0) continue;
     F.ft_newly[sk] = 0;
     if (F.ft_assigned[sk] >= 0 || F.ft_ncand[sk] <= round) continue;
     const int c = F.ft_cand[sk * kMaxCand + round];
@@ -934,12 +1045,12 @@ __global__ void k_amb_resolve(FrameDev F, KParams P, int round) {
 __global__ void k_amb_mark(FrameDev F, KParams P, int round) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  const long tot = (long)nf * P.inner_rows;
+  const long tot = (long)nf * (P.inner_rows + P.ext_rows);
   for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
        w += (long)gridDim.x * blockDim.x) {
-    const int f = (int)(w / P.inner_rows), k = (int)(w % P.inner_rows);
-    if (!F.ft_ok[f] || !inner_station(F, P, f, k)) continue;
-    const long sk = (long)f * kMaxInner + k;
+    int f;
+    const long sk = amb_slot(F, P, w, f);
+    if (sk < 0) continue;
     if (F.ft_ncand[sk] <= round) continue;
     const int c = F.ft_cand[sk * kMaxCand + round];
     if (F.ft_newly[sk]) F.taken[c] = 1;
@@ -976,14 +1087,25 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
     int n = 0;
     Trk<float> out = L.t;
     int out_sec = L.sector;
-    for (int k = ns - 1; k >= 0; --k) {
+    // the stations inward, then the rows extrapolated below the innermost one
+    const int next = P.ext_rows > 0 ? F.ft_next[f] : 0;
+    const int rs0 = SR[0];
+    for (int k = ns - 1; k >= -next; --k) {
       // the station's cluster is requested before the station change (it
       // does not depend on the state); inner stations hold at most
       // inner_rows <= kMaxInner entries, as rows increase along a track
-      const int rs = SR[k];
-      const int sec = rs / NR, row = rs % NR;
-      const bool inner = row < P.inner_rows;
-      const int c = inner ? F.ft_assigned[(long)f * kMaxInner + k] : (flag[k] ? -1 : SC[k]);
+      int sec, row, c;
+      if (k >= 0) {
+        const int rs = SR[k];
+        sec = rs / NR;
+        row = rs % NR;
+        const bool inner = row < P.inner_rows;
+        c = inner ? F.ft_assigned[(long)f * F.nslot + k] : (flag[k] ? -1 : SC[k]);
+      } else {
+        sec = rs0 / NR;
+        row = rs0 % NR + k;
+        c = F.ft_assigned[(long)f * F.nslot + kMaxInner - 1 - k];
+      }
       float cy = 0.0f, cz = 0.0f;
       if (c >= 0) {
         const float2 pc = F.syz[c];

@@ -23,8 +23,8 @@ struct KParams {
   float seed_c[5];
   float follow_chi2, max_snp, fit_max_snp, score_w, shared_frac;
   float merge_chi2, merge_dy, merge_dz, merge_zspan;
-  float int_chi2, final_chi2, attach_margin, edge_margin, looper_qpt;
-  int max_miss, min_hits, merge_max_gap, inner_rows, cand_k;
+  float int_chi2, final_chi2, attach_margin, edge_margin, looper_qpt, ext_chi2;
+  int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, ext_rows;
   int n_rows, n_sectors;  // n_sectors: all sectors of the call (frames x sectors)
   int n_phi;         // azimuthal sectors of one TPC half (sector % n_phi, side = sector / n_phi)
   float grid_dy;     // target y bin size [cm]
@@ -78,6 +78,7 @@ constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
+constexpr int kMaxExt = 32;      // Phase III: rows extrapolated below a track (slots after the inner ones)
 // Scheduling buckets of the sector refit (most clusters first).
 constexpr int kOrdBuckets = 128;
 
@@ -204,11 +205,16 @@ struct FrameDev {
   float* ft_store;         // [cap_ft][kMaxRows][5] iteration-1 predictions
   uint8_t* ft_flag;        // [cap_ft][kMaxRows]
   float* ft_end2;          // [cap_ft][kStateF] end of iteration 2 (+ sector)
-  uint8_t* ft_ncand;       // [cap_ft][kMaxInner]
-  int* ft_cand;            // [cap_ft][kMaxInner][kMaxCand]
-  float* ft_cchi;          // [cap_ft][kMaxInner][kMaxCand]
-  int* ft_assigned;        // [cap_ft][kMaxInner]
-  uint8_t* ft_newly;       // [cap_ft][kMaxInner]
+  // candidate slots per fit track: nslot = kMaxInner inner-station slots
+  // (station k) followed by ext_rows extrapolation slots (row r_first - 1 - e)
+  int nslot;
+  uint8_t* ft_ncand;       // [cap_ft][nslot]
+  int* ft_cand;            // [cap_ft][nslot][kMaxCand]
+  float* ft_cchi;          // [cap_ft][nslot][kMaxCand]
+  int* ft_assigned;        // [cap_ft][nslot]
+  uint8_t* ft_newly;       // [cap_ft][nslot]
+  int* ft_next;            // [cap_ft] rows extrapolated below the innermost station
+  uint8_t* ft_fixed;       // [n] sorted cluster held by a station outside the inner region
   unsigned long long* bid; // [n] per sorted cluster
   uint8_t* taken;          // [n]
   int* ft_n;               // iteration 3 results

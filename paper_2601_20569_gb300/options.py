@@ -7,7 +7,11 @@ values; the defaults below are this library's readings of it:
   the mitigation described in Sec. 2);
 * the "inner region" where Phase II re-attaches clusters = the 20 innermost
   pad rows (Sec. 2 and Sec. 4 both single out rows below 20);
-* Phase II candidate depth (tracks may fall back to their k-th candidate) = 4.
+* Phase II candidate depth (tracks may fall back to their k-th candidate) = 4;
+* Phase III (Sec. 3): tracks are extrapolated inward over at most ``ext_rows``
+  rows below their innermost cluster, with a candidate cut of chi2 < 9
+  (stricter than the interpolation cut of 25); off by default, as the paper
+  describes it as work in progress.
 """
 from __future__ import annotations
 
@@ -41,6 +45,9 @@ class TrackerOptions:
     attach_margin: float = 0.5      # widening of the Phase II search window [cm]
     looper_qpt: float = 1.0 / 0.15  # |q/pT| above which the fit update runs in FP64
     edge_margin: float = 1.0        # following stops beyond the sector edge + this [cm]
+    ext_rows: int = 0               # Phase III: rows searched below a track's innermost
+                                    # cluster by inward extrapolation (0: off, <= 32)
+    ext_chi2: float = 9.0           # Phase III candidate cut (2 dof), stricter than int_chi2
     max_miss: int = 10              # consecutive empty rows ending the following
     min_hits: int = 10
     merge_max_gap: int = 20         # rows between merged segments
@@ -56,9 +63,10 @@ class TrackerOptions:
 
 FLOAT_FIELDS = ("bz", "sigma_y", "sigma_z", "ms_theta", "link_wy", "link_wz", "link_chi2")
 FLOAT_FIELDS2 = ("follow_chi2", "max_snp", "fit_max_snp", "score_w", "shared_frac", "merge_chi2", "merge_dy",
-                 "merge_dz", "int_chi2", "final_chi2", "attach_margin", "looper_qpt", "edge_margin")
+                 "merge_dz", "int_chi2", "final_chi2", "attach_margin", "looper_qpt", "edge_margin",
+                 "ext_chi2")
 INT_FIELDS = ("max_miss", "min_hits", "merge_max_gap", "inner_rows", "cand_k", "brute_force",
-              "n_rows", "n_sectors")
+              "n_rows", "n_sectors", "ext_rows")
 
 
 def ctypes_fields():

@@ -51,11 +51,12 @@ class Options(ctypes.Structure):
         ("merge_dy", ctypes.c_float), ("merge_dz", ctypes.c_float), ("int_chi2", ctypes.c_float),
         ("final_chi2", ctypes.c_float), ("attach_margin", ctypes.c_float),
         ("edge_margin", ctypes.c_float), ("looper_qpt", ctypes.c_float),
+        ("ext_chi2", ctypes.c_float),
         ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32), ("merge_max_gap", ctypes.c_int32),
         ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("max_frames", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("ext_rows", ctypes.c_int32),
         ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
         ("cap_tracks", ctypes.c_int64),
     ]
@@ -147,8 +148,6 @@ def make_options(opts: dict | TrackerOptions | None = None, *, mode: int = 0,
             o.max_frames = int(max_frames)
         elif name == "use_graphs":
             o.use_graphs = int(bool(use_graphs))
-        elif name == "reserved":
-            o.reserved = 0
         elif typ is ctypes.c_float:
             setattr(o, name, float(d[name]))
         else:
@@ -167,12 +166,12 @@ _DBG_DTYPE = {
     "st_ie": np.float32, "st_oe": np.float32, "ft_key": np.int32, "ft_ok": np.int32,
     "ft_nst": np.int32, "ft_st_cl": np.int32, "ft_st_rs": np.uint16, "ft_flag": np.uint8,
     "ft_ncand": np.uint8, "ft_cand": np.int32, "ft_cchi": np.float32, "ft_assigned": np.int32,
-    "ft_n": np.int32, "out_par": np.float32, "out_cov": np.float32, "out_chi2": np.float32,
+    "ft_n": np.int32, "ft_next": np.int32, "out_par": np.float32, "out_cov": np.float32, "out_chi2": np.float32,
     "out_x": np.float32, "out_ndf": np.int32, "out_sector": np.int32, "out_ncl": np.int32,
     "out_offset": np.int32, "out_ids": np.int32, "out_key": np.int32, "attach": np.int32,
 }
 STATE_F = 22       # floats per stored state: p[5], c[15], x, sector bits
-MAX_INNER = 32     # inner-row slots per fit track
+MAX_INNER = 32     # inner-row slots per fit track (extrapolated rows follow them)
 MAX_CAND = 8       # candidate slots per inner row
 ROWGRID_DTYPE = np.dtype([("bin0", "<i4"), ("nY", "<i4"), ("nZ", "<i4"), ("cl0", "<i4"),
                           ("ncl", "<i4"), ("y0", "<f4"), ("invDy", "<f4"), ("z0", "<f4"),

@@ -66,10 +66,11 @@ def compare_full(tr, f, opts, dist_map=None):
     fok = tr.debug("ft_ok")
     nst = tr.debug("ft_nst")
     rs = tr.debug("ft_st_rs").reshape(-1, 160)
-    nc = tr.debug("ft_ncand").reshape(-1, 32)
-    cand = tr.debug("ft_cand").reshape(-1, 32, 8)
-    cchi = tr.debug("ft_cchi").reshape(-1, 32, 8)
-    asg = tr.debug("ft_assigned").reshape(-1, 32)
+    ns = 32 + opts.get("ext_rows", 0)  # inner-station slots, then extrapolation slots
+    nc = tr.debug("ft_ncand").reshape(-1, ns)
+    cand = tr.debug("ft_cand").reshape(-1, ns, 8)
+    cchi = tr.debug("ft_cchi").reshape(-1, ns, 8)
+    asg = tr.debug("ft_assigned").reshape(-1, ns)
     K = opts["cand_k"]
     gpu_c = {}
     for t in np.nonzero(fok == 1)[0]:
@@ -88,6 +89,27 @@ def compare_full(tr, f, opts, dist_map=None):
         ref_c[(int(ref["cand_key"][i]), int(ref["cand_row"][i]))] = (
             rc[i, :n].tolist(), bits(rx[i, :n]).tolist(), int(ref["cand_assigned"][i]))
     assert gpu_c == ref_c
+    if opts.get("ext_rows", 0) > 0:
+        # Phase III: rows extrapolated per track, candidates and assignments per row
+        nxt = tr.debug("ft_next")
+        assert np.array_equal(np.sort(nxt[fok == 1]), np.sort(ref["fit_next"][ref["fit_fail"] < 0]))
+        gpu_e = {}
+        for t in np.nonzero(fok == 1)[0]:
+            r0 = rs[t, 0] % 152
+            for e in range(nxt[t]):
+                s_ = 32 + e
+                ids = sid[cand[t, s_, :nc[t, s_]]]
+                a = sid[asg[t, s_]] if asg[t, s_] >= 0 else -1
+                gpu_e[(int(fk[t]), int(r0 - 1 - e))] = (ids.tolist(),
+                                                         bits(cchi[t, s_, :nc[t, s_]]).tolist(), a)
+        ref_e = {}
+        ec = ref["ext_ids"].reshape(-1, K)
+        ex = ref["ext_chi2"].reshape(-1, K)
+        for i in range(len(ref["ext_key"])):
+            n = ref["ext_n"][i]
+            ref_e[(int(ref["ext_key"][i]), int(ref["ext_row"][i]))] = (
+                ec[i, :n].tolist(), bits(ex[i, :n]).tolist(), int(ref["ext_assigned"][i]))
+        assert gpu_e == ref_e
     # a11: output tracks by key, bit-exact
     g = gpu_tracks(tr)
     rk = ref["trk_key"]
@@ -179,3 +201,40 @@ def test_fast_mode_within_tolerance():
     assert frac >= 0.9, frac
     assert np.median(rel) < 1e-5
     assert pull.max() < 2.0
+
+
+class _Cut:
+    """A frame without the clusters of rows lo..hi (generator arrays only)."""
+
+    def __init__(self, f, lo, hi):
+        keep = (f.row < lo) | (f.row > hi)
+        self.y, self.z, self.q = f.y[keep], f.z[keep], f.q[keep]
+        self.row, self.sector, self.label = f.row[keep], f.sector[keep], f.label[keep]
+        self.n = int(keep.sum())
+
+
+@pytest.mark.parametrize("workload,kw,cut", [
+    ("one_sector", {"n_primaries": 150, "noise_frac": 0.0}, (8, 19)),
+    ("central_event", {"n_primaries": 2500}, (8, 19)),
+    ("central_event", {"n_primaries": 2500}, None),
+])
+def test_inward_extrapolation_bit_exact(workload, kw, cut):
+    """Phase III: inward extrapolation over 20 rows, its candidates, their
+    assignment by the second ambiguity and the extended third iteration,
+    strict parity (on frames with rows 8-19 emptied, where the extrapolation
+    has inner segments to find, and on a complete event)."""
+    f = synth.generate(workload, **kw)
+    if cut is not None:
+        f = _Cut(f, *cut)
+    opts = TrackerOptions(ext_rows=20).as_dict()
+    tr = run_gpu(f, opts)
+    ref, g = compare_full(tr, f, opts)
+    if cut is not None:
+        assert np.count_nonzero(ref["ext_assigned"] >= 0) > 0
+
+
+def test_inward_extrapolation_bit_exact_with_distortion_map():
+    f = synth.generate("central_event", n_primaries=1500, distort=True)
+    opts = TrackerOptions(ext_rows=20).as_dict()
+    tr = run_gpu(f, opts, dist_map=f.map)
+    compare_full(tr, f, opts, dist_map=f.map)

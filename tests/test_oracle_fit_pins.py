@@ -214,3 +214,43 @@ def test_full_chain_quality_and_track_invariants():
         assert np.all(np.diff(f.row[h].astype(int)[f.sector[h] == f.sector[h[0]]]) > 0)
     for c in np.nonzero(att >= 0)[0][:3000]:
         assert c in tr[att[c]]
+
+
+def _cut_rows(f, lo, hi):
+    """Frame without the clusters of rows lo..hi (a gap longer than the
+    following's miss limit, so the inner parts below it are left unfound)."""
+    keep = (f.row < lo) | (f.row > hi)
+    return (f.y[keep], f.z[keep], f.row[keep], f.sector[keep], f.label[keep])
+
+
+def test_inward_extrapolation_recovers_inner_segments():
+    """Phase III (Sec. 3): with rows 8-19 emptied, the sector tracking cannot
+    bridge the gap (10 consecutive empty rows end the following) and the 8-row
+    inner parts stay below the minimum track length, so their clusters are
+    unattached.  Inward extrapolation over 20 rows from the outer parts finds
+    them again: almost all inner clusters of tracked particles get attached,
+    each to the track of its own particle, and nothing changes above the gap."""
+    f = synth.generate("one_sector", n_primaries=150, noise_frac=0.0)
+    y, z, row, sec, lab = _cut_rows(f, 8, 19)
+    base = oracle.track(y, z, row, sec, RX.astype(np.float32), opts(), full=True)
+    ext = oracle.track(y, z, row, sec, RX.astype(np.float32), opts(ext_rows=20), full=True)
+    inner = row < 8
+    assert np.all(base["attach"][inner] < 0)
+    tr = tracks_of(ext)
+    tlab = np.array([majority(lab[h])[0] for h in tr])
+    # inner clusters of particles that have a track above the gap
+    tracked = set(tlab[tlab >= 0].tolist())
+    cand = inner & np.isin(lab, list(tracked))
+    att = ext["attach"]
+    got = cand & (att >= 0)
+    assert got.sum() >= 0.9 * cand.sum(), (got.sum(), cand.sum())
+    right = tlab[att[got]] == lab[got]
+    assert right.mean() > 0.98, right.mean()
+    # above the gap the attachment is that of the run without extrapolation
+    assert np.array_equal(base["attach"][row > 19] >= 0, att[row > 19] >= 0)
+    # candidate lists: sorted by chi2, inside the cut, on rows below the innermost cluster
+    n, ids, chi = ext["ext_n"], ext["ext_ids"].reshape(-1, 4), ext["ext_chi2"].reshape(-1, 4)
+    for j in range(len(n)):
+        c = chi[j, :n[j]]
+        assert np.all(np.diff(c) >= 0) and np.all(c < 9.0)
+        assert np.all(row[ids[j, :n[j]]] == ext["ext_row"][j])
