@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--collisions", type=float, default=0.0,
                     help="mean collisions per frame instead of the workload's (small "
                          "profiling cases)")
+    ap.add_argument("--no-refit", action="store_true",
+                    help="skip the refit + adjoint timing on one distorted frame")
+    ap.add_argument("--ext-rows", type=int, default=0,
+                    help="Phase III inward extrapolation over this many rows (0: off)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up plus one step and exit (for ncu launch lists)")
     return ap.parse_args()
@@ -236,6 +240,65 @@ def stage_bytes(name: str, c: dict) -> float:
     return float(table.get(name, 0.0))
 
 
+def measured_traffic(stage: str, c: dict):
+    """DRAM bytes (read + write) per launch of the dominant stage, from the
+    committed ncu summary of its kernels on a smaller frame, scaled to this
+    call by the clusters processed; None without one."""
+    import re
+
+    path = os.path.join(ROOT, "profiles", "heavy_kernels_timeframe_sections.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    m = re.search(r"^traffic\s+" + re.escape(stage) + r"\s+bytes_per_cluster\s+([0-9.eE+-]+)", text,
+                  re.M)
+    if not m:
+        return None, None
+    return float(m.group(1)) * c["clusters"], "ncu DRAM bytes per cluster on a smaller frame " \
+        "(profiles/heavy_kernels_timeframe_sections.md), times this call's clusters"
+
+
+def refit_timing(mode):
+    """Refit with fixed clusters (tpc_refit) and its adjoint (tpc_refit_backward,
+    d sum(chi2) / d map) on one space-charge distorted 2.8 ms frame: ms per
+    call, CUDA events on the calling stream."""
+    import torch
+
+    from paper_2601_20569_gb300 import synth, tpc
+    from paper_2601_20569_gb300.options import TrackerOptions
+
+    f = synth.generate("timeframe_distorted", frame=0)
+    tr = tpc.Tracker(synth.row_x(), TrackerOptions(), mode=mode, cap_clusters=f.n)
+    coeff = torch.as_tensor(f.map).cuda()
+    tr.set_map(coeff)
+    dev = tr.to_device(f.y, f.z, f.q, f.row, f.sector)
+    tr.track(*dev)
+    res = tr.result()
+    tracks = {k: res[k].clone() for k in ("cl_offset", "cl_ids", "params", "x", "sector")}
+    nt = int(tracks["params"].shape[0])
+    w = torch.ones(nt, device="cuda")
+    tr.refit(dev, tracks, coeff)
+    tr.refit_backward(w)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = 3
+    ev[0].record(stream)
+    for _ in range(reps):
+        tr.refit(dev, tracks, coeff)
+    ev[1].record(stream)
+    for _ in range(reps):
+        tr.refit_backward(w)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    out = {"workload": f"one distorted 2.8 ms frame: {f.n} clusters, {nt} tracks, "
+                       f"map 18x16x20x3", "refit_ms": ev[0].elapsed_time(ev[1]) / reps,
+           "backward_ms": ev[1].elapsed_time(ev[2]) / reps, "tracks": nt}
+    tr.close()
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -261,7 +324,8 @@ def main():
     note(f"{len(frames)} frames generated")
     n_per_step = sum(f.n for f in frames)
     mode = MODE_FAST if args.mode == "fast" else MODE_STRICT
-    tr = tpc.Tracker(synth.row_x(), TrackerOptions(), mode=mode, cap_clusters=n_per_step,
+    topts = TrackerOptions(ext_rows=args.ext_rows)
+    tr = tpc.Tracker(synth.row_x(), topts, mode=mode, cap_clusters=n_per_step,
                      max_frames=len(frames), use_graphs=True)
     dev = [tr.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
     stream = torch.cuda.current_stream()
@@ -316,8 +380,7 @@ def main():
 
     note(f"timed region: {ms:.1f} ms")
     # the plain form on the same inputs: one call (one launch per stage) per frame
-    plain = tpc.Tracker(synth.row_x(), TrackerOptions(), mode=mode,
-                        cap_clusters=max(f.n for f in frames))
+    plain = tpc.Tracker(synth.row_x(), topts, mode=mode, cap_clusters=max(f.n for f in frames))
     for d in dev:
         plain.track(*d, stream=stream)
     torch.cuda.synchronize()
@@ -349,8 +412,9 @@ def main():
     dom = max(stages, key=lambda s: s["ms"])
     per_call_ms = dom["ms"] / max(1, dom["calls"])
     achieved = stage_bytes(dom["name"], counts) / (per_call_ms / 1e3) / 1e9
+    traffic, traffic_src = measured_traffic(dom["name"], counts)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
+            "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_src,
             "kernel": f"stage '{dom['name']}' ({dom['launches'] // max(1, dom['calls'])} kernels "
                       f"per batch call)", "peak_source": f"{peak_kind} hbm_gbs",
             "stage_bytes_per_call": stage_bytes(dom["name"], counts)}
@@ -382,6 +446,10 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     note("end-to-end timed")
+    refit = None
+    if not args.no_refit:
+        refit = refit_timing(mode)
+        note("refit and adjoint timed")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -390,7 +458,8 @@ def main():
                                f"{n_per_step} clusters per step, one batched pass", "frames": args.frames,
                    "clusters_per_step": n_per_step, "mode": args.mode,
                    "l2": "inputs larger than L2 (each frame > 129 MB resident)",
-                   "parallelism": f"replicas x{world}", "launch": "batched + CUDA graph"},
+                   "parallelism": f"replicas x{world}", "launch": "batched + CUDA graph",
+                   "phase3_ext_rows": args.ext_rows},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -400,6 +469,8 @@ def main():
         "stages_ms_per_batch": {s_["name"]: s_["ms"] / max(1, s_["calls"]) for s_ in stages},
         "launch_config": tuned,
     }
+    if refit is not None:
+        line["refit_adjoint"] = refit
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(frames, args.cpu_seconds)
         note("cpu baseline done")

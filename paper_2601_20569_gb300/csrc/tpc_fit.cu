@@ -729,15 +729,16 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
   }
 }
 
-// Iterations 1 and 2 of the final fit as a per-lane state machine: every loop
-// iteration is one station (station change, then the iteration's own work,
-// then the update) of the lane's current track, and a lane whose track ends
-// takes the next one from the work queue.  The lanes of a warp thus issue the
-// update (FP64 for loopers) together however unequal their tracks are.
-// Iteration 1 runs inward storing the predictions; iteration 2 runs outward,
-// interpolates with them, flags outliers and collects the inner-row
-// candidates (Sec. 3).
-enum : int { kFitIdle = 0, kFitIn, kFitOut, kFitExt };
+// Iterations 1 and 2 of the final fit (k_fit1, k_fit2) run as per-lane state
+// machines: every loop iteration is one station (station change, then the
+// iteration's own work, then the update) of the lane's current track, and a
+// lane whose track ends takes the next one from the work queue, so the lanes
+// of a warp issue the update (FP64 for loopers) together however unequal
+// their tracks are.  Iteration 1 runs inward storing the predictions;
+// iteration 2 runs outward, interpolates with them, flags outliers and
+// collects the inner-row candidates (Sec. 3).  Two kernels rather than one:
+// each carries only its own iteration's code and registers.
+enum : int { kFitIdle = 0, kFitIn, kFitExt };
 
 __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, const MapDev& M,
                                                  int f, int k, int rs, const Lin& L,
@@ -853,7 +854,12 @@ __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, co
   F.ft_assigned[slot] = -1;
 }
 
-__global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev M) {
+// Iteration 1 (inward, storing the predictions) and the Phase III
+// extrapolation below the track, as a per-lane state machine: every loop
+// iteration is one station (or extrapolated row) of the lane's current track,
+// and a lane whose track ends takes the next one from the work queue.  The
+// end state of iteration 1 goes to ft_end2 for k_fit2.
+__global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M) {
   __shared__ float rx[kMaxRows];
   for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
   __syncthreads();
@@ -867,7 +873,6 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
   const int* SC = nullptr;
   const uint16_t* SR = nullptr;
   float* store = nullptr;
-  uint8_t* flag = nullptr;
   Lin L;
   for (;;) {
     if (phase == kFitIdle) {
@@ -875,15 +880,12 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
       if (q >= nf) break;
       f = F.ft_order[q];
       ns = F.ft_nst[f];
-      if (ns == 0) {  // not reached: every chain holds clusters
-        F.ft_ok[f] = 0;
-        continue;
-      }
+      F.ft_ok[f] = 0;
+      if (ns == 0) continue;  // not reached: every chain holds clusters
       z0 = F.ft_z0[f];
       SC = F.ft_st_cl + (long)f * kMaxRows;
       SR = F.ft_st_rs + (long)f * kMaxRows;
       store = F.ft_store + (long)f * kMaxRows * 5;
-      flag = F.ft_flag + (long)f * kMaxRows;
       Trk<float> s0;
       get_state(F.st_oe + (long)F.ft_last[f] * kStateF, s0);
       lin_start(L, s0, SR[ns - 1] / NR, P);
@@ -893,8 +895,7 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
     }
     if (phase == kFitExt) {
       // Phase III: one row of the inward extrapolation below the innermost
-      // station (k counts the rows done); at its end iteration 2 starts from
-      // the state iteration 1 ended with
+      // station (k counts the rows done)
       const int rs0 = SR[0];
       const int r = rs0 % NR - 1 - k;
       bool go = k < P.ext_rows && r >= 0;
@@ -905,18 +906,94 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
         ++k;
       } else {
         F.ft_next[f] = k;
-        Trk<float> s1;
-        get_state(F.ft_end2 + (long)f * kStateF, s1);
-        lin_start(L, s1, rs0 / NR, P);
-        k = 0;
-        phase = kFitOut;
+        F.ft_ok[f] = 1;
+        phase = kFitIdle;
       }
       continue;
     }
-    // ---- one station.  The cluster and, outward, the stored prediction do
-    // not depend on the state: they are requested before the station change
-    // so that their latency overlaps its arithmetic.
-    const bool out = phase == kFitOut;
+    // ---- one station.  The cluster does not depend on the state: it is
+    // requested before the station change so that its latency overlaps the
+    // arithmetic.
+    const int rs = SR[k];
+    const int c = SC[k];
+    const int sec = rs / NR, row = rs % NR;
+    float cy = 0.0f, cz = 0.0f;
+    if (c >= 0) {
+      const float2 pc = F.syz[c];
+      cy = pc.x;
+      cz = pc.y;
+    }
+    bool ok = true;
+    if (k != ns - 1) ok = lin_goto(L, sec, rx[row], P);
+    bool have = false;
+    float my = 0.0f, mz = 0.0f;
+    if (ok) {
+      float* st = store + k * 5;
+      st[0] = L.t.p[0]; st[1] = L.t.p[1]; st[2] = L.t.c[0]; st[3] = L.t.c[1]; st[4] = L.t.c[2];
+      if (c >= 0) {
+        ok = corrected(M, P, sec, L.t.x, cy, cz, z0, L.r, my, mz);
+        have = ok;
+      }
+    }
+    if (have) fit_update(L.t, residual(L.t, my, mz, P), P);
+    if (!ok) {
+      phase = kFitIdle;
+      continue;
+    }
+    if (--k < 0) {
+      // the end of iteration 1 starts iteration 2
+      put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
+      if (P.ext_rows > 0) {
+        k = 0;
+        phase = kFitExt;
+      } else {
+        F.ft_ok[f] = 1;
+        phase = kFitIdle;
+      }
+    }
+  }
+}
+
+// Iteration 2 (outward) as the same kind of state machine: interpolation with
+// the stored predictions, flags of outliers, inner-row candidates (Sec. 3,
+// Phases I and II).  Starts from the end of iteration 1, ends in ft_end2.
+__global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M) {
+  __shared__ float rx[kMaxRows];
+  for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
+  __syncthreads();
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  const int nL = min(F.cnt->n_loopers, nf);
+  const int NR = P.n_rows;
+  bool busy = false;
+  int f = 0, ns = 0, k = 0;
+  float z0 = 0.0f;
+  const int* SC = nullptr;
+  const uint16_t* SR = nullptr;
+  const float* store = nullptr;
+  uint8_t* flag = nullptr;
+  Lin L;
+  for (;;) {
+    if (!busy) {
+      const int q = fit_next(F.cnt, kQFit2, kQFit2N, nL, nf);
+      if (q >= nf) break;
+      f = F.ft_order[q];
+      if (!F.ft_ok[f]) continue;
+      ns = F.ft_nst[f];
+      z0 = F.ft_z0[f];
+      SC = F.ft_st_cl + (long)f * kMaxRows;
+      SR = F.ft_st_rs + (long)f * kMaxRows;
+      store = F.ft_store + (long)f * kMaxRows * 5;
+      flag = F.ft_flag + (long)f * kMaxRows;
+      Trk<float> s1;
+      get_state(F.ft_end2 + (long)f * kStateF, s1);
+      lin_start(L, s1, SR[0] / NR, P);
+      k = 0;
+      busy = true;
+      continue;
+    }
+    // ---- one station.  The cluster and the stored prediction do not depend
+    // on the state: they are requested before the station change.
     const int rs = SR[k];
     const int c = SC[k];
     const int sec = rs / NR, row = rs % NR;
@@ -927,29 +1004,21 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
       cz = pc.y;
     }
     float sv[5];
-    if (out) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) sv[i] = store[k * 5 + i];
-    }
+    for (int i = 0; i < 5; ++i) sv[i] = store[k * 5 + i];
     bool ok = true;
-    if (k != (out ? 0 : ns - 1)) ok = lin_goto(L, sec, rx[row], P);
-    const bool inner = out && row < P.inner_rows;
+    if (k != 0) ok = lin_goto(L, sec, rx[row], P);
+    const bool inner = row < P.inner_rows;
     bool have = false;
     float my = 0.0f, mz = 0.0f;
-    Interp I;
     if (ok) {
-      if (!out) {
-        float* st = store + k * 5;
-        st[0] = L.t.p[0]; st[1] = L.t.p[1]; st[2] = L.t.c[0]; st[3] = L.t.c[1]; st[4] = L.t.c[2];
-      } else {
-        const float a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
-        I = interpolate(a, sv);
-        flag[k] = 0;
-      }
+      const float a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
+      const Interp I = interpolate(a, sv);
+      flag[k] = 0;
       if (c >= 0 && !inner) {
         ok = corrected(M, P, sec, L.t.x, cy, cz, z0, L.r, my, mz);
         have = ok;
-        if (ok && out) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
+        if (ok) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
       }
       if (ok && inner) {
         inner_candidates(F, P, M, f, k, rs, L, I, z0);
@@ -962,28 +1031,12 @@ __global__ void __launch_bounds__(256, 2) k_fit12(FrameDev F, KParams P, MapDev 
     if (have) fit_update(L.t, residual(L.t, my, mz, P), P);
     if (!ok) {
       F.ft_ok[f] = 0;
-      phase = kFitIdle;
+      busy = false;
       continue;
     }
-    if (!out) {
-      if (--k < 0) {
-        if (P.ext_rows > 0) {
-          // keep the end of iteration 1 for iteration 2; extrapolate first
-          put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
-          k = 0;
-          phase = kFitExt;
-        } else {
-          // iteration 2 starts from the inner end of iteration 1
-          const Trk<float> s1 = L.t;
-          lin_start(L, s1, SR[0] / NR, P);
-          k = 0;
-          phase = kFitOut;
-        }
-      }
-    } else if (++k == ns) {
+    if (++k == ns) {
       put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
-      F.ft_ok[f] = 1;
-      phase = kFitIdle;
+      busy = false;
     }
   }
 }
@@ -1208,10 +1261,19 @@ __global__ void k_out_write(FrameDev F, KParams P) {
   const int* used = F.ft_used + (long)f * kMaxRows;
   const bool fits = (long)off + n <= F.cap_refs;
   if (!fits) atomicOr(&F.cnt->err, kErrCapRefs);
-  for (int j = 0; j < n; ++j) {
-    const int id = F.sid[used[n - 1 - j]];
-    if (fits) F.out_ids[off + j] = id;
-    atomicMin(&F.attach_key[id], F.ft_key[f]);
+  const int key = F.ft_key[f];
+  for (int j0 = 0; j0 < n; j0 += 8) {  // groups of 8 with their loads issued together
+    int u[8], id[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) u[j] = j0 + j < n ? used[n - 1 - (j0 + j)] : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) id[j] = u[j] >= 0 ? F.sid[u[j]] : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (id[j] < 0) continue;
+      if (fits) F.out_ids[off + j0 + j] = id[j];
+      atomicMin(&F.attach_key[id[j]], key);
+    }
   }
 }
 
@@ -1222,10 +1284,18 @@ __global__ void k_out_attach(FrameDev F, KParams P) {
     const int t = F.ft_outidx[f];
     if (t < 0) continue;
     const int n = F.ft_n[f], key = F.ft_key[f];
-    const int* used = F.ft_used + (long)f * kMaxRows;
-    for (int j = 0; j < n; ++j) {
-      const int id = F.sid[used[j]];
-      if (F.attach_key[id] == key) F.attach[id] = t;
+    // the track's input ids as written to the output, in groups of 8 whose
+    // loads are issued together
+    const int* ids = F.out_ids + F.out_offset[t];
+    for (int j0 = 0; j0 < n; j0 += 8) {
+      int id[8], ak[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) id[j] = j0 + j < n ? ids[j0 + j] : -1;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ak[j] = id[j] >= 0 ? F.attach_key[id[j]] : 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (id[j] >= 0 && ak[j] == key) F.attach[id[j]] = t;
     }
     if (t == F.cnt->n_out - 1) F.out_offset[t + 1] = F.cnt->n_refs;
   }
@@ -1602,8 +1672,9 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 
 int stage_fit12(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_fit_stations<<<sms * 8, kBlock, 0, s>>>(F, P);
-  k_fit12<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, F.map);
-  return 2;
+  k_fit1<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, F.map);
+  k_fit2<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, F.map);
+  return 3;
 }
 
 int stage_ambiguity2(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

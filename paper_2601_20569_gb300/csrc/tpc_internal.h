@@ -43,7 +43,8 @@ struct LaunchCfg {
 // The fit kernels keep two queues each: FP64-update loopers (kQFit12, kQFit3)
 // and the other tracks (kQFit12N, kQFit3N).
 enum QueueSlot : int {
-  kQTracklets = 0, kQSectorRefit, kQMerge, kQFit12, kQFit3, kQFit12N, kQFit3N, kQNum
+  kQTracklets = 0, kQSectorRefit, kQMerge, kQFit12, kQFit3, kQFit12N, kQFit3N, kQFit2, kQFit2N,
+  kQNum
 };
 
 // Search grid of one (sector, row): bins iz*nY + iy, clusters of a bin are

@@ -558,9 +558,14 @@ __global__ void k_sel_owner(FrameDev F, KParams P) {
     if (F.tl_n[ti] == 0) continue;
     const unsigned long long key = tracklet_key(F, P, ti);
     const int* H = F.tl_hits + (long)ti * kMaxRows;
-    for (int r = F.tl_rlo[ti]; r <= F.tl_rhi[ti]; ++r) {
-      const int k = H[r];
-      if (k >= 0) atomicMax(&F.owner_key[k], key);
+    const int rlo = F.tl_rlo[ti], rhi = F.tl_rhi[ti];
+    for (int rg = rlo; rg <= rhi; rg += 8) {  // the group's hit indices requested together
+      int h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = rg + j <= rhi ? H[rg + j] : -1;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (h[j] >= 0) atomicMax(&F.owner_key[h[j]], key);
     }
   }
 }
