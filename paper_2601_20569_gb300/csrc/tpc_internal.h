@@ -44,7 +44,7 @@ struct LaunchCfg {
 // and the other tracks (kQFit12N, kQFit3N).
 enum QueueSlot : int {
   kQTracklets = 0, kQSectorRefit, kQMerge, kQFit12, kQFit3, kQFit12N, kQFit3N, kQFit2, kQFit2N,
-  kQNum
+  kQTlDown, kQNum
 };
 
 // Search grid of one (sector, row): bins iz*nY + iy, clusters of a bin are

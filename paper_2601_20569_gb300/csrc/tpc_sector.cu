@@ -352,7 +352,7 @@ __global__ void k_chain_info(FrameDev F, KParams P) {
   }
 }
 
-// Tracklet constructor as a per-lane state machine: every loop iteration is
+// Tracklet constructor as per-lane state machines: every loop iteration is
 // one row step (propagate, choose the row's cluster, update) of the lane's
 // current tracklet, and a lane whose tracklet ends takes the next one from the
 // work queue in the same loop.  The lanes of a warp therefore stay busy on
@@ -360,18 +360,24 @@ __global__ void k_chain_info(FrameDev F, KParams P) {
 // of operations is that of the constructor (Sec. 2): seed from the chain's
 // first, middle and last clusters; follow the CA chain upwards; extend
 // upwards by the best cluster of each row until max_miss rows in a row have
-// none; restart from the top with reset covariance, refit downwards over the
-// found clusters and extend below the start the same way.
-enum : int { kTlIdle = 0, kTlChain, kTlUp, kTlDown };
+// none (k_tl_up); restart from the top with reset covariance, refit downwards
+// over the found clusters and extend below the start the same way (k_tl_down).
+// Two kernels rather than one: each carries only its own pass's code and
+// state, and all lanes of a kernel run the same kind of step.
+enum : int { kTlIdle = 0, kTlChain, kTlUp };
 
-// The state the constructor only saves and restores -- the state at the
-// innermost hit of the downward pass, and the state and position at the top
-// hit of the upward pass -- lives in shared memory (kTlShared floats per
-// thread, field-major so that a warp's accesses hit distinct banks), which
-// keeps the register count low enough for three 256-thread blocks per SM.
-constexpr int kTlShared = 29;  // inner p[5], c[15], x; top p[5], x, y_hit, z_hit
+// Per-thread shared-memory state of the two tracklet kernels: the state they
+// only save and restore (downward: the state at the innermost hit; upward:
+// the state and position at the top hit), field-major so that a warp's
+// accesses hit distinct banks.  It keeps both kernels at 64 registers, four
+// 256-thread blocks per SM.
+constexpr int kTlShared = 21;  // saved state: p[5], c[15], x (or p[5], x, y_hit, z_hit)
 
-__global__ void __launch_bounds__(256, 3) k_tracklets(FrameDev F, KParams P) {
+// Upward pass: seed, CA chain, extension by the best cluster of each row.
+// The state at the top hit and that hit's position are left in tl_seed[0..5],
+// tl_chi2 and tl_x for the downward pass; tl_n = -1 marks a tracklet that
+// has one.
+__global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
   extern __shared__ float tl_sh[];
   float* const S = tl_sh + threadIdx.x;
   const int BS = blockDim.x;
@@ -379,24 +385,15 @@ __global__ void __launch_bounds__(256, 3) k_tracklets(FrameDev F, KParams P) {
   if (F.cnt->err) return;
   const int NR = P.n_rows;
   int phase = kTlIdle;
-  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, c = 0, cn = 0, hn = -1, left = 0, miss = 0,
-      n = 0, rlo = 0;
+  int ti = 0, sbase = 0, top = 0, rcur = 0, c = 0, cn = 0, left = 0, miss = 0;
   int* H = nullptr;
-  float chi2 = 0.0f;
   Trk<float> t;
-  auto save_inner = [&]() {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) S[i * BS] = t.p[i];
-#pragma unroll
-    for (int i = 0; i < 15; ++i) S[(5 + i) * BS] = t.c[i];
-    S[20 * BS] = t.x;
-  };
   auto save_top = [&](float y, float z) {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) S[(21 + i) * BS] = t.p[i];
-    S[26 * BS] = t.x;
-    S[27 * BS] = y;
-    S[28 * BS] = z;
+    for (int i = 0; i < 5; ++i) S[i * BS] = t.p[i];
+    S[5 * BS] = t.x;
+    S[6 * BS] = y;
+    S[7 * BS] = z;
   };
   for (;;) {
     if (phase == kTlIdle) {
@@ -413,7 +410,7 @@ __global__ void __launch_bounds__(256, 3) k_tracklets(FrameDev F, KParams P) {
       F.tl_n[ti] = 0;
       if (__float_as_int(sv[7]) == 0) continue;  // no seed
       const int rr0 = __float_as_int(sv[6]);
-      r0 = rr0 % NR;
+      const int r0 = rr0 % NR;
       sbase = rr0 - r0;  // sector * n_rows
 #pragma unroll
       for (int i = 0; i < 5; ++i) t.p[i] = sv[i];
@@ -434,67 +431,38 @@ __global__ void __launch_bounds__(256, 3) k_tracklets(FrameDev F, KParams P) {
       phase = left > 0 ? kTlChain : kTlUp;
       continue;
     }
-    // ---- one row step.  Everything the step reads that does not depend on
-    // the propagated state is requested before the propagation so that its
-    // latency overlaps the arithmetic: the next chain link and the next
-    // stored hit (both one step ahead), the position of a cluster already
-    // known (chain, stored hit), the row's grid record.  A CA link always
+    // ---- one row step.  What the step reads that does not depend on the
+    // propagated state is requested before the propagation so that its
+    // latency overlaps the arithmetic: the next chain link (one step ahead),
+    // the chain cluster's position, the row's grid record.  A CA link always
     // joins adjacent pad rows of one sector, so the chain's next row is known.
-    int r, k = -1;
-    bool stop;
+    int k = -1;
+    const int r = rcur + 1;
+    bool stop = r >= NR;
+    RowGrid g;
+    float ky = 0.0f, kz = 0.0f;
     if (phase == kTlChain) {
       k = cn;
       c = k;
       if (left > 1) cn = F.cup[k];
-      r = rcur + 1;
-      stop = false;
-    } else if (phase == kTlUp) {
-      r = rcur + 1;
-      stop = r >= NR;
-    } else {
-      r = rcur - 1;
-      stop = r < 0;
-    }
-    const bool stored = phase == kTlDown && r >= r0;
-    RowGrid g;
-    float ky = 0.0f, kz = 0.0f;
-    if (!stop) {
-      if (stored) {
-        k = hn;
-        hn = r - 1 >= r0 ? H[r - 1] : -1;
-      } else if (phase != kTlChain) {
-        g = F.rows[sbase + r];
-      }
-      if (k >= 0) {
-        const float2 pk = F.syz[k];
-        ky = pk.x;
-        kz = pk.y;
-      }
+      const float2 pk = F.syz[k];
+      ky = pk.x;
+      kz = pk.y;
+    } else if (!stop) {
+      g = F.rows[sbase + r];
     }
     if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);
     if (!stop && phase != kTlChain) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
     bool miss_out = false;
     if (!stop) {
-      if (phase != kTlChain && !stored) k = pick(F, P, t, g, ky, kz);
+      if (phase != kTlChain) k = pick(F, P, t, g, ky, kz);
       if (k >= 0) {
-        const Resid R = residual(t, ky, kz, P);
-        if (phase == kTlDown) chi2 = chi2 + R.chi2;
-        update(t, R);
-        if (phase == kTlDown) {
-          if (r < r0) {
-            H[r] = k;
-            miss = 0;
-          }
-          ++n;
-          save_inner();
-          rlo = r;
-        } else {
-          H[r] = k;
-          save_top(ky, kz);
-          top = r;
-          miss = 0;
-        }
-      } else if (phase != kTlDown || r < r0) {
+        update(t, residual(t, ky, kz, P));
+        H[r] = k;
+        save_top(ky, kz);
+        top = r;
+        miss = 0;
+      } else {
         H[r] = -1;
         miss_out = ++miss >= P.max_miss;
       }
@@ -504,41 +472,128 @@ __global__ void __launch_bounds__(256, 3) k_tracklets(FrameDev F, KParams P) {
         miss = 0;
       }
     }
-    if (phase == kTlDown) {
-      if (!(stop || miss_out)) continue;
-      // tracklet done
-      phase = kTlIdle;
-      if (n < P.min_hits) continue;
-      F.tl_n[ti] = n;
-      F.tl_rlo[ti] = rlo;
-      F.tl_rhi[ti] = top;
-      F.tl_chi2[ti] = chi2;
-      F.tl_x[ti] = S[20 * BS];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = S[i * BS];
-#pragma unroll
-      for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = S[(5 + i) * BS];
-      continue;
-    }
     if (!(stop || miss_out)) continue;
-    // upward part done (chain broken, no more rows, edge or max_miss misses):
-    // restart at the top with reset covariance and refit downwards
+    // upward part done (chain broken, no more rows, edge or max_miss misses)
+    float* sd = F.tl_seed + (long)ti * kSeedF;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) t.p[i] = S[(21 + i) * BS];
-    t.x = S[26 * BS];
-    reset_cov(t.c, P);
-    {
-      const Resid R = residual(t, S[27 * BS], S[28 * BS], P);
+    for (int i = 0; i < 6; ++i) sd[i] = S[i * BS];
+    F.tl_chi2[ti] = S[6 * BS];
+    F.tl_x[ti] = S[7 * BS];
+    F.tl_rhi[ti] = top;
+    F.tl_n[ti] = -1;
+    phase = kTlIdle;
+  }
+}
+
+// Downward pass: restart at the top hit with reset covariance, refit down
+// over the hits found on the way up, extend below the start the same way.
+__global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
+  extern __shared__ float tl_sh[];
+  float* const S = tl_sh + threadIdx.x;
+  const int BS = blockDim.x;
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  if (F.cnt->err) return;
+  const int NR = P.n_rows;
+  bool busy = false;
+  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, hn = -1, miss = 0, n = 0, rlo = 0;
+  int* H = nullptr;
+  float chi2 = 0.0f;
+  Trk<float> t;
+  auto save_inner = [&]() {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[i * BS] = t.p[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) S[(5 + i) * BS] = t.c[i];
+    S[20 * BS] = t.x;
+  };
+  for (;;) {
+    if (!busy) {
+      ti = queue_next(&F.cnt->queue[kQTlDown]);
+      if (ti >= nst) break;
+      if (F.tl_n[ti] != -1) continue;
+      H = F.tl_hits + (long)ti * kMaxRows;
+      const float* sd = F.tl_seed + (long)ti * kSeedF;
+      float sv[kSeedF];
+#pragma unroll
+      for (int i = 0; i < kSeedF; ++i) sv[i] = sd[i];
+      const float ty = F.tl_chi2[ti], tz = F.tl_x[ti];
+      top = F.tl_rhi[ti];
+      const int rr0 = __float_as_int(sv[6]);
+      r0 = rr0 % NR;
+      sbase = rr0 - r0;
+      F.tl_n[ti] = 0;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) t.p[i] = sv[i];
+      t.x = sv[5];
+      reset_cov(t.c, P);
+      const Resid R = residual(t, ty, tz, P);
       chi2 = R.chi2;
       update(t, R);
+      hn = top - 1 >= r0 ? H[top - 1] : -1;
+      n = 1;
+      save_inner();
+      rlo = top;
+      rcur = top;
+      miss = 0;
+      busy = true;
+      continue;
     }
-    hn = top - 1 >= r0 ? H[top - 1] : -1;
-    n = 1;
-    save_inner();
-    rlo = top;
-    rcur = top;
-    miss = 0;
-    phase = kTlDown;
+    // ---- one row step (the next stored hit one step ahead, its position and
+    // the row's grid record before the propagation)
+    const int r = rcur - 1;
+    bool stop = r < 0;
+    const bool stored = r >= r0;
+    int k = -1;
+    RowGrid g;
+    float ky = 0.0f, kz = 0.0f;
+    if (!stop) {
+      if (stored) {
+        k = hn;
+        hn = r - 1 >= r0 ? H[r - 1] : -1;
+        if (k >= 0) {
+          const float2 pk = F.syz[k];
+          ky = pk.x;
+          kz = pk.y;
+        }
+      } else {
+        g = F.rows[sbase + r];
+      }
+    }
+    if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);
+    if (!stop) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
+    bool miss_out = false;
+    if (!stop) {
+      if (!stored) k = pick(F, P, t, g, ky, kz);
+      if (k >= 0) {
+        const Resid R = residual(t, ky, kz, P);
+        chi2 = chi2 + R.chi2;
+        update(t, R);
+        if (r < r0) {
+          H[r] = k;
+          miss = 0;
+        }
+        ++n;
+        save_inner();
+        rlo = r;
+      } else if (r < r0) {
+        H[r] = -1;
+        miss_out = ++miss >= P.max_miss;
+      }
+      rcur = r;
+    }
+    if (!(stop || miss_out)) continue;
+    // tracklet done
+    busy = false;
+    if (n < P.min_hits) continue;
+    F.tl_n[ti] = n;
+    F.tl_rlo[ti] = rlo;
+    F.tl_rhi[ti] = top;
+    F.tl_chi2[ti] = chi2;
+    F.tl_x[ti] = S[20 * BS];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = S[i * BS];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = S[(5 + i) * BS];
   }
 }
 
@@ -658,9 +713,10 @@ int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_chain_info<<<sms * 8, kBlock, 0, s>>>(F, P);
   const int tb = F.lc.block[kLTracklets];
-  k_tracklets<<<persistent_grid(F.lc, kLTracklets, sms), tb, sizeof(float) * kTlShared * tb, s>>>(
-      F, P);
-  return 2;
+  const size_t sh = sizeof(float) * kTlShared * tb;
+  k_tl_up<<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+  k_tl_down<<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+  return 3;
 }
 
 int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
