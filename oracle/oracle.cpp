@@ -431,13 +431,12 @@ void update(Track<Real>& t, const Resid<Real>& R) {
     for (int j = 0; j <= i; ++j) t.c[ci(i, j)] = t.c[ci(i, j)] - (k0[i] * h0[j] + k1[i] * h1[j]);
 }
 
-// Kalman update of the final fit and refit: for low-pT loopers
-// (|q/pT| > looper_qpt) the gain and covariance update run in FP64 and are
-// rounded back (the float build; the double build is FP64 throughout).
+// Kalman update with the gain and covariance arithmetic in FP64 when
+// `fp64`, rounded back (the float build; the double build is FP64 throughout).
 template <typename Real>
-void fit_update(Track<Real>& t, const Resid<Real>& R, const Params<Real>& P) {
+void update_as(Track<Real>& t, const Resid<Real>& R, bool fp64) {
   if constexpr (std::is_same<Real, float>::value) {
-    if (P.looper_qpt > 0.0f && std::fabs(t.p[4]) > P.looper_qpt) {
+    if (fp64) {
       Track<double> d;
       for (int i = 0; i < 5; ++i) d.p[i] = t.p[i];
       for (int i = 0; i < 15; ++i) d.c[i] = t.c[i];
@@ -450,6 +449,16 @@ void fit_update(Track<Real>& t, const Resid<Real>& R, const Params<Real>& P) {
     }
   }
   update(t, R);
+}
+
+// Kalman update of the refit: FP64 for low-pT loopers, judged at the update
+// by the current |q/pT| > looper_qpt.
+template <typename Real>
+void fit_update(Track<Real>& t, const Resid<Real>& R, const Params<Real>& P) {
+  if constexpr (std::is_same<Real, float>::value)
+    update_as(t, R, P.looper_qpt > 0.0f && std::fabs(t.p[4]) > P.looper_qpt);
+  else
+    update(t, R);
 }
 
 // Rotation of the local frame by +/-20 deg (to an adjacent sector): the
@@ -1182,6 +1191,7 @@ struct FitTrack {
   std::vector<int> cand;   // [station][cand_k]
   std::vector<Real> cchi;  // [station][cand_k]
   std::vector<int> assigned;
+  bool looper = false;     // the final fit's updates run in FP64 (low-pT looper)
   int n_ext = 0;           // Phase III: rows extrapolated below the innermost station;
                            // their candidate slots follow the stations' in ncand/cand/cchi
   bool ok = true;
@@ -1288,7 +1298,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
         T.ok = false;
         return;
       }
-      fit_update(L.t, residual(L.t, my, mz, P), P);
+      update_as(L.t, residual(L.t, my, mz, P), T.looper);
     }
   }
   if (phase2 && P.ext_rows > 0) extrapolate_inward(F, P, M, fixed, T, L);
@@ -1356,7 +1366,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
         T.ok = false;
         return;
       }
-      fit_update(L.t, residual(L.t, my, mz, P), P);
+      update_as(L.t, residual(L.t, my, mz, P), T.looper);
     }
   }
   it2_end = L.t;
@@ -1396,7 +1406,7 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
     const Resid<Real> R = residual(L.t, my, mz, P);
     if (R.chi2 > P.final_chi2) continue;
     T.chi2 = T.chi2 + R.chi2;
-    fit_update(L.t, R, P);
+    update_as(L.t, R, T.looper);
     ++T.n;
     T.used.push_back(c);
     T.out = L.t;
@@ -1674,6 +1684,9 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     T.st = make_stations(F, P, cl, true);
     T.outer = ST[last].oe;
     const Track<Real>& ie = ST[h].ie;
+    // a low-pT looper (|q/pT| at the inner end of its first segment above
+    // looper_qpt) runs every update of its final fit in FP64
+    T.looper = P.looper_qpt > Real(0) && o_fabs(ie.p[4]) > P.looper_qpt;
     T.z0 = ie.p[1] - ie.p[3] * o_sqrt(ie.x * ie.x + ie.p[0] * ie.p[0]);
     FT.push_back(std::move(T));
   }

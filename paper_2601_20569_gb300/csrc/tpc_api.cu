@@ -350,6 +350,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ft_assigned, FT * NS);
   ok &= dalloc(ctx, &F.ft_newly, FT * NS);
   ok &= dalloc(ctx, &F.ft_next, FT);
+  ok &= dalloc(ctx, &F.ft_ipol, FT * kMaxInner * kIpolF);
   ok &= dalloc(ctx, &F.ft_fixed, n);
   ok &= dalloc(ctx, &F.bid, n);
   ok &= dalloc(ctx, &F.taken, n);

@@ -741,19 +741,19 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
 enum : int { kFitIdle = 0, kFitIn, kFitExt };
 
 __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, const MapDev& M,
-                                                 int f, int k, int rs, const Lin& L,
+                                                 int f, int k, int rs, float x, const float* ref,
                                                  const Interp& I, float z0) {
   const int sec = rs / P.n_rows;
   float cy = I.y, cz = I.z;
   {
     float D[3];
-    map_eval(M, P, sec, L.t.x, I.y, I.z - z0, D);
+    map_eval(M, P, sec, x, I.y, I.z - z0, D);
     float sy = D[1], sz = D[2];
     if (D[0] != 0.0f) {
       StepJ stp;
-      if (helix_step(L.r, D[0], P, stp, P.fit_max_snp)) {
-        sy = sy - (stp.p0 - L.r[0]);
-        sz = sz - (stp.p1 - L.r[1]);
+      if (helix_step(ref, D[0], P, stp, P.fit_max_snp)) {
+        sy = sy - (stp.p0 - ref[0]);
+        sz = sz - (stp.p1 - ref[1]);
       }
     }
     cy = I.y - sy;
@@ -772,7 +772,7 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
     const float yk = pk.x, zk = pk.y;
     if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
     float my, mz;
-    if (!corrected(M, P, sec, L.t.x, yk, zk, z0, L.r, my, mz)) return;
+    if (!corrected(M, P, sec, x, yk, zk, z0, ref, my, mz)) return;
     const float c2 = chi2_interp(I, my, mz, P);
     if (!(c2 < P.int_chi2)) return;
     const int id = F.sid[kk];
@@ -869,6 +869,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
   const int NR = P.n_rows;
   int phase = kFitIdle;
   int f = 0, ns = 0, k = 0;
+  bool lp = false;  // FP64 updates (low-pT looper)
   float z0 = 0.0f;
   const int* SC = nullptr;
   const uint16_t* SR = nullptr;
@@ -879,6 +880,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
       const int q = fit_next(F.cnt, kQFit12, kQFit12N, nL, nf);
       if (q >= nf) break;
       f = F.ft_order[q];
+      lp = F.ft_looper[f] != 0;
       ns = F.ft_nst[f];
       F.ft_ok[f] = 0;
       if (ns == 0) continue;  // not reached: every chain holds clusters
@@ -935,7 +937,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
         have = ok;
       }
     }
-    if (have) fit_update(L.t, residual(L.t, my, mz, P), P);
+    if (have) update_as(L.t, residual(L.t, my, mz, P), lp);
     if (!ok) {
       phase = kFitIdle;
       continue;
@@ -967,6 +969,7 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
   const int NR = P.n_rows;
   bool busy = false;
   int f = 0, ns = 0, k = 0;
+  bool lp = false;  // FP64 updates (low-pT looper)
   float z0 = 0.0f;
   const int* SC = nullptr;
   const uint16_t* SR = nullptr;
@@ -979,6 +982,7 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
       if (q >= nf) break;
       f = F.ft_order[q];
       if (!F.ft_ok[f]) continue;
+      lp = F.ft_looper[f] != 0;
       ns = F.ft_nst[f];
       z0 = F.ft_z0[f];
       SC = F.ft_st_cl + (long)f * kMaxRows;
@@ -1021,14 +1025,20 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
         if (ok) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
       }
       if (ok && inner) {
-        inner_candidates(F, P, M, f, k, rs, L, I, z0);
+        // Phase II candidates of this inner station: the search runs later in
+        // k_inner_cand, over all (track, inner station) pairs at once
+        float* ip = F.ft_ipol + ((long)f * kMaxInner + k) * kIpolF;
+        ip[0] = I.y; ip[1] = I.z; ip[2] = I.c00; ip[3] = I.c01; ip[4] = I.c11;
+        ip[5] = L.t.x;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) ip[6 + i] = L.r[i];
         if (c >= 0) {
           ok = corrected(M, P, sec, L.t.x, cy, cz, z0, L.r, my, mz);
           have = ok;
         }
       }
     }
-    if (have) fit_update(L.t, residual(L.t, my, mz, P), P);
+    if (have) update_as(L.t, residual(L.t, my, mz, P), lp);
     if (!ok) {
       F.ft_ok[f] = 0;
       busy = false;
@@ -1044,6 +1054,31 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
 // Second ambiguity solving, round k: bids (chi2, track key) per free cluster.
 __device__ __forceinline__ bool inner_station(const FrameDev& F, const KParams& P, int f, int k) {
   return k < F.ft_nst[f] && (F.ft_st_rs[(long)f * kMaxRows + k] % P.n_rows) < P.inner_rows;
+}
+
+// Phase II candidate search of every inner station of every fit track, from
+// the interpolation k_fit2 left for it (one thread per (track, station)).
+__global__ void k_inner_cand(FrameDev F, KParams P, MapDev M) {
+  const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
+  if (F.cnt->err) return;
+  const long tot = (long)nf * P.inner_rows;
+  for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
+       w += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(w / P.inner_rows), k = (int)(w % P.inner_rows);
+    if (!F.ft_ok[f] || !inner_station(F, P, f, k)) continue;
+    const float* ip = F.ft_ipol + ((long)f * kMaxInner + k) * kIpolF;
+    Interp I;
+    I.y = ip[0];
+    I.z = ip[1];
+    I.c00 = ip[2];
+    I.c01 = ip[3];
+    I.c11 = ip[4];
+    float ref[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ref[i] = ip[6 + i];
+    inner_candidates(F, P, M, f, k, F.ft_st_rs[(long)f * kMaxRows + k], ip[5], ref, I,
+                     F.ft_z0[f]);
+  }
 }
 
 // Work item w of the second ambiguity: (fit track, candidate slot).  Slots
@@ -1123,6 +1158,7 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
   for (int q = fit_next(F.cnt, kQFit3, kQFit3N, nL, nf); q < nf;
        q = fit_next(F.cnt, kQFit3, kQFit3N, nL, nf)) {
     const int f = F.ft_order[q];
+    const bool lp = F.ft_looper[f] != 0;  // FP64 updates (low-pT looper)
     F.ft_n[f] = 0;
     if (!F.ft_ok[f]) continue;
     const int ns = F.ft_nst[f];
@@ -1172,7 +1208,7 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
       const Resid R = residual(L.t, my, mz, P);
       if (R.chi2 > P.final_chi2) continue;
       chi2 = chi2 + R.chi2;
-      fit_update(L.t, R, P);
+      update_as(L.t, R, lp);
       used[n] = c;
       ++n;
       out = L.t;
@@ -1674,7 +1710,8 @@ int stage_fit12(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_fit_stations<<<sms * 8, kBlock, 0, s>>>(F, P);
   k_fit1<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, F.map);
   k_fit2<<<persistent_grid(F.lc, kLFit12, sms), F.lc.block[kLFit12], 0, s>>>(F, P, F.map);
-  return 3;
+  k_inner_cand<<<sms * 8, kBlock, 0, s>>>(F, P, F.map);
+  return 4;
 }
 
 int stage_ambiguity2(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {

@@ -77,6 +77,7 @@ constexpr int kMaxBinOcc = 1024;
 
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
+constexpr int kIpolF = 11;      // interpolation record of an inner station
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 constexpr int kMaxExt = 32;      // Phase III: rows extrapolated below a track (slots after the inner ones)
@@ -215,6 +216,8 @@ struct FrameDev {
   int* ft_assigned;        // [cap_ft][nslot]
   uint8_t* ft_newly;       // [cap_ft][nslot]
   int* ft_next;            // [cap_ft] rows extrapolated below the innermost station
+  float* ft_ipol;          // [cap_ft][kMaxInner][kIpolF] iteration-2 interpolation at inner
+                           // stations (y, z, Cyy, Cyz, Czz, x, reference p[5]) for k_inner_cand
   uint8_t* ft_fixed;       // [n] sorted cluster held by a station outside the inner region
   unsigned long long* bid; // [n] per sorted cluster
   uint8_t* taken;          // [n]

@@ -303,12 +303,19 @@ __device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
 #endif
 }
 
-// Update of the final fit and refit: FP64 for loopers (|q/pT| > looper_qpt).
-__device__ __forceinline__ void fit_update(Trk<float>& t, const Resid& R, const KParams& P) {
-  if (P.looper_qpt > 0.0f && fabsf(t.p[4]) > P.looper_qpt)
+// Update with the gain and covariance arithmetic in FP64 when `fp64`.
+__device__ __forceinline__ void update_as(Trk<float>& t, const Resid& R, bool fp64) {
+  if (fp64)
     update_fp64(t, R);
   else
     update(t, R);
+}
+
+// Update of the refit: FP64 for loopers, judged at the update by the current
+// |q/pT| > looper_qpt.  (The final fit classifies a track once, from its
+// first segment's inner end, and calls update_as.)
+__device__ __forceinline__ void fit_update(Trk<float>& t, const Resid& R, const KParams& P) {
+  update_as(t, R, P.looper_qpt > 0.0f && fabsf(t.p[4]) > P.looper_qpt);
 }
 
 // Frame rotation to the adjacent sector (dir = +1: +20 deg).
