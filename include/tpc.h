@@ -209,7 +209,8 @@ tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kern
 
 /* Set the launch shape of heavy kernel `slot` (0..4, as tpc_launch_config
  * numbers them), e.g. to reapply a shape the autotuner chose earlier on the
- * same GPU.  block: multiple of 32 in [32, 1024]; blocks_per_sm in [1, 32].
+ * same GPU.  block: multiple of 32 in [32, 256] (the kernels are compiled for
+ * at most 256 threads per block); blocks_per_sm in [1, 32].
  * The shape changes only scheduling: results are identical for every shape.
  * TPC_ERR_INVALID_ARG for any other value. */
 tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,

@@ -682,7 +682,7 @@ tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kern
 tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
                                  int32_t blocks_per_sm) {
   if (!ctx) return TPC_ERR_INVALID_ARG;
-  if (slot < 0 || slot >= kLNum || block < 32 || block > 1024 || block % 32 != 0 ||
+  if (slot < 0 || slot >= kLNum || block < 32 || block > 256 || block % 32 != 0 ||
       blocks_per_sm < 1 || blocks_per_sm > 32)
     return fail(ctx, TPC_ERR_INVALID_ARG, "launch shape slot %d: block %d, %d per SM", slot, block,
                 blocks_per_sm);

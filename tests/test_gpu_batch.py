@@ -87,6 +87,31 @@ def test_autotune_keeps_results():
         assert np.array_equal(before[k].view(np.uint8), after[k].view(np.uint8)), k
 
 
+def test_set_launch_config_keeps_results_and_rejects_bad_shapes():
+    """Launch shapes set through the C ABI change only scheduling; shapes
+    outside the documented range are refused."""
+    from paper_2601_20569_gb300 import tpc
+
+    f = synth.generate("central_event", n_primaries=800, seed=23)
+    tb = tpc.Tracker(RX, TrackerOptions(), mode=0, cap_clusters=f.n)
+    dev = tb.to_device(f.y, f.z, f.q, f.row, f.sector)
+    tb.track(*dev)
+    before = host(tb)
+    shapes = [{"block": b, "blocks_per_sm": q} for b, q in ((64, 2), (32, 1), (224, 1),
+                                                              (96, 3), (256, 32))]
+    tb.set_launch_config(shapes)
+    assert [(c["block"], c["blocks_per_sm"]) for c in tb.launch_config()] == \
+        [(s["block"], s["blocks_per_sm"]) for s in shapes]
+    tb.track(*dev)
+    after = host(tb)
+    for k in ("params", "cov", "key", "cl_ids", "attach"):
+        assert np.array_equal(before[k].view(np.uint8), after[k].view(np.uint8)), k
+    for bad in ({"block": 48, "blocks_per_sm": 4}, {"block": 512, "blocks_per_sm": 4},
+                {"block": 128, "blocks_per_sm": 0}, {"block": 128, "blocks_per_sm": 33}):
+        with pytest.raises(tpc.TpcError):
+            tb.set_launch_config([bad])
+
+
 def test_full_size_frames_sampled_sector_parity():
     """Two full 2.8 ms frames (~4e7 clusters) tracked as one batch; the
     tracklets and sector owners of two sampled sectors equal the oracle's on
