@@ -108,6 +108,10 @@ typedef struct {
   int32_t use_graphs;       /* 1: replay each call's chain from a captured CUDA graph */
   int32_t ext_rows;         /* Phase III (Sec. 3): rows below a track's innermost cluster searched
                                by inward extrapolation, 0..32 (0: off) */
+  int32_t seed_iters;       /* Sec. 3: sector-tracking iterations, 1..4; every later one runs the
+                               neighbour finding, tracklet construction and selection again on
+                               the clusters that no accepted tracklet of the earlier ones kept
+                               (0 or 1: off) */
   int64_t cap_clusters;     /* max clusters per call (all frames of a batch) */
   int64_t cap_tracklets;    /* max tracklets per frame (0: n/16 + 4096) */
   int64_t cap_tracks;       /* max tracks per frame (0: cap_tracklets) */

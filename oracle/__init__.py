@@ -53,6 +53,7 @@ class _Opt(ctypes.Structure):
         ("n_rows", ctypes.c_int32),
         ("n_sectors", ctypes.c_int32),
         ("ext_rows", ctypes.c_int32),
+        ("seed_iters", ctypes.c_int32),
     ]
 
 

@@ -71,6 +71,7 @@ struct orc_options {
   int32_t n_rows;
   int32_t n_sectors;
   int32_t ext_rows;     // Phase III: rows searched below a track's innermost cluster (0: off)
+  int32_t seed_iters;   // sector-tracking iterations, the later ones on leftover clusters (>= 1)
 };
 // Correction map of the oracle (host memory): layout [3][n_z][n_r][n_phi].
 struct orc_map {
@@ -245,7 +246,7 @@ struct Params {
       shared_frac, merge_chi2, merge_dy, merge_dz, int_chi2, final_chi2, attach_margin,
       edge_margin, looper_qpt, merge_zspan, ext_chi2;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors,
-      ext_rows;
+      ext_rows, seed_iters;
   std::vector<Real> row_x;
 };
 
@@ -280,6 +281,7 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
   P.inner_rows = o.inner_rows; P.cand_k = o.cand_k; P.brute_force = o.brute_force;
   P.n_rows = o.n_rows; P.n_sectors = o.n_sectors;
   P.ext_chi2 = o.ext_chi2; P.ext_rows = o.ext_rows;
+  P.seed_iters = o.seed_iters < 1 ? 1 : o.seed_iters;
   P.row_x.resize(o.n_rows);
   for (int r = 0; r < o.n_rows; ++r) P.row_x[r] = (Real)row_x[r];
   return P;
@@ -545,7 +547,11 @@ struct Frame {
   std::vector<int> row, sector;
   // a1: ids of each (sector,row), sorted by (z, id)
   std::vector<std::vector<int>> rows;
+  // clusters taken by the tracks of earlier seeding iterations (empty in the
+  // first): the sector tracking of a later iteration does not see them
+  std::vector<uint8_t> used;
   int rid(int s, int r, const Params<Real>& P) const { return s * P.n_rows + r; }
+  bool taken(long id) const { return !used.empty() && used[id]; }
 };
 
 template <typename Real>
@@ -587,11 +593,11 @@ void find_links(const Frame<Real>& F, const Params<Real>& P, std::vector<int>& u
   const Real margin = Real(0.01);
   for (long c = 0; c < F.n; ++c) {
     const int r = F.row[c], s = F.sector[c];
-    if (r < 1 || r > P.n_rows - 2) continue;
+    if (r < 1 || r > P.n_rows - 2 || F.taken(c)) continue;
     const Real yc = F.y[c], zc = F.z[c];
     std::vector<int> U, D;
     auto inwin = [&](int id) {
-      return o_fabs(F.y[id] - yc) <= P.link_wy && o_fabs(F.z[id] - zc) <= P.link_wz;
+      return !F.taken(id) && o_fabs(F.y[id] - yc) <= P.link_wy && o_fabs(F.z[id] - zc) <= P.link_wz;
     };
     for_row_range(F, P, s, r + 1, zc - P.link_wz - margin, zc + P.link_wz + margin, [&](int id) {
       if (inwin(id)) U.push_back(id);
@@ -662,6 +668,7 @@ int pick(const Frame<Real>& F, const Params<Real>& P, const Track<Real>& t, int 
   const Real ylo = t.p[0] - hy, yhi = t.p[0] + hy;
   const Real margin = Real(0.01);
   for_row_range(F, P, s, r, t.p[1] - hz - margin, t.p[1] + hz + margin, [&](int id) {
+    if (F.taken(id)) return;
     if (!(F.y[id] >= ylo && F.y[id] <= yhi)) return;
     if (o_fabs(F.z[id] - t.p[1]) > hz) return;
     const Resid<Real> R = residual(t, F.y[id], F.z[id], P);
@@ -1810,24 +1817,64 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   res.put("ext_assigned", ex_assigned, "i4");
 }
 
+// Sector tracking a2-a6, seed_iters times.  Sec. 3 (Phase III) runs the
+// seeding again on the clusters left over after the ambiguity solving: every
+// later iteration repeats a2-a6 on the clusters that no accepted tracklet of
+// an earlier iteration kept, as if the others were not there.  A cluster is
+// taken if an accepted tracklet kept it or starts at it (so that no two
+// accepted tracklets share a start cluster, the sector tracks' key); the
+// selection of an iteration is among its own tracklets.  The per-tracklet
+// outputs are those of all iterations in order (tl_iter), the link arrays
+// those of the last iteration.
 template <typename Real>
-SectorResult<Real> run_sector_tracking(const Frame<Real>& F, const Params<Real>& P, Result& res) {
-  std::vector<int> up, dn, cu, cd;
-  find_links(F, P, up, dn);
-  clean_links(up, dn, cu, cd);
-  std::vector<int> starts = start_hits(cu, cd);
+SectorResult<Real> run_sector_tracking(Frame<Real>& F, const Params<Real>& P, Result& res) {
+  const int R = P.n_rows;
+  SectorResult<Real> SR;
+  std::vector<int> up, dn, cu, cd, all_starts, tl_iter;
+  std::vector<uint64_t> keys;
+  std::vector<int> owner(F.n, -1);
+  for (int it = 0; it < P.seed_iters; ++it) {
+    find_links(F, P, up, dn);
+    clean_links(up, dn, cu, cd);
+    const std::vector<int> starts = start_hits(cu, cd);
+    std::vector<Tracklet<Real>> TL(starts.size());
+    for (size_t i = 0; i < starts.size(); ++i) TL[i] = construct(F, P, cu, starts[i]);
+    Selection<Real> S = select(F, P, TL);
+    // sector-level attachment: the owner tracklet's start id if it is accepted
+    std::map<int, size_t> by_start;
+    for (size_t i = 0; i < TL.size(); ++i) by_start[TL[i].start] = i;
+    for (long c = 0; c < F.n; ++c) {
+      const uint64_t k = S.owner_key[c];
+      if (!k) continue;
+      const int sid = (int)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
+      if (S.accepted[by_start[sid]]) owner[c] = sid;
+    }
+    if (F.used.empty()) F.used.assign(F.n, 0);
+    for (size_t i = 0; i < TL.size(); ++i) {
+      all_starts.push_back(TL[i].start);
+      tl_iter.push_back(it);
+      keys.push_back(TL[i].n ? make_key(score_of(TL[i], P), TL[i].start) : 0);
+      if (S.accepted[i]) {
+        for (int c : S.kept[i]) F.used[c] = 1;
+        F.used[TL[i].start] = 1;
+      }
+      SR.TL.push_back(std::move(TL[i]));
+      SR.S.accepted.push_back(S.accepted[i]);
+      SR.S.kept.push_back(std::move(S.kept[i]));
+    }
+  }
+  F.used.clear();  // the stages after the sector tracking see every cluster
   res.put("link_up", up, "i4");
   res.put("link_dn", dn, "i4");
   res.put("clean_up", cu, "i4");
   res.put("clean_dn", cd, "i4");
-  res.put("start", starts, "i4");
-  std::vector<Tracklet<Real>> TL(starts.size());
-  for (size_t i = 0; i < starts.size(); ++i) TL[i] = construct(F, P, cu, starts[i]);
-  const int R = P.n_rows;
-  std::vector<int> tl_n(TL.size()), tl_ndf(TL.size()), tl_hits(TL.size() * R, -1);
-  std::vector<Real> tl_par(TL.size() * 5), tl_cov(TL.size() * 15), tl_chi2(TL.size()),
-      tl_x(TL.size());
-  for (size_t i = 0; i < TL.size(); ++i) {
+  res.put("start", all_starts, "i4");
+  const std::vector<Tracklet<Real>>& TL = SR.TL;
+  const size_t nt = TL.size();
+  std::vector<int> tl_n(nt), tl_ndf(nt), tl_hits(nt * R, -1);
+  std::vector<Real> tl_par(nt * 5), tl_cov(nt * 15), tl_chi2(nt), tl_x(nt);
+  std::vector<int> acc(nt), nk(nt), kept(nt * R, -1);
+  for (size_t i = 0; i < nt; ++i) {
     tl_n[i] = TL[i].n;
     tl_ndf[i] = TL[i].ndf;
     tl_chi2[i] = TL[i].chi2;
@@ -1835,8 +1882,12 @@ SectorResult<Real> run_sector_tracking(const Frame<Real>& F, const Params<Real>&
     for (int k = 0; k < 5; ++k) tl_par[i * 5 + k] = TL[i].t.p[k];
     for (int k = 0; k < 15; ++k) tl_cov[i * 15 + k] = TL[i].t.c[k];
     for (size_t k = 0; k < TL[i].hits.size(); ++k) tl_hits[i * R + k] = TL[i].hits[k];
+    acc[i] = SR.S.accepted[i];
+    nk[i] = (int)SR.S.kept[i].size();
+    for (size_t k = 0; k < SR.S.kept[i].size(); ++k) kept[i * R + k] = SR.S.kept[i][k];
   }
-  res.put("tl_start", starts, "i4");
+  res.put("tl_start", all_starts, "i4");
+  res.put("tl_iter", tl_iter, "i4");
   res.put("tl_n", tl_n, "i4");
   res.put("tl_ndf", tl_ndf, "i4");
   res.put("tl_hits", tl_hits, "i4");
@@ -1844,34 +1895,11 @@ SectorResult<Real> run_sector_tracking(const Frame<Real>& F, const Params<Real>&
   res.put("tl_cov", tl_cov, real_name<Real>());
   res.put("tl_chi2", tl_chi2, real_name<Real>());
   res.put("tl_x", tl_x, real_name<Real>());
-  Selection<Real> S = select(F, P, TL);
-  std::vector<int> acc(TL.size()), nk(TL.size()), kept(TL.size() * R, -1);
-  std::vector<uint64_t> keys(TL.size(), 0);
-  for (size_t i = 0; i < TL.size(); ++i) {
-    acc[i] = S.accepted[i];
-    nk[i] = (int)S.kept[i].size();
-    for (size_t k = 0; k < S.kept[i].size(); ++k) kept[i * R + k] = S.kept[i][k];
-    if (TL[i].n) keys[i] = make_key(score_of(TL[i], P), TL[i].start);
-  }
-  // sector-level attachment: owner tracklet's start id if that tracklet is accepted
-  std::vector<int> owner(F.n, -1);
-  std::map<int, size_t> by_start;
-  for (size_t i = 0; i < TL.size(); ++i) by_start[TL[i].start] = i;
-  for (long c = 0; c < F.n; ++c) {
-    const uint64_t k = S.owner_key[c];
-    if (!k) continue;
-    const int sid = (int)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
-    const size_t i = by_start[sid];
-    if (S.accepted[i]) owner[c] = sid;
-  }
   res.put("tl_key", keys, "u8");
   res.put("tl_accept", acc, "i4");
   res.put("tl_nkept", nk, "i4");
   res.put("tl_kept", kept, "i4");
   res.put("sector_owner", owner, "i4");
-  SectorResult<Real> SR;
-  SR.TL = std::move(TL);
-  SR.S = std::move(S);
   return SR;
 }
 
@@ -2035,7 +2063,7 @@ static int track_impl(long n, const In* y, const In* z, const uint8_t* row, cons
   auto run = [&](auto tag) {
     using Real = decltype(tag);
     const auto P = orc::make_params<Real>(*opt, row_x);
-    const auto F = orc::make_frame<Real>(n, y, z, row, sector, P);
+    auto F = orc::make_frame<Real>(n, y, z, row, sector, P);
     auto SR = orc::run_sector_tracking(F, P, R->r);
     if (stages >= 1) orc::run_merge_fit(F, P, orc::make_map<Real>(map), SR, R->r);
   };

@@ -11,11 +11,14 @@ values; the defaults below are this library's readings of it:
 * Phase III (Sec. 3): tracks are extrapolated inward over at most ``ext_rows``
   rows below their innermost cluster, with a candidate cut of chi2 < 9
   (stricter than the interpolation cut of 25); off by default, as the paper
-  describes it as work in progress.
+  describes it as work in progress;
+* seeding iterations on leftover clusters (Sec. 3): ``seed_iters`` sector-
+  tracking passes with the same cuts, each later one on the clusters that no
+  accepted tracklet of the earlier ones kept; off by default for the same
+  reason.
 """
 from __future__ import annotations
 
-import ctypes
 from dataclasses import asdict, dataclass, field
 
 MODE_STRICT = 0  # FP32, no FMA contraction: bit-identical to the strict CPU oracle
@@ -48,6 +51,8 @@ class TrackerOptions:
     ext_rows: int = 0               # Phase III: rows searched below a track's innermost
                                     # cluster by inward extrapolation (0: off, <= 32)
     ext_chi2: float = 9.0           # Phase III candidate cut (2 dof), stricter than int_chi2
+    seed_iters: int = 1             # sector-tracking iterations; each later one seeds again on
+                                    # the clusters the accepted tracklets left (1: off, <= 4)
     max_miss: int = 10              # consecutive empty rows ending the following
     min_hits: int = 10
     merge_max_gap: int = 20         # rows between merged segments
@@ -59,30 +64,3 @@ class TrackerOptions:
 
     def as_dict(self) -> dict:
         return asdict(self)
-
-
-FLOAT_FIELDS = ("bz", "sigma_y", "sigma_z", "ms_theta", "link_wy", "link_wz", "link_chi2")
-FLOAT_FIELDS2 = ("follow_chi2", "max_snp", "fit_max_snp", "score_w", "shared_frac", "merge_chi2", "merge_dy",
-                 "merge_dz", "int_chi2", "final_chi2", "attach_margin", "looper_qpt", "edge_margin",
-                 "ext_chi2")
-INT_FIELDS = ("max_miss", "min_hits", "merge_max_gap", "inner_rows", "cand_k", "brute_force",
-              "n_rows", "n_sectors", "ext_rows")
-
-
-def ctypes_fields():
-    """Field layout shared by the C option structs (floats, then ints)."""
-    f = [(k, ctypes.c_float) for k in FLOAT_FIELDS]
-    f.append(("seed_c", ctypes.c_float * 5))
-    f += [(k, ctypes.c_float) for k in FLOAT_FIELDS2]
-    f += [(k, ctypes.c_int32) for k in INT_FIELDS]
-    return f
-
-
-def fill(struct, opts: dict):
-    for k in FLOAT_FIELDS + FLOAT_FIELDS2:
-        setattr(struct, k, float(opts[k]))
-    for k in INT_FIELDS:
-        setattr(struct, k, int(opts[k]))
-    for i, v in enumerate(opts["seed_c"]):
-        struct.seed_c[i] = float(v)
-    return struct

@@ -56,7 +56,7 @@ class Options(ctypes.Structure):
         ("min_hits", ctypes.c_int32), ("merge_max_gap", ctypes.c_int32),
         ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("max_frames", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-        ("ext_rows", ctypes.c_int32),
+        ("ext_rows", ctypes.c_int32), ("seed_iters", ctypes.c_int32),
         ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
         ("cap_tracks", ctypes.c_int64),
     ]
