@@ -52,6 +52,9 @@ def parse():
                     help="skip the refit + adjoint timing on one distorted frame")
     ap.add_argument("--ext-rows", type=int, default=0,
                     help="Phase III inward extrapolation over this many rows (0: off)")
+    ap.add_argument("--seed-iters", type=int, default=1,
+                    help="sector-tracking iterations, the later ones on leftover clusters "
+                         "(Sec. 3; 1 = off, the default)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up plus one step and exit (for ncu launch lists)")
     return ap.parse_args()
@@ -207,9 +210,11 @@ def run_reference(args):
 
 # Algorithmic bytes of each stage: the minimum it must move, from the counts
 # of one call (clusters n, tracklet hits th, tracklets nt, sector-track hits
-# sh, sector tracks ns, fit stations fst, fitted hits fh, fit tracks nf).
+# sh, sector tracks ns, fit stations fst, fitted hits fh, fit tracks nf; the
+# tracklet hits rh and tracklets rt of the later seeding iterations).
 def stage_bytes(name: str, c: dict) -> float:
     n, th, nt = c["clusters"], c["tl_hits"], c["tracklets"]
+    rh, rt, iters = c.get("re_hits", 0), c.get("re_tracklets", 0), c.get("seed_iters", 1)
     sh, ns, fh, nf = c["st_hits"], c["sector_tracks"], c["fit_hits"], c["fit_tracks"]
     fst = c["fit_stations"]
     table = {
@@ -236,6 +241,10 @@ def stage_bytes(name: str, c: dict) -> float:
         "fit3": fst * (6 + 1 + 8 + 4) + nf * 2 * 88,
         # used clusters and state per output track
         "output": fh * 12 + nf * 100,
+        # per later iteration: taken flags and owner keys of all clusters, the
+        # neighbour finding and start hits again; the tracklets and selection
+        # of those iterations as above
+        "reseed": (iters - 1) * n * (1 + 8 + 36 + 8) + rh * (28 + 24) + rt * (96 + 16 + 4),
     }
     return float(table.get(name, 0.0))
 
@@ -324,7 +333,7 @@ def main():
     note(f"{len(frames)} frames generated")
     n_per_step = sum(f.n for f in frames)
     mode = MODE_FAST if args.mode == "fast" else MODE_STRICT
-    topts = TrackerOptions(ext_rows=args.ext_rows)
+    topts = TrackerOptions(ext_rows=args.ext_rows, seed_iters=args.seed_iters)
     tr = tpc.Tracker(synth.row_x(), topts, mode=mode, cap_clusters=n_per_step,
                      max_frames=len(frames), use_graphs=True)
     dev = [tr.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
@@ -402,9 +411,12 @@ def main():
     torch.cuda.synchronize()
     stages = tr.stage_stats()
     tr.profile(False)
+    tl_n = tr.debug("tl_n")
+    first = int(tr.debug("pass_start")[1]) if args.seed_iters > 1 else tl_n.size
     counts = {
-        "clusters": n_per_step, "tl_hits": int(tr.debug("tl_n").sum()),
-        "tracklets": int(tr.debug("tl_n").size), "st_hits": int(tr.debug("tl_nkept").sum()),
+        "clusters": n_per_step, "tl_hits": int(tl_n[:first].sum()), "tracklets": first,
+        "re_hits": int(tl_n[first:].sum()), "re_tracklets": int(tl_n.size - first),
+        "seed_iters": args.seed_iters, "st_hits": int(tr.debug("tl_nkept").sum()),
         "sector_tracks": int(tr.debug("st_key").size), "fit_hits": int(tr.debug("ft_n").sum()),
         "fit_tracks": int(tr.debug("ft_n").size), "fit_stations": int(tr.debug("ft_nst").sum()),
     }
@@ -459,7 +471,7 @@ def main():
                    "clusters_per_step": n_per_step, "mode": args.mode,
                    "l2": "inputs larger than L2 (each frame > 129 MB resident)",
                    "parallelism": f"replicas x{world}", "launch": "batched + CUDA graph",
-                   "phase3_ext_rows": args.ext_rows},
+                   "phase3_ext_rows": args.ext_rows, "seed_iters": args.seed_iters},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,

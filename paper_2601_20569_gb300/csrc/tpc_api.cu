@@ -29,6 +29,7 @@ const StageDef kStages[] = {
     {"starts", strict::stage_starts, fast::stage_starts},
     {"tracklets", strict::stage_tracklets, fast::stage_tracklets},
     {"select", strict::stage_select, fast::stage_select},
+    {"reseed", strict::stage_reseed, fast::stage_reseed},
     {"sector_refit", strict::stage_sector_refit, fast::stage_sector_refit},
     {"merge", strict::stage_merge, fast::stage_merge},
     {"fit12", strict::stage_fit12, fast::stage_fit12},
@@ -156,6 +157,7 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.looper_qpt = o.looper_qpt;
   P.ext_chi2 = o.ext_chi2;
   P.ext_rows = o.ext_rows;
+  P.seed_iters = o.seed_iters > 1 ? o.seed_iters : 1;
   // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
   P.merge_zspan = (float)((double)(o.merge_max_gap + 2) *
                           (((double)row_x[nr - 1] - (double)row_x[0]) / (double)(nr - 1)) /
@@ -210,6 +212,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
       (opt->mode != 0 && opt->mode != 1) || opt->cap_clusters > (1L << 30) ||
       opt->inner_rows < 0 || opt->inner_rows > kMaxInner || opt->merge_max_gap < 1 ||
       opt->ext_rows < 0 || opt->ext_rows > kMaxExt || !(opt->ext_chi2 > 0.0f) ||
+      opt->seed_iters < 0 || opt->seed_iters > kMaxSeedIters ||
       opt->max_frames < 0 || opt->max_frames > 64 ||
       (long)geo->n_sectors * (opt->max_frames > 1 ? opt->max_frames : 1) * geo->n_rows > 65535 ||
       !(opt->fit_max_snp > 0.0f && opt->fit_max_snp < 1.0f) ||
@@ -284,6 +287,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.tl_nkept, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_kept, F.cap_tl * kMaxRows);
   ok &= dalloc(ctx, &F.sec_owner, n);
+  ok &= dalloc(ctx, &F.sused, n);
   ok &= dalloc(ctx, &F.cnt, 1);
   // a7
   const long T = F.cap_tl;
@@ -421,6 +425,7 @@ tpc_status enqueue_chain(tpc_ctx* ctx, FrameDev& F, const KParams& Pc, cudaStrea
     CK(cudaMemsetAsync(F.attach, 0xFF, sizeof(int) * n, s));
     CK(cudaMemsetAsync(F.attach_key, 0x7F, sizeof(int) * n, s));
     if (Pc.ext_rows > 0) CK(cudaMemsetAsync(F.ft_fixed, 0, n, s));
+    if (Pc.seed_iters > 1) CK(cudaMemsetAsync(F.sused, 0, n, s));
   }
   CK(cudaMemsetAsync(F.ie_cnt, 0, sizeof(int) * (nrr * kMergeZ + 1), s));
   CK(cudaMemsetAsync(F.st_ord_cnt, 0, sizeof(int) * kOrdBuckets, s));
@@ -846,6 +851,8 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   else if (w == "tl_nkept") { src = F.tl_nkept; nb = 4 * nst; }
   else if (w == "owner_key") { src = F.owner_key; nb = 8 * n; }
   else if (w == "sec_owner") { src = F.sec_owner; nb = 4 * n; }
+  else if (w == "sused") { src = F.sused; nb = n; }
+  else if (w == "pass_start") { src = F.cnt->pass_start; nb = sizeof(int) * kMaxSeedIters; }
   else if (w == "st_tl") { src = F.st_tl; nb = 4L * c.n_tracks; }
   else if (w == "st_ok") { src = F.st_ok; nb = 4L * c.n_tracks; }
   else if (w == "st_key") { src = F.st_key; nb = 4L * c.n_tracks; }

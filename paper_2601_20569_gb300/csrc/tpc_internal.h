@@ -25,6 +25,7 @@ struct KParams {
   float merge_chi2, merge_dy, merge_dz, merge_zspan;
   float int_chi2, final_chi2, attach_margin, edge_margin, looper_qpt, ext_chi2;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, ext_rows;
+  int seed_iters;  // sector-tracking iterations (the later ones on leftover clusters)
   int n_rows, n_sectors;  // n_sectors: all sectors of the call (frames x sectors)
   int n_phi;         // azimuthal sectors of one TPC half (sector % n_phi, side = sector / n_phi)
   float grid_dy;     // target y bin size [cm]
@@ -80,6 +81,7 @@ constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, 
 constexpr int kIpolF = 11;      // interpolation record of an inner station
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
+constexpr int kMaxSeedIters = 4;  // sector-tracking iterations
 constexpr int kMaxExt = 32;      // Phase III: rows extrapolated below a track (slots after the inner ones)
 // Scheduling buckets of the sector refit (most clusters first).
 constexpr int kOrdBuckets = 128;
@@ -108,6 +110,9 @@ struct Counters {
   int queue[kQNum];  // work-queue heads
   int n_loopers;     // fit tracks whose updates run in FP64
   int n_pos;         // kept-cluster positions of the sector tracks
+  int tl_base;       // first tracklet of the current sector-tracking iteration
+  int n_new;         // start hits found by the current iteration
+  int pass_start[kMaxSeedIters];  // first tracklet of each iteration
 };
 
 // Working set of one frame on the device.
@@ -160,6 +165,8 @@ struct FrameDev {
   int* tl_nkept;
   int* tl_kept;            // [cap_tl*kMaxRows] outermost first
   int* sec_owner;          // [n] sorted index space: tracklet index or -1
+  uint8_t* sused;          // [n] sorted cluster taken by an accepted tracklet of an earlier
+                           // sector-tracking iteration (iterations after the first)
   Counters* cnt;
 
   // a7 sector tracks (capacity cap_tl)

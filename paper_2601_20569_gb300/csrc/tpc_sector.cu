@@ -146,16 +146,18 @@ __global__ void k_bin_sort(FrameDev F) {
 // paired with the list.  The best pair minimises the distance of the middle
 // cluster to the straight line through the pair; ties go to the smaller
 // input id of the upper, then of the lower cluster, so the result does not
-// depend on the visiting order.
+// depend on the visiting order.  In the iterations after the first (kLeft)
+// the clusters taken by earlier iterations neither link nor are linked to.
 constexpr int kLinkList = 8;
 
+template <bool kLeft>
 __global__ void k_links(FrameDev F, KParams P) {
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= F.n || F.cnt->err) return;
   const int rr = F.srow[k];
   const int r = rr % P.n_rows;
   int bu = -1, bd = -1;
-  if (r >= 1 && r <= P.n_rows - 2) {
+  if (r >= 1 && r <= P.n_rows - 2 && !(kLeft && F.sused[k])) {
     const float2 pc = F.syz[k];
     const float yc = pc.x, zc = pc.y;
     const float xd = F.row_x[r - 1], xc = F.row_x[r], xu = F.row_x[r + 1];
@@ -168,6 +170,7 @@ __global__ void k_links(FrameDev F, KParams P) {
     int nd = 0;
     bool dense = false;
     for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
+      if (kLeft && F.sused[d]) return;
       const float2 pd = F.syz[d];
       const float yd = pd.x, zd = pd.y;
       if (!(fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)) return;
@@ -197,6 +200,7 @@ __global__ void k_links(FrameDev F, KParams P) {
     };
     if (nd > 0)
       for_window(F.bin_first, gu, ylo, yhi, zlo, zhi, [&](int u) {
+        if (kLeft && F.sused[u]) return;
         const float2 pu = F.syz[u];
         const float yu = pu.x, zu = pu.y;
         if (!(fabsf(yu - yc) <= P.link_wy && fabsf(zu - zc) <= P.link_wz)) return;
@@ -205,8 +209,9 @@ __global__ void k_links(FrameDev F, KParams P) {
           for (int j = 0; j < nd; ++j) pair(u, yu, zu, uid, dl[j]);
         } else {
           for_window(F.bin_first, gd, ylo, yhi, zlo, zhi, [&](int d) {
+            if (kLeft && F.sused[d]) return;
             const float2 pd = F.syz[d];
-      const float yd = pd.x, zd = pd.y;
+            const float yd = pd.x, zd = pd.y;
             if (fabsf(yd - yc) <= P.link_wy && fabsf(zd - zc) <= P.link_wz)
               pair(u, yu, zu, uid, d);
           });
@@ -228,7 +233,8 @@ __global__ void k_clean(FrameDev F) {
 
 // ------------------------------------------------------------ a4 start hits
 // Compaction without atomics: per-block counts, scan of the counts, then each
-// block writes its flagged elements at its offset in order.
+// block writes its flagged elements at its offset in order.  An iteration's
+// start hits follow those of the earlier iterations (from cnt->tl_base).
 constexpr int kCompactItems = 4;  // elements per thread
 
 __device__ __forceinline__ bool is_start(const FrameDev& F, long k) {
@@ -255,7 +261,7 @@ __global__ void k_start_write(FrameDev F) {
   __shared__ int off;
   if (F.cnt->err) return;
   const long base = (long)blockIdx.x * blockDim.x * kCompactItems;
-  if (threadIdx.x == 0) off = F.scan_tmp[blockIdx.x];
+  if (threadIdx.x == 0) off = F.cnt->tl_base + F.scan_tmp[blockIdx.x];
   __syncthreads();
   for (int j = 0; j < kCompactItems; ++j) {
     const long k = base + (long)j * blockDim.x + threadIdx.x;
@@ -271,6 +277,7 @@ __global__ void k_start_write(FrameDev F) {
 }
 
 __global__ void k_start_check(FrameDev F) {
+  F.cnt->n_starts = F.cnt->tl_base + F.cnt->n_new;
   if (F.cnt->n_starts > F.cap_tl) {
     atomicOr(&F.cnt->err, kErrCapTracklets);
     atomicMax(&F.cnt->need_tracklets, F.cnt->n_starts);
@@ -284,7 +291,9 @@ struct Pick {
 };
 
 // Best cluster of row (s, r) with chi2 < follow_chi2 (ties: smaller input id);
-// the y/z box is the widened 2x2 Mahalanobis bound of the cut.
+// the y/z box is the widened 2x2 Mahalanobis bound of the cut.  kLeft: the
+// clusters taken by earlier sector-tracking iterations are not candidates.
+template <bool kLeft>
 __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const Trk<float>& t,
                                     const RowGrid& g, float& by, float& bz) {
   const float hy = sqrtf(P.follow_chi2 * (t.c[0] + P.sy2)) * 1.001f + 0.01f;
@@ -294,6 +303,7 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
   int best = -1, bid = 0;
   float bchi = 0.0f;
   for_window(F.bin_first, g, ylo, yhi, zlo, zhi, [&](int k) {
+    if (kLeft && F.sused[k]) return;
     const float2 pk = F.syz[k];
     const float yk = pk.x, zk = pk.y;
     if (!(yk >= ylo && yk <= yhi)) return;
@@ -320,7 +330,8 @@ __global__ void k_chain_info(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+  for (int ti = F.cnt->tl_base + blockIdx.x * blockDim.x + threadIdx.x; ti < nst;
+       ti += gridDim.x * blockDim.x) {
     const int start = F.starts[ti];
     int L = 1, last = start, mid = start;
     while (F.cup[last] >= 0) {
@@ -377,11 +388,13 @@ constexpr int kTlShared = 21;  // saved state: p[5], c[15], x (or p[5], x, y_hit
 // The state at the top hit and that hit's position are left in tl_seed[0..5],
 // tl_chi2 and tl_x for the downward pass; tl_n = -1 marks a tracklet that
 // has one.
+template <bool kLeft>
 __global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
   extern __shared__ float tl_sh[];
   float* const S = tl_sh + threadIdx.x;
   const int BS = blockDim.x;
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  const int tbase = F.cnt->tl_base;
   if (F.cnt->err) return;
   const int NR = P.n_rows;
   int phase = kTlIdle;
@@ -398,7 +411,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
   for (;;) {
     if (phase == kTlIdle) {
       // take the next tracklet and seed it
-      ti = queue_next(&F.cnt->queue[kQTracklets]);
+      ti = tbase + queue_next(&F.cnt->queue[kQTracklets]);
       if (ti >= nst) break;
       const int start = F.starts[ti];
       H = F.tl_hits + (long)ti * kMaxRows;
@@ -455,7 +468,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
     if (!stop && phase != kTlChain) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
     bool miss_out = false;
     if (!stop) {
-      if (phase != kTlChain) k = pick(F, P, t, g, ky, kz);
+      if (phase != kTlChain) k = pick<kLeft>(F, P, t, g, ky, kz);
       if (k >= 0) {
         update(t, residual(t, ky, kz, P));
         H[r] = k;
@@ -487,11 +500,13 @@ __global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
 
 // Downward pass: restart at the top hit with reset covariance, refit down
 // over the hits found on the way up, extend below the start the same way.
+template <bool kLeft>
 __global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
   extern __shared__ float tl_sh[];
   float* const S = tl_sh + threadIdx.x;
   const int BS = blockDim.x;
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  const int tbase = F.cnt->tl_base;
   if (F.cnt->err) return;
   const int NR = P.n_rows;
   bool busy = false;
@@ -508,7 +523,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
   };
   for (;;) {
     if (!busy) {
-      ti = queue_next(&F.cnt->queue[kQTlDown]);
+      ti = tbase + queue_next(&F.cnt->queue[kQTlDown]);
       if (ti >= nst) break;
       if (F.tl_n[ti] != -1) continue;
       H = F.tl_hits + (long)ti * kMaxRows;
@@ -563,7 +578,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
     if (!stop) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
     bool miss_out = false;
     if (!stop) {
-      if (!stored) k = pick(F, P, t, g, ky, kz);
+      if (!stored) k = pick<kLeft>(F, P, t, g, ky, kz);
       if (k >= 0) {
         const Resid R = residual(t, ky, kz, P);
         chi2 = chi2 + R.chi2;
@@ -609,7 +624,8 @@ __device__ __forceinline__ unsigned long long tracklet_key(const FrameDev& F, co
 __global__ void k_sel_owner(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
-  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+  for (int ti = F.cnt->tl_base + blockIdx.x * blockDim.x + threadIdx.x; ti < nst;
+       ti += gridDim.x * blockDim.x) {
     if (F.tl_n[ti] == 0) continue;
     const unsigned long long key = tracklet_key(F, P, ti);
     const int* H = F.tl_hits + (long)ti * kMaxRows;
@@ -633,7 +649,8 @@ constexpr int kWalkGroup = 8;
 __global__ void k_sel_walk(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
-  for (int ti = blockIdx.x * blockDim.x + threadIdx.x; ti < nst; ti += gridDim.x * blockDim.x) {
+  for (int ti = F.cnt->tl_base + blockIdx.x * blockDim.x + threadIdx.x; ti < nst;
+       ti += gridDim.x * blockDim.x) {
     F.tl_acc[ti] = 0;
     F.tl_nkept[ti] = 0;
     if (F.tl_n[ti] == 0) continue;
@@ -672,6 +689,41 @@ __global__ void k_sel_walk(FrameDev F, KParams P) {
   }
 }
 
+// ------------------------------------------- later seeding iterations
+// Sec. 3 (Phase III) seeds again on the clusters left over after the ambiguity
+// solving.  Between two iterations: every cluster kept by an accepted tracklet
+// of the iteration just done, and its start cluster, become taken; the owner
+// keys of the clusters still free are cleared for the next selection (only the
+// next iteration's tracklets, which hold free clusters only, compete there).
+__global__ void k_mark_used(FrameDev F) {
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  if (F.cnt->err) return;
+  for (int ti = F.cnt->tl_base + blockIdx.x * blockDim.x + threadIdx.x; ti < nst;
+       ti += gridDim.x * blockDim.x) {
+    if (!F.tl_acc[ti]) continue;
+    const int nk = F.tl_nkept[ti];
+    const int* K = F.tl_kept + (long)ti * kMaxRows;
+    for (int j = 0; j < nk; ++j) F.sused[K[j]] = 1;
+    F.sused[F.starts[ti]] = 1;
+  }
+}
+
+__global__ void k_owner_reset(FrameDev F) {
+  if (F.cnt->err) return;
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < F.n;
+       k += (long)gridDim.x * blockDim.x)
+    if (!F.sused[k]) F.owner_key[k] = 0ull;
+}
+
+// The next iteration's tracklets follow the current ones.
+__global__ void k_pass_begin(FrameDev F, int pass) {
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  F.cnt->tl_base = nst;
+  F.cnt->pass_start[pass] = nst;
+  F.cnt->queue[kQTracklets] = 0;
+  F.cnt->queue[kQTlDown] = 0;
+}
+
 }  // namespace
 
 // Stage launchers; each returns the number of kernels it enqueued.
@@ -694,7 +746,7 @@ int stage_links(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   (void)sms;
   const long n = F.n;
   if (n <= 0) return 0;
-  k_links<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+  k_links<false><<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
   k_clean<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
   return 2;
 }
@@ -704,7 +756,7 @@ int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const long n = F.n;
   const int nb = (int)blocks_for(n > 0 ? n : 1, kBlock * kCompactItems);
   k_start_count<<<nb, kBlock, 0, s>>>(F);
-  k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb, &F.cnt->n_starts);
+  k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb, &F.cnt->n_new);
   k_start_write<<<nb, kBlock, 0, s>>>(F);
   k_start_check<<<1, 1, 0, s>>>(F);
   return 4;
@@ -714,8 +766,8 @@ int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_chain_info<<<sms * 8, kBlock, 0, s>>>(F, P);
   const int tb = F.lc.block[kLTracklets];
   const size_t sh = sizeof(float) * kTlShared * tb;
-  k_tl_up<<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
-  k_tl_down<<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+  k_tl_up<false><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+  k_tl_down<false><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
   return 3;
 }
 
@@ -723,6 +775,36 @@ int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_sel_owner<<<sms * 8, kBlock, 0, s>>>(F, P);
   k_sel_walk<<<sms * 8, kBlock, 0, s>>>(F, P);
   return 2;
+}
+
+// Sector-tracking iterations 2..seed_iters, each on the clusters the accepted
+// tracklets of the earlier ones left: the same neighbour finding, cleaning,
+// start hits, tracklet construction and selection, over the free clusters.
+int stage_reseed(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  const long n = F.n;
+  if (P.seed_iters <= 1 || n <= 0) return 0;
+  int k = 0;
+  const int nb = (int)blocks_for(n, kBlock * kCompactItems);
+  const int tb = F.lc.block[kLTracklets];
+  const size_t sh = sizeof(float) * kTlShared * tb;
+  for (int pass = 1; pass < P.seed_iters; ++pass) {
+    k_mark_used<<<sms * 8, kBlock, 0, s>>>(F);
+    k_owner_reset<<<sms * 8, kBlock, 0, s>>>(F);
+    k_pass_begin<<<1, 1, 0, s>>>(F, pass);
+    k_links<true><<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+    k_clean<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
+    k_start_count<<<nb, kBlock, 0, s>>>(F);
+    k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb, &F.cnt->n_new);
+    k_start_write<<<nb, kBlock, 0, s>>>(F);
+    k_start_check<<<1, 1, 0, s>>>(F);
+    k_chain_info<<<sms * 8, kBlock, 0, s>>>(F, P);
+    k_tl_up<true><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+    k_tl_down<true><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+    k_sel_owner<<<sms * 8, kBlock, 0, s>>>(F, P);
+    k_sel_walk<<<sms * 8, kBlock, 0, s>>>(F, P);
+    k += 14;
+  }
+  return k;
 }
 
 // ------------------------------------------------------------------- scan

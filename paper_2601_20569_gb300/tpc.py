@@ -162,6 +162,7 @@ _DBG_DTYPE = {
     "tl_chi2": np.float32, "tl_x": np.float32, "tl_par": np.float32, "tl_cov": np.float32,
     "tl_hits": np.int32, "tl_kept": np.int32, "tl_acc": np.int32, "tl_nkept": np.int32,
     "owner_key": np.uint64, "sec_owner": np.int32, "counters": np.int32,
+    "sused": np.uint8, "pass_start": np.int32,
     "st_tl": np.int32, "st_ok": np.int32, "st_key": np.int32, "st_next": np.int32,
     "st_ie": np.float32, "st_oe": np.float32, "ft_key": np.int32, "ft_ok": np.int32,
     "ft_nst": np.int32, "ft_st_cl": np.int32, "ft_st_rs": np.uint16, "ft_flag": np.uint8,

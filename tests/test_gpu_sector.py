@@ -70,8 +70,12 @@ def compare_sector(tr, y, z, row, sec, opts, R=152):
     starts = tr.debug("starts")
     st_id = sid[starts]
     assert np.array_equal(np.sort(st_id), np.sort(ref["start"]))
-    # a5: tracklets keyed by start id, bit-exact
-    order = {int(s): i for i, s in enumerate(ref["tl_start"])}
+    # a5: tracklets keyed by (sector-tracking iteration, start id), bit-exact
+    it_g = np.zeros(len(starts), np.int64)
+    if opts.get("seed_iters", 1) > 1:
+        ps = tr.debug("pass_start")[:opts["seed_iters"]]
+        it_g = np.searchsorted(ps, np.arange(len(starts)), side="right") - 1
+    order = {(int(i), int(s)): j for j, (i, s) in enumerate(zip(ref["tl_iter"], ref["tl_start"]))}
     tl_n = tr.debug("tl_n")
     par, cov = tr.debug("tl_par").reshape(-1, 5), tr.debug("tl_cov").reshape(-1, 15)
     chi2, x = tr.debug("tl_chi2"), tr.debug("tl_x")
@@ -82,7 +86,7 @@ def compare_sector(tr, y, z, row, sec, opts, R=152):
     rpar, rcov = ref["tl_param"].reshape(-1, 5), ref["tl_cov"].reshape(-1, 15)
     rhits, rkept = ref["tl_hits"].reshape(-1, R), ref["tl_kept"].reshape(-1, R)
     for gi, s in enumerate(st_id):
-        oi = order[int(s)]
+        oi = order[(int(it_g[gi]), int(s))]
         assert tl_n[gi] == ref["tl_n"][oi], (s, tl_n[gi], ref["tl_n"][oi])
         if tl_n[gi] == 0:
             continue
