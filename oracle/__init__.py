@@ -44,6 +44,16 @@ class _Opt(ctypes.Structure):
         ("looper_qpt", ctypes.c_float),
         ("edge_margin", ctypes.c_float),
         ("ext_chi2", ctypes.c_float),
+        ("cr_qpt", ctypes.c_float),
+        ("cr_protect", ctypes.c_float),
+        ("cr_remove", ctypes.c_float),
+        ("cr_edge", ctypes.c_float),
+        ("cr_occ_w", ctypes.c_float),
+        ("cr_p2_grow", ctypes.c_float),
+        ("cr_p2_shrink", ctypes.c_float),
+        ("cr_leg_dq", ctypes.c_float),
+        ("cr_leg_dtgl", ctypes.c_float),
+        ("cr_leg_dc", ctypes.c_float),
         ("max_miss", ctypes.c_int32),
         ("min_hits", ctypes.c_int32),
         ("merge_max_gap", ctypes.c_int32),
@@ -54,6 +64,8 @@ class _Opt(ctypes.Structure):
         ("n_sectors", ctypes.c_int32),
         ("ext_rows", ctypes.c_int32),
         ("seed_iters", ctypes.c_int32),
+        ("cr_mode", ctypes.c_int32),
+        ("cr_occ_max", ctypes.c_int32),
     ]
 
 

@@ -62,6 +62,17 @@ struct orc_options {
   float looper_qpt;      // |q/pT| above which the fit's update runs in FP64 (0: never)
   float edge_margin;     // following stops |y| > x*tan(10 deg) + edge_margin [cm]
   float ext_chi2;        // Phase III: candidate cut of the inward extrapolation (2 dof)
+  // online cluster removal (Sec. 4)
+  float cr_qpt;          // |q/pT| above which a track is very low pT (removal class)
+  float cr_protect;      // half-width of the protective tube around physics tracks [cm]
+  float cr_remove;       // half-width of the removal tube around removal-class tracks [cm]
+  float cr_edge;         // protection 2: distance to the sector edge counted as "at the edge" [cm]
+  float cr_occ_w;        // protection 2: half-width of the occupancy window [cm]
+  float cr_p2_grow;      // protection 2: factor on the protective tube
+  float cr_p2_shrink;    // protection 2: factor on the removal tube
+  float cr_leg_dq;       // looper legs: relative |q/pT| difference
+  float cr_leg_dtgl;     // looper legs: |tan(lambda_a) + tan(lambda_b)|
+  float cr_leg_dc;       // looper legs: distance of the circle centres [cm]
   int32_t max_miss;
   int32_t min_hits;
   int32_t merge_max_gap;
@@ -72,6 +83,8 @@ struct orc_options {
   int32_t n_sectors;
   int32_t ext_rows;     // Phase III: rows searched below a track's innermost cluster (0: off)
   int32_t seed_iters;   // sector-tracking iterations, the later ones on leftover clusters (>= 1)
+  int32_t cr_mode;      // cluster removal: 0 off, 1 tubes + history, 2 also protection 2
+  int32_t cr_occ_max;   // protection 2: clusters in the occupancy window above which it applies
 };
 // Correction map of the oracle (host memory): layout [3][n_z][n_r][n_phi].
 struct orc_map {
@@ -245,9 +258,12 @@ struct Params {
   Real seed_c[5], meas_sy2, meas_sz2, ms_theta2, row_pitch_inv, follow_chi2, max_snp, fit_max_snp, score_w,
       shared_frac, merge_chi2, merge_dy, merge_dz, int_chi2, final_chi2, attach_margin,
       edge_margin, looper_qpt, merge_zspan, ext_chi2;
+  Real cr_qpt, cr_protect, cr_remove, cr_edge, cr_occ_w, cr_p2_grow, cr_p2_shrink, cr_leg_dq,
+      cr_leg_dtgl, cr_leg_dc;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors,
-      ext_rows, seed_iters;
+      ext_rows, seed_iters, cr_mode, cr_occ_max;
   std::vector<Real> row_x;
+  std::vector<Real> sec_cos, sec_sin;  // axis of sector s mod 18: ((s mod 18) + 0.5) * 20 deg
 };
 
 template <typename Real>
@@ -282,6 +298,17 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
   P.n_rows = o.n_rows; P.n_sectors = o.n_sectors;
   P.ext_chi2 = o.ext_chi2; P.ext_rows = o.ext_rows;
   P.seed_iters = o.seed_iters < 1 ? 1 : o.seed_iters;
+  P.cr_qpt = o.cr_qpt; P.cr_protect = o.cr_protect; P.cr_remove = o.cr_remove;
+  P.cr_edge = o.cr_edge; P.cr_occ_w = o.cr_occ_w; P.cr_p2_grow = o.cr_p2_grow;
+  P.cr_p2_shrink = o.cr_p2_shrink; P.cr_leg_dq = o.cr_leg_dq; P.cr_leg_dtgl = o.cr_leg_dtgl;
+  P.cr_leg_dc = o.cr_leg_dc; P.cr_mode = o.cr_mode; P.cr_occ_max = o.cr_occ_max;
+  P.sec_cos.resize(18);
+  P.sec_sin.resize(18);
+  for (int k = 0; k < 18; ++k) {
+    const double a = ((double)k + 0.5) * 20.0 * pi / 180.0;
+    P.sec_cos[k] = (Real)std::cos(a);
+    P.sec_sin[k] = (Real)std::sin(a);
+  }
   P.row_x.resize(o.n_rows);
   for (int r = 0; r < o.n_rows; ++r) P.row_x[r] = (Real)row_x[r];
   return P;
@@ -945,6 +972,7 @@ void map_eval(const MapR<Real>& M, const Params<Real>& P, int sector, Real x, Re
 template <typename Real>
 struct SectorTrack {
   int key = -1;          // input id of the tracklet's start cluster
+  int tl = -1;           // index of the tracklet
   int sector = 0;
   int rmin = 0, rmax = 0;
   std::vector<int> cl;   // kept clusters, innermost first
@@ -1208,6 +1236,7 @@ struct FitTrack {
   Real chi2 = 0;
   int n = 0;
   std::vector<int> used;   // clusters of iteration 3, innermost first
+  std::vector<int> seg;    // sector tracks of the chain, first to last
 };
 
 // One three-iteration fit (Sec. 3, Phase I, with the Phase II candidate search
@@ -1609,6 +1638,138 @@ struct SectorResult {
   Selection<Real> S;
 };
 
+// ------------------------------------------------ online cluster removal
+// Sec. 4: clusters inside a protective tube around physics tracks are kept;
+// of the others, those inside a removal tube around the secondary legs of
+// loopers and around very-low-pT tracks are removed; the clusters of the
+// tracklets a physics track was built from (its seeding history) are
+// protected as well.  Readings (the section states the rules in words only):
+// * a track is very low pT if |q/pT| at its innermost cluster > cr_qpt;
+// * two looper tracks (|q/pT| > looper_qpt) of the same side are legs of one
+//   looper if their |q/pT| differ by at most cr_leg_dq relative, their
+//   tan(lambda) are opposite within cr_leg_dtgl and their circle centres in
+//   global coordinates lie within cr_leg_dc; every leg is parametrised
+//   outwards, so legs flown inwards carry the opposite signs.  Along a
+//   looper |z| grows from the vertex and side * z_measured differs from |z|
+//   by one constant of the collision, so the leg with the smallest side * z
+//   at its innermost cluster comes first; a leg linked to one before it is a
+//   secondary leg, and its parent is the first such leg (smallest
+//   (side * z, index));
+// * the tube follows the track's clusters: on a row with a cluster of the
+//   track its centre is that cluster, on the rows between two consecutive
+//   clusters of the same sector the linear interpolation from the lower-row
+//   one; it holds the clusters of that row within the half-width in y and z;
+// * protection 1 is the choice of a wide protective and a narrow removal tube
+//   (cr_protect > cr_remove); protection 2 (cr_mode 2) multiplies them by
+//   cr_p2_grow and cr_p2_shrink on the inner_rows innermost rows, within
+//   cr_edge of the sector edge, and where more than cr_occ_max clusters lie
+//   within cr_occ_w of the centre.
+// Flags per cluster: 1 in a protective tube, 2 seeding history, 4 in a
+// removal tube, 8 removed (4 and neither 1 nor 2).
+template <typename Real>
+void cluster_removal(const Frame<Real>& F, const Params<Real>& P, const SectorResult<Real>& SR,
+                     const std::vector<SectorTrack<Real>>& ST,
+                     const std::vector<const FitTrack<Real>*>& T, Result& res) {
+  const int nt = (int)T.size();
+  const int half = P.n_sectors / 2;
+  std::vector<int> cls(nt, 0), parent(nt, -1), looper(nt, 0), blk(nt);
+  std::vector<Real> cx(nt), cy(nt), zk(nt);
+  for (int t = 0; t < nt; ++t) {
+    const Track<Real>& o = T[t]->out;
+    const int s = T[t]->out_sector;
+    const Real q = o.p[4];
+    blk[t] = s / half;
+    const Real side = (s % P.n_sectors) < half ? Real(1) : Real(-1);
+    zk[t] = side * o.p[1];
+    if (o_fabs(q) > P.cr_qpt) cls[t] = 1;
+    looper[t] = P.looper_qpt > Real(0) && o_fabs(q) > P.looper_qpt;
+    // circle centre: the curvature centre lies 1/kappa along the left normal
+    const Real rk = Real(1) / (P.kb * q);
+    const Real sn = o.p[2];
+    const Real cs = o_sqrt(Real(1) - sn * sn);
+    const Real xc = o.x - sn * rk, yc = o.p[0] + cs * rk;
+    const int a = s % 18;
+    cx[t] = xc * P.sec_cos[a] - yc * P.sec_sin[a];
+    cy[t] = xc * P.sec_sin[a] + yc * P.sec_cos[a];
+  }
+  // looper legs
+  for (int a = 0; a < nt; ++a) {
+    if (!looper[a]) continue;
+    int best = -1;
+    for (int b = 0; b < nt; ++b) {
+      if (b == a || !looper[b] || blk[b] != blk[a]) continue;
+      const Real qa = T[a]->out.p[4], qb = T[b]->out.p[4];
+      if ((qa > Real(0)) == (qb > Real(0))) continue;
+      const Real aa = o_fabs(qa), ab = o_fabs(qb);
+      const Real mx = aa > ab ? aa : ab;
+      if (!(o_fabs(aa - ab) <= P.cr_leg_dq * mx)) continue;
+      if (!(o_fabs(T[a]->out.p[3] + T[b]->out.p[3]) <= P.cr_leg_dtgl)) continue;
+      const Real dx = cx[a] - cx[b], dy = cy[a] - cy[b];
+      if (!(dx * dx + dy * dy <= P.cr_leg_dc * P.cr_leg_dc)) continue;
+      const bool before = zk[b] < zk[a] || (zk[b] == zk[a] && b < a);
+      if (!before) continue;
+      if (best < 0 || zk[b] < zk[best] || (zk[b] == zk[best] && b < best)) best = b;
+    }
+    parent[a] = best;
+    if (best >= 0) cls[a] = 2;
+  }
+  // tubes
+  std::vector<int> flags(F.n, 0);
+  auto tube = [&](int s, int r, Real yc, Real zc, bool protect) {
+    Real h = protect ? P.cr_protect : P.cr_remove;
+    if (P.cr_mode >= 2) {
+      bool dyn = r < P.inner_rows || o_fabs(yc) > P.row_x[r] * P.tan_half - P.cr_edge;
+      if (!dyn) {
+        int occ = 0;
+        for_row_range(F, P, s, r, zc - P.cr_occ_w, zc + P.cr_occ_w, [&](int id) {
+          if (o_fabs(F.y[id] - yc) <= P.cr_occ_w && o_fabs(F.z[id] - zc) <= P.cr_occ_w) ++occ;
+        });
+        dyn = occ > P.cr_occ_max;
+      }
+      if (dyn) h = h * (protect ? P.cr_p2_grow : P.cr_p2_shrink);
+    }
+    for_row_range(F, P, s, r, zc - h, zc + h, [&](int id) {
+      if (o_fabs(F.y[id] - yc) <= h && o_fabs(F.z[id] - zc) <= h) flags[id] |= protect ? 1 : 4;
+    });
+  };
+  for (int t = 0; t < nt; ++t) {
+    const bool protect = cls[t] == 0;
+    const std::vector<int>& u = T[t]->used;
+    for (size_t i = 0; i < u.size(); ++i) {
+      const int c = u[i];
+      tube(F.sector[c], F.row[c], F.y[c], F.z[c], protect);
+      if (i + 1 == u.size()) break;
+      const int d = u[i + 1];
+      if (F.sector[d] != F.sector[c]) continue;
+      const int lo = F.row[c] < F.row[d] ? c : d, hi = lo == c ? d : c;
+      const int rl = F.row[lo], rh = F.row[hi];
+      for (int r = rl + 1; r < rh; ++r) {
+        const Real f = Real(r - rl) / Real(rh - rl);
+        tube(F.sector[c], r, F.y[lo] + (F.y[hi] - F.y[lo]) * f,
+             F.z[lo] + (F.z[hi] - F.z[lo]) * f, protect);
+      }
+    }
+    if (protect)  // seeding history: every hit of the track's tracklets
+      for (int sgi : T[t]->seg)
+        for (int c : SR.TL[ST[sgi].tl].hits) flags[c] |= 2;
+  }
+  long nrem = 0;
+  for (long c = 0; c < F.n; ++c)
+    if ((flags[c] & 4) && !(flags[c] & 3)) {
+      flags[c] |= 8;
+      ++nrem;
+    }
+  res.put("cr_flags", flags, "i4");
+  res.put("cr_class", cls, "i4");
+  res.put("cr_parent", parent, "i4");
+  std::vector<Real> cxy;
+  for (int t = 0; t < nt; ++t) {
+    cxy.push_back(cx[t]);
+    cxy.push_back(cy[t]);
+  }
+  res.put("cr_centre", cxy, real_name<Real>());
+}
+
 template <typename Real>
 void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
                    const SectorResult<Real>& SR, Result& res) {
@@ -1618,6 +1779,7 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     if (!SR.S.accepted[i]) continue;
     SectorTrack<Real> S;
     S.key = SR.TL[i].start;
+    S.tl = (int)i;
     S.cl.assign(SR.S.kept[i].rbegin(), SR.S.kept[i].rend());
     S.sector = F.sector[S.cl[0]];
     S.rmin = F.row[S.cl.front()];
@@ -1686,6 +1848,7 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     int last = h;
     for (int s = h; s >= 0; s = next[s]) {
       cl.insert(cl.end(), ST[s].cl.begin(), ST[s].cl.end());
+      T.seg.push_back(s);
       last = s;
     }
     T.st = make_stations(F, P, cl, true);
@@ -1743,6 +1906,12 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   res.put("trk_param", par, real_name<Real>());
   res.put("trk_cov", cov, real_name<Real>());
   res.put("attach", attach, "i4");
+  if (P.cr_mode > 0) {
+    std::vector<const FitTrack<Real>*> out;
+    for (const auto& T : FT)
+      if (T.ok && T.n >= P.min_hits) out.push_back(&T);
+    cluster_removal(F, P, SR, ST, out, res);
+  }
   // per merged track diagnostics (all chains, including rejected ones)
   std::vector<int> fk, fflag_n, fcand_n, fassigned_n, ffail, fn;
   for (auto& T : FT) {

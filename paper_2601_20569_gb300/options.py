@@ -53,6 +53,20 @@ class TrackerOptions:
     ext_chi2: float = 9.0           # Phase III candidate cut (2 dof), stricter than int_chi2
     seed_iters: int = 1             # sector-tracking iterations; each later one seeds again on
                                     # the clusters the accepted tracklets left (1: off, <= 4)
+    # online cluster removal (Sec. 4), run by Tracker.cluster_removal after a tracking call
+    cr_mode: int = 0                # 0: off, 1: protective / removal tubes + seeding
+                                    # history, 2: also protection 2 (dynamic tube sizes)
+    cr_qpt: float = 10.0            # |q/pT| above which a track is very low pT (pT < 0.1 GeV)
+    cr_protect: float = 1.5         # protective tube half-width around physics tracks [cm]
+    cr_remove: float = 0.75         # removal tube half-width (protection 1: narrower) [cm]
+    cr_edge: float = 2.0            # protection 2: sector-edge band [cm]
+    cr_occ_w: float = 2.0           # protection 2: occupancy window half-width [cm]
+    cr_occ_max: int = 6             # protection 2: clusters in the window above which it applies
+    cr_p2_grow: float = 2.0         # protection 2: factor on the protective tube
+    cr_p2_shrink: float = 0.5       # protection 2: factor on the removal tube
+    cr_leg_dq: float = 0.1          # looper legs: relative |q/pT| difference
+    cr_leg_dtgl: float = 0.05       # looper legs: |tan(lambda_a) + tan(lambda_b)|
+    cr_leg_dc: float = 3.0          # looper legs: circle-centre distance [cm]
     max_miss: int = 10              # consecutive empty rows ending the following
     min_hits: int = 10
     merge_max_gap: int = 20         # rows between merged segments
