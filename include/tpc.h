@@ -187,6 +187,64 @@ tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* clusters, const tpc_track
 tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dL_dchi2, float* dL_dmap,
                               void* cuda_stream);
 
+/* Online cluster removal (Sec. 4, cluster reduction) on the tracks of the
+ * last successful tpc_track_timeframe / tpc_track_batch call of this
+ * context.  Clusters inside a protective tube around physics tracks are kept;
+ * of the others, those inside a removal tube around secondary legs of
+ * looping tracks and around very-low-pT tracks are flagged for removal; the
+ * clusters of the tracklets a physics track was seeded from (its history)
+ * are protected as well.  The section states the rules in words; these are
+ * the readings:
+ *  - a track is very low pT if |q/pT| at its innermost cluster exceeds qpt;
+ *  - two looper tracks (|q/pT| above the tracker's looper_qpt) of one side are
+ *    legs of one looper if their |q/pT| differ by at most leg_dq relative,
+ *    their tan(lambda) are opposite within leg_dtgl and their circle centres
+ *    (global x, y) lie within leg_dc cm; of linked legs the one with the
+ *    smallest side*z at its innermost cluster comes first (track key on exact
+ *    ties), every other one is a secondary leg whose parent is the first
+ *    earlier leg;
+ *  - a tube follows the track's clusters (linear interpolation from the
+ *    lower-row cluster over rows between two clusters of one sector) and holds
+ *    the clusters of each row within the half-width in y and z;
+ *  - protection 1 is the choice protect > remove; protection 2 (mode 2)
+ *    multiplies the protective tube by p2_grow and the removal tube by
+ *    p2_shrink on the tracker's inner_rows innermost rows, within edge cm of a
+ *    sector edge and where more than occ_max clusters lie within occ_w cm of
+ *    the tube centre.
+ * Strict mode gives the CPU oracle's flags bit for bit. */
+typedef struct {
+  float qpt;         /* |q/pT| above which a track is very low pT [1/GeV] */
+  float protect;     /* protective tube half-width around physics tracks [cm] */
+  float remove;      /* removal tube half-width [cm] */
+  float edge;        /* protection 2: sector-edge band [cm] */
+  float occ_w;       /* protection 2: occupancy window half-width [cm] */
+  float p2_grow;     /* protection 2: factor on the protective tube */
+  float p2_shrink;   /* protection 2: factor on the removal tube */
+  float leg_dq;      /* looper legs: relative |q/pT| difference */
+  float leg_dtgl;    /* looper legs: |tan(lambda_a) + tan(lambda_b)| */
+  float leg_dc;      /* looper legs: circle-centre distance [cm], > 0 */
+  int32_t mode;      /* 1: tubes + history, 2: also protection 2 */
+  int32_t occ_max;   /* protection 2: occupancy threshold */
+} tpc_removal_options;
+
+/* Results (device memory owned by the context, valid until its next call). */
+typedef struct {
+  int64_t n_clusters;          /* clusters of the last tracking call (all frames of a batch) */
+  int64_t n_tracks;            /* tracks of the last tracking call */
+  int64_t n_removed;           /* clusters flagged 8 */
+  const uint8_t* flags;        /* [n_clusters] by input (batch) id: 1 in a protective tube,
+                                  2 seeding history of a physics track, 4 in a removal tube,
+                                  8 removed (4 and neither 1 nor 2) */
+  const int32_t* track_class;  /* [n_tracks] 0 physics, 1 very low pT, 2 secondary looper leg */
+  const int32_t* leg_parent;   /* [n_tracks] index of the first earlier leg of a secondary
+                                  leg, else -1 */
+} tpc_removal;
+
+/* Errors: TPC_ERR_INVALID_ARG for null pointers or options out of range,
+ * TPC_ERR_STATE without a preceding successful tracking call, TPC_ERR_CUDA. */
+tpc_status tpc_cluster_removal(tpc_ctx* ctx, const tpc_removal_options* opt, tpc_removal* out,
+                               void* cuda_stream);
+
 /* Track several time frames in one pass: the frames are concatenated (frame
  * f's sector s becomes batch sector f*n_sectors + s, its cluster i batch id
  * sum_{g<f} n_g + i) and every stage runs once over all of them, the heavy

@@ -1654,7 +1654,7 @@ struct SectorResult {
 //   by one constant of the collision, so the leg with the smallest side * z
 //   at its innermost cluster comes first; a leg linked to one before it is a
 //   secondary leg, and its parent is the first such leg (smallest
-//   (side * z, index));
+//   (side * z, key), the key breaking exact ties);
 // * the tube follows the track's clusters: on a row with a cluster of the
 //   track its centre is that cluster, on the rows between two consecutive
 //   clusters of the same sector the linear interpolation from the lower-row
@@ -1706,9 +1706,10 @@ void cluster_removal(const Frame<Real>& F, const Params<Real>& P, const SectorRe
       if (!(o_fabs(T[a]->out.p[3] + T[b]->out.p[3]) <= P.cr_leg_dtgl)) continue;
       const Real dx = cx[a] - cx[b], dy = cy[a] - cy[b];
       if (!(dx * dx + dy * dy <= P.cr_leg_dc * P.cr_leg_dc)) continue;
-      const bool before = zk[b] < zk[a] || (zk[b] == zk[a] && b < a);
+      const bool before = zk[b] < zk[a] || (zk[b] == zk[a] && T[b]->key < T[a]->key);
       if (!before) continue;
-      if (best < 0 || zk[b] < zk[best] || (zk[b] == zk[best] && b < best)) best = b;
+      if (best < 0 || zk[b] < zk[best] || (zk[b] == zk[best] && T[b]->key < T[best]->key))
+        best = b;
     }
     parent[a] = best;
     if (best >= 0) cls[a] = 2;

@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + CSRC,
                  "-I" + INCLUDE]
-KERNEL_TUS = ["tpc_sector.cu", "tpc_fit.cu"]  # compiled when present
+KERNEL_TUS = ["tpc_sector.cu", "tpc_fit.cu", "tpc_removal.cu"]  # compiled when present
 HOST_TUS = ["tpc_api.cu", "tpc_noalloc.cu"]
 
 

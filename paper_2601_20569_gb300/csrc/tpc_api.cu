@@ -92,6 +92,8 @@ struct tpc_ctx {
   RefitDev R{};
   bool refit_alloc = false;
   bool refit_done = false;
+  bool tracked = false;  // the last tracking call succeeded (its tracks are resident)
+  int last_nf = 1;       // frames of that call
   long refit_tracks = -1, refit_refs = -1;
   int* steps3 = nullptr;
   long gpart_cap = 0;
@@ -288,6 +290,10 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.tl_kept, F.cap_tl * kMaxRows);
   ok &= dalloc(ctx, &F.sec_owner, n);
   ok &= dalloc(ctx, &F.sused, n);
+  ok &= dalloc(ctx, &F.cr_flags, n);
+  ok &= dalloc(ctx, &F.cr_out, n);
+  ok &= dalloc(ctx, &F.cr_bin_cnt, kCrBins + 1);
+  ok &= dalloc(ctx, &F.cr_bin_first, kCrBins + 1);
   ok &= dalloc(ctx, &F.cnt, 1);
   // a7
   const long T = F.cap_tl;
@@ -363,6 +369,12 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ft_out, FT * kStateF);
   ok &= dalloc(ctx, &F.ft_used, FT * kMaxRows);
   ok &= dalloc(ctx, &F.ft_outidx, FT);
+  ok &= dalloc(ctx, &F.cr_cls, FT);
+  ok &= dalloc(ctx, &F.cr_parent, FT);
+  ok &= dalloc(ctx, &F.cr_cx, FT);
+  ok &= dalloc(ctx, &F.cr_cy, FT);
+  ok &= dalloc(ctx, &F.cr_zk, FT);
+  ok &= dalloc(ctx, &F.cr_bin_items, FT);
   ok &= dalloc(ctx, &F.out_par, FT * 5);
   ok &= dalloc(ctx, &F.out_cov, FT * 15);
   ok &= dalloc(ctx, &F.out_chi2, FT);
@@ -452,6 +464,8 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   KParams Pc = ctx->P;
   Pc.n_sectors = ctx->n_sectors * nf;
   F.map = make_mapdev(ctx->map);
+  ctx->tracked = false;
+  ctx->last_nf = nf;
   ctx->last_stream = s;
   long launches = 0;
   const bool graph = ctx->opt.use_graphs && !ctx->prof;
@@ -542,6 +556,7 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   out->cl_ids = F.out_ids;
   out->key = F.out_key;
   out->attach = F.attach;
+  ctx->tracked = true;
   return TPC_OK;
 }
 
@@ -815,6 +830,65 @@ tpc_status tpc_refit_backward(tpc_ctx* ctx, const float* dl_dchi2, float* dl_dma
   return TPC_OK;
 }
 
+tpc_status tpc_cluster_removal(tpc_ctx* ctx, const tpc_removal_options* o, tpc_removal* out,
+                               void* cuda_stream) {
+  if (!ctx) return TPC_ERR_INVALID_ARG;
+  if (!o || !out) return fail(ctx, TPC_ERR_INVALID_ARG, "null options or output");
+  if ((o->mode != 1 && o->mode != 2) || !(o->qpt > 0.0f) || !(o->protect >= 0.0f) ||
+      !(o->remove >= 0.0f) || !(o->edge >= 0.0f) || !(o->occ_w >= 0.0f) ||
+      !(o->p2_grow >= 0.0f) || !(o->p2_shrink >= 0.0f) || !(o->leg_dq >= 0.0f) ||
+      !(o->leg_dtgl >= 0.0f) || !(o->leg_dc > 0.0f) || o->occ_max < 0)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "cluster removal option out of range");
+  if (!ctx->tracked)
+    return fail(ctx, TPC_ERR_STATE, "cluster removal needs a preceding successful tracking call");
+  FrameDev& F = ctx->F;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  ctx->last_stream = s;
+  RemovalParams R{};
+  R.qpt = o->qpt; R.protect = o->protect; R.remove = o->remove; R.edge = o->edge;
+  R.occ_w = o->occ_w; R.p2_grow = o->p2_grow; R.p2_shrink = o->p2_shrink;
+  R.leg_dq = o->leg_dq; R.leg_dtgl = o->leg_dtgl; R.leg_dc = o->leg_dc;
+  R.mode = o->mode; R.occ_max = o->occ_max;
+  R.half = ctx->n_sectors / 2;
+  R.nsec_frame = ctx->n_sectors;
+  // centre-x bins at least the leg distance wide (with a margin for rounding)
+  double cell = (double)o->leg_dc * 1.01 + 0.01;
+  if (600.0 / cell > kCrMaxBinsX) cell = 600.0 / kCrMaxBinsX;
+  R.nbx = (int)std::ceil(600.0 / cell);
+  if (R.nbx < 1) R.nbx = 1;
+  if (R.nbx > kCrMaxBinsX) R.nbx = kCrMaxBinsX;
+  R.inv_cell = (float)(1.0 / cell);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < 18; ++k) {
+    const double a = ((double)k + 0.5) * 20.0 * pi / 180.0;
+    R.sec_cos[k] = (float)std::cos(a);
+    R.sec_sin[k] = (float)std::sin(a);
+  }
+  const int nblk = (ctx->n_sectors * ctx->last_nf + R.half - 1) / R.half;
+  if ((long)nblk * R.nbx > kCrBins)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "too many side blocks for the leg search");
+  KParams Pc = ctx->P;
+  Pc.n_sectors = ctx->n_sectors * ctx->last_nf;
+  const long n = F.n;
+  if (n > 0) CK(cudaMemsetAsync(F.cr_flags, 0, sizeof(unsigned) * n, s));
+  CK(cudaMemsetAsync(F.cr_bin_cnt, 0, sizeof(int) * ((long)nblk * R.nbx + 1), s));
+  CK(cudaMemsetAsync(&F.cnt->n_removed, 0, sizeof(int), s));
+  const int k = ctx->opt.mode == 0 ? strict::cluster_removal(F, Pc, R, nblk, ctx->sms, s)
+                                   : fast::cluster_removal(F, Pc, R, nblk, ctx->sms, s);
+  ctx->launches_last = k;
+  CK(cudaGetLastError());
+  int nrem = 0;
+  CK(cudaMemcpyAsync(&nrem, &F.cnt->n_removed, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out->n_clusters = n;
+  out->n_tracks = ctx->host_cnt.n_out;
+  out->n_removed = nrem;
+  out->flags = F.cr_out;
+  out->track_class = F.cr_cls;
+  out->leg_parent = F.cr_parent;
+  return TPC_OK;
+}
+
 tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_t cap,
                           int64_t* bytes) {
   if (!ctx || !name) return TPC_ERR_INVALID_ARG;
@@ -852,6 +926,9 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   else if (w == "owner_key") { src = F.owner_key; nb = 8 * n; }
   else if (w == "sec_owner") { src = F.sec_owner; nb = 4 * n; }
   else if (w == "sused") { src = F.sused; nb = n; }
+  else if (w == "cr_flags") { src = F.cr_flags; nb = 4 * n; }
+  else if (w == "cr_centre_x") { src = F.cr_cx; nb = 4L * c.n_out; }
+  else if (w == "cr_centre_y") { src = F.cr_cy; nb = 4L * c.n_out; }
   else if (w == "pass_start") { src = F.cnt->pass_start; nb = sizeof(int) * kMaxSeedIters; }
   else if (w == "st_tl") { src = F.st_tl; nb = 4L * c.n_tracks; }
   else if (w == "st_ok") { src = F.st_ok; nb = 4L * c.n_tracks; }

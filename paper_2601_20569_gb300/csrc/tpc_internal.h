@@ -32,6 +32,15 @@ struct KParams {
   float grid_occ;    // target clusters per bin
 };
 
+// Options of the online cluster removal (Sec. 4), derived on the host.
+struct RemovalParams {
+  float qpt, protect, remove, edge, occ_w, p2_grow, p2_shrink, leg_dq, leg_dtgl, leg_dc;
+  float inv_cell;          // 1 / width of a centre-x bin (at least the leg distance)
+  int mode, occ_max, nbx;  // nbx: centre-x bins per side block over [-300, 300) cm
+  int half, nsec_frame;    // sectors per side and per frame
+  float sec_cos[18], sec_sin[18];  // sector axis ((s mod 18) + 0.5) * 20 deg
+};
+
 // Launch shape of the heavy per-item kernels (block size, blocks per SM),
 // chosen by the autotuner.
 enum LaunchSlot : int { kLTracklets = 0, kLSectorRefit, kLMerge, kLFit12, kLFit3, kLNum };
@@ -82,6 +91,8 @@ constexpr int kIpolF = 11;      // interpolation record of an inner station
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 constexpr int kMaxSeedIters = 4;  // sector-tracking iterations
+constexpr int kCrMaxBinsX = 1024;  // cluster removal: centre-x bins per side block
+constexpr int kCrBins = 128 * kCrMaxBinsX;  // 64 frames x 2 sides
 constexpr int kMaxExt = 32;      // Phase III: rows extrapolated below a track (slots after the inner ones)
 // Scheduling buckets of the sector refit (most clusters first).
 constexpr int kOrdBuckets = 128;
@@ -113,6 +124,7 @@ struct Counters {
   int tl_base;       // first tracklet of the current sector-tracking iteration
   int n_new;         // start hits found by the current iteration
   int pass_start[kMaxSeedIters];  // first tracklet of each iteration
+  int n_removed;     // cluster removal: clusters flagged for removal
 };
 
 // Working set of one frame on the device.
@@ -167,6 +179,18 @@ struct FrameDev {
   int* sec_owner;          // [n] sorted index space: tracklet index or -1
   uint8_t* sused;          // [n] sorted cluster taken by an accepted tracklet of an earlier
                            // sector-tracking iteration (iterations after the first)
+  // online cluster removal (after a tracking call)
+  unsigned* cr_flags;      // [n] sorted index space: 1 protective tube, 2 seeding history,
+                           // 4 removal tube, 8 removed
+  uint8_t* cr_out;         // [n] the flags in input order
+  int* cr_cls;             // [cap_ft] per output track: 0 physics, 1 very low pT, 2 secondary leg
+  int* cr_parent;          // [cap_ft] first leg of a secondary leg's looper, or -1
+  float* cr_cx;            // [cap_ft] circle centre, global x [cm]
+  float* cr_cy;            // [cap_ft] circle centre, global y [cm]
+  float* cr_zk;            // [cap_ft] side * z at the innermost cluster (leg order)
+  int* cr_bin_cnt;         // [kCrBins + 1] loopers per (side block, centre-x bin)
+  int* cr_bin_first;       // [kCrBins + 1]
+  int* cr_bin_items;       // [cap_ft]
   Counters* cnt;
 
   // a7 sector tracks (capacity cap_tl)

@@ -25,7 +25,9 @@ namespace tpc {
   int refit_forward(RefitDev& R, const KParams& P, int* steps3, int sms, cudaStream_t s); \
   int refit_backward(RefitDev& R, const KParams& P, const int* steps3, int sms,          \
                      cudaStream_t s);                                                    \
-  int scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s);
+  int scan_exclusive(const int* in, int* out, long n, int* tmp, cudaStream_t s);           \
+  int cluster_removal(FrameDev& F, const KParams& P, const RemovalParams& R, int nblk,     \
+                      int sms, cudaStream_t s);
 
 namespace strict {
 TPC_DECLARE_LAUNCHERS

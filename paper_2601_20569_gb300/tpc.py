@@ -75,6 +75,19 @@ class Tracks(ctypes.Structure):
                 ("cl_ids", ctypes.c_void_p), ("key", ctypes.c_void_p), ("attach", ctypes.c_void_p)]
 
 
+class RemovalOptions(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("qpt", "protect", "remove", "edge", "occ_w",
+                                              "p2_grow", "p2_shrink", "leg_dq", "leg_dtgl",
+                                              "leg_dc")] + \
+               [("mode", ctypes.c_int32), ("occ_max", ctypes.c_int32)]
+
+
+class Removal(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_int64), ("n_tracks", ctypes.c_int64),
+                ("n_removed", ctypes.c_int64), ("flags", ctypes.c_void_p),
+                ("track_class", ctypes.c_void_p), ("leg_parent", ctypes.c_void_p)]
+
+
 class _DevArray:
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
@@ -86,7 +99,7 @@ def wrap_device(ptr, shape, typestr):
     import torch
 
     if not ptr or 0 in tuple(shape):
-        dt = {"<i4": torch.int32, "<f4": torch.float32}[typestr]
+        dt = {"<i4": torch.int32, "<f4": torch.float32, "|u1": torch.uint8}[typestr]
         return torch.empty(shape, dtype=dt, device="cuda")
     return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
 
@@ -162,7 +175,8 @@ _DBG_DTYPE = {
     "tl_chi2": np.float32, "tl_x": np.float32, "tl_par": np.float32, "tl_cov": np.float32,
     "tl_hits": np.int32, "tl_kept": np.int32, "tl_acc": np.int32, "tl_nkept": np.int32,
     "owner_key": np.uint64, "sec_owner": np.int32, "counters": np.int32,
-    "sused": np.uint8, "pass_start": np.int32,
+    "sused": np.uint8, "pass_start": np.int32, "cr_flags": np.uint32, "cr_centre_x": np.float32,
+    "cr_centre_y": np.float32,
     "st_tl": np.int32, "st_ok": np.int32, "st_key": np.int32, "st_next": np.int32,
     "st_ie": np.float32, "st_oe": np.float32, "ft_key": np.int32, "ft_ok": np.int32,
     "ft_nst": np.int32, "ft_st_cl": np.int32, "ft_st_rs": np.uint16, "ft_flag": np.uint8,
@@ -335,6 +349,38 @@ class Tracker:
             "cl_ids": wrap_device(out.cl_ids, (nr,), i), "key": wrap_device(out.key, (nt,), i),
             "attach": wrap_device(out.attach, (n,), i),
         }
+
+    def cluster_removal(self, opts: dict | TrackerOptions | None = None, mode: int | None = None,
+                        stream=None) -> dict:
+        """Online cluster removal (tpc_cluster_removal) on the last tracking call's
+        tracks, with the cr_* fields of the options (``mode`` overrides cr_mode;
+        an unset cr_mode means 1).  Returns zero-copy views of the per-cluster
+        flags (uint8, 1 protective tube, 2 seeding history, 4 removal tube,
+        8 removed), the track classes and leg parents, and the removed count."""
+        import torch
+
+        d = (opts or TrackerOptions())
+        d = d.as_dict() if isinstance(d, TrackerOptions) else dict(d)
+        o = RemovalOptions()
+        for k in ("qpt", "protect", "remove", "edge", "occ_w", "p2_grow", "p2_shrink", "leg_dq",
+                  "leg_dtgl", "leg_dc"):
+            setattr(o, k, float(d["cr_" + k]))
+        o.mode = int(mode if mode is not None else (d["cr_mode"] or 1))
+        o.occ_max = int(d["cr_occ_max"])
+        fn = self.lib.tpc_cluster_removal
+        fn.argtypes = [ctypes.c_void_p, ctypes.POINTER(RemovalOptions), ctypes.POINTER(Removal),
+                       ctypes.c_void_p]
+        fn.restype = ctypes.c_int
+        out = Removal()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = fn(self._ctx, ctypes.byref(o), ctypes.byref(out), ctypes.c_void_p(s.cuda_stream))
+        if rc:
+            raise TpcError(rc, self.last_error())
+        n, nt = int(out.n_clusters), int(out.n_tracks)
+        return {"flags": wrap_device(out.flags, (n,), "|u1"),
+                "track_class": wrap_device(out.track_class, (nt,), "<i4"),
+                "leg_parent": wrap_device(out.leg_parent, (nt,), "<i4"),
+                "n_removed": int(out.n_removed)}
 
     def refit(self, clusters, tracks: dict, coeff=None, *, freeze: bool = False,
               r_range=(85.0, 245.0), z_range=(-250.0, 250.0), stream=None) -> dict:
