@@ -458,6 +458,22 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     note("end-to-end timed")
+    # online cluster removal (tpc_cluster_removal, protection 2) on the batch just tracked
+    ropts = TrackerOptions(cr_mode=2)
+    rem = tr.cluster_removal(ropts)
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(3):
+        rem = tr.cluster_removal(ropts, stream=stream)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rem_ms = r0.elapsed_time(r1) / 3
+    removal = {"ms_per_batch": rem_ms, "clusters_per_s": n_per_step / (rem_ms / 1e3),
+               "removed_fraction": rem["n_removed"] / n_per_step,
+               "form": "protective / removal tubes with protection 2 and seeding history, "
+                       "on the tracks of the batch"}
+    note("cluster removal timed")
     refit = None
     if not args.no_refit:
         refit = refit_timing(mode)
@@ -481,6 +497,7 @@ def main():
         "stages_ms_per_batch": {s_["name"]: s_["ms"] / max(1, s_["calls"]) for s_ in stages},
         "launch_config": tuned,
     }
+    line["cluster_removal"] = removal
     if refit is not None:
         line["refit_adjoint"] = refit
     if rank == 0 and not args.no_cpu_baseline:

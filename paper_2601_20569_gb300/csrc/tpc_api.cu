@@ -851,10 +851,10 @@ tpc_status tpc_cluster_removal(tpc_ctx* ctx, const tpc_removal_options* o, tpc_r
   R.mode = o->mode; R.occ_max = o->occ_max;
   R.half = ctx->n_sectors / 2;
   R.nsec_frame = ctx->n_sectors;
-  // centre-x bins at least the leg distance wide (with a margin for rounding)
+  // centre bins at least the leg distance wide (with a margin for rounding)
   double cell = (double)o->leg_dc * 1.01 + 0.01;
-  if (600.0 / cell > kCrMaxBinsX) cell = 600.0 / kCrMaxBinsX;
-  R.nbx = (int)std::ceil(600.0 / cell);
+  if (512.0 / cell > kCrMaxBinsX) cell = 512.0 / kCrMaxBinsX;
+  R.nbx = (int)std::ceil(512.0 / cell);
   if (R.nbx < 1) R.nbx = 1;
   if (R.nbx > kCrMaxBinsX) R.nbx = kCrMaxBinsX;
   R.inv_cell = (float)(1.0 / cell);
@@ -865,13 +865,13 @@ tpc_status tpc_cluster_removal(tpc_ctx* ctx, const tpc_removal_options* o, tpc_r
     R.sec_sin[k] = (float)std::sin(a);
   }
   const int nblk = (ctx->n_sectors * ctx->last_nf + R.half - 1) / R.half;
-  if ((long)nblk * R.nbx > kCrBins)
+  if ((long)nblk * R.nbx * R.nbx > kCrBins)
     return fail(ctx, TPC_ERR_INVALID_ARG, "too many side blocks for the leg search");
   KParams Pc = ctx->P;
   Pc.n_sectors = ctx->n_sectors * ctx->last_nf;
   const long n = F.n;
   if (n > 0) CK(cudaMemsetAsync(F.cr_flags, 0, sizeof(unsigned) * n, s));
-  CK(cudaMemsetAsync(F.cr_bin_cnt, 0, sizeof(int) * ((long)nblk * R.nbx + 1), s));
+  CK(cudaMemsetAsync(F.cr_bin_cnt, 0, sizeof(int) * ((long)nblk * R.nbx * R.nbx + 1), s));
   CK(cudaMemsetAsync(&F.cnt->n_removed, 0, sizeof(int), s));
   const int k = ctx->opt.mode == 0 ? strict::cluster_removal(F, Pc, R, nblk, ctx->sms, s)
                                    : fast::cluster_removal(F, Pc, R, nblk, ctx->sms, s);

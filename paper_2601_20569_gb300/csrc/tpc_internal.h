@@ -35,8 +35,8 @@ struct KParams {
 // Options of the online cluster removal (Sec. 4), derived on the host.
 struct RemovalParams {
   float qpt, protect, remove, edge, occ_w, p2_grow, p2_shrink, leg_dq, leg_dtgl, leg_dc;
-  float inv_cell;          // 1 / width of a centre-x bin (at least the leg distance)
-  int mode, occ_max, nbx;  // nbx: centre-x bins per side block over [-300, 300) cm
+  float inv_cell;          // 1 / width of a centre bin (at least the leg distance)
+  int mode, occ_max, nbx;  // nbx: centre bins per axis and side block over [-256, 256) cm
   int half, nsec_frame;    // sectors per side and per frame
   float sec_cos[18], sec_sin[18];  // sector axis ((s mod 18) + 0.5) * 20 deg
 };
@@ -91,8 +91,8 @@ constexpr int kIpolF = 11;      // interpolation record of an inner station
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 constexpr int kMaxSeedIters = 4;  // sector-tracking iterations
-constexpr int kCrMaxBinsX = 1024;  // cluster removal: centre-x bins per side block
-constexpr int kCrBins = 128 * kCrMaxBinsX;  // 64 frames x 2 sides
+constexpr int kCrMaxBinsX = 170;   // cluster removal: circle-centre bins per axis and side block
+constexpr int kCrBins = 128 * kCrMaxBinsX * kCrMaxBinsX;  // 64 frames x 2 sides
 constexpr int kMaxExt = 32;      // Phase III: rows extrapolated below a track (slots after the inner ones)
 // Scheduling buckets of the sector refit (most clusters first).
 constexpr int kOrdBuckets = 128;
@@ -188,7 +188,7 @@ struct FrameDev {
   float* cr_cx;            // [cap_ft] circle centre, global x [cm]
   float* cr_cy;            // [cap_ft] circle centre, global y [cm]
   float* cr_zk;            // [cap_ft] side * z at the innermost cluster (leg order)
-  int* cr_bin_cnt;         // [kCrBins + 1] loopers per (side block, centre-x bin)
+  int* cr_bin_cnt;         // [kCrBins + 1] loopers per (side block, centre bin)
   int* cr_bin_first;       // [kCrBins + 1]
   int* cr_bin_items;       // [cap_ft]
   Counters* cnt;

@@ -32,12 +32,18 @@ namespace tpc {
 namespace TPC_NS {
 namespace {
 
-constexpr float kCrHalfRange = 300.0f;  // circle centres binned over [-300, 300) cm
+constexpr float kCrHalfRange = 256.0f;  // circle centres binned over [-256, 256) cm per axis
+
+// Centre bin of a circle centre (clamped: centres outside the range share the
+// edge bins, which keeps any two centres within one bin width in adjacent bins).
+__device__ __forceinline__ int centre_bin(float c, const RemovalParams& R) {
+  return min(R.nbx - 1, max(0, (int)floorf((c + kCrHalfRange) * R.inv_cell)));
+}
 
 __device__ __forceinline__ int out_count(const FrameDev& F) { return F.cnt->n_out; }
 
 // Class, looper flag, leg order key and circle centre of every output track;
-// loopers are counted per (side block, centre-x bin).
+// loopers are counted per (side block, centre bin).
 __global__ void k_cr_tracks(FrameDev F, KParams P, RemovalParams R) {
   const int nt = out_count(F);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
@@ -59,15 +65,15 @@ __global__ void k_cr_tracks(FrameDev F, KParams P, RemovalParams R) {
     F.cr_cx[t] = cx;
     F.cr_cy[t] = cy;
     if (P.looper_qpt > 0.0f && fabsf(q) > P.looper_qpt) {
-      const int xb = min(R.nbx - 1, max(0, (int)floorf((cx + kCrHalfRange) * R.inv_cell)));
-      atomicAdd(&F.cr_bin_cnt[(s / R.half) * R.nbx + xb], 1);
+      const int b = ((s / R.half) * R.nbx + centre_bin(cy, R)) * R.nbx + centre_bin(cx, R);
+      atomicAdd(&F.cr_bin_cnt[b], 1);
     }
   }
 }
 
 __device__ __forceinline__ int cr_bin(const FrameDev& F, const RemovalParams& R, int t) {
-  const int xb = min(R.nbx - 1, max(0, (int)floorf((F.cr_cx[t] + kCrHalfRange) * R.inv_cell)));
-  return (F.out_sector[t] / R.half) * R.nbx + xb;
+  return ((F.out_sector[t] / R.half) * R.nbx + centre_bin(F.cr_cy[t], R)) * R.nbx +
+         centre_bin(F.cr_cx[t], R);
 }
 
 __device__ __forceinline__ bool is_looper(const FrameDev& F, const KParams& P, int t) {
@@ -85,8 +91,8 @@ __global__ void k_cr_scatter(FrameDev F, KParams P, RemovalParams R) {
   }
 }
 
-// Secondary legs: the first earlier leg among the loopers of the three
-// neighbouring centre-x bins (bins are at least leg_dc wide).
+// Secondary legs: the first earlier leg among the loopers of the 3 x 3
+// neighbouring centre bins (bins are at least leg_dc wide).
 __global__ void k_cr_legs(FrameDev F, KParams P, RemovalParams R) {
   const int nt = out_count(F);
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nt; a += gridDim.x * blockDim.x) {
@@ -96,12 +102,15 @@ __global__ void k_cr_legs(FrameDev F, KParams P, RemovalParams R) {
     const float aa = fabsf(qa);
     const int ka = F.out_key[a];
     const int b0 = cr_bin(F, R, a);
-    const int xb = b0 % R.nbx;
+    const int xb = b0 % R.nbx, yb = (b0 / R.nbx) % R.nbx;
     int best = -1, bk = 0;
     float bz = 0.0f;
-    for (int d = -1; d <= 1; ++d) {
-      if (xb + d < 0 || xb + d >= R.nbx) continue;
-      const int lo = F.cr_bin_first[b0 + d], hi = F.cr_bin_first[b0 + d + 1];
+    for (int e = -1; e <= 1; ++e) {
+      if (yb + e < 0 || yb + e >= R.nbx) continue;
+      // the three x bins of centre row yb + e are contiguous
+      const int x0 = max(0, xb - 1), x1 = min(R.nbx - 1, xb + 1);
+      const int row0 = b0 - xb + e * R.nbx;
+      const int lo = F.cr_bin_first[row0 + x0], hi = F.cr_bin_first[row0 + x1 + 1];
       for (int j = lo; j < hi; ++j) {
         const int b = F.cr_bin_items[j];
         if (b == a) continue;
@@ -131,26 +140,53 @@ __global__ void k_cr_legs(FrameDev F, KParams P, RemovalParams R) {
 }
 
 // One tube cross-section: the clusters of batch row rr within h of (yc, zc).
+// Where protection 2 depends on the occupancy, one scan of the window that
+// covers both the occupancy window and the larger of the two possible tubes
+// counts the occupancy and lists the tube candidates (up to kCrList; a denser
+// window is scanned again once h is known).
+constexpr int kCrList = 12;
+
 __device__ __forceinline__ void cr_tube(const FrameDev& F, const KParams& P,
                                         const RemovalParams& R, int rr, float yc, float zc,
                                         bool protect) {
   const int r = rr % P.n_rows;
   const RowGrid g = F.rows[rr];
-  float h = protect ? R.protect : R.remove;
-  if (R.mode >= 2) {
-    bool dyn = r < P.inner_rows || fabsf(yc) > F.row_x[r] * P.tan_half - R.edge;
-    if (!dyn) {
-      const float w = R.occ_w;
-      int occ = 0;
-      for_window(F.bin_first, g, yc - w, yc + w, zc - w, zc + w, [&](int k) {
-        const float2 pk = F.syz[k];
-        if (fabsf(pk.x - yc) <= w && fabsf(pk.y - zc) <= w) ++occ;
-      });
-      dyn = occ > R.occ_max;
-    }
-    if (dyn) h = h * (protect ? R.p2_grow : R.p2_shrink);
-  }
+  const float h0 = protect ? R.protect : R.remove;
+  const float fac = protect ? R.p2_grow : R.p2_shrink;
   const unsigned bit = protect ? 1u : 4u;
+  float h = h0;
+  if (R.mode >= 2) {
+    if (r < P.inner_rows || fabsf(yc) > F.row_x[r] * P.tan_half - R.edge) {
+      h = h0 * fac;
+    } else {
+      const float w = R.occ_w;
+      const float hg = h0 * fac;
+      const float hm = hg > h0 ? hg : h0;  // the larger tube the occupancy may select
+      const float wb = hm > w ? hm : w;
+      int occ = 0, nc = 0;
+      bool over = false;
+      int cand[kCrList];
+      for_window(F.bin_first, g, yc - wb, yc + wb, zc - wb, zc + wb, [&](int k) {
+        const float2 pk = F.syz[k];
+        const float dy = fabsf(pk.x - yc), dz = fabsf(pk.y - zc);
+        if (dy <= w && dz <= w) ++occ;
+        if (dy <= hm && dz <= hm) {
+          if (nc < kCrList)
+            cand[nc++] = k;
+          else
+            over = true;
+        }
+      });
+      if (occ > R.occ_max) h = hg;
+      if (!over) {
+        for (int j = 0; j < nc; ++j) {
+          const float2 pk = F.syz[cand[j]];
+          if (fabsf(pk.x - yc) <= h && fabsf(pk.y - zc) <= h) atomicOr(&F.cr_flags[cand[j]], bit);
+        }
+        return;
+      }
+    }
+  }
   for_window(F.bin_first, g, yc - h, yc + h, zc - h, zc + h, [&](int k) {
     const float2 pk = F.syz[k];
     if (fabsf(pk.x - yc) <= h && fabsf(pk.y - zc) <= h) atomicOr(&F.cr_flags[k], bit);
@@ -171,11 +207,12 @@ __global__ void k_cr_tubes(FrameDev F, KParams P, RemovalParams R) {
     int crr = F.srow[used[0]];
     float2 pc = F.syz[used[0]];
     for (int i = 0; i < n; ++i) {
+      // the next cluster is requested before this one's tube is scanned
+      const int d = i + 1 < n ? used[i + 1] : -1;
+      const int drr = d >= 0 ? F.srow[d] : -1;
+      const float2 pd = d >= 0 ? F.syz[d] : make_float2(0.0f, 0.0f);
       cr_tube(F, P, R, crr, pc.x, pc.y, protect);
-      if (i + 1 == n) break;
-      const int d = used[i + 1];
-      const int drr = F.srow[d];
-      const float2 pd = F.syz[d];
+      if (d < 0) break;
       if (drr / NR == crr / NR) {
         const bool cl = crr < drr;  // interpolate from the lower-row cluster
         const int rl = (cl ? crr : drr) % NR, rh = (cl ? drr : crr) % NR;
@@ -218,7 +255,7 @@ __global__ void k_cr_final(FrameDev F) {
 
 int cluster_removal(FrameDev& F, const KParams& P, const RemovalParams& R, int nblk, int sms,
                     cudaStream_t s) {
-  const int nbins = nblk * R.nbx;
+  const int nbins = nblk * R.nbx * R.nbx;
   const int g = sms * 8;
   k_cr_tracks<<<g, kBlock, 0, s>>>(F, P, R);
   int k = 1 + scan_exclusive(F.cr_bin_cnt, F.cr_bin_first, nbins + 1, F.scan_tmp, s);
