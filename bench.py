@@ -56,7 +56,8 @@ def parse():
                     help="sector-tracking iterations, the later ones on leftover clusters "
                          "(Sec. 3; 1 = off, the default)")
     ap.add_argument("--profile-only", action="store_true",
-                    help="run warm-up plus one step and exit (for ncu launch lists)")
+                    help="run warm-up plus one step, then one cluster removal on its tracks, "
+                         "and exit (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -172,6 +173,45 @@ def cpu_baseline(frames, seconds):
             "sample": f"{3 * groups} of 36 sectors of frame 0 in groups of 3 adjacent sectors "
                       f"({n_done} clusters, {t_done:.1f} s), full chain, strict FP32 oracle, "
                       f"single thread"}
+
+
+def _oracle_group(cols):
+    """One oracle call on one group of sectors (a worker of the parallel baseline)."""
+    import oracle
+    from paper_2601_20569_gb300 import synth
+    from paper_2601_20569_gb300.options import TrackerOptions
+
+    y, z, row, sec = cols
+    t0 = time.perf_counter()
+    oracle.track(y, z, row, sec, synth.row_x(), TrackerOptions().as_dict(), full=True)
+    return time.perf_counter() - t0
+
+
+def _nothing(_):
+    return 0
+
+
+def cpu_baseline_parallel(frames):
+    """The same oracle on all 12 groups of three adjacent sectors of the first
+    frame at once, one process per group on the host cores (spawned workers,
+    started and warmed before the timed region)."""
+    import multiprocessing
+
+    import numpy as np
+
+    f = frames[0]
+    groups = [np.nonzero((f.sector // 3) == g)[0] for g in range(12)]
+    cols = [(f.y[i], f.z[i], f.row[i], f.sector[i]) for i in groups]
+    workers = max(1, min(os.cpu_count() or 1, len(groups)))
+    with multiprocessing.get_context("spawn").Pool(workers) as pool:
+        pool.map(_nothing, range(workers))
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_group, cols, chunksize=1)
+        wall = time.perf_counter() - t0
+    return {"value": f.n / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"all 36 sectors of frame 0 ({f.n} clusters) as 12 groups of 3 adjacent "
+                      f"sectors, one process per group, {wall:.1f} s wall "
+                      f"({sum(per):.1f} s of oracle time), full chain, strict FP32 oracle"}
 
 
 def run_reference(args):
@@ -357,6 +397,7 @@ def main():
     torch.cuda.synchronize()
     if args.profile_only:
         step()
+        tr.cluster_removal(TrackerOptions(cr_mode=2))  # after the step: listed apart
         torch.cuda.synchronize()
         return
 
@@ -462,13 +503,15 @@ def main():
     ropts = TrackerOptions(cr_mode=2)
     rem = tr.cluster_removal(ropts)
     torch.cuda.synchronize()
-    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    r0.record(stream)
-    for _ in range(3):
+    rem_times = []
+    for _ in range(5):  # median of five calls, each between its own events
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
         rem = tr.cluster_removal(ropts, stream=stream)
-    r1.record(stream)
-    torch.cuda.synchronize()
-    rem_ms = r0.elapsed_time(r1) / 3
+        r1.record(stream)
+        torch.cuda.synchronize()
+        rem_times.append(r0.elapsed_time(r1))
+    rem_ms = statistics.median(rem_times)
     removal = {"ms_per_batch": rem_ms, "clusters_per_s": n_per_step / (rem_ms / 1e3),
                "removed_fraction": rem["n_removed"] / n_per_step,
                "form": "protective / removal tubes with protection 2 and seeding history, "
@@ -503,6 +546,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(frames, args.cpu_seconds)
         note("cpu baseline done")
+        line["cpu_baseline_parallel"] = cpu_baseline_parallel(frames)
+        note("parallel cpu baseline done")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
