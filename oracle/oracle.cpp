@@ -1229,6 +1229,8 @@ struct FitTrack {
   bool looper = false;     // the final fit's updates run in FP64 (low-pT looper)
   int n_ext = 0;           // Phase III: rows extrapolated below the innermost station;
                            // their candidate slots follow the stations' in ncand/cand/cchi
+  int n_out = 0;           // Phase III: rows extrapolated above the outermost station; their
+                           // slots follow the ext_rows inward ones
   bool ok = true;
   int fail_at = -1;        // diagnostics: 100*iteration + station of a failed step
   Track<Real> out{};
@@ -1254,6 +1256,56 @@ struct FitTrack {
 // becomes a candidate, except clusters already held by a station outside the
 // inner region of some track (`fixed`).  The candidates join the second
 // ambiguity solving; iteration 3 continues over the extrapolated rows.
+// Phase III candidates of one extrapolated row r of sector sec into slot
+// `slot`: every cluster of the row not held by a station outside the inner
+// region of some track (`fixed`) whose chi2 to the prediction E is below
+// ext_chi2 -- the stricter cut of the extrapolation --, the best cand_k by
+// (chi2, id).
+template <typename Real>
+void ext_row_candidates(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
+                        const std::vector<char>& fixed, FitTrack<Real>& T, const Lin<Real>& E,
+                        int sec, int r, size_t slot) {
+  // window centre: the prediction moved back by the map's shift there
+  Real cy, cz;
+  {
+    Real D[3];
+    map_eval(M, P, sec, E.t.x, E.t.p[0], E.t.p[1] - T.z0, D);
+    Real sy = D[1], sz = D[2];
+    if (D[0] != Real(0)) {
+      Step<Real> stp;
+      if (helix_step(E.r, D[0], P, stp, P.fit_max_snp)) {
+        sy = sy - (stp.p[0] - E.r[0]);
+        sz = sz - (stp.p[1] - E.r[1]);
+      }
+    }
+    cy = E.t.p[0] - sy;
+    cz = E.t.p[1] - sz;
+  }
+  const Real wy = o_sqrt(P.ext_chi2 * (E.t.c[0] + P.meas_sy2)) * Real(1.001) + P.attach_margin;
+  const Real wz = o_sqrt(P.ext_chi2 * (E.t.c[2] + P.meas_sz2)) * Real(1.001) + P.attach_margin;
+  std::vector<std::pair<Real, int>> cands;
+  for_row_range(F, P, sec, r, cz - wz - Real(0.01), cz + wz + Real(0.01), [&](int id) {
+    if (fixed[id]) return;
+    if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - cz) <= wz)) return;
+    Real my, mz;
+    if (!corrected(M, P, sec, E.t.x, F.y[id], F.z[id], T.z0, E.r, my, mz)) return;
+    const Real c2 = residual(E.t, my, mz, P).chi2;
+    if (c2 < P.ext_chi2) cands.push_back({c2, id});
+  });
+  std::sort(cands.begin(), cands.end(), [](const auto& u, const auto& v) {
+    return u.first < v.first || (u.first == v.first && u.second < v.second);
+  });
+  const int nc = std::min((int)cands.size(), P.cand_k);
+  T.ncand[slot] = nc;
+  for (int j = 0; j < nc; ++j) {
+    T.cand[slot * P.cand_k + j] = cands[j].second;
+    T.cchi[slot * P.cand_k + j] = cands[j].first;
+  }
+}
+
+// Phase III (Sec. 3) inward: from the state after iteration 1 at the
+// innermost station, row by row over at most ext_rows rows below it in its
+// sector, stopping where the propagation fails or the track leaves the sector.
 template <typename Real>
 void extrapolate_inward(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
                         const std::vector<char>& fixed, FitTrack<Real>& T, Lin<Real> E) {
@@ -1264,44 +1316,25 @@ void extrapolate_inward(const Frame<Real>& F, const Params<Real>& P, const MapR<
     const int r = r_first - 1 - e;
     if (!lin_goto(E, sec, P.row_x[r], P)) break;
     if (o_fabs(E.t.p[0]) > E.t.x * P.tan_half + P.edge_margin) break;
-    // window centre: the prediction moved back by the map's shift there
-    Real cy, cz;
-    {
-      Real D[3];
-      map_eval(M, P, sec, E.t.x, E.t.p[0], E.t.p[1] - T.z0, D);
-      Real sy = D[1], sz = D[2];
-      if (D[0] != Real(0)) {
-        Step<Real> stp;
-        if (helix_step(E.r, D[0], P, stp, P.fit_max_snp)) {
-          sy = sy - (stp.p[0] - E.r[0]);
-          sz = sz - (stp.p[1] - E.r[1]);
-        }
-      }
-      cy = E.t.p[0] - sy;
-      cz = E.t.p[1] - sz;
-    }
-    const Real wy = o_sqrt(P.ext_chi2 * (E.t.c[0] + P.meas_sy2)) * Real(1.001) + P.attach_margin;
-    const Real wz = o_sqrt(P.ext_chi2 * (E.t.c[2] + P.meas_sz2)) * Real(1.001) + P.attach_margin;
-    std::vector<std::pair<Real, int>> cands;
-    for_row_range(F, P, sec, r, cz - wz - Real(0.01), cz + wz + Real(0.01), [&](int id) {
-      if (fixed[id]) return;
-      if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - cz) <= wz)) return;
-      Real my, mz;
-      if (!corrected(M, P, sec, E.t.x, F.y[id], F.z[id], T.z0, E.r, my, mz)) return;
-      const Real c2 = residual(E.t, my, mz, P).chi2;
-      if (c2 < P.ext_chi2) cands.push_back({c2, id});
-    });
-    std::sort(cands.begin(), cands.end(), [](const auto& u, const auto& v) {
-      return u.first < v.first || (u.first == v.first && u.second < v.second);
-    });
-    const int nc = std::min((int)cands.size(), P.cand_k);
-    const size_t slot = (size_t)ns + e;
-    T.ncand[slot] = nc;
-    for (int j = 0; j < nc; ++j) {
-      T.cand[slot * P.cand_k + j] = cands[j].second;
-      T.cchi[slot * P.cand_k + j] = cands[j].first;
-    }
+    ext_row_candidates(F, P, M, fixed, T, E, sec, r, (size_t)ns + e);
     T.n_ext = e + 1;
+  }
+}
+
+// Phase III outward: from the state after iteration 2 at the outermost
+// station, the same over at most ext_rows rows above it in its sector.
+template <typename Real>
+void extrapolate_outward(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
+                         const std::vector<char>& fixed, FitTrack<Real>& T, Lin<Real> E) {
+  const int ns = (int)T.st.size();
+  const int sec = T.st[ns - 1].sector, r_last = T.st[ns - 1].row;
+  T.n_out = 0;
+  for (int e = 0; e < P.ext_rows && r_last + 1 + e < P.n_rows; ++e) {
+    const int r = r_last + 1 + e;
+    if (!lin_goto(E, sec, P.row_x[r], P)) break;
+    if (o_fabs(E.t.p[0]) > E.t.x * P.tan_half + P.edge_margin) break;
+    ext_row_candidates(F, P, M, fixed, T, E, sec, r, (size_t)ns + P.ext_rows + e);
+    T.n_out = e + 1;
   }
 }
 
@@ -1310,7 +1343,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
                       const std::vector<char>& fixed, FitTrack<Real>& T, bool phase2,
                       std::vector<Real>& store, Track<Real>& it2_end) {
   const int ns = (int)T.st.size();
-  const int nslot = ns + (phase2 ? P.ext_rows : 0);
+  const int nslot = ns + (phase2 ? 2 * P.ext_rows : 0);
   store.assign((size_t)ns * 5, Real(0));
   T.flag.assign(ns, 0);
   T.ncand.assign(nslot, 0);
@@ -1406,6 +1439,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
     }
   }
   it2_end = L.t;
+  if (phase2 && P.ext_rows > 0) extrapolate_outward(F, P, M, fixed, T, L);
 }
 
 template <typename Real>
@@ -1418,6 +1452,46 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
   T.n = 0;
   T.used.clear();
   bool have = false, reached = true;
+  auto take = [&](int sector, int c) {
+    Real my, mz;
+    if (!corrected(M, P, sector, L.t.x, F.y[c], F.z[c], T.z0, L.r, my, mz)) return;
+    const Resid<Real> R = residual(L.t, my, mz, P);
+    if (R.chi2 > P.final_chi2) return;
+    T.chi2 = T.chi2 + R.chi2;
+    update_as(L.t, R, T.looper);
+    ++T.n;
+    T.used.push_back(c);
+    T.out = L.t;
+    T.out_sector = L.sector;
+    have = true;
+  };
+  // Phase III outward rows: each assigned cluster is tested (simple cut) and
+  // filtered against a forward extrapolation of the iteration-2 end state
+  // (its own covariance, not reset), so that it joins the track without
+  // moving the fit of the stations; they precede the stations in the list
+  std::vector<int> outc;
+  if (T.n_out > 0) {
+    const size_t o0 = (size_t)ns + P.ext_rows;
+    const int sec_out = T.st[ns - 1].sector;
+    Lin<Real> E;
+    E.t = start;
+    for (int i = 0; i < 5; ++i) E.r[i] = detach(start.p[i]);
+    E.sector = sec_out;
+    for (int e = 0; e < T.n_out; ++e) {
+      if (!lin_goto(E, sec_out, P.row_x[T.st[ns - 1].row + 1 + e], P)) break;
+      const int c = T.assigned[o0 + e];
+      if (c < 0) continue;
+      Real my, mz;
+      if (!corrected(M, P, sec_out, E.t.x, F.y[c], F.z[c], T.z0, E.r, my, mz)) continue;
+      const Resid<Real> R = residual(E.t, my, mz, P);
+      if (R.chi2 > P.final_chi2) continue;
+      T.chi2 = T.chi2 + R.chi2;
+      update_as(E.t, R, T.looper);
+      ++T.n;
+      outc.push_back(c);
+    }
+  }
+  for (size_t i = outc.size(); i-- > 0;) T.used.push_back(outc[i]);
   // the stations inward, then the rows extrapolated below the innermost one
   for (int k = ns - 1; k >= -T.n_ext; --k) {
     int sector, row, c;
@@ -1436,18 +1510,7 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
       reached = false;
       break;
     }
-    if (c < 0) continue;
-    Real my, mz;
-    if (!corrected(M, P, sector, L.t.x, F.y[c], F.z[c], T.z0, L.r, my, mz)) continue;
-    const Resid<Real> R = residual(L.t, my, mz, P);
-    if (R.chi2 > P.final_chi2) continue;
-    T.chi2 = T.chi2 + R.chi2;
-    update_as(L.t, R, T.looper);
-    ++T.n;
-    T.used.push_back(c);
-    T.out = L.t;
-    T.out_sector = L.sector;
-    have = true;
+    if (c >= 0) take(sector, c);
   }
   (void)reached;
   std::reverse(T.used.begin(), T.used.end());
@@ -1960,25 +2023,30 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   res.put("cand_ids", cs_cand, "i4");
   res.put("cand_chi2", cs_chi, real_name<Real>());
   res.put("cand_assigned", cs_assigned, "i4");
-  // Phase III candidates and assignments of every extrapolated row
-  std::vector<int> ex_key, ex_row, ex_n, ex_cand, ex_assigned, fit_next;
+  // Phase III candidates and assignments of every extrapolated row (inward
+  // rows, then outward rows)
+  std::vector<int> ex_key, ex_row, ex_n, ex_cand, ex_assigned, fit_next, fit_nout;
   std::vector<Real> ex_chi;
   for (auto& T : FT) {
     fit_next.push_back(T.ok ? T.n_ext : 0);
+    fit_nout.push_back(T.ok ? T.n_out : 0);
     if (!T.ok) continue;
     const size_t ns = T.st.size();
-    for (int e = 0; e < T.n_ext; ++e) {
+    auto put = [&](size_t slot, int row) {
       ex_key.push_back(T.key);
-      ex_row.push_back(T.st[0].row - 1 - e);
-      ex_n.push_back(T.ncand[ns + e]);
+      ex_row.push_back(row);
+      ex_n.push_back(T.ncand[slot]);
       for (int k = 0; k < P.cand_k; ++k) {
-        ex_cand.push_back(T.cand[(ns + e) * P.cand_k + k]);
-        ex_chi.push_back(T.cchi[(ns + e) * P.cand_k + k]);
+        ex_cand.push_back(T.cand[slot * P.cand_k + k]);
+        ex_chi.push_back(T.cchi[slot * P.cand_k + k]);
       }
-      ex_assigned.push_back(T.assigned[ns + e]);
-    }
+      ex_assigned.push_back(T.assigned[slot]);
+    };
+    for (int e = 0; e < T.n_ext; ++e) put(ns + e, T.st[0].row - 1 - e);
+    for (int e = 0; e < T.n_out; ++e) put(ns + P.ext_rows + e, T.st[ns - 1].row + 1 + e);
   }
   res.put("fit_next", fit_next, "i4");
+  res.put("fit_nout", fit_nout, "i4");
   res.put("ext_key", ex_key, "i4");
   res.put("ext_row", ex_row, "i4");
   res.put("ext_n", ex_n, "i4");

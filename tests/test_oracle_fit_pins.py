@@ -246,11 +246,40 @@ def test_inward_extrapolation_recovers_inner_segments():
     assert got.sum() >= 0.9 * cand.sum(), (got.sum(), cand.sum())
     right = tlab[att[got]] == lab[got]
     assert right.mean() > 0.98, right.mean()
-    # above the gap the attachment is that of the run without extrapolation
-    assert np.array_equal(base["attach"][row > 19] >= 0, att[row > 19] >= 0)
+    # above the gap nothing attached is lost; the outward extrapolation of the
+    # same phase may attach more, each cluster to its own particle's track
+    up = row > 19
+    assert not np.any((base["attach"][up] >= 0) & (att[up] < 0))
+    new = np.nonzero(up & (base["attach"] < 0) & (att >= 0))[0]
+    assert np.all(tlab[att[new]] == lab[new])
     # candidate lists: sorted by chi2, inside the cut, on rows below the innermost cluster
     n, ids, chi = ext["ext_n"], ext["ext_ids"].reshape(-1, 4), ext["ext_chi2"].reshape(-1, 4)
     for j in range(len(n)):
         c = chi[j, :n[j]]
         assert np.all(np.diff(c) >= 0) and np.all(c < 9.0)
         assert np.all(row[ids[j, :n[j]]] == ext["ext_row"][j])
+
+
+def test_outward_extrapolation_recovers_outer_segments():
+    """Phase III outward (Sec. 3 extrapolates inwards and outwards): with rows
+    132-143 emptied the 8-row outer parts are too short to be tracked; the
+    extrapolation over 20 rows above each track's outermost cluster attaches
+    them to the track of their own particle, without losing any cluster the
+    run without extrapolation attached."""
+    f = synth.generate("one_sector", n_primaries=150, noise_frac=0.0)
+    y, z, row, sec, lab = _cut_rows(f, 132, 143)
+    base = oracle.track(y, z, row, sec, RX.astype(np.float32), opts(), full=True)
+    ext = oracle.track(y, z, row, sec, RX.astype(np.float32), opts(ext_rows=20), full=True)
+    outer = row > 143
+    assert np.all(base["attach"][outer] < 0)
+    tr = tracks_of(ext)
+    tlab = np.array([majority(lab[h])[0] for h in tr])
+    tracked = set(tlab[tlab >= 0].tolist())
+    cand = outer & np.isin(lab, list(tracked))
+    att = ext["attach"]
+    got = cand & (att >= 0)
+    assert got.sum() >= 0.8 * cand.sum(), (got.sum(), cand.sum())
+    assert np.mean(tlab[att[got]] == lab[got]) > 0.98
+    assert not np.any((base["attach"] >= 0) & (att < 0))
+    # outward candidate rows lie above the track's outermost station
+    assert np.any(ext["fit_nout"] > 0)
