@@ -352,7 +352,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ft_store, FT * kMaxRows * 5);
   ok &= dalloc(ctx, &F.ft_flag, FT * kMaxRows);
   ok &= dalloc(ctx, &F.ft_end2, FT * kStateF);
-  F.nslot = kMaxInner + opt->ext_rows;
+  F.nslot = kMaxInner + 2 * opt->ext_rows;
   const long NS = F.nslot;
   ok &= dalloc(ctx, &F.ft_ncand, FT * NS);
   ok &= dalloc(ctx, &F.ft_cand, FT * NS * kMaxCand);
@@ -360,6 +360,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ft_assigned, FT * NS);
   ok &= dalloc(ctx, &F.ft_newly, FT * NS);
   ok &= dalloc(ctx, &F.ft_next, FT);
+  ok &= dalloc(ctx, &F.ft_nout, FT);
   ok &= dalloc(ctx, &F.ft_ipol, FT * kMaxInner * kIpolF);
   ok &= dalloc(ctx, &F.ft_fixed, n);
   ok &= dalloc(ctx, &F.bid, n);
@@ -947,6 +948,7 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   else if (w == "ft_cchi") { src = F.ft_cchi; nb = 4L * F.nslot * kMaxCand * nft; }
   else if (w == "ft_assigned") { src = F.ft_assigned; nb = 4L * F.nslot * nft; }
   else if (w == "ft_next") { src = F.ft_next; nb = 4L * nft; }
+  else if (w == "ft_nout") { src = F.ft_nout; nb = 4L * nft; }
   else if (w == "ft_n") { src = F.ft_n; nb = 4L * nft; }
   else if (w == "out_par") { src = F.out_par; nb = 4L * 5 * c.n_out; }
   else if (w == "out_cov") { src = F.out_cov; nb = 4L * 15 * c.n_out; }

@@ -718,6 +718,7 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
     F.ft_last[f] = last;
     F.ft_z0[f] = zoff(F.st_ie + (long)head * kStateF);
     F.ft_next[f] = 0;
+    F.ft_nout[f] = 0;
     if (P.ext_rows > 0) {
       // Phase III: clusters held by a station outside the inner region are
       // not extrapolation candidates of any track
@@ -795,12 +796,12 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
   F.ft_assigned[(long)f * F.nslot + k] = -1;
 }
 
-// Phase III (Sec. 3): candidates of extrapolated row slot e (sorted (sector,
-// row) rr) -- every cluster not held by a station outside the inner region
-// whose chi2 to the prediction is below ext_chi2, the best cand_k by
-// (chi2, id), for the second ambiguity solving.
+// Phase III (Sec. 3): candidates of an extrapolated row (sorted (sector, row)
+// rr) into candidate slot `js` of track f -- every cluster not held by a
+// station outside the inner region whose chi2 to the prediction is below
+// ext_chi2, the best cand_k by (chi2, id), for the second ambiguity solving.
 __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, const MapDev& M, int f,
-                                            int e, int rr, const Lin& L, float z0) {
+                                            int js, int rr, const Lin& L, float z0) {
   const int sec = rr / P.n_rows;
   float cy, cz;
   {
@@ -819,7 +820,7 @@ __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, co
   }
   const float wy = sqrtf(P.ext_chi2 * (L.t.c[0] + P.sy2)) * 1.001f + P.attach_margin;
   const float wz = sqrtf(P.ext_chi2 * (L.t.c[2] + P.sz2)) * 1.001f + P.attach_margin;
-  const long slot = (long)f * F.nslot + kMaxInner + e;
+  const long slot = (long)f * F.nslot + js;
   int* cand = F.ft_cand + slot * kMaxCand;
   float* cchi = F.ft_cchi + slot * kMaxCand;
   int nc = 0;
@@ -904,7 +905,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
       if (go) go = lin_goto(L, rs0 / NR, rx[r], P);
       if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
       if (go) {
-        ext_candidates(F, P, M, f, k, rs0 - rs0 % NR + r, L, z0);
+        ext_candidates(F, P, M, f, kMaxInner + k, rs0 - rs0 % NR + r, L, z0);
         ++k;
       } else {
         F.ft_next[f] = k;
@@ -958,7 +959,10 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
 
 // Iteration 2 (outward) as the same kind of state machine: interpolation with
 // the stored predictions, flags of outliers, inner-row candidates (Sec. 3,
-// Phases I and II).  Starts from the end of iteration 1, ends in ft_end2.
+// Phases I and II), then the Phase III extrapolation above the outermost
+// station.  Starts from the end of iteration 1, ends in ft_end2.
+enum : int { kFit2Idle = 0, kFit2St, kFit2Out };
+
 __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M) {
   __shared__ float rx[kMaxRows];
   for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
@@ -967,7 +971,7 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
   if (F.cnt->err) return;
   const int nL = min(F.cnt->n_loopers, nf);
   const int NR = P.n_rows;
-  bool busy = false;
+  int phase = kFit2Idle;
   int f = 0, ns = 0, k = 0;
   bool lp = false;  // FP64 updates (low-pT looper)
   float z0 = 0.0f;
@@ -977,7 +981,7 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
   uint8_t* flag = nullptr;
   Lin L;
   for (;;) {
-    if (!busy) {
+    if (phase == kFit2Idle) {
       const int q = fit_next(F.cnt, kQFit2, kQFit2N, nL, nf);
       if (q >= nf) break;
       f = F.ft_order[q];
@@ -993,7 +997,24 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
       get_state(F.ft_end2 + (long)f * kStateF, s1);
       lin_start(L, s1, SR[0] / NR, P);
       k = 0;
-      busy = true;
+      phase = kFit2St;
+      continue;
+    }
+    if (phase == kFit2Out) {
+      // Phase III: one row of the outward extrapolation above the outermost
+      // station (k counts the rows done)
+      const int rsl = SR[ns - 1];
+      const int r = rsl % NR + 1 + k;
+      bool go = k < P.ext_rows && r < NR;
+      if (go) go = lin_goto(L, rsl / NR, rx[r], P);
+      if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
+      if (go) {
+        ext_candidates(F, P, M, f, kMaxInner + P.ext_rows + k, rsl - rsl % NR + r, L, z0);
+        ++k;
+      } else {
+        F.ft_nout[f] = k;
+        phase = kFit2Idle;
+      }
       continue;
     }
     // ---- one station.  The cluster and the stored prediction do not depend
@@ -1041,12 +1062,13 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
     if (have) update_as(L.t, residual(L.t, my, mz, P), lp);
     if (!ok) {
       F.ft_ok[f] = 0;
-      busy = false;
+      phase = kFit2Idle;
       continue;
     }
     if (++k == ns) {
       put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
-      busy = false;
+      k = 0;
+      phase = P.ext_rows > 0 ? kFit2Out : kFit2Idle;
     }
   }
 }
@@ -1083,21 +1105,26 @@ __global__ void k_inner_cand(FrameDev F, KParams P, MapDev M) {
 
 // Work item w of the second ambiguity: (fit track, candidate slot).  Slots
 // 0..inner_rows-1 are the inner stations, the next ext_rows slots the rows
-// extrapolated below the track (Phase III); returns -1 for an unused slot.
+// extrapolated below the track, the ext_rows after them the rows extrapolated
+// above it (Phase III); returns -1 for an unused slot.
+__device__ __forceinline__ int amb_per(const KParams& P) { return P.inner_rows + 2 * P.ext_rows; }
+
 __device__ __forceinline__ long amb_slot(const FrameDev& F, const KParams& P, long w, int& f) {
-  const int per = P.inner_rows + P.ext_rows;
+  const int per = amb_per(P);
   f = (int)(w / per);
   const int k = (int)(w % per);
   if (!F.ft_ok[f]) return -1;
   if (k < P.inner_rows) return inner_station(F, P, f, k) ? (long)f * F.nslot + k : -1;
   const int e = k - P.inner_rows;
-  return e < F.ft_next[f] ? (long)f * F.nslot + kMaxInner + e : -1;
+  if (e < P.ext_rows) return e < F.ft_next[f] ? (long)f * F.nslot + kMaxInner + e : -1;
+  const int eo = e - P.ext_rows;
+  return eo < F.ft_nout[f] ? (long)f * F.nslot + kMaxInner + P.ext_rows + eo : -1;
 }
 
 __global__ void k_amb_bid(FrameDev F, KParams P, int round) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  const long tot = (long)nf * (P.inner_rows + P.ext_rows);
+  const long tot = (long)nf * amb_per(P);
   for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
        w += (long)gridDim.x * blockDim.x) {
     int f;
@@ -1113,7 +1140,7 @@ __global__ void k_amb_bid(FrameDev F, KParams P, int round) {
 __global__ void k_amb_resolve(FrameDev F, KParams P, int round) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  const long tot = (long)nf * (P.inner_rows + P.ext_rows);
+  const long tot = (long)nf * amb_per(P);
   for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
        w += (long)gridDim.x * blockDim.x) {
     int f;
@@ -1133,7 +1160,7 @@ __global__ void k_amb_resolve(FrameDev F, KParams P, int round) {
 __global__ void k_amb_mark(FrameDev F, KParams P, int round) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  const long tot = (long)nf * (P.inner_rows + P.ext_rows);
+  const long tot = (long)nf * amb_per(P);
   for (long w = (long)blockIdx.x * blockDim.x + threadIdx.x; w < tot;
        w += (long)gridDim.x * blockDim.x) {
     int f;
@@ -1147,7 +1174,7 @@ __global__ void k_amb_mark(FrameDev F, KParams P, int round) {
 }
 
 // Iteration 3: inward with the surviving and re-attached clusters, simple cut.
-__global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
+__global__ void __launch_bounds__(256, 2) k_fit3(FrameDev F, KParams P, MapDev M) {
   __shared__ float rx[kMaxRows];
   for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) rx[r] = F.row_x[r];
   __syncthreads();
@@ -1176,6 +1203,41 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
     int n = 0;
     Trk<float> out = L.t;
     int out_sec = L.sector;
+    bool have = false;
+    // Phase III outward rows: each assigned cluster is tested and filtered
+    // against a forward extrapolation of the iteration-2 end state (its own
+    // covariance), so that it joins the track without moving the fit of the
+    // stations; in the list the outward clusters precede the stations
+    const int nout = P.ext_rows > 0 ? F.ft_nout[f] : 0;
+    if (nout > 0) {
+      const int rsl = SR[ns - 1];
+      const int secl = rsl / NR, rl = rsl % NR;
+      Lin E;
+      E.t = s2;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) E.r[i] = s2.p[i];
+      E.sector = secl;
+      const long o0 = (long)f * F.nslot + kMaxInner + P.ext_rows;
+      for (int e = 0; e < nout; ++e) {
+        if (!lin_goto(E, secl, rx[rl + 1 + e], P)) break;
+        const int c = F.ft_assigned[o0 + e];
+        if (c < 0) continue;
+        const float2 pc = F.syz[c];
+        float my, mz;
+        if (!corrected(M, P, secl, E.t.x, pc.x, pc.y, z0, E.r, my, mz)) continue;
+        const Resid R = residual(E.t, my, mz, P);
+        if (R.chi2 > P.final_chi2) continue;
+        chi2 = chi2 + R.chi2;
+        update_as(E.t, R, lp);
+        used[n] = c;
+        ++n;
+      }
+      for (int i = 0, j = n - 1; i < j; ++i, --j) {  // outermost first
+        const int u = used[i];
+        used[i] = used[j];
+        used[j] = u;
+      }
+    }
     // the stations inward, then the rows extrapolated below the innermost one
     const int next = P.ext_rows > 0 ? F.ft_next[f] : 0;
     const int rs0 = SR[0];
@@ -1213,8 +1275,9 @@ __global__ void __launch_bounds__(256) k_fit3(FrameDev F, KParams P, MapDev M) {
       ++n;
       out = L.t;
       out_sec = L.sector;
+      have = true;
     }
-    F.ft_n[f] = n;
+    F.ft_n[f] = have ? n : 0;
     F.ft_chi2[f] = chi2;
     put_state(F.ft_out + (long)f * kStateF, out, out_sec);
   }

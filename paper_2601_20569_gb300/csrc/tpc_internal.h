@@ -240,6 +240,7 @@ struct FrameDev {
   float* ft_end2;          // [cap_ft][kStateF] end of iteration 2 (+ sector)
   // candidate slots per fit track: nslot = kMaxInner inner-station slots
   // (station k) followed by ext_rows extrapolation slots (row r_first - 1 - e)
+  // and ext_rows outward slots (row r_last + 1 + e)
   int nslot;
   uint8_t* ft_ncand;       // [cap_ft][nslot]
   int* ft_cand;            // [cap_ft][nslot][kMaxCand]
@@ -247,6 +248,7 @@ struct FrameDev {
   int* ft_assigned;        // [cap_ft][nslot]
   uint8_t* ft_newly;       // [cap_ft][nslot]
   int* ft_next;            // [cap_ft] rows extrapolated below the innermost station
+  int* ft_nout;            // [cap_ft] rows extrapolated above the outermost station
   float* ft_ipol;          // [cap_ft][kMaxInner][kIpolF] iteration-2 interpolation at inner
                            // stations (y, z, Cyy, Cyz, Czz, x, reference p[5]) for k_inner_cand
   uint8_t* ft_fixed;       // [n] sorted cluster held by a station outside the inner region

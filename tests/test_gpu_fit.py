@@ -66,7 +66,7 @@ def compare_full(tr, f, opts, dist_map=None):
     fok = tr.debug("ft_ok")
     nst = tr.debug("ft_nst")
     rs = tr.debug("ft_st_rs").reshape(-1, 160)
-    ns = 32 + opts.get("ext_rows", 0)  # inner-station slots, then extrapolation slots
+    ns = 32 + 2 * opts.get("ext_rows", 0)  # inner-station slots, inward then outward rows
     nc = tr.debug("ft_ncand").reshape(-1, ns)
     cand = tr.debug("ft_cand").reshape(-1, ns, 8)
     cchi = tr.debug("ft_cchi").reshape(-1, ns, 8)
@@ -92,16 +92,22 @@ def compare_full(tr, f, opts, dist_map=None):
     if opts.get("ext_rows", 0) > 0:
         # Phase III: rows extrapolated per track, candidates and assignments per row
         nxt = tr.debug("ft_next")
-        assert np.array_equal(np.sort(nxt[fok == 1]), np.sort(ref["fit_next"][ref["fit_fail"] < 0]))
+        nout = tr.debug("ft_nout")
+        ok_ref = ref["fit_fail"] < 0
+        assert np.array_equal(np.sort(nxt[fok == 1]), np.sort(ref["fit_next"][ok_ref]))
+        assert np.array_equal(np.sort(nout[fok == 1]), np.sort(ref["fit_nout"][ok_ref]))
+        E = opts["ext_rows"]
         gpu_e = {}
         for t in np.nonzero(fok == 1)[0]:
             r0 = rs[t, 0] % 152
-            for e in range(nxt[t]):
-                s_ = 32 + e
+            rl = rs[t, nst[t] - 1] % 152
+            rows = [(32 + e, r0 - 1 - e) for e in range(nxt[t])] + \
+                   [(32 + E + e, rl + 1 + e) for e in range(nout[t])]
+            for s_, r_ in rows:
                 ids = sid[cand[t, s_, :nc[t, s_]]]
                 a = sid[asg[t, s_]] if asg[t, s_] >= 0 else -1
-                gpu_e[(int(fk[t]), int(r0 - 1 - e))] = (ids.tolist(),
-                                                         bits(cchi[t, s_, :nc[t, s_]]).tolist(), a)
+                gpu_e[(int(fk[t]), int(r_))] = (ids.tolist(),
+                                                bits(cchi[t, s_, :nc[t, s_]]).tolist(), a)
         ref_e = {}
         ec = ref["ext_ids"].reshape(-1, K)
         ex = ref["ext_chi2"].reshape(-1, K)
@@ -215,14 +221,16 @@ class _Cut:
 
 @pytest.mark.parametrize("workload,kw,cut", [
     ("one_sector", {"n_primaries": 150, "noise_frac": 0.0}, (8, 19)),
+    ("one_sector", {"n_primaries": 150, "noise_frac": 0.0}, (132, 143)),
     ("central_event", {"n_primaries": 2500}, (8, 19)),
     ("central_event", {"n_primaries": 2500}, None),
 ])
 def test_inward_extrapolation_bit_exact(workload, kw, cut):
-    """Phase III: inward extrapolation over 20 rows, its candidates, their
-    assignment by the second ambiguity and the extended third iteration,
-    strict parity (on frames with rows 8-19 emptied, where the extrapolation
-    has inner segments to find, and on a complete event)."""
+    """Phase III: inward and outward extrapolation over 20 rows, their
+    candidates, their assignment by the second ambiguity and the extended
+    third iteration, strict parity (on frames with rows 8-19 or 132-143
+    emptied, where the extrapolation has segments to find, and on a complete
+    event)."""
     f = synth.generate(workload, **kw)
     if cut is not None:
         f = _Cut(f, *cut)
