@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-refit", action="store_true",
                     help="skip the refit + adjoint timing on one distorted frame")
     ap.add_argument("--ext-rows", type=int, default=0,
-                    help="Phase III inward extrapolation over this many rows (0: off)")
+                    help="Phase III extrapolation over this many rows below and above each track (0: off)")
     ap.add_argument("--seed-iters", type=int, default=1,
                     help="sector-tracking iterations, the later ones on leftover clusters "
                          "(Sec. 3; 1 = off, the default)")

@@ -97,7 +97,7 @@ typedef struct {
   float edge_margin;        /* following stops at |y| > x*tan(10 deg) + edge_margin [cm] */
   float looper_qpt;         /* |q/pT| above which the final fit's Kalman update runs in FP64
                                (low-pT loopers); 0 disables */
-  float ext_chi2;           /* Phase III: candidate cut of the inward extrapolation (2 dof) */
+  float ext_chi2;           /* Phase III: candidate cut of the extrapolation (2 dof) */
   int32_t max_miss;         /* consecutive empty rows ending the following */
   int32_t min_hits;         /* minimum clusters of a tracklet / track */
   int32_t merge_max_gap;    /* max rows between merged segments */
@@ -106,8 +106,8 @@ typedef struct {
   int32_t mode;             /* 0 = strict FP32 (no FMA), 1 = fast FP32 (FMA) */
   int32_t max_frames;       /* frames per tpc_track_batch call (<= 64; 0 or 1: single frames) */
   int32_t use_graphs;       /* 1: replay each call's chain from a captured CUDA graph */
-  int32_t ext_rows;         /* Phase III (Sec. 3): rows below a track's innermost cluster searched
-                               by inward extrapolation, 0..32 (0: off) */
+  int32_t ext_rows;         /* Phase III (Sec. 3): rows below a track's innermost and above its
+                               outermost cluster searched by extrapolation, 0..32 (0: off) */
   int32_t seed_iters;       /* Sec. 3: sector-tracking iterations, 1..4; every later one runs the
                                neighbour finding, tracklet construction and selection again on
                                the clusters that no accepted tracklet of the earlier ones kept

@@ -8,8 +8,9 @@ values; the defaults below are this library's readings of it:
 * the "inner region" where Phase II re-attaches clusters = the 20 innermost
   pad rows (Sec. 2 and Sec. 4 both single out rows below 20);
 * Phase II candidate depth (tracks may fall back to their k-th candidate) = 4;
-* Phase III (Sec. 3): tracks are extrapolated inward over at most ``ext_rows``
-  rows below their innermost cluster, with a candidate cut of chi2 < 9
+* Phase III (Sec. 3): tracks are extrapolated over at most ``ext_rows`` rows
+  below their innermost and above their outermost cluster, with a candidate cut
+  of chi2 < 9
   (stricter than the interpolation cut of 25); off by default, as the paper
   describes it as work in progress;
 * seeding iterations on leftover clusters (Sec. 3): ``seed_iters`` sector-
@@ -48,8 +49,8 @@ class TrackerOptions:
     attach_margin: float = 0.5      # widening of the Phase II search window [cm]
     looper_qpt: float = 1.0 / 0.15  # |q/pT| above which the fit update runs in FP64
     edge_margin: float = 1.0        # following stops beyond the sector edge + this [cm]
-    ext_rows: int = 0               # Phase III: rows searched below a track's innermost
-                                    # cluster by inward extrapolation (0: off, <= 32)
+    ext_rows: int = 0               # Phase III: rows searched below a track's innermost and
+                                    # above its outermost cluster (0: off, <= 32)
     ext_chi2: float = 9.0           # Phase III candidate cut (2 dof), stricter than int_chi2
     seed_iters: int = 1             # sector-tracking iterations; each later one seeds again on
                                     # the clusters the accepted tracklets left (1: off, <= 4)
