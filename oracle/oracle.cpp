@@ -61,7 +61,7 @@ struct orc_options {
   float attach_margin;   // widening of the Phase II search window [cm]
   float looper_qpt;      // |q/pT| above which the fit's update runs in FP64 (0: never)
   float edge_margin;     // following stops |y| > x*tan(10 deg) + edge_margin [cm]
-  float ext_chi2;        // Phase III: candidate cut of the inward extrapolation (2 dof)
+  float ext_chi2;        // Phase III: candidate cut of the extrapolation (2 dof)
   // online cluster removal (Sec. 4)
   float cr_qpt;          // |q/pT| above which a track is very low pT (removal class)
   float cr_protect;      // half-width of the protective tube around physics tracks [cm]
@@ -81,7 +81,7 @@ struct orc_options {
   int32_t brute_force;  // 1: candidate search scans whole rows (self-check)
   int32_t n_rows;
   int32_t n_sectors;
-  int32_t ext_rows;     // Phase III: rows searched below a track's innermost cluster (0: off)
+  int32_t ext_rows;     // Phase III: rows searched below / above a track's end clusters (0: off)
   int32_t seed_iters;   // sector-tracking iterations, the later ones on leftover clusters (>= 1)
   int32_t cr_mode;      // cluster removal: 0 off, 1 tubes + history, 2 also protection 2
   int32_t cr_occ_max;   // protection 2: clusters in the occupancy window above which it applies
@@ -1249,13 +1249,16 @@ struct FitTrack {
 // simple chi2 cut.  Iteration 3 runs in fit_iteration3 after the second
 // ambiguity solving.
 // Phase III (Sec. 3): from the state at the innermost station after
-// iteration 1, the track is extrapolated inward row by row over at most
+// iteration 1 the track is extrapolated inward, from the state at the
+// outermost station after iteration 2 outward, row by row over at most
 // ext_rows rows of the same sector (stopping where the propagation fails or
-// the track leaves the sector), and every cluster of a row whose chi2 to the
+// the track leaves the sector); every cluster of a row whose chi2 to the
 // prediction is below ext_chi2 -- the stricter cut of the extrapolation --
 // becomes a candidate, except clusters already held by a station outside the
 // inner region of some track (`fixed`).  The candidates join the second
-// ambiguity solving; iteration 3 continues over the extrapolated rows.
+// ambiguity solving; iteration 3 continues over the inward rows and takes the
+// outward ones through a forward extrapolation of the iteration-2 end state.
+//
 // Phase III candidates of one extrapolated row r of sector sec into slot
 // `slot`: every cluster of the row not held by a station outside the inner
 // region of some track (`fixed`) whose chi2 to the prediction E is below
