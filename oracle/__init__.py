@@ -66,6 +66,7 @@ class _Opt(ctypes.Structure):
         ("seed_iters", ctypes.c_int32),
         ("cr_mode", ctypes.c_int32),
         ("cr_occ_max", ctypes.c_int32),
+        ("ac_merge", ctypes.c_int32),
     ]
 
 

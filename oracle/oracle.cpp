@@ -85,6 +85,7 @@ struct orc_options {
   int32_t seed_iters;   // sector-tracking iterations, the later ones on leftover clusters (>= 1)
   int32_t cr_mode;      // cluster removal: 0 off, 1 tubes + history, 2 also protection 2
   int32_t cr_occ_max;   // protection 2: clusters in the occupancy window above which it applies
+  int32_t ac_merge;     // 1: merging across the central electrode (A <-> C sides)
 };
 // Correction map of the oracle (host memory): layout [3][n_z][n_r][n_phi].
 struct orc_map {
@@ -261,7 +262,7 @@ struct Params {
   Real cr_qpt, cr_protect, cr_remove, cr_edge, cr_occ_w, cr_p2_grow, cr_p2_shrink, cr_leg_dq,
       cr_leg_dtgl, cr_leg_dc;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors,
-      ext_rows, seed_iters, cr_mode, cr_occ_max;
+      ext_rows, seed_iters, cr_mode, cr_occ_max, ac_merge;
   std::vector<Real> row_x;
   std::vector<Real> sec_cos, sec_sin;  // axis of sector s mod 18: ((s mod 18) + 0.5) * 20 deg
 };
@@ -302,6 +303,7 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
   P.cr_edge = o.cr_edge; P.cr_occ_w = o.cr_occ_w; P.cr_p2_grow = o.cr_p2_grow;
   P.cr_p2_shrink = o.cr_p2_shrink; P.cr_leg_dq = o.cr_leg_dq; P.cr_leg_dtgl = o.cr_leg_dtgl;
   P.cr_leg_dc = o.cr_leg_dc; P.cr_mode = o.cr_mode; P.cr_occ_max = o.cr_occ_max;
+  P.ac_merge = o.ac_merge;
   P.sec_cos.resize(18);
   P.sec_sin.resize(18);
   for (int k = 0; k < 18; ++k) {
@@ -1029,6 +1031,64 @@ Real chi2_5(const Real* d, const Real* c) {
   return chi2;
 }
 
+// chi2 of the 4-vector (y, sin phi, tan lambda, q/pT) of a 5-vector difference
+// with the marginal covariance (z left out), by the same Cholesky steps.
+template <typename Real>
+Real chi2_4z(const Real* d, const Real* c) {
+  const int ix[4] = {0, 2, 3, 4};
+  Real L[4][4] = {};
+  for (int j = 0; j < 4; ++j) {
+    Real s = c[ci(ix[j], ix[j])];
+    for (int k = 0; k < j; ++k) s = s - L[j][k] * L[j][k];
+    if (!(s > Real(0))) return Real(-1);
+    L[j][j] = o_sqrt(s);
+    for (int i = j + 1; i < 4; ++i) {
+      Real v = c[ci(ix[i], ix[j])];
+      for (int k = 0; k < j; ++k) v = v - L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  Real yv[4];
+  Real chi2 = Real(0);
+  for (int i = 0; i < 4; ++i) {
+    Real v = d[ix[i]];
+    for (int k = 0; k < i; ++k) v = v - L[i][k] * yv[k];
+    yv[i] = v / L[i][i];
+    chi2 = chi2 + yv[i] * yv[i];
+  }
+  return chi2;
+}
+
+// Candidate pair across the central electrode (Sec. 2: the merging joins
+// tracks inside sectors, then between adjacent sectors of one half, then
+// across the central electrode): the outer end of A and the inner end of B in
+// the same azimuthal sector on the two sides, B's innermost row 1 to
+// merge_max_gap rows above A's outermost.  In continuous readout the measured
+// z of the two sides differ by 2 vd t0 with t0 unknown (Sec. 1), so z stays
+// out of the chi2 (4 dof, summed covariances, below merge_chi2); instead the
+// true z at B's inner end, half the sum of the two sides' z there, must lie
+// within merge_dz + |tan lambda| * merge_zspan of the electrode.  dz = z_A -
+// z_B at B's x is the shift that brings B's side into A's measured z.
+template <typename Real>
+bool cross_test(const Params<Real>& P, const SectorTrack<Real>& A, const SectorTrack<Real>& B,
+                Real& chi2, Real& dz) {
+  const int half = P.n_sectors / 2;
+  if (A.sector / half == B.sector / half || A.sector % half != B.sector % half) return false;
+  const int gap = B.rmin - A.rmax;
+  if (gap < 1 || gap > P.merge_max_gap) return false;
+  Track<Real> t = A.oe;
+  if (!propagate(t, B.ie.x, P, P.fit_max_snp)) return false;
+  const Real zwin = P.merge_dz + o_fabs(A.oe.p[3]) * P.merge_zspan;
+  if (!(o_fabs(t.p[1] + B.ie.p[1]) <= zwin + zwin)) return false;
+  Real d[5], c[15];
+  for (int i = 0; i < 5; ++i) d[i] = B.ie.p[i] - t.p[i];
+  if (!(o_fabs(d[0]) <= P.merge_dy)) return false;
+  for (int i = 0; i < 15; ++i) c[i] = t.c[i] + B.ie.c[i];
+  chi2 = chi2_4z(d, c);
+  dz = t.p[1] - B.ie.p[1];
+  return chi2 >= Real(0) && chi2 < P.merge_chi2;
+}
+
 // Candidate pair for merging the outer end of A with the inner end of B (Sec. 2:
 // merging inside a sector and between adjacent sectors of one TPC half).
 template <typename Real>
@@ -1144,9 +1204,11 @@ bool lin_goto(Lin<Real>& L, int sector, Real x, const Params<Real>& P) {
       if (!lin_rotate(L, 1, P)) return false;
     } else if (ds == half - 1) {
       if (!lin_rotate(L, -1, P)) return false;
-    } else {
+    } else if (ds != 0) {
       return false;
     }
+    // ds == 0: the same azimuthal sector on the other side of the central
+    // electrode, whose local frame is the same
     L.sector = sector;
   }
   return lin_propagate(L, x, P);
@@ -1239,7 +1301,26 @@ struct FitTrack {
   int n = 0;
   std::vector<int> used;   // clusters of iteration 3, innermost first
   std::vector<int> seg;    // sector tracks of the chain, first to last
+  int side0 = 0;           // TPC side of the first segment
+  Real zshift = 0;         // z shift of the clusters on the other side (merged across the
+                           // central electrode): their measured z + zshift is in the first
+                           // side's measured z
 };
+
+// Measured z of cluster id on sector `sector` in the frame of track T's first side.
+template <typename Real>
+Real track_z(const Frame<Real>& F, const Params<Real>& P, const FitTrack<Real>& T, int sector,
+             int id) {
+  const int half = P.n_sectors / 2;
+  return T.zshift != Real(0) && (sector / half) % 2 != T.side0 ? F.z[id] + T.zshift : F.z[id];
+}
+
+// Shift of the window centre cz (first side's frame) into the measured z of `sector`.
+template <typename Real>
+Real window_z(const Params<Real>& P, const FitTrack<Real>& T, int sector, Real cz) {
+  const int half = P.n_sectors / 2;
+  return T.zshift != Real(0) && (sector / half) % 2 != T.side0 ? cz - T.zshift : cz;
+}
 
 // One three-iteration fit (Sec. 3, Phase I, with the Phase II candidate search
 // when `phase2`): iteration 1 inward stores the predicted (y,z) and covariance
@@ -1287,11 +1368,13 @@ void ext_row_candidates(const Frame<Real>& F, const Params<Real>& P, const MapR<
   const Real wy = o_sqrt(P.ext_chi2 * (E.t.c[0] + P.meas_sy2)) * Real(1.001) + P.attach_margin;
   const Real wz = o_sqrt(P.ext_chi2 * (E.t.c[2] + P.meas_sz2)) * Real(1.001) + P.attach_margin;
   std::vector<std::pair<Real, int>> cands;
-  for_row_range(F, P, sec, r, cz - wz - Real(0.01), cz + wz + Real(0.01), [&](int id) {
+  const Real czm = window_z(P, T, sec, cz);  // the row's measured z
+  for_row_range(F, P, sec, r, czm - wz - Real(0.01), czm + wz + Real(0.01), [&](int id) {
     if (fixed[id]) return;
-    if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - cz) <= wz)) return;
+    if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - czm) <= wz)) return;
     Real my, mz;
-    if (!corrected(M, P, sec, E.t.x, F.y[id], F.z[id], T.z0, E.r, my, mz)) return;
+    if (!corrected(M, P, sec, E.t.x, F.y[id], track_z(F, P, T, sec, id), T.z0, E.r, my, mz))
+      return;
     const Real c2 = residual(E.t, my, mz, P).chi2;
     if (c2 < P.ext_chi2) cands.push_back({c2, id});
   });
@@ -1366,7 +1449,8 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
     sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
     if (s.cl >= 0) {
       Real my, mz;
-      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], T.z0, L.r, my, mz)) {
+      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], track_z(F, P, T, s.sector, s.cl), T.z0,
+                     L.r, my, mz)) {
         T.ok = false;
         return;
       }
@@ -1389,7 +1473,8 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
     const bool inner = phase2 && s.row < P.inner_rows;
     if (s.cl >= 0 && !inner) {
       Real my, mz;
-      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], T.z0, L.r, my, mz)) {
+      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], track_z(F, P, T, s.sector, s.cl), T.z0,
+                     L.r, my, mz)) {
         T.ok = false;
         return;
       }
@@ -1415,10 +1500,13 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
       const Real wy = o_sqrt(P.int_chi2 * (I.c00 + P.meas_sy2)) * Real(1.001) + P.attach_margin;
       const Real wz = o_sqrt(P.int_chi2 * (I.c11 + P.meas_sz2)) * Real(1.001) + P.attach_margin;
       std::vector<std::pair<Real, int>> cands;
-      for_row_range(F, P, s.sector, s.row, cz - wz - Real(0.01), cz + wz + Real(0.01), [&](int id) {
-        if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - cz) <= wz)) return;
+      const Real czm = window_z(P, T, s.sector, cz);  // the row's measured z
+      for_row_range(F, P, s.sector, s.row, czm - wz - Real(0.01), czm + wz + Real(0.01), [&](int id) {
+        if (!(o_fabs(F.y[id] - cy) <= wy && o_fabs(F.z[id] - czm) <= wz)) return;
         Real my, mz;
-        if (!corrected(M, P, s.sector, L.t.x, F.y[id], F.z[id], T.z0, L.r, my, mz)) return;
+        if (!corrected(M, P, s.sector, L.t.x, F.y[id], track_z(F, P, T, s.sector, id), T.z0, L.r,
+                       my, mz))
+          return;
         const Real c2 = chi2_interp(I, my, mz, P);
         if (c2 < P.int_chi2) cands.push_back({c2, id});
       });
@@ -1434,7 +1522,8 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
     }
     if (s.cl >= 0) {
       Real my, mz;
-      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], T.z0, L.r, my, mz)) {
+      if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], track_z(F, P, T, s.sector, s.cl), T.z0,
+                     L.r, my, mz)) {
         T.ok = false;
         return;
       }
@@ -1457,7 +1546,8 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
   bool have = false, reached = true;
   auto take = [&](int sector, int c) {
     Real my, mz;
-    if (!corrected(M, P, sector, L.t.x, F.y[c], F.z[c], T.z0, L.r, my, mz)) return;
+    if (!corrected(M, P, sector, L.t.x, F.y[c], track_z(F, P, T, sector, c), T.z0, L.r, my, mz))
+      return;
     const Resid<Real> R = residual(L.t, my, mz, P);
     if (R.chi2 > P.final_chi2) return;
     T.chi2 = T.chi2 + R.chi2;
@@ -1485,7 +1575,9 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
       const int c = T.assigned[o0 + e];
       if (c < 0) continue;
       Real my, mz;
-      if (!corrected(M, P, sec_out, E.t.x, F.y[c], F.z[c], T.z0, E.r, my, mz)) continue;
+      if (!corrected(M, P, sec_out, E.t.x, F.y[c], track_z(F, P, T, sec_out, c), T.z0, E.r, my,
+                     mz))
+        continue;
       const Resid<Real> R = residual(E.t, my, mz, P);
       if (R.chi2 > P.final_chi2) continue;
       T.chi2 = T.chi2 + R.chi2;
@@ -1891,6 +1983,38 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
       next[a] = bestB[a];
       prev[bestB[a]] = a;
     }
+  // then across the central electrode: chain ends (no successor) against
+  // chain starts (no predecessor) on the other side, mutual best by (chi2, key)
+  std::vector<Real> xdz(nst, Real(0));  // z shift of the side that starts at b
+  if (P.ac_merge) {
+    std::vector<int> xB(nst, -1), xA(nst, -1);
+    std::vector<Real> xchiB(nst, 0), xchiA(nst, 0), xdzB(nst, 0);
+    for (int a = 0; a < nst; ++a) {
+      if (next[a] >= 0) continue;
+      const int sb = (ST[a].sector + half) % (2 * half);
+      for (int rb = ST[a].rmax + 1; rb <= ST[a].rmax + P.merge_max_gap && rb < P.n_rows; ++rb)
+        for (int b : by_sector[(size_t)sb * P.n_rows + rb]) {
+          if (prev[b] >= 0) continue;
+          Real chi2, dz;
+          if (!cross_test(P, ST[a], ST[b], chi2, dz)) continue;
+          if (xB[a] < 0 || chi2 < xchiB[a] || (chi2 == xchiB[a] && ST[b].key < ST[xB[a]].key)) {
+            xB[a] = b;
+            xchiB[a] = chi2;
+            xdzB[a] = dz;
+          }
+          if (xA[b] < 0 || chi2 < xchiA[b] || (chi2 == xchiA[b] && ST[a].key < ST[xA[b]].key)) {
+            xA[b] = a;
+            xchiA[b] = chi2;
+          }
+        }
+    }
+    for (int a = 0; a < nst; ++a)
+      if (xB[a] >= 0 && xA[xB[a]] == a) {
+        next[a] = xB[a];
+        prev[xB[a]] = a;
+        xdz[xB[a]] = xdzB[a];
+      }
+  }
   std::vector<int> st_key(nst), st_next(nst);
   std::vector<Real> st_ie(nst * 5), st_oe(nst * 5);
   for (int i = 0; i < nst; ++i) {
@@ -1913,10 +2037,16 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     T.key = ST[h].key;
     std::vector<int> cl;
     int last = h;
+    T.side0 = (ST[h].sector / half) % 2;
+    bool crossed = false;
     for (int s = h; s >= 0; s = next[s]) {
       cl.insert(cl.end(), ST[s].cl.begin(), ST[s].cl.end());
       T.seg.push_back(s);
       last = s;
+      if (!crossed && (ST[s].sector / half) % 2 != T.side0) {
+        crossed = true;
+        T.zshift = xdz[s];
+      }
     }
     T.st = make_stations(F, P, cl, true);
     T.outer = ST[last].oe;
@@ -1943,7 +2073,7 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     if (FT[i].ok) fit_iteration3(F, P, M, FT[i], true, it2_end[i]);
   // a11: output tracks with at least min_hits clusters, attachments
   std::vector<int> key, ncl, offs(1, 0), ids, sect, ndf, flags;
-  std::vector<Real> par, cov, chi2, xs;
+  std::vector<Real> par, cov, chi2, xs, zsh;
   std::vector<int> attach(F.n, -1);
   for (auto& T : FT) {
     if (!T.ok || T.n < P.min_hits) continue;
@@ -1959,6 +2089,7 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     ndf.push_back(2 * T.n - 5);
     chi2.push_back(T.chi2);
     xs.push_back(T.out.x);
+    zsh.push_back(T.zshift);
     for (int k = 0; k < 5; ++k) par.push_back(T.out.p[k]);
     for (int k = 0; k < 15; ++k) cov.push_back(T.out.c[k]);
   }
@@ -1970,6 +2101,7 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   res.put("trk_ndf", ndf, "i4");
   res.put("trk_chi2", chi2, real_name<Real>());
   res.put("trk_x", xs, real_name<Real>());
+  res.put("trk_zshift", zsh, real_name<Real>());
   res.put("trk_param", par, real_name<Real>());
   res.put("trk_cov", cov, real_name<Real>());
   res.put("attach", attach, "i4");

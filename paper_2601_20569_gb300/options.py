@@ -68,6 +68,8 @@ class TrackerOptions:
     cr_leg_dq: float = 0.1          # looper legs: relative |q/pT| difference
     cr_leg_dtgl: float = 0.05       # looper legs: |tan(lambda_a) + tan(lambda_b)|
     cr_leg_dc: float = 3.0          # looper legs: circle-centre distance [cm]
+    ac_merge: int = 0               # 1: merge across the central electrode (A <-> C), with
+                                    # the z shift of the far side (2 vd t0) estimated
     max_miss: int = 10              # consecutive empty rows ending the following
     min_hits: int = 10
     merge_max_gap: int = 20         # rows between merged segments

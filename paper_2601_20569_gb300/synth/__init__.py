@@ -86,6 +86,7 @@ class _Config(ctypes.Structure):
         ("map_rmax", ctypes.c_double),
         ("map_zmin", ctypes.c_double),
         ("map_zmax", ctypes.c_double),
+        ("vz_sigma", ctypes.c_double),
     ]
 
 
@@ -210,7 +211,7 @@ def generate(workload: str = "one_sector", frame: int = 0, *, seed: int | None =
         eta_min=-0.9, eta_max=0.9, phi_min=0.0, phi_max=2 * math.pi, sec_frac=0.02,
         sec_rmax=30.0, ms_theta=1e-3, sigma=0.1, noise_frac=0.05, looper_frac=0.0,
         looper_pt_min=0.06, looper_pt_max=0.15, only_sector=-1, thin_sectors=0, max_legs=2,
-        distort=False, map_amp=5.0, aim_radius=0.0,
+        distort=False, map_amp=5.0, aim_radius=0.0, vz_sigma=0.0,
     )
     p.update(PRESETS[workload])
     p.update(overrides)
@@ -222,7 +223,7 @@ def generate(workload: str = "one_sector", frame: int = 0, *, seed: int | None =
     for k in ("mean_collisions", "mean_mult", "frame_us", "vdrift", "bz", "pt_min", "pt_max",
               "pt_power", "eta_min", "eta_max", "phi_min", "phi_max", "sec_frac", "sec_rmax",
               "ms_theta", "sigma", "noise_frac", "looper_frac", "looper_pt_min", "looper_pt_max",
-              "aim_radius"):
+              "aim_radius", "vz_sigma"):
         setattr(cfg, k, float(p[k]))
     cfg.n_threads = n_threads
     cfg.store_truth = int(store_truth)

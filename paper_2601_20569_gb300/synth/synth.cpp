@@ -135,6 +135,7 @@ struct synth_config {
   const float* map;  // distortion control points [3][nz][nr][nphi] or NULL
   int32_t map_nphi, map_nr, map_nz, map_pad;
   double map_rmin, map_rmax, map_zmin, map_zmax;
+  double vz_sigma;  // >0: Gaussian spread of the collision vertex along z [cm] (else z = 0)
 };
 
 struct synth_result;
@@ -154,7 +155,7 @@ namespace {
 
 
 struct Particle {
-  double pt, q, tgl, phi0, vx, vy, t0;
+  double pt, q, tgl, phi0, vx, vy, vz, t0;
   int secondary;
 };
 
@@ -260,7 +261,7 @@ void advance(Helix& h, double s) {
 }
 
 void trace(const synth_config& cfg, const Particle& p, Rng& rng, std::vector<Crossing>& out) {
-  Helix h{p.vx, p.vy, 0.0, p.phi0, p.tgl, -p.q * cfg.bz * kBToCurv / p.pt};
+  Helix h{p.vx, p.vy, p.vz, p.phi0, p.tgl, -p.q * cfg.bz * kBToCurv / p.pt};
   const double th = tan_half();
   const double s_eps = 1e-7;
   const double s_max = 2.0 * kPi / std::fabs(h.kappa) - 1e-6;
@@ -431,6 +432,13 @@ int synth_generate(const synth_config* cfgp, synth_result** out) {
   }
   long pid = 0;
   for (size_t ic = 0; ic < coll_t0.size(); ++ic) {
+    // vertex z of the collision, from a stream of its own (drawn only when
+    // the spread is on, so that the other draws do not change)
+    double vz = 0.0;
+    if (cfg.vz_sigma > 0) {
+      Rng vr(cfg.seed, (uint32_t)ic, kStreamEvent + 16, (uint32_t)cfg.frame);
+      vz = cfg.vz_sigma * vr.gauss();
+    }
     for (long j = 0; j < coll_mult[ic]; ++j, ++pid) {
       Rng pr(cfg.seed, (uint32_t)pid, kStreamParticle, (uint32_t)cfg.frame);
       Particle p{};
@@ -453,6 +461,7 @@ int synth_generate(const synth_config* cfgp, synth_result** out) {
       }
       const double phi_mid = p.phi0 + bend;
       p.t0 = coll_t0[ic];
+      p.vz = vz;
       p.secondary = 0;
       p.vx = p.vy = 0;
       if (cfg.sec_frac > 0 && pr.uni() < cfg.sec_frac) {
