@@ -1066,9 +1066,10 @@ Real chi2_4z(const Real* d, const Real* c) {
 // merge_max_gap rows above A's outermost.  In continuous readout the measured
 // z of the two sides differ by 2 vd t0 with t0 unknown (Sec. 1), so z stays
 // out of the chi2 (4 dof, summed covariances, below merge_chi2); instead the
-// true z at B's inner end, half the sum of the two sides' z there, must lie
-// within merge_dz + |tan lambda| * merge_zspan of the electrode.  dz = z_A -
-// z_B at B's x is the shift that brings B's side into A's measured z.
+// sum of A's outer-end and B's inner-end z, in which t0 cancels, must lie
+// within twice merge_dz + |tan lambda| * merge_zspan (the electrode lies
+// between the two ends).  dz = z_A - z_B at B's x (A propagated there) is the
+// shift that brings B's side into A's measured z.
 template <typename Real>
 bool cross_test(const Params<Real>& P, const SectorTrack<Real>& A, const SectorTrack<Real>& B,
                 Real& chi2, Real& dz) {
@@ -1076,10 +1077,10 @@ bool cross_test(const Params<Real>& P, const SectorTrack<Real>& A, const SectorT
   if (A.sector / half == B.sector / half || A.sector % half != B.sector % half) return false;
   const int gap = B.rmin - A.rmax;
   if (gap < 1 || gap > P.merge_max_gap) return false;
+  const Real zwin = P.merge_dz + o_fabs(A.oe.p[3]) * P.merge_zspan;
+  if (!(o_fabs(A.oe.p[1] + B.ie.p[1]) <= zwin + zwin)) return false;
   Track<Real> t = A.oe;
   if (!propagate(t, B.ie.x, P, P.fit_max_snp)) return false;
-  const Real zwin = P.merge_dz + o_fabs(A.oe.p[3]) * P.merge_zspan;
-  if (!(o_fabs(t.p[1] + B.ie.p[1]) <= zwin + zwin)) return false;
   Real d[5], c[15];
   for (int i = 0; i < 5; ++i) d[i] = B.ie.p[i] - t.p[i];
   if (!(o_fabs(d[0]) <= P.merge_dy)) return false;
