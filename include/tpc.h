@@ -112,6 +112,8 @@ typedef struct {
                                neighbour finding, tracklet construction and selection again on
                                the clusters that no accepted tracklet of the earlier ones kept
                                (0 or 1: off) */
+  int32_t ac_merge;         /* 1: merging also across the central electrode (Sec. 2), the far
+                               side's z shifted by the estimated 2 vd t0 (Sec. 1); 0: off */
   int64_t cap_clusters;     /* max clusters per call (all frames of a batch) */
   int64_t cap_tracklets;    /* max tracklets per frame (0: n/16 + 4096) */
   int64_t cap_tracks;       /* max tracks per frame (0: cap_tracklets) */
@@ -143,6 +145,9 @@ typedef struct {
   const int32_t* key;       /* [n_tracks] identity: input id of the start cluster of
                                the track's first segment */
   const int32_t* attach;    /* [n_clusters of the frame]: owning track index or -1 */
+  const float* z_shift;     /* [n_tracks] tracks merged across the central electrode: shift
+                               added to the measured z of their clusters on the side other than
+                               that of their innermost cluster (= -2 * side * vd * t0); else 0 */
 } tpc_tracks;
 
 /* Create a context: copies the geometry, derives the model constants from

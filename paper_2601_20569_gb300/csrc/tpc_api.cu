@@ -160,6 +160,7 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.ext_chi2 = o.ext_chi2;
   P.ext_rows = o.ext_rows;
   P.seed_iters = o.seed_iters > 1 ? o.seed_iters : 1;
+  P.ac_merge = o.ac_merge ? 1 : 0;
   // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
   P.merge_zspan = (float)((double)(o.merge_max_gap + 2) *
                           (((double)row_x[nr - 1] - (double)row_x[0]) / (double)(nr - 1)) /
@@ -318,6 +319,11 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.st_bestB, T);
   ok &= dalloc(ctx, &F.st_bestchi, T);
   ok &= dalloc(ctx, &F.st_bestA, T);
+  ok &= dalloc(ctx, &F.st_xbestB, T);
+  ok &= dalloc(ctx, &F.st_xchi, T);
+  ok &= dalloc(ctx, &F.st_xdz, T);
+  ok &= dalloc(ctx, &F.st_xbestA, T);
+  ok &= dalloc(ctx, &F.st_dz, T);
   ok &= dalloc(ctx, &F.ie_cnt, nmb + 1);
   ok &= dalloc(ctx, &F.ie_first, nmb + 1);
   ok &= dalloc(ctx, &F.ie_slot, T);
@@ -371,6 +377,8 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ft_used, FT * kMaxRows);
   ok &= dalloc(ctx, &F.ft_outidx, FT);
   ok &= dalloc(ctx, &F.cr_cls, FT);
+  ok &= dalloc(ctx, &F.ft_side0, FT);
+  ok &= dalloc(ctx, &F.ft_zsh, FT);
   ok &= dalloc(ctx, &F.cr_parent, FT);
   ok &= dalloc(ctx, &F.cr_cx, FT);
   ok &= dalloc(ctx, &F.cr_cy, FT);
@@ -380,6 +388,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.out_cov, FT * 15);
   ok &= dalloc(ctx, &F.out_chi2, FT);
   ok &= dalloc(ctx, &F.out_x, FT);
+  ok &= dalloc(ctx, &F.out_zsh, FT);
   ok &= dalloc(ctx, &F.out_ndf, FT);
   ok &= dalloc(ctx, &F.out_sector, FT);
   ok &= dalloc(ctx, &F.out_ncl, FT);
@@ -557,6 +566,7 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   out->cl_ids = F.out_ids;
   out->key = F.out_key;
   out->attach = F.attach;
+  out->z_shift = F.out_zsh;
   ctx->tracked = true;
   return TPC_OK;
 }

@@ -235,6 +235,9 @@ __global__ void __launch_bounds__(256) k_sector_refit(FrameDev F, KParams P) {
     F.st_hasprev[i] = 0;
     F.st_bestB[i] = -1;
     F.st_bestA[i] = ~0ull;
+    F.st_xbestB[i] = -1;
+    F.st_xbestA[i] = ~0ull;
+    F.st_dz[i] = 0.0f;
     Trk<float> t;
 #pragma unroll
     for (int k = 0; k < 5; ++k) t.p[k] = F.tl_par[(long)ti * 5 + k];
@@ -423,6 +426,132 @@ __global__ void k_merge_link(FrameDev F) {
     if (F.st_bestA[b] == pack_chi_key(F.st_bestchi[a], F.st_key[a])) {
       F.st_next[a] = b;
       F.st_hasprev[b] = 1;
+    }
+  }
+}
+
+// ------------------------------------------ across the central electrode
+// chi2 of the 4-vector (y, sin phi, tan lambda, q/pT) of a 5-vector difference
+// with the marginal covariance (z left out).
+__device__ __forceinline__ float chi2_4z(const float* d, const float* c) {
+  const int ix[4] = {0, 2, 3, 4};
+  float L[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float sj = c[ix[j] * (ix[j] + 1) / 2 + ix[j]];
+    for (int k = 0; k < j; ++k) sj = sj - L[j][k] * L[j][k];
+    if (!(sj > 0.0f)) return -1.0f;
+    L[j][j] = sqrtf(sj);
+    for (int i = j + 1; i < 4; ++i) {
+      float v = c[ix[i] * (ix[i] + 1) / 2 + ix[j]];
+      for (int k = 0; k < j; ++k) v = v - L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  float yv[4];
+  float chi2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float v = d[ix[i]];
+    for (int k = 0; k < i; ++k) v = v - L[i][k] * yv[k];
+    yv[i] = v / L[i][i];
+    chi2 = chi2 + yv[i] * yv[i];
+  }
+  return chi2;
+}
+
+// Pair test across the central electrode (Sec. 2 merges "then across the
+// central electrode"): the outer end of A and the inner end of B in the same
+// azimuthal sector of one frame on the two sides, B's innermost row 1 to
+// merge_max_gap rows above A's outermost.  The measured z of the two sides
+// differ by 2 vd t0 with t0 unknown in continuous readout (Sec. 1): z stays out
+// of the chi2 (4 dof, summed covariances, below merge_chi2), and the sum of
+// the two ends' z, in which t0 cancels, must lie within twice merge_dz +
+// |tan lambda| * merge_zspan.  dz = z_A - z_B at B's x is the shift that
+// brings B's side into A's measured z.
+__device__ __forceinline__ bool cross_test(const FrameDev& F, const KParams& P, int a, int b,
+                                           float& chi2, float& dz) {
+  const int half = P.n_phi;
+  const int sa = F.st_sector[a], sb = F.st_sector[b];
+  if (sa / (2 * half) != sb / (2 * half) || sa / half == sb / half || sa % half != sb % half)
+    return false;
+  const int gap = F.st_rmin[b] - F.st_rmax[a];
+  if (gap < 1 || gap > P.merge_max_gap) return false;
+  const float* oe = F.st_oe + (long)a * kStateF;
+  const float* ie = F.st_ie + (long)b * kStateF;
+  const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
+  if (!(fabsf(oe[1] + ie[1]) <= zwin + zwin)) return false;
+  Trk<float> t;
+  get_state(oe, t);
+  if (!propagate(t, ie[20], P, P.fit_max_snp)) return false;
+  float d[5], c[15];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) d[i] = ie[i] - t.p[i];
+  if (!(fabsf(d[0]) <= P.merge_dy)) return false;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) c[i] = t.c[i] + ie[5 + i];
+  chi2 = chi2_4z(d, c);
+  dz = t.p[1] - ie[1];
+  return chi2 >= 0.0f && chi2 < P.merge_chi2;
+}
+
+// Chain ends against chain starts of the other side (after the merging within
+// each side): the best start of every end; each start keeps its best end.
+__global__ void k_cross_best(FrameDev F, KParams P) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  const int half = P.n_phi;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < ns; a += gridDim.x * blockDim.x) {
+    if (!F.st_ok[a] || F.st_next[a] >= 0) continue;
+    const int keyA = F.st_key[a];
+    const int sa = F.st_sector[a];
+    const int base = sa - sa % (2 * half);
+    const int sb = base + (sa % (2 * half) + half) % (2 * half);
+    const float* oe = F.st_oe + (long)a * kStateF;
+    const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
+    const int r0 = F.st_rmax[a] + 1;
+    const int r1 = min(F.st_rmax[a] + P.merge_max_gap, P.n_rows - 1);
+    if (r0 > r1) continue;
+    // the test needs |z_A + z_B| <= 2 zwin: B's inner-end z around -z_A
+    const float m = 0.01f;
+    const int z0 = merge_zbin(F, sb, -oe[1] - 2.0f * zwin - m);
+    const int z1 = merge_zbin(F, sb, -oe[1] + 2.0f * zwin + m);
+    int bb = -1, bkey = 0;
+    float bchi = 0.0f, bdz = 0.0f;
+    for (int zb = z0; zb <= z1; ++zb) {
+      const int bin0 = (sb * kMergeZ + zb) * P.n_rows;
+      const int lo = F.ie_first[bin0 + r0], hi = F.ie_first[bin0 + r1 + 1];
+      for (int k = lo; k < hi; ++k) {
+        const int b = F.ie_idx[k];
+        if (!F.st_ok[b] || F.st_hasprev[b]) continue;
+        float chi2, dz;
+        if (!cross_test(F, P, a, b, chi2, dz)) continue;
+        const int kb = F.st_key[b];
+        if (bb < 0 || chi2 < bchi || (chi2 == bchi && kb < bkey)) {
+          bb = b;
+          bchi = chi2;
+          bkey = kb;
+          bdz = dz;
+        }
+        atomicMin(&F.st_xbestA[b], pack_chi_key(chi2, keyA));
+      }
+    }
+    F.st_xbestB[a] = bb;
+    F.st_xchi[a] = bchi;
+    F.st_xdz[a] = bdz;
+  }
+}
+
+__global__ void k_cross_link(FrameDev F) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < ns; a += gridDim.x * blockDim.x) {
+    const int b = F.st_xbestB[a];
+    if (b < 0) continue;
+    if (F.st_xbestA[b] == pack_chi_key(F.st_xchi[a], F.st_key[a])) {
+      F.st_next[a] = b;
+      F.st_hasprev[b] = 1;
+      F.st_dz[b] = F.st_xdz[a];
     }
   }
 }
@@ -620,12 +749,15 @@ __device__ __forceinline__ bool lin_goto(Lin& L, int sector, float x, const KPar
     const int ds = ((sector % half) - (L.sector % half) + half) % half;
     if (ds == 1) {
       if (!lin_rotate(L, 1, P, jrec)) return false;
+      if (rotated) *rotated = true;
     } else if (ds == half - 1) {
       if (!lin_rotate(L, -1, P, jrec)) return false;
-    } else {
+      if (rotated) *rotated = true;
+    } else if (ds != 0) {
       return false;
     }
-    if (rotated) *rotated = true;
+    // ds == 0: the same azimuthal sector on the other side of the central
+    // electrode, whose local frame is the same
     L.sector = sector;
   }
   return lin_propagate(L, x, P, frec);
@@ -711,7 +843,21 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
     const int head = F.ft_head[f];
     int last = head;
-    while (F.st_next[last] >= 0) last = F.st_next[last];
+    // across the central electrode: the side of the first segment, and the
+    // z shift of the clusters on the other side (set at the first segment
+    // there, 0 for a chain on one side)
+    const int side0 = (F.st_sector[head] / P.n_phi) & 1;
+    float zsh = 0.0f;
+    bool crossed = false;
+    for (int sg = head; sg >= 0; sg = F.st_next[sg]) {
+      last = sg;
+      if (!crossed && ((F.st_sector[sg] / P.n_phi) & 1) != side0) {
+        crossed = true;
+        zsh = F.st_dz[sg];
+      }
+    }
+    F.ft_side0[f] = side0;
+    F.ft_zsh[f] = zsh;
     const int ns = build_stations(F, P, f, head);
     F.ft_nst[f] = ns;
     F.ft_key[f] = F.st_key[head];
@@ -741,9 +887,25 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
 // each carries only its own iteration's code and registers.
 enum : int { kFitIdle = 0, kFitIn, kFitExt };
 
+// Tracks merged across the central electrode: the measured z of a cluster of
+// sector sec in the frame of the track's first side (zside: the side whose
+// clusters take the shift zsh, -1 for a track on one side), and the window
+// centre cz of that frame in the measured z of sector sec.
+__device__ __forceinline__ int shift_side(const FrameDev& F, int f) {
+  return F.ft_zsh[f] != 0.0f ? 1 - F.ft_side0[f] : -1;
+}
+__device__ __forceinline__ float track_z(float z, int sec, int zside, float zsh, const KParams& P) {
+  return zside >= 0 && ((sec / P.n_phi) & 1) == zside ? z + zsh : z;
+}
+__device__ __forceinline__ float window_z(float cz, int sec, int zside, float zsh,
+                                          const KParams& P) {
+  return zside >= 0 && ((sec / P.n_phi) & 1) == zside ? cz - zsh : cz;
+}
+
 __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, const MapDev& M,
                                                  int f, int k, int rs, float x, const float* ref,
-                                                 const Interp& I, float z0) {
+                                                 const Interp& I, float z0, int zside,
+                                                 float zsh) {
   const int sec = rs / P.n_rows;
   float cy = I.y, cz = I.z;
   {
@@ -762,6 +924,7 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
   }
   const float wy = sqrtf(P.int_chi2 * (I.c00 + P.sy2)) * 1.001f + P.attach_margin;
   const float wz = sqrtf(P.int_chi2 * (I.c11 + P.sz2)) * 1.001f + P.attach_margin;
+  cz = window_z(cz, sec, zside, zsh, P);  // the row's measured z
   int* cand = F.ft_cand + ((long)f * F.nslot + k) * kMaxCand;
   float* cchi = F.ft_cchi + ((long)f * F.nslot + k) * kMaxCand;
   int nc = 0;
@@ -773,7 +936,7 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
     const float yk = pk.x, zk = pk.y;
     if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
     float my, mz;
-    if (!corrected(M, P, sec, x, yk, zk, z0, ref, my, mz)) return;
+    if (!corrected(M, P, sec, x, yk, track_z(zk, sec, zside, zsh, P), z0, ref, my, mz)) return;
     const float c2 = chi2_interp(I, my, mz, P);
     if (!(c2 < P.int_chi2)) return;
     const int id = F.sid[kk];
@@ -801,7 +964,8 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
 // station outside the inner region whose chi2 to the prediction is below
 // ext_chi2, the best cand_k by (chi2, id), for the second ambiguity solving.
 __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, const MapDev& M, int f,
-                                            int js, int rr, const Lin& L, float z0) {
+                                            int js, int rr, const Lin& L, float z0, int zside,
+                                            float zsh) {
   const int sec = rr / P.n_rows;
   float cy, cz;
   {
@@ -820,6 +984,7 @@ __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, co
   }
   const float wy = sqrtf(P.ext_chi2 * (L.t.c[0] + P.sy2)) * 1.001f + P.attach_margin;
   const float wz = sqrtf(P.ext_chi2 * (L.t.c[2] + P.sz2)) * 1.001f + P.attach_margin;
+  cz = window_z(cz, sec, zside, zsh, P);  // the row's measured z
   const long slot = (long)f * F.nslot + js;
   int* cand = F.ft_cand + slot * kMaxCand;
   float* cchi = F.ft_cchi + slot * kMaxCand;
@@ -833,7 +998,8 @@ __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, co
     const float yk = pk.x, zk = pk.y;
     if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
     float my, mz;
-    if (!corrected(M, P, sec, L.t.x, yk, zk, z0, L.r, my, mz)) return;
+    if (!corrected(M, P, sec, L.t.x, yk, track_z(zk, sec, zside, zsh, P), z0, L.r, my, mz))
+      return;
     const float c2 = chi2_of(L.t, my, mz, P);
     if (!(c2 < P.ext_chi2)) return;
     const int id = F.sid[kk];
@@ -872,6 +1038,8 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
   int f = 0, ns = 0, k = 0;
   bool lp = false;  // FP64 updates (low-pT looper)
   float z0 = 0.0f;
+  int zside = -1;   // central-electrode merging: side whose z takes zsh
+  float zsh = 0.0f;
   const int* SC = nullptr;
   const uint16_t* SR = nullptr;
   float* store = nullptr;
@@ -886,6 +1054,8 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
       F.ft_ok[f] = 0;
       if (ns == 0) continue;  // not reached: every chain holds clusters
       z0 = F.ft_z0[f];
+      zsh = F.ft_zsh[f];
+      zside = shift_side(F, f);
       SC = F.ft_st_cl + (long)f * kMaxRows;
       SR = F.ft_st_rs + (long)f * kMaxRows;
       store = F.ft_store + (long)f * kMaxRows * 5;
@@ -905,7 +1075,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
       if (go) go = lin_goto(L, rs0 / NR, rx[r], P);
       if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
       if (go) {
-        ext_candidates(F, P, M, f, kMaxInner + k, rs0 - rs0 % NR + r, L, z0);
+        ext_candidates(F, P, M, f, kMaxInner + k, rs0 - rs0 % NR + r, L, z0, zside, zsh);
         ++k;
       } else {
         F.ft_next[f] = k;
@@ -924,7 +1094,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
     if (c >= 0) {
       const float2 pc = F.syz[c];
       cy = pc.x;
-      cz = pc.y;
+      cz = track_z(pc.y, sec, zside, zsh, P);
     }
     bool ok = true;
     if (k != ns - 1) ok = lin_goto(L, sec, rx[row], P);
@@ -975,6 +1145,8 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
   int f = 0, ns = 0, k = 0;
   bool lp = false;  // FP64 updates (low-pT looper)
   float z0 = 0.0f;
+  int zside = -1;   // central-electrode merging: side whose z takes zsh
+  float zsh = 0.0f;
   const int* SC = nullptr;
   const uint16_t* SR = nullptr;
   const float* store = nullptr;
@@ -989,6 +1161,8 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
       lp = F.ft_looper[f] != 0;
       ns = F.ft_nst[f];
       z0 = F.ft_z0[f];
+      zsh = F.ft_zsh[f];
+      zside = shift_side(F, f);
       SC = F.ft_st_cl + (long)f * kMaxRows;
       SR = F.ft_st_rs + (long)f * kMaxRows;
       store = F.ft_store + (long)f * kMaxRows * 5;
@@ -1009,7 +1183,8 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
       if (go) go = lin_goto(L, rsl / NR, rx[r], P);
       if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
       if (go) {
-        ext_candidates(F, P, M, f, kMaxInner + P.ext_rows + k, rsl - rsl % NR + r, L, z0);
+        ext_candidates(F, P, M, f, kMaxInner + P.ext_rows + k, rsl - rsl % NR + r, L, z0, zside,
+                       zsh);
         ++k;
       } else {
         F.ft_nout[f] = k;
@@ -1026,7 +1201,7 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
     if (c >= 0) {
       const float2 pc = F.syz[c];
       cy = pc.x;
-      cz = pc.y;
+      cz = track_z(pc.y, sec, zside, zsh, P);
     }
     float sv[5];
 #pragma unroll
@@ -1099,7 +1274,7 @@ __global__ void k_inner_cand(FrameDev F, KParams P, MapDev M) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) ref[i] = ip[6 + i];
     inner_candidates(F, P, M, f, k, F.ft_st_rs[(long)f * kMaxRows + k], ip[5], ref, I,
-                     F.ft_z0[f]);
+                     F.ft_z0[f], shift_side(F, f), F.ft_zsh[f]);
   }
 }
 
@@ -1194,6 +1369,8 @@ __global__ void __launch_bounds__(256, 2) k_fit3(FrameDev F, KParams P, MapDev M
     const uint8_t* flag = F.ft_flag + (long)f * kMaxRows;
     int* used = F.ft_used + (long)f * kMaxRows;
     const float z0 = F.ft_z0[f];
+    const float zsh = F.ft_zsh[f];
+    const int zside = shift_side(F, f);
     Trk<float> s2;
     const float* e2 = F.ft_end2 + (long)f * kStateF;
     get_state(e2, s2);
@@ -1224,7 +1401,9 @@ __global__ void __launch_bounds__(256, 2) k_fit3(FrameDev F, KParams P, MapDev M
         if (c < 0) continue;
         const float2 pc = F.syz[c];
         float my, mz;
-        if (!corrected(M, P, secl, E.t.x, pc.x, pc.y, z0, E.r, my, mz)) continue;
+        if (!corrected(M, P, secl, E.t.x, pc.x, track_z(pc.y, secl, zside, zsh, P), z0, E.r, my,
+                       mz))
+          continue;
         const Resid R = residual(E.t, my, mz, P);
         if (R.chi2 > P.final_chi2) continue;
         chi2 = chi2 + R.chi2;
@@ -1261,7 +1440,7 @@ __global__ void __launch_bounds__(256, 2) k_fit3(FrameDev F, KParams P, MapDev M
       if (c >= 0) {
         const float2 pc = F.syz[c];
         cy = pc.x;
-        cz = pc.y;
+        cz = track_z(pc.y, sec, zside, zsh, P);
       }
       if (k != ns - 1 && !lin_goto(L, sec, rx[row], P)) break;
       if (c < 0) continue;
@@ -1350,6 +1529,7 @@ __global__ void k_out_write(FrameDev F, KParams P) {
   for (int i = 0; i < 5; ++i) F.out_par[(long)t * 5 + i] = o[i];
   for (int i = 0; i < 15; ++i) F.out_cov[(long)t * 15 + i] = o[5 + i];
   F.out_x[t] = o[20];
+  F.out_zsh[t] = F.ft_zsh[f];
   F.out_sector[t] = __float_as_int(o[21]);
   F.out_chi2[t] = F.ft_chi2[f];
   const int n = F.ft_n[f];
@@ -1758,6 +1938,11 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_ie_scatter<<<sms * 8, kBlock, 0, s>>>(F);
   k_merge_best<<<persistent_grid(F.lc, kLMerge, sms), F.lc.block[kLMerge], 0, s>>>(F, P);
   k_merge_link<<<sms * 8, kBlock, 0, s>>>(F);
+  if (P.ac_merge) {
+    k_cross_best<<<sms * 8, kBlock, 0, s>>>(F, P);
+    k_cross_link<<<sms * 8, kBlock, 0, s>>>(F);
+    k += 2;
+  }
   k_head_count<<<nb_tl, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_tl, &F.cnt->n_merged);
   k_head_write<<<nb_tl, kBlock, 0, s>>>(F, P);

@@ -26,6 +26,7 @@ struct KParams {
   float int_chi2, final_chi2, attach_margin, edge_margin, looper_qpt, ext_chi2;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, ext_rows;
   int seed_iters;  // sector-tracking iterations (the later ones on leftover clusters)
+  int ac_merge;    // merging across the central electrode
   int n_rows, n_sectors;  // n_sectors: all sectors of the call (frames x sectors)
   int n_phi;         // azimuthal sectors of one TPC half (sector % n_phi, side = sector / n_phi)
   float grid_dy;     // target y bin size [cm]
@@ -214,6 +215,12 @@ struct FrameDev {
   int* st_bestB;
   float* st_bestchi;
   unsigned long long* st_bestA;
+  // merging across the central electrode
+  int* st_xbestB;          // best chain start on the other side of a chain end
+  float* st_xchi;
+  float* st_xdz;           // z shift of that candidate's side
+  unsigned long long* st_xbestA;
+  float* st_dz;            // z shift of the side that starts at this sector track (0: none)
   int* ie_cnt;             // [n_sectors*kMergeZ*n_rows]
   int* ie_first;           // [n_sectors*kMergeZ*n_rows + 1]
   int* ie_slot;            // [cap_tl]
@@ -225,6 +232,8 @@ struct FrameDev {
   // a9/a10 fit tracks (capacity cap_ft)
   long cap_ft;
   int* ft_head;            // first sector track of the chain
+  int* ft_side0;           // TPC side of the first segment
+  float* ft_zsh;           // z shift of the clusters on the other side (0: one side only)
   int* ft_last;            // last sector track of the chain
   int* ft_order;           // [cap_ft] order in which the fit kernels take the tracks:
                            // FP64-update loopers first, then the rest, each in list order
@@ -264,6 +273,7 @@ struct FrameDev {
   float* out_cov;
   float* out_chi2;
   float* out_x;
+  float* out_zsh;          // [cap_ft] z shift of the far side (central-electrode merging)
   int* out_ndf;
   int* out_sector;
   int* out_ncl;

@@ -56,7 +56,7 @@ class Options(ctypes.Structure):
         ("min_hits", ctypes.c_int32), ("merge_max_gap", ctypes.c_int32),
         ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("max_frames", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-        ("ext_rows", ctypes.c_int32), ("seed_iters", ctypes.c_int32),
+        ("ext_rows", ctypes.c_int32), ("seed_iters", ctypes.c_int32), ("ac_merge", ctypes.c_int32),
         ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
         ("cap_tracks", ctypes.c_int64),
     ]
@@ -72,7 +72,8 @@ class Tracks(ctypes.Structure):
                 ("params", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
                 ("x", ctypes.c_void_p), ("ndf", ctypes.c_void_p), ("sector", ctypes.c_void_p),
                 ("n_clusters", ctypes.c_void_p), ("cl_offset", ctypes.c_void_p),
-                ("cl_ids", ctypes.c_void_p), ("key", ctypes.c_void_p), ("attach", ctypes.c_void_p)]
+                ("cl_ids", ctypes.c_void_p), ("key", ctypes.c_void_p), ("attach", ctypes.c_void_p),
+                ("z_shift", ctypes.c_void_p)]
 
 
 class RemovalOptions(ctypes.Structure):
@@ -348,6 +349,7 @@ class Tracker:
             "cl_offset": wrap_device(out.cl_offset, (nt + 1,), i),
             "cl_ids": wrap_device(out.cl_ids, (nr,), i), "key": wrap_device(out.key, (nt,), i),
             "attach": wrap_device(out.attach, (n,), i),
+            "z_shift": wrap_device(out.z_shift, (nt,), f),
         }
 
     def cluster_removal(self, opts: dict | TrackerOptions | None = None, mode: int | None = None,

@@ -246,3 +246,21 @@ def test_inward_extrapolation_bit_exact_with_distortion_map():
     opts = TrackerOptions(ext_rows=20).as_dict()
     tr = run_gpu(f, opts, dist_map=f.map)
     compare_full(tr, f, opts, dist_map=f.map)
+
+
+@pytest.mark.parametrize("workload,kw", [
+    ("central_event", {"n_primaries": 3000, "seed": 9, "vz_sigma": 10.0}),
+    ("timeframe", {"mean_collisions": 4, "vz_sigma": 10.0}),
+])
+def test_central_electrode_merging_bit_exact(workload, kw):
+    """Merging across the central electrode (collisions spread along z, so
+    that some particles cross it): links, fits, attachments and the far
+    side's z shift, strict parity; in continuous readout (the time-frame case)
+    the shift carries the collision time."""
+    f = synth.generate(workload, **kw)
+    opts = TrackerOptions(ac_merge=1).as_dict()
+    tr = run_gpu(f, opts)
+    ref, g = compare_full(tr, f, opts)
+    o = np.argsort(g["key"])
+    assert np.array_equal(bits(g["z_shift"][o]), bits(ref["trk_zshift"]))
+    assert np.count_nonzero(ref["trk_zshift"]) >= 2
