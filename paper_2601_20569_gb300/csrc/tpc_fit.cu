@@ -897,15 +897,14 @@ __device__ __forceinline__ int shift_side(const FrameDev& F, int f) {
 __device__ __forceinline__ float track_z(float z, int sec, int zside, float zsh, const KParams& P) {
   return zside >= 0 && ((sec / P.n_phi) & 1) == zside ? z + zsh : z;
 }
-__device__ __forceinline__ float window_z(float cz, int sec, int zside, float zsh,
-                                          const KParams& P) {
-  return zside >= 0 && ((sec / P.n_phi) & 1) == zside ? cz - zsh : cz;
+// The shift that applies to the clusters of sector sec (0: none).
+__device__ __forceinline__ float row_shift(int sec, int zside, float zsh, const KParams& P) {
+  return zside >= 0 && ((sec / P.n_phi) & 1) == zside ? zsh : 0.0f;
 }
 
 __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, const MapDev& M,
                                                  int f, int k, int rs, float x, const float* ref,
-                                                 const Interp& I, float z0, int zside,
-                                                 float zsh) {
+                                                 const Interp& I, float z0, float zadd) {
   const int sec = rs / P.n_rows;
   float cy = I.y, cz = I.z;
   {
@@ -924,7 +923,7 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
   }
   const float wy = sqrtf(P.int_chi2 * (I.c00 + P.sy2)) * 1.001f + P.attach_margin;
   const float wz = sqrtf(P.int_chi2 * (I.c11 + P.sz2)) * 1.001f + P.attach_margin;
-  cz = window_z(cz, sec, zside, zsh, P);  // the row's measured z
+  if (zadd != 0.0f) cz = cz - zadd;  // the row's measured z
   int* cand = F.ft_cand + ((long)f * F.nslot + k) * kMaxCand;
   float* cchi = F.ft_cchi + ((long)f * F.nslot + k) * kMaxCand;
   int nc = 0;
@@ -936,7 +935,7 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
     const float yk = pk.x, zk = pk.y;
     if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
     float my, mz;
-    if (!corrected(M, P, sec, x, yk, track_z(zk, sec, zside, zsh, P), z0, ref, my, mz)) return;
+    if (!corrected(M, P, sec, x, yk, zadd != 0.0f ? zk + zadd : zk, z0, ref, my, mz)) return;
     const float c2 = chi2_interp(I, my, mz, P);
     if (!(c2 < P.int_chi2)) return;
     const int id = F.sid[kk];
@@ -964,8 +963,8 @@ __device__ __forceinline__ void inner_candidates(FrameDev& F, const KParams& P, 
 // station outside the inner region whose chi2 to the prediction is below
 // ext_chi2, the best cand_k by (chi2, id), for the second ambiguity solving.
 __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, const MapDev& M, int f,
-                                            int js, int rr, const Lin& L, float z0, int zside,
-                                            float zsh) {
+                                            int js, int rr, const Lin& L, float z0,
+                                            float zadd) {
   const int sec = rr / P.n_rows;
   float cy, cz;
   {
@@ -984,7 +983,7 @@ __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, co
   }
   const float wy = sqrtf(P.ext_chi2 * (L.t.c[0] + P.sy2)) * 1.001f + P.attach_margin;
   const float wz = sqrtf(P.ext_chi2 * (L.t.c[2] + P.sz2)) * 1.001f + P.attach_margin;
-  cz = window_z(cz, sec, zside, zsh, P);  // the row's measured z
+  if (zadd != 0.0f) cz = cz - zadd;  // the row's measured z
   const long slot = (long)f * F.nslot + js;
   int* cand = F.ft_cand + slot * kMaxCand;
   float* cchi = F.ft_cchi + slot * kMaxCand;
@@ -998,8 +997,7 @@ __device__ __forceinline__ void ext_candidates(FrameDev& F, const KParams& P, co
     const float yk = pk.x, zk = pk.y;
     if (!(fabsf(yk - cy) <= wy && fabsf(zk - cz) <= wz)) return;
     float my, mz;
-    if (!corrected(M, P, sec, L.t.x, yk, track_z(zk, sec, zside, zsh, P), z0, L.r, my, mz))
-      return;
+    if (!corrected(M, P, sec, L.t.x, yk, zadd != 0.0f ? zk + zadd : zk, z0, L.r, my, mz)) return;
     const float c2 = chi2_of(L.t, my, mz, P);
     if (!(c2 < P.ext_chi2)) return;
     const int id = F.sid[kk];
@@ -1075,7 +1073,8 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
       if (go) go = lin_goto(L, rs0 / NR, rx[r], P);
       if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
       if (go) {
-        ext_candidates(F, P, M, f, kMaxInner + k, rs0 - rs0 % NR + r, L, z0, zside, zsh);
+        ext_candidates(F, P, M, f, kMaxInner + k, rs0 - rs0 % NR + r, L, z0,
+                       row_shift(rs0 / NR, zside, zsh, P));
         ++k;
       } else {
         F.ft_next[f] = k;
@@ -1183,8 +1182,8 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
       if (go) go = lin_goto(L, rsl / NR, rx[r], P);
       if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
       if (go) {
-        ext_candidates(F, P, M, f, kMaxInner + P.ext_rows + k, rsl - rsl % NR + r, L, z0, zside,
-                       zsh);
+        ext_candidates(F, P, M, f, kMaxInner + P.ext_rows + k, rsl - rsl % NR + r, L, z0,
+                       row_shift(rsl / NR, zside, zsh, P));
         ++k;
       } else {
         F.ft_nout[f] = k;
@@ -1273,8 +1272,9 @@ __global__ void k_inner_cand(FrameDev F, KParams P, MapDev M) {
     float ref[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) ref[i] = ip[6 + i];
-    inner_candidates(F, P, M, f, k, F.ft_st_rs[(long)f * kMaxRows + k], ip[5], ref, I,
-                     F.ft_z0[f], shift_side(F, f), F.ft_zsh[f]);
+    const int rs = F.ft_st_rs[(long)f * kMaxRows + k];
+    inner_candidates(F, P, M, f, k, rs, ip[5], ref, I, F.ft_z0[f],
+                     row_shift(rs / P.n_rows, shift_side(F, f), F.ft_zsh[f], P));
   }
 }
 
