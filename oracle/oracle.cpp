@@ -1294,6 +1294,7 @@ struct FitTrack {
                            // their candidate slots follow the stations' in ncand/cand/cchi
   int n_out = 0;           // Phase III: rows extrapolated above the outermost station; their
                            // slots follow the ext_rows inward ones
+  std::vector<int> ext_sec;  // sector of each extrapolated row (inward e, then ext_rows + e)
   bool ok = true;
   int fail_at = -1;        // diagnostics: 100*iteration + station of a failed step
   Track<Real> out{};
@@ -1390,37 +1391,56 @@ void ext_row_candidates(const Frame<Real>& F, const Params<Real>& P, const MapR<
   }
 }
 
+// One row step of the Phase III extrapolation, also over sector boundaries
+// (Sec. 3): to row r in the current sector; beyond the sector's edge there
+// (|y| > x tan 10 deg) the track continues in the neighbouring sector of the
+// same side on that edge (rotation, then the row's x in the new frame), and
+// stops if it still lies beyond that sector's edge plus edge_margin.
+template <typename Real>
+bool ext_step(Lin<Real>& E, int& sec, int r, const Params<Real>& P) {
+  if (!lin_goto(E, sec, P.row_x[r], P)) return false;
+  if (o_fabs(E.t.p[0]) > E.t.x * P.tan_half) {
+    const int half = P.n_sectors / 2;
+    const int base = sec - sec % half;
+    const int nsec = base + (sec % half + (E.t.p[0] > Real(0) ? 1 : half - 1)) % half;
+    if (!lin_goto(E, nsec, P.row_x[r], P)) return false;
+    sec = nsec;
+  }
+  return !(o_fabs(E.t.p[0]) > E.t.x * P.tan_half + P.edge_margin);
+}
+
 // Phase III (Sec. 3) inward: from the state after iteration 1 at the
-// innermost station, row by row over at most ext_rows rows below it in its
-// sector, stopping where the propagation fails or the track leaves the sector.
+// innermost station, row by row over at most ext_rows rows below it.
 template <typename Real>
 void extrapolate_inward(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
                         const std::vector<char>& fixed, FitTrack<Real>& T, Lin<Real> E) {
   const int ns = (int)T.st.size();
-  const int sec = T.st[0].sector, r_first = T.st[0].row;
+  int sec = T.st[0].sector;
+  const int r_first = T.st[0].row;
   T.n_ext = 0;
   for (int e = 0; e < P.ext_rows && r_first - 1 - e >= 0; ++e) {
     const int r = r_first - 1 - e;
-    if (!lin_goto(E, sec, P.row_x[r], P)) break;
-    if (o_fabs(E.t.p[0]) > E.t.x * P.tan_half + P.edge_margin) break;
+    if (!ext_step(E, sec, r, P)) break;
     ext_row_candidates(F, P, M, fixed, T, E, sec, r, (size_t)ns + e);
+    T.ext_sec[e] = sec;
     T.n_ext = e + 1;
   }
 }
 
 // Phase III outward: from the state after iteration 2 at the outermost
-// station, the same over at most ext_rows rows above it in its sector.
+// station, the same over at most ext_rows rows above it.
 template <typename Real>
 void extrapolate_outward(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& M,
                          const std::vector<char>& fixed, FitTrack<Real>& T, Lin<Real> E) {
   const int ns = (int)T.st.size();
-  const int sec = T.st[ns - 1].sector, r_last = T.st[ns - 1].row;
+  int sec = T.st[ns - 1].sector;
+  const int r_last = T.st[ns - 1].row;
   T.n_out = 0;
   for (int e = 0; e < P.ext_rows && r_last + 1 + e < P.n_rows; ++e) {
     const int r = r_last + 1 + e;
-    if (!lin_goto(E, sec, P.row_x[r], P)) break;
-    if (o_fabs(E.t.p[0]) > E.t.x * P.tan_half + P.edge_margin) break;
+    if (!ext_step(E, sec, r, P)) break;
     ext_row_candidates(F, P, M, fixed, T, E, sec, r, (size_t)ns + P.ext_rows + e);
+    T.ext_sec[P.ext_rows + e] = sec;
     T.n_out = e + 1;
   }
 }
@@ -1434,6 +1454,7 @@ void fit_iterations12(const Frame<Real>& F, const Params<Real>& P, const MapR<Re
   store.assign((size_t)ns * 5, Real(0));
   T.flag.assign(ns, 0);
   T.ncand.assign(nslot, 0);
+  T.ext_sec.assign(phase2 ? 2 * P.ext_rows : 0, -1);
   T.cand.assign((size_t)nslot * P.cand_k, -1);
   T.cchi.assign((size_t)nslot * P.cand_k, Real(0));
   Lin<Real> L;
@@ -1566,12 +1587,12 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
   std::vector<int> outc;
   if (T.n_out > 0) {
     const size_t o0 = (size_t)ns + P.ext_rows;
-    const int sec_out = T.st[ns - 1].sector;
     Lin<Real> E;
     E.t = start;
     for (int i = 0; i < 5; ++i) E.r[i] = detach(start.p[i]);
-    E.sector = sec_out;
+    E.sector = T.st[ns - 1].sector;
     for (int e = 0; e < T.n_out; ++e) {
+      const int sec_out = T.ext_sec[P.ext_rows + e];
       if (!lin_goto(E, sec_out, P.row_x[T.st[ns - 1].row + 1 + e], P)) break;
       const int c = T.assigned[o0 + e];
       if (c < 0) continue;
@@ -1598,7 +1619,7 @@ void fit_iteration3(const Frame<Real>& F, const Params<Real>& P, const MapR<Real
       const bool inner = phase2 && s.row < P.inner_rows;
       c = inner ? T.assigned[k] : (T.flag[k] ? -1 : s.cl);
     } else {
-      sector = T.st[0].sector;
+      sector = T.ext_sec[-1 - k];
       row = T.st[0].row + k;
       c = T.assigned[ns - 1 - k];
     }
@@ -2161,16 +2182,17 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   res.put("cand_assigned", cs_assigned, "i4");
   // Phase III candidates and assignments of every extrapolated row (inward
   // rows, then outward rows)
-  std::vector<int> ex_key, ex_row, ex_n, ex_cand, ex_assigned, fit_next, fit_nout;
+  std::vector<int> ex_key, ex_row, ex_sec, ex_n, ex_cand, ex_assigned, fit_next, fit_nout;
   std::vector<Real> ex_chi;
   for (auto& T : FT) {
     fit_next.push_back(T.ok ? T.n_ext : 0);
     fit_nout.push_back(T.ok ? T.n_out : 0);
     if (!T.ok) continue;
     const size_t ns = T.st.size();
-    auto put = [&](size_t slot, int row) {
+    auto put = [&](size_t slot, int row, int sector) {
       ex_key.push_back(T.key);
       ex_row.push_back(row);
+      ex_sec.push_back(sector);
       ex_n.push_back(T.ncand[slot]);
       for (int k = 0; k < P.cand_k; ++k) {
         ex_cand.push_back(T.cand[slot * P.cand_k + k]);
@@ -2178,13 +2200,15 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
       }
       ex_assigned.push_back(T.assigned[slot]);
     };
-    for (int e = 0; e < T.n_ext; ++e) put(ns + e, T.st[0].row - 1 - e);
-    for (int e = 0; e < T.n_out; ++e) put(ns + P.ext_rows + e, T.st[ns - 1].row + 1 + e);
+    for (int e = 0; e < T.n_ext; ++e) put(ns + e, T.st[0].row - 1 - e, T.ext_sec[e]);
+    for (int e = 0; e < T.n_out; ++e)
+      put(ns + P.ext_rows + e, T.st[ns - 1].row + 1 + e, T.ext_sec[P.ext_rows + e]);
   }
   res.put("fit_next", fit_next, "i4");
   res.put("fit_nout", fit_nout, "i4");
   res.put("ext_key", ex_key, "i4");
   res.put("ext_row", ex_row, "i4");
+  res.put("ext_sector", ex_sec, "i4");
   res.put("ext_n", ex_n, "i4");
   res.put("ext_ids", ex_cand, "i4");
   res.put("ext_chi2", ex_chi, real_name<Real>());

@@ -283,3 +283,32 @@ def test_outward_extrapolation_recovers_outer_segments():
     assert not np.any((base["attach"] >= 0) & (att < 0))
     # outward candidate rows lie above the track's outermost station
     assert np.any(ext["fit_nout"] > 0)
+
+
+def test_extrapolation_continues_into_the_neighbouring_sector():
+    """Phase III over sector boundaries (Sec. 3): a track whose extrapolation
+    leaves its sector through an edge continues in the neighbouring sector of
+    the same side.  On a complete event the clusters attached only through the
+    extrapolation belong to the track's own particle, and many of them lie in
+    a sector that holds none of the track's other clusters."""
+    f = synth.generate("central_event", n_primaries=2500)
+    lab = f.label
+    base = oracle.track(f.y, f.z, f.row, f.sector, RX.astype(np.float32), opts(), full=True)
+    ext = oracle.track(f.y, f.z, f.row, f.sector, RX.astype(np.float32), opts(ext_rows=20), full=True)
+    tr = tracks_of(ext)
+    tlab = np.array([majority(lab[h])[0] for h in tr])
+    att = ext["attach"]
+    new = np.nonzero((base["attach"] < 0) & (att >= 0))[0]
+    assert len(new) > 1000
+    assert np.mean(tlab[att[new]] != lab[new]) < 0.01
+    newset = set(new.tolist())
+    other = 0
+    for c in new:
+        own = {int(f.sector[k]) for k in tr[att[c]] if int(k) not in newset}
+        other += int(f.sector[c]) not in own
+    assert other > 100, other
+    # the extrapolation stays on the track's side of the central electrode
+    side = {int(k): int(f.sector[h[0]]) // 18 for k, h in zip(ext["trk_key"], tr)}
+    rows = [j for j in range(len(ext["ext_key"])) if int(ext["ext_key"][j]) in side]
+    assert rows and all(int(ext["ext_sector"][j]) // 18 == side[int(ext["ext_key"][j])]
+                        for j in rows)
