@@ -367,6 +367,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ft_newly, FT * NS);
   ok &= dalloc(ctx, &F.ft_next, FT);
   ok &= dalloc(ctx, &F.ft_nout, FT);
+  ok &= dalloc(ctx, &F.ft_ext_sec, FT * (opt->ext_rows > 0 ? 2 * opt->ext_rows : 1));
   ok &= dalloc(ctx, &F.ft_ipol, FT * kMaxInner * kIpolF);
   ok &= dalloc(ctx, &F.ft_fixed, n);
   ok &= dalloc(ctx, &F.bid, n);
@@ -959,6 +960,7 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   else if (w == "ft_assigned") { src = F.ft_assigned; nb = 4L * F.nslot * nft; }
   else if (w == "ft_next") { src = F.ft_next; nb = 4L * nft; }
   else if (w == "ft_nout") { src = F.ft_nout; nb = 4L * nft; }
+  else if (w == "ft_ext_sec") { src = F.ft_ext_sec; nb = 2L * 2 * ctx->P.ext_rows * nft; }
   else if (w == "ft_n") { src = F.ft_n; nb = 4L * nft; }
   else if (w == "out_par") { src = F.out_par; nb = 4L * 5 * c.n_out; }
   else if (w == "out_cov") { src = F.out_cov; nb = 4L * 15 * c.n_out; }

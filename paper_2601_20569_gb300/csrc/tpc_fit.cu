@@ -887,6 +887,24 @@ __global__ void k_fit_stations(FrameDev F, KParams P) {
 // each carries only its own iteration's code and registers.
 enum : int { kFitIdle = 0, kFitIn, kFitExt };
 
+// One row step of the Phase III extrapolation, also over sector boundaries
+// (Sec. 3): to row r in sector sec; beyond the sector's edge there (|y| >
+// x tan 10 deg) the track continues in the neighbouring sector of the same
+// side on that edge (rotation, then the row's x in the new frame), and stops
+// if it still lies beyond that sector's edge plus edge_margin.
+__device__ __forceinline__ bool ext_step(Lin& L, int& sec, int r, const float* rx,
+                                         const KParams& P) {
+  if (!lin_goto(L, sec, rx[r], P)) return false;
+  if (fabsf(L.t.p[0]) > L.t.x * P.tan_half) {
+    const int half = P.n_phi;
+    const int base = sec - sec % half;
+    const int nsec = base + (sec % half + (L.t.p[0] > 0.0f ? 1 : half - 1)) % half;
+    if (!lin_goto(L, nsec, rx[r], P)) return false;
+    sec = nsec;
+  }
+  return !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
+}
+
 // Tracks merged across the central electrode: the measured z of a cluster of
 // sector sec in the frame of the track's first side (zside: the side whose
 // clusters take the shift zsh, -1 for a track on one side), and the window
@@ -1038,6 +1056,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
   float z0 = 0.0f;
   int zside = -1;   // central-electrode merging: side whose z takes zsh
   float zsh = 0.0f;
+  int xsec = 0;     // sector of the extrapolation
   const int* SC = nullptr;
   const uint16_t* SR = nullptr;
   float* store = nullptr;
@@ -1067,14 +1086,13 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
     if (phase == kFitExt) {
       // Phase III: one row of the inward extrapolation below the innermost
       // station (k counts the rows done)
-      const int rs0 = SR[0];
-      const int r = rs0 % NR - 1 - k;
+      const int r = SR[0] % NR - 1 - k;
       bool go = k < P.ext_rows && r >= 0;
-      if (go) go = lin_goto(L, rs0 / NR, rx[r], P);
-      if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
+      if (go) go = ext_step(L, xsec, r, rx, P);
       if (go) {
-        ext_candidates(F, P, M, f, kMaxInner + k, rs0 - rs0 % NR + r, L, z0,
-                       row_shift(rs0 / NR, zside, zsh, P));
+        ext_candidates(F, P, M, f, kMaxInner + k, xsec * NR + r, L, z0,
+                       row_shift(xsec, zside, zsh, P));
+        F.ft_ext_sec[(long)f * 2 * P.ext_rows + k] = (uint16_t)xsec;
         ++k;
       } else {
         F.ft_next[f] = k;
@@ -1117,6 +1135,7 @@ __global__ void __launch_bounds__(256, 2) k_fit1(FrameDev F, KParams P, MapDev M
       put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
       if (P.ext_rows > 0) {
         k = 0;
+        xsec = SR[0] / NR;
         phase = kFitExt;
       } else {
         F.ft_ok[f] = 1;
@@ -1146,6 +1165,7 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
   float z0 = 0.0f;
   int zside = -1;   // central-electrode merging: side whose z takes zsh
   float zsh = 0.0f;
+  int xsec = 0;     // sector of the extrapolation
   const int* SC = nullptr;
   const uint16_t* SR = nullptr;
   const float* store = nullptr;
@@ -1176,14 +1196,13 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
     if (phase == kFit2Out) {
       // Phase III: one row of the outward extrapolation above the outermost
       // station (k counts the rows done)
-      const int rsl = SR[ns - 1];
-      const int r = rsl % NR + 1 + k;
+      const int r = SR[ns - 1] % NR + 1 + k;
       bool go = k < P.ext_rows && r < NR;
-      if (go) go = lin_goto(L, rsl / NR, rx[r], P);
-      if (go) go = !(fabsf(L.t.p[0]) > L.t.x * P.tan_half + P.edge_margin);
+      if (go) go = ext_step(L, xsec, r, rx, P);
       if (go) {
-        ext_candidates(F, P, M, f, kMaxInner + P.ext_rows + k, rsl - rsl % NR + r, L, z0,
-                       row_shift(rsl / NR, zside, zsh, P));
+        ext_candidates(F, P, M, f, kMaxInner + P.ext_rows + k, xsec * NR + r, L, z0,
+                       row_shift(xsec, zside, zsh, P));
+        F.ft_ext_sec[(long)f * 2 * P.ext_rows + P.ext_rows + k] = (uint16_t)xsec;
         ++k;
       } else {
         F.ft_nout[f] = k;
@@ -1242,6 +1261,7 @@ __global__ void __launch_bounds__(256, 2) k_fit2(FrameDev F, KParams P, MapDev M
     if (++k == ns) {
       put_state(F.ft_end2 + (long)f * kStateF, L.t, L.sector);
       k = 0;
+      xsec = SR[ns - 1] / NR;
       phase = P.ext_rows > 0 ? kFit2Out : kFit2Idle;
     }
   }
@@ -1395,13 +1415,15 @@ __global__ void __launch_bounds__(256, 2) k_fit3(FrameDev F, KParams P, MapDev M
       for (int i = 0; i < 5; ++i) E.r[i] = s2.p[i];
       E.sector = secl;
       const long o0 = (long)f * F.nslot + kMaxInner + P.ext_rows;
+      const uint16_t* xs = F.ft_ext_sec + (long)f * 2 * P.ext_rows + P.ext_rows;
       for (int e = 0; e < nout; ++e) {
-        if (!lin_goto(E, secl, rx[rl + 1 + e], P)) break;
+        const int sx = xs[e];
+        if (!lin_goto(E, sx, rx[rl + 1 + e], P)) break;
         const int c = F.ft_assigned[o0 + e];
         if (c < 0) continue;
         const float2 pc = F.syz[c];
         float my, mz;
-        if (!corrected(M, P, secl, E.t.x, pc.x, track_z(pc.y, secl, zside, zsh, P), z0, E.r, my,
+        if (!corrected(M, P, sx, E.t.x, pc.x, track_z(pc.y, sx, zside, zsh, P), z0, E.r, my,
                        mz))
           continue;
         const Resid R = residual(E.t, my, mz, P);
@@ -1432,7 +1454,7 @@ __global__ void __launch_bounds__(256, 2) k_fit3(FrameDev F, KParams P, MapDev M
         const bool inner = row < P.inner_rows;
         c = inner ? F.ft_assigned[(long)f * F.nslot + k] : (flag[k] ? -1 : SC[k]);
       } else {
-        sec = rs0 / NR;
+        sec = F.ft_ext_sec[(long)f * 2 * P.ext_rows - 1 - k];
         row = rs0 % NR + k;
         c = F.ft_assigned[(long)f * F.nslot + kMaxInner - 1 - k];
       }

@@ -258,6 +258,8 @@ struct FrameDev {
   uint8_t* ft_newly;       // [cap_ft][nslot]
   int* ft_next;            // [cap_ft] rows extrapolated below the innermost station
   int* ft_nout;            // [cap_ft] rows extrapolated above the outermost station
+  uint16_t* ft_ext_sec;    // [cap_ft][2 ext_rows] sector of each extrapolated row (inward,
+                           // then outward): the extrapolation may cross a sector edge
   float* ft_ipol;          // [cap_ft][kMaxInner][kIpolF] iteration-2 interpolation at inner
                            // stations (y, z, Cyy, Cyz, Czz, x, reference p[5]) for k_inner_cand
   uint8_t* ft_fixed;       // [n] sorted cluster held by a station outside the inner region

@@ -182,7 +182,7 @@ _DBG_DTYPE = {
     "st_ie": np.float32, "st_oe": np.float32, "ft_key": np.int32, "ft_ok": np.int32,
     "ft_nst": np.int32, "ft_st_cl": np.int32, "ft_st_rs": np.uint16, "ft_flag": np.uint8,
     "ft_ncand": np.uint8, "ft_cand": np.int32, "ft_cchi": np.float32, "ft_assigned": np.int32,
-    "ft_n": np.int32, "ft_next": np.int32, "ft_nout": np.int32, "out_par": np.float32, "out_cov": np.float32, "out_chi2": np.float32,
+    "ft_n": np.int32, "ft_next": np.int32, "ft_nout": np.int32, "ft_ext_sec": np.uint16, "out_par": np.float32, "out_cov": np.float32, "out_chi2": np.float32,
     "out_x": np.float32, "out_ndf": np.int32, "out_sector": np.int32, "out_ncl": np.int32,
     "out_offset": np.int32, "out_ids": np.int32, "out_key": np.int32, "attach": np.int32,
 }

@@ -97,16 +97,17 @@ def compare_full(tr, f, opts, dist_map=None):
         assert np.array_equal(np.sort(nxt[fok == 1]), np.sort(ref["fit_next"][ok_ref]))
         assert np.array_equal(np.sort(nout[fok == 1]), np.sort(ref["fit_nout"][ok_ref]))
         E = opts["ext_rows"]
+        xsec = tr.debug("ft_ext_sec").reshape(-1, 2 * E)
         gpu_e = {}
         for t in np.nonzero(fok == 1)[0]:
             r0 = rs[t, 0] % 152
             rl = rs[t, nst[t] - 1] % 152
-            rows = [(32 + e, r0 - 1 - e) for e in range(nxt[t])] + \
-                   [(32 + E + e, rl + 1 + e) for e in range(nout[t])]
-            for s_, r_ in rows:
+            rows = [(32 + e, r0 - 1 - e, e) for e in range(nxt[t])] + \
+                   [(32 + E + e, rl + 1 + e, E + e) for e in range(nout[t])]
+            for s_, r_, j_ in rows:
                 ids = sid[cand[t, s_, :nc[t, s_]]]
                 a = sid[asg[t, s_]] if asg[t, s_] >= 0 else -1
-                gpu_e[(int(fk[t]), int(r_))] = (ids.tolist(),
+                gpu_e[(int(fk[t]), int(r_))] = (int(xsec[t, j_]), ids.tolist(),
                                                 bits(cchi[t, s_, :nc[t, s_]]).tolist(), a)
         ref_e = {}
         ec = ref["ext_ids"].reshape(-1, K)
@@ -114,7 +115,8 @@ def compare_full(tr, f, opts, dist_map=None):
         for i in range(len(ref["ext_key"])):
             n = ref["ext_n"][i]
             ref_e[(int(ref["ext_key"][i]), int(ref["ext_row"][i]))] = (
-                ec[i, :n].tolist(), bits(ex[i, :n]).tolist(), int(ref["ext_assigned"][i]))
+                int(ref["ext_sector"][i]), ec[i, :n].tolist(), bits(ex[i, :n]).tolist(),
+                int(ref["ext_assigned"][i]))
         assert gpu_e == ref_e
     # a11: output tracks by key, bit-exact
     g = gpu_tracks(tr)
