@@ -9,8 +9,8 @@ values; the defaults below are this library's readings of it:
   pad rows (Sec. 2 and Sec. 4 both single out rows below 20);
 * Phase II candidate depth (tracks may fall back to their k-th candidate) = 4;
 * Phase III (Sec. 3): tracks are extrapolated over at most ``ext_rows`` rows
-  below their innermost and above their outermost cluster, with a candidate cut
-  of chi2 < 9
+  below their innermost and above their outermost cluster, into the
+  neighbouring sector where they leave theirs, with a candidate cut of chi2 < 9
   (stricter than the interpolation cut of 25); off by default, as the paper
   describes it as work in progress;
 * seeding iterations on leftover clusters (Sec. 3): ``seed_iters`` sector-
