@@ -263,7 +263,8 @@ def correct(sector, x, y, z, z0, ref, row_x, opts, dist_map):
 
 class _TracksIn(ctypes.Structure):
     _fields_ = [("n_tracks", ctypes.c_long), ("offset", ctypes.c_void_p), ("ids", ctypes.c_void_p),
-                ("par", ctypes.c_void_p), ("x", ctypes.c_void_p), ("sector", ctypes.c_void_p)]
+                ("par", ctypes.c_void_p), ("x", ctypes.c_void_p), ("sector", ctypes.c_void_p),
+                ("zshift", ctypes.c_void_p)]
 
 
 class _Frozen(ctypes.Structure):
@@ -273,7 +274,9 @@ class _Frozen(ctypes.Structure):
 def refit(y, z, row, sector, row_x, opts: dict, tracks: dict, *, dist_map=None, frozen=None,
           weights=None, mode: str = "f64") -> Result:
     """Refit tracks with fixed cluster lists (a12).  ``tracks``: offset, ids
-    (innermost first), par [n,5] and x, sector of the start parameters.
+    (innermost first), par [n,5] and x, sector of the start parameters, and
+    optionally z_shift [n] (tracks merged across the central electrode: shift
+    of the measured z on the side other than the innermost cluster's).
     ``frozen``: the frz_* arrays of a previous call (references and decisions
     held fixed).  mode: "f32", "f64" or "tape" (FP64 plus the gradient of
     sum w_t chi2_t with respect to the map coefficients, key "grad")."""
@@ -295,8 +298,11 @@ def refit(y, z, row, sector, row_x, opts: dict, tracks: dict, *, dist_map=None, 
     tx = np.ascontiguousarray(tracks["x"], dtype=np.float64)
     ts = np.ascontiguousarray(tracks["sector"], dtype=np.int32)
     nt = len(off) - 1
+    zsh = None
+    if tracks.get("z_shift") is not None:
+        zsh = np.ascontiguousarray(tracks["z_shift"], dtype=np.float64)
     T = _TracksIn(nt, off.ctypes.data, ids.ctypes.data, par.ctypes.data, tx.ctypes.data,
-                  ts.ctypes.data)
+                  ts.ctypes.data, zsh.ctypes.data if zsh is not None else None)
     w = np.ascontiguousarray(np.ones(nt) if weights is None else weights, dtype=np.float64)
     keep = []
     fz = None
@@ -324,6 +330,9 @@ def refit(y, z, row, sector, row_x, opts: dict, tracks: dict, *, dist_map=None, 
 def tracks_for_refit(res: Result, fp64: bool = True) -> dict:
     """Refit input built from an oracle full-chain result (start = final params)."""
     n = len(res["trk_key"])
-    return {"offset": res["trk_offset"], "ids": res["trk_ids"],
-            "par": res["trk_param"].reshape(n, 5).astype(np.float64),
-            "x": res["trk_x"].astype(np.float64), "sector": res["trk_sector"]}
+    out = {"offset": res["trk_offset"], "ids": res["trk_ids"],
+           "par": res["trk_param"].reshape(n, 5).astype(np.float64),
+           "x": res["trk_x"].astype(np.float64), "sector": res["trk_sector"]}
+    if "trk_zshift" in res:
+        out["z_shift"] = res["trk_zshift"].astype(np.float64)
+    return out

@@ -1713,6 +1713,8 @@ struct RefitIO {
   int n = 0;
   Track<Real> out{};
   int out_sector = 0;
+  Real zshift = Real(0);  // z shift of the clusters on the side other than side0's
+  int side0 = 0;          // side of the innermost cluster
 };
 
 template <typename Real>
@@ -1734,6 +1736,11 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
   if (ns < 1) return;
   const int half = P.n_sectors / 2;
   const Real z0 = R.in_p[1] - R.in_p[3] * o_sqrt(R.in_x * R.in_x + R.in_p[0] * R.in_p[0]);
+  // measured z of a station's cluster in the frame of the innermost cluster's side
+  auto zof = [&](const Station<Real>& s) {
+    return R.zshift != Real(0) && (s.sector / half) % 2 != R.side0 ? F.z[s.cl] + R.zshift
+                                                                    : F.z[s.cl];
+  };
   // start of iteration 1: extended-Kalman pass outward, uncorrected clusters
   Track<Real> t;
   for (int i = 0; i < 5; ++i) t.p[i] = R.in_p[i];
@@ -1743,13 +1750,14 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
   for (int k = 0; k < ns; ++k) {
     const Station<Real>& s = R.st[k];
     if (s.sector != sec) {
+      // ds == 0: the same azimuthal sector across the central electrode
       const int ds = ((s.sector % half) - (sec % half) + half) % half;
-      if (ds != 1 && ds != half - 1) return;
-      if (!rotate(t, ds == 1 ? 1 : -1, P, P.fit_max_snp)) return;
+      if (ds != 0 && ds != 1 && ds != half - 1) return;
+      if (ds != 0 && !rotate(t, ds == 1 ? 1 : -1, P, P.fit_max_snp)) return;
       sec = s.sector;
     }
     if (!propagate(t, P.row_x[s.row], P, P.fit_max_snp)) return;
-    update(t, residual(t, F.y[s.cl], F.z[s.cl], P));
+    update(t, residual(t, F.y[s.cl], zof(s), P));
   }
   // iteration 1: inward, predictions stored
   std::vector<Real> store((size_t)ns * 5);
@@ -1761,7 +1769,7 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
     Real* sv = &store[(size_t)k * 5];
     sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
     Real my, mz;
-    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) return;
+    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], zof(s), z0, L.r, my, mz)) return;
     fit_update(L.t, residual(L.t, my, mz, P), P);
   }
   // iteration 2: outward, interpolation flags
@@ -1779,7 +1787,7 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
     const Real a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
     const Interp<Real> I = interpolate(a, &store[(size_t)k * 5]);
     Real my, mz;
-    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) return;
+    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], zof(s), z0, L.r, my, mz)) return;
     if (!frozen) R.flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
     fit_update(L.t, residual(L.t, my, mz, P), P);
   }
@@ -1797,7 +1805,7 @@ void refit_track(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>& 
     if (k != ns - 1 && !lin_goto(L, s.sector, P.row_x[s.row], P)) break;
     if (R.flag[k]) continue;
     Real my, mz;
-    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], F.z[s.cl], z0, L.r, my, mz)) continue;
+    if (!corrected(M, P, s.sector, L.t.x, F.y[s.cl], zof(s), z0, L.r, my, mz)) continue;
     const Resid<Real> Rs = residual(L.t, my, mz, P);
     const bool accept = frozen ? R.acc[k] != 0 : !(Rs.chi2 > P.final_chi2);
     if (!frozen) R.acc[k] = accept ? 1 : 0;
@@ -2344,6 +2352,8 @@ struct orc_tracks_in {
   const double* par;      // [n_tracks][5]
   const double* x;
   const int32_t* sector;
+  const double* zshift;   // [n_tracks] z shift of the far side (merged across the central
+                          // electrode), or NULL for none
 };
 // Frozen references and decisions of a previous refit (optional).
 struct orc_frozen {
@@ -2380,6 +2390,8 @@ static void refit_impl(long n, const float* y, const float* z, const uint8_t* ro
     for (int i = 0; i < 5; ++i) R.in_p[i] = Real(T->par[t * 5 + i]);
     R.in_x = Real(T->x[t]);
     R.in_sector = T->sector[t];
+    R.zshift = T->zshift ? Real(T->zshift[t]) : Real(0);
+    if (!R.st.empty()) R.side0 = (R.st[0].sector / (P.n_sectors / 2)) % 2;
     const bool frozen = frz != nullptr;
     if (frozen) {
       for (int i = 0; i < 5; ++i) {

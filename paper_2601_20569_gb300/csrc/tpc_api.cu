@@ -749,6 +749,7 @@ tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* cl, const tpc_tracks* in,
     bool ok = true;
     ok &= dalloc(ctx, &R.ref, T * 10);
     ok &= dalloc(ctx, &R.flag, NR);
+    ok &= dalloc(ctx, &R.zref, NR);
     ok &= dalloc(ctx, &R.acc, NR);
     ok &= dalloc(ctx, &R.z0, T);
     ok &= dalloc(ctx, &R.ckpt, T * 3 * kCkptSeg * kCkptF);
@@ -780,6 +781,7 @@ tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* cl, const tpc_tracks* in,
   R.in_par = in->params;
   R.in_x = in->x;
   R.in_sector = in->sector;
+  R.in_zsh = in->z_shift;
   R.row_x = F.row_x;
   R.freeze = freeze ? 1 : 0;
   R.map = make_mapdev(mp);
@@ -805,6 +807,7 @@ tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* cl, const tpc_tracks* in,
   out->cl_ids = in->cl_ids;
   out->key = in->key;
   out->attach = in->attach;
+  out->z_shift = in->z_shift;
   return TPC_OK;
 }
 

@@ -1603,6 +1603,14 @@ __global__ void k_out_attach(FrameDev F, KParams P) {
 }
 
 // ------------------------------------------- a12 refit with fixed clusters
+// Tracks merged across the central electrode carry the shift of their far
+// side (in_zsh): zsh and the side whose clusters take it (zside, -1: none;
+// the other side than the innermost cluster's), for track_z.
+__device__ __forceinline__ void refit_shift(const RefitDev& R, const KParams& P, int t,
+                                            float& zsh, int& zside) {
+  zsh = R.in_zsh ? R.in_zsh[t] : 0.0f;
+  zside = zsh != 0.0f ? 1 - ((R.sector[R.ids[R.offset[t]]] / P.n_phi) & 1) : -1;
+}
 __device__ __forceinline__ void save_ckpt(float* d, const Lin& L) {
 #pragma unroll
   for (int i = 0; i < 5; ++i) d[i] = L.t.p[i];
@@ -1655,6 +1663,13 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
     const float inx = R.in_x[t];
     const float z0 = ip[1] - ip[3] * sqrtf(inx * inx + ip[0] * ip[0]);
     R.z0[t] = z0;
+    float* zr = R.zref + o0;  // each cluster's z in the innermost side's frame
+    {
+      float zsh;
+      int zside;
+      refit_shift(R, P, t, zsh, zside);
+      for (int k = 0; k < ns; ++k) zr[k] = track_z(R.z[ids[k]], R.sector[ids[k]], zside, zsh, P);
+    }
     Trk<float> t0;
 #pragma unroll
     for (int i = 0; i < 5; ++i) t0.p[i] = ip[i];
@@ -1667,14 +1682,16 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
       const int s = R.sector[c];
       if (s != sec) {
         const int ds = ((s % half) - (sec % half) + half) % half;
-        if ((ds != 1 && ds != half - 1) || !rotate(t0, ds == 1 ? 1 : -1, P, P.fit_max_snp)) {
+        // ds == 0: the same azimuthal sector across the central electrode
+        if ((ds != 0 && ds != 1 && ds != half - 1) ||
+            (ds != 0 && !rotate(t0, ds == 1 ? 1 : -1, P, P.fit_max_snp))) {
           ok = false;
           break;
         }
         sec = s;
       }
       if (!propagate(t0, R.row_x[R.row[c]], P, P.fit_max_snp)) { ok = false; break; }
-      update(t0, residual(t0, R.y[c], R.z[c], P));
+      update(t0, residual(t0, R.y[c], zr[k], P));
     }
     if (!ok) continue;
     float* store = R.store + (long)t * kMaxRows * 5;
@@ -1691,7 +1708,10 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
       float* sv = store + k * 5;
       sv[0] = L.t.p[0]; sv[1] = L.t.p[1]; sv[2] = L.t.c[0]; sv[3] = L.t.c[1]; sv[4] = L.t.c[2];
       float my, mz;
-      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) { ok = false; break; }
+      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], zr[k], z0, L.r, my, mz)) {
+        ok = false;
+        break;
+      }
       fit_update(L.t, residual(L.t, my, mz, P), P);
     }
     if (!ok) continue;
@@ -1708,7 +1728,10 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
       const float a[5] = {L.t.p[0], L.t.p[1], L.t.c[0], L.t.c[1], L.t.c[2]};
       const Interp I = interpolate(a, store + k * 5);
       float my, mz;
-      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) { ok = false; break; }
+      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], zr[k], z0, L.r, my, mz)) {
+        ok = false;
+        break;
+      }
       if (!R.freeze) flag[k] = chi2_interp(I, my, mz, P) > P.int_chi2 ? 1 : 0;
       fit_update(L.t, residual(L.t, my, mz, P), P);
     }
@@ -1730,7 +1753,8 @@ __global__ void __launch_bounds__(128) k_refit(RefitDev R, KParams P, int* steps
       if (j != 0 && !lin_goto(L, R.sector[c], R.row_x[R.row[c]], P)) break;
       if (flag[k]) continue;
       float my, mz;
-      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], R.z[c], z0, L.r, my, mz)) continue;
+      if (!corrected(M, P, R.sector[c], L.t.x, R.y[c], zr[k], z0, L.r, my, mz))
+        continue;
       const Resid Rs = residual(L.t, my, mz, P);
       const bool accept = R.freeze ? acc[k] != 0 : !(Rs.chi2 > P.final_chi2);
       if (!R.freeze) acc[k] = accept ? 1 : 0;
@@ -1768,8 +1792,8 @@ struct StepRec {
 // recording the Jacobians, gain and residual.  Returns false when the
 // forward pass stopped at this step.
 __device__ __forceinline__ bool replay_step(const RefitDev& R, const KParams& P, int t, int it,
-                                            int j, int ns, const int* ids, float z0, Lin& L,
-                                            StepRec& S) {
+                                            int j, int ns, const int* ids, const float* zr,
+                                            float z0, Lin& L, StepRec& S) {
   const int k = it == 1 ? j : ns - 1 - j;
   const int c = ids[k];
   S.bits = 0;
@@ -1786,8 +1810,9 @@ __device__ __forceinline__ bool replay_step(const RefitDev& R, const KParams& P,
   if (it == 2 && R.flag[R.offset[t] + k]) return true;
   // measurement with its derivative by the x displacement
   float D[3];
-  map_eval(R.map, P, R.sector[c], L.t.x, R.y[c], R.z[c] - z0, D);
-  float my = R.y[c] + D[1], mz = R.z[c] + D[2];
+  const float zc = zr[k];
+  map_eval(R.map, P, R.sector[c], L.t.x, R.y[c], zc - z0, D);
+  float my = R.y[c] + D[1], mz = zc + D[2];
   float snp1 = L.r[2];
   if (D[0] != 0.0f) {
     StepJ st;
@@ -1837,6 +1862,7 @@ __global__ void __launch_bounds__(256) k_refit_adjoint(RefitDev R, KParams P,
     const int o0 = R.offset[t], ns = R.offset[t + 1] - o0;
     const int* ids = R.ids + o0;
     const float z0 = R.z0[t];
+    const float* zr = R.zref + o0;  // cluster z in the innermost side's frame (k_refit)
     float* dD = R.dD + (long)o0 * 3;
     for (int i = 0; i < 3 * ns; ++i) dD[i] = 0.0f;
     const float* ck = R.ckpt + (long)t * 3 * kCkptSeg * kCkptF;
@@ -1849,7 +1875,8 @@ __global__ void __launch_bounds__(256) k_refit_adjoint(RefitDev R, KParams P,
         StepRec rec[kCkptStride];
         Lin L;
         load_ckpt(ck + (it * kCkptSeg + sg) * kCkptF, L);
-        for (int j = j0; j < j1; ++j) replay_step(R, P, t, it, j, ns, ids, z0, L, rec[j - j0]);
+        for (int j = j0; j < j1; ++j)
+          replay_step(R, P, t, it, j, ns, ids, zr, z0, L, rec[j - j0]);
         for (int j = j1 - 1; j >= j0; --j) {
           const StepRec& S = rec[j - j0];
           const int k = it == 1 ? j : ns - 1 - j;
@@ -1890,7 +1917,7 @@ __global__ void __launch_bounds__(256) k_refit_adjoint(RefitDev R, KParams P,
       for (int k = 0; k < ns; ++k) {
         const int c = ids[k];
         const SplinePt sp =
-            spline_point(M, P, R.sector[c], R.row_x[R.row[c]], R.y[c], R.z[c] - z0);
+            spline_point(M, P, R.sector[c], R.row_x[R.row[c]], R.y[c], zr[k] - z0);
         int pidx[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) pidx[e] = phi_index(sp.ip, e, M.nphi);

@@ -308,11 +308,13 @@ struct RefitDev {
   const float* in_par;     // [n_tracks][5]
   const float* in_x;
   const int* in_sector;
+  const float* in_zsh;     // [n_tracks] z shift of the far side (central electrode), or NULL
   const float* row_x;
   int freeze;
   // state kept for freezing and for the adjoint
   float* ref;              // [cap][10]
   uint8_t* flag;           // [cap_refs]
+  float* zref;             // [cap_refs] cluster z in the frame of the track's innermost side
   uint8_t* acc;            // [cap_refs]
   float* z0;               // [cap]
   float* ckpt;             // [cap][3][kCkptSeg][kCkptF]

@@ -416,6 +416,8 @@ class Tracker:
         tin.sector = keep["sector"].data_ptr()
         tin.cl_offset = keep["cl_offset"].data_ptr()
         tin.cl_ids = keep["cl_ids"].data_ptr()
+        if "z_shift" in keep:  # tracks merged across the central electrode
+            tin.z_shift = keep["z_shift"].data_ptr()
         mp = None
         if coeff is not None:
             nz, nr, nphi = coeff.shape[1:]

@@ -206,3 +206,30 @@ def test_full_size_frame_sampled_gradient():
           f"components: median {np.median(rel):.2e}")
     assert err < 1e-2, err
     assert np.median(rel) < 2e-3
+
+
+def test_refit_of_tracks_merged_across_the_electrode():
+    """Tracks merged across the central electrode in a continuous-readout frame
+    carry the far side's z shift; the refit applies it (strict parity with the
+    oracle refit given the same shifts)."""
+    from paper_2601_20569_gb300 import tpc
+
+    f = synth.generate("timeframe", mean_collisions=4, vz_sigma=10.0)
+    opts = TrackerOptions(ac_merge=1).as_dict()
+    tr = tpc.Tracker(RX, opts, mode=0, cap_clusters=f.n)
+    dev = tr.to_device(f.y, f.z, f.q, f.row, f.sector)
+    tr.track(*dev)
+    res = {k: v.clone() for k, v in tr.result().items()}
+    zs = res["z_shift"].cpu().numpy()
+    assert np.count_nonzero(zs) >= 2
+    tracks = {k: res[k] for k in ("cl_offset", "cl_ids", "params", "x", "sector", "z_shift")}
+    out = tr.refit(dev, tracks)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    h = host_tracks(tracks)
+    h["z_shift"] = zs.astype(np.float64)
+    r = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, h, mode="f32")
+    ok = r["rf_ok"] == 1
+    assert ok[np.nonzero(zs)[0]].any()
+    assert np.array_equal(g["n_clusters"], r["rf_n"])
+    assert np.array_equal(bits(g["chi2"][ok]), bits(r["rf_chi2"][ok]))
+    assert np.array_equal(bits(g["params"][ok]), bits(r["rf_par"].reshape(-1, 5)[ok]))

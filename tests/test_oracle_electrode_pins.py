@@ -79,3 +79,30 @@ def test_far_side_shift_measures_the_collision_time():
         want = -2.0 * (1.0 if side0 == 0 else -1.0) * VD * t0[p]
         assert abs(want) > 100.0  # continuous readout: a large offset to recover
         assert abs(r["trk_zshift"][t] - want) < 0.5, (r["trk_zshift"][t], want)
+
+
+def test_refit_applies_the_far_side_shift():
+    """The refit of tracks merged across the electrode (continuous readout):
+    with the tracks' z shift the far side joins the fit (chi2/ndf of a track
+    of one side); without it the z step of 2 vd t0 breaks the fit."""
+    f = synth.generate("timeframe", mean_collisions=4, vz_sigma=10.0)
+    r = run(f, ac_merge=1)
+    sp = [t for t, _, _ in spanning(f, r)]
+    assert len(sp) >= 2
+    opts = TrackerOptions(ac_merge=1).as_dict()
+    tr = oracle.tracks_for_refit(r)
+    sel = {k: v for k, v in tr.items()}
+    with_shift = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, sel, mode="f32")
+    sel.pop("z_shift")
+    without = oracle.refit(f.y, f.z, f.row, f.sector, RX, opts, sel, mode="f32")
+    ok, chi = with_shift["rf_ok"], with_shift["rf_chi2"]
+    # the refit starts from the innermost parameters and cannot bridge every
+    # merged gap; the tracks it fits with the shift match the final fit's chi2
+    good = [t for t in sp if ok[t]]
+    assert good
+    for t in good:
+        assert chi[t] < 1.2 * r["trk_chi2"][t] + 10.0, (chi[t], r["trk_chi2"][t])
+        assert not without["rf_ok"][t] or without["rf_chi2"][t] > 10.0 * chi[t]
+    # tracks on one side are refitted identically either way
+    one = np.setdiff1d(np.arange(len(ok)), sp)
+    assert np.array_equal(with_shift["rf_chi2"][one], without["rf_chi2"][one])
