@@ -137,13 +137,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def replica_frame_ids(rank, frames):
+    """Frames of one replica: every rank tracks its own frames (weak scaling,
+    no data exchange between ranks)."""
+    return [rank * frames + k for k in range(frames)]
+
+
+def reduce_job(ms, n_local, world):
+    """Whole-job view of a timed region: the slowest rank's time and the
+    clusters all ranks processed (rank 0 reports their ratio)."""
+    if world <= 1:
+        return ms, n_local
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    n = torch.tensor([n_local], dtype=torch.int64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def make_frames(args, rank):
     from paper_2601_20569_gb300 import synth
 
     frames = []
-    for k in range(args.frames):
+    for fid in replica_frame_ids(rank, args.frames):
         kw = {"mean_collisions": args.collisions} if args.collisions > 0 else {}
-        frames.append(synth.generate(args.workload, frame=rank * args.frames + k, **kw))
+        frames.append(synth.generate(args.workload, frame=fid, **kw))
     return frames
 
 
@@ -419,14 +441,8 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n_per_step * world * args.steps / (ms / 1e3)
+    ms, n_job = reduce_job(ev0.elapsed_time(ev1), n_per_step, world)
+    value = n_job * args.steps / (ms / 1e3)
 
     note(f"timed region: {ms:.1f} ms")
     # the plain form on the same inputs: one call (one launch per stage) per frame
@@ -441,7 +457,8 @@ def main():
             plain.track(*d, stream=stream)
     p1.record(stream)
     torch.cuda.synchronize()
-    plain_value = n_per_step * world * args.steps / (p0.elapsed_time(p1) / 1e3)
+    pm, pn = reduce_job(p0.elapsed_time(p1), n_per_step, world)
+    plain_value = pn * args.steps / (pm / 1e3)
     plain.close()
 
     note("plain per-frame form timed")
@@ -494,8 +511,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     d2h = 4 * n_per_step
-    e2e_ms = e0.elapsed_time(e1)
-    e2e = {"value": n_per_step * world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+    e2e_ms, e2e_n = reduce_job(e0.elapsed_time(e1), n_per_step, world)
+    e2e = {"value": e2e_n * args.steps / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     note("end-to-end timed")
