@@ -31,6 +31,11 @@
 //   a9 three-iteration refit       (Sec. 3 Phase I interpolation scheme)
 //   a10 inner-region attachment    (Sec. 3 Phase II second ambiguity)
 //   a12 refit gradient             (FP64 reverse-mode tape)
+// and the optional parts, each behind an option that is off by default:
+//   seeding iterations on leftover clusters       (Sec. 3, seed_iters)
+//   merging across the central electrode          (Sec. 2 merging, Sec. 1 t0; ac_merge)
+//   extrapolation inward, outward, over sectors   (Sec. 3 Phase III; ext_rows)
+//   online cluster removal flags                  (Sec. 4; cr_mode)
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
