@@ -176,7 +176,11 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_t
  * the final cut) of the previous refit of the same tracks are reused, making
  * the chi2 a smooth function of the map (TPC_ERR_STATE otherwise).  out:
  * chi2, ndf, n_clusters and parameters of every input track (same order);
- * cl_offset/cl_ids/key/attach are passed through from `in`.  Synchronous.
+ * cl_offset/cl_ids/key/attach/z_shift are passed through from `in`.  in->z_shift
+ * may be NULL; where given (tracks merged across the central electrode), each
+ * track's clusters on the side other than its innermost cluster's enter the
+ * refit and the adjoint with their z plus the shift.  `in` and its arrays must
+ * stay valid until the matching tpc_refit_backward.  Synchronous.
  * Not in the paper: the differentiable form serves distortion calibration
  * (Sec. 2 names the space-charge correction maps as the limiting factor). */
 tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* clusters, const tpc_tracks* in,
