@@ -15,6 +15,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "liboracle.so")
+# A test may point the binding at a variant of the oracle built elsewhere
+# (tests/test_oracle_mutations.py plants mistakes to show that pins catch them).
+_VARIANT = os.environ.get("TPC_ORACLE_VARIANT_LIB")
 _lib = None
 
 _DT = {"i4": np.int32, "f4": np.float32, "f8": np.float64, "u8": np.uint64}
@@ -72,6 +75,8 @@ class _Opt(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so: strict IEEE evaluation (no contraction, no fast math)."""
+    if _VARIANT:
+        return _VARIANT
     src = os.path.join(_HERE, "oracle.cpp")
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(src):
         tmp = _LIB + f".tmp{os.getpid()}"
@@ -84,8 +89,7 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        lib = ctypes.CDLL(build())
         lib.orc_track.restype = ctypes.c_int
         lib.orc_track.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 5 + [
             ctypes.POINTER(_Opt), ctypes.c_void_p, ctypes.c_int, ctypes.c_int,

@@ -1,0 +1,55 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake in
+a copy of the oracle's source (a swapped comparison, a dropped term, a wrong
+factor or sign), builds it on the CPU, and runs the pin that must notice it
+against that copy; the pin has to fail.  The product is not involved."""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.cpp")
+
+CASES = [
+    # (what, original text, planted mistake, pin that must fail)
+    ("helix step: half-angle factor of the arc length",
+     "const Real u = kappa * chord * Real(0.5);", "const Real u = kappa * chord * Real(0.25);",
+     "tests/test_oracle_pins.py::test_propagation_matches_closed_form_helix_fp64"),
+    ("neighbour finding: worst instead of best pair",
+     "if (bu < 0 || d2 < best ||", "if (bu < 0 || d2 > best ||",
+     "tests/test_oracle_pins.py::test_neighbours_equal_brute_force_on_tiny_frames"),
+    ("selector: shared-cluster budget off by one",
+     "Real(shared + 1) <= P.shared_frac * Real(kept + 1)",
+     "Real(shared) <= P.shared_frac * Real(kept + 1)",
+     "tests/test_oracle_pins.py::test_selector_matches_greedy_restatement_and_budget"),
+    ("seeding iterations: start clusters of accepted tracklets left free",
+     "        F.used[TL[i].start] = 1;\n", "",
+     "tests/test_oracle_seeding_pins.py::test_second_iteration_equals_tracking_the_leftover_clusters"),
+    ("cluster removal: interpolation of the tube centre shifted by a row",
+     "const Real f = Real(r - rl) / Real(rh - rl);", "const Real f = Real(r - rl + 1) / Real(rh - rl);",
+     "tests/test_oracle_removal_pins.py::test_tubes_equal_all_pairs_scan"),
+    ("central electrode: sign of the far side's z shift",
+     "  dz = t.p[1] - B.ie.p[1];", "  dz = B.ie.p[1] - t.p[1];",
+     "tests/test_oracle_electrode_pins.py::test_far_side_shift_measures_the_collision_time"),
+]
+
+
+@pytest.mark.parametrize("what,orig,planted,pin", CASES, ids=[c[0] for c in CASES])
+def test_pin_catches_planted_mistake(tmp_path, what, orig, planted, pin):
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site of '{what}' not found once"
+    src = tmp_path / "oracle.cpp"
+    src.write_text(text.replace(orig, planted))
+    lib = tmp_path / "liboracle_variant.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", str(src), "-o", str(lib)])
+    env = dict(os.environ, TPC_ORACLE_VARIANT_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        pin], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pin did not catch '{what}':\n{r.stdout[-2000:]}"
