@@ -32,6 +32,18 @@ CASES = [
     ("cluster removal: interpolation of the tube centre shifted by a row",
      "const Real f = Real(r - rl) / Real(rh - rl);", "const Real f = Real(r - rl + 1) / Real(rh - rl);",
      "tests/test_oracle_removal_pins.py::test_tubes_equal_all_pairs_scan"),
+    ("Kalman update: cross term of the covariance update dropped",
+     "t.c[ci(i, j)] = t.c[ci(i, j)] - (k0[i] * h0[j] + k1[i] * h1[j]);",
+     "t.c[ci(i, j)] = t.c[ci(i, j)] - (k0[i] * h0[j]);",
+     "tests/test_oracle_pins.py::test_update_equals_information_form"),
+    ("B-spline: wrong coefficient in the second weight",
+     "w[1] = (Real(3) * f3 - Real(6) * f2 + Real(4)) / Real(6);",
+     "w[1] = (Real(3) * f3 - Real(6) * f2 + Real(3)) / Real(6);",
+     "tests/test_oracle_fit_pins.py::test_spline_partition_of_unity_and_linear_reproduction"),
+    ("merging: rotation into the neighbouring sector with the wrong sense",
+     "if (ds == 1 && !rotate(t, 1, P, P.fit_max_snp)) return false;",
+     "if (ds == 1 && !rotate(t, -1, P, P.fit_max_snp)) return false;",
+     "tests/test_oracle_fit_pins.py::test_merging_restores_sector_crossing_tracks"),
     ("central electrode: sign of the far side's z shift",
      "  dz = t.p[1] - B.ie.p[1];", "  dz = B.ie.p[1] - t.p[1];",
      "tests/test_oracle_electrode_pins.py::test_far_side_shift_measures_the_collision_time"),
