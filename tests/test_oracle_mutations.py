@@ -36,6 +36,9 @@ CASES = [
      "t.c[ci(i, j)] = t.c[ci(i, j)] - (k0[i] * h0[j] + k1[i] * h1[j]);",
      "t.c[ci(i, j)] = t.c[ci(i, j)] - (k0[i] * h0[j]);",
      "tests/test_oracle_pins.py::test_update_equals_information_form"),
+    ("scattering: (1 + tan^2 lambda) not squared for tan lambda",
+     "c[9] = c[9] + th2 * a * a;", "c[9] = c[9] + th2 * a;",
+     "tests/test_oracle_pins.py::test_scattering_noise_matches_the_generated_random_walk"),
     ("B-spline: wrong coefficient in the second weight",
      "w[1] = (Real(3) * f3 - Real(6) * f2 + Real(4)) / Real(6);",
      "w[1] = (Real(3) * f3 - Real(6) * f2 + Real(3)) / Real(6);",

@@ -459,3 +459,47 @@ def test_sector_tracking_efficiency_against_truth():
     hits = [h[h >= 0] for h in hits]
     q = quality(f.label, hits, r["sector_owner"])
     assert q["eff"] > 0.95 and q["fake_rate"] < 0.02, q
+
+
+def test_scattering_noise_matches_the_generated_random_walk():
+    """The propagator's scattering noise against the generator's own random
+    walk (it kicks phi by theta*g*sqrt(1+tan^2) and lambda by theta*g at every
+    row): over 30 rows of a leg the truth sin(phi) and tan(lambda) deviate from
+    the noise-free propagation of their start by N(0, C) with C the
+    propagated covariance (from C = 0), so the normalised deviations have unit
+    width.  Steep tracks only (|tan lambda| > 0.5), where the tan(lambda) term
+    (1 + tan^2)^2 matters most."""
+    theta = 0.02
+    f = synth.generate("central_event", n_primaries=4000, noise_frac=0.0, sigma=0.0,
+                       sec_frac=0.0, ms_theta=theta, store_truth=True, seed=4242)
+    o = opts(ms_theta=theta)
+    lab, row, sec = f.label, f.row.astype(int), f.sector.astype(int)
+    n = 30
+    zs, zt = [], []
+    for i in range(len(lab) - n):
+        j = i + n
+        if lab[i] < 0 or lab[j] != lab[i] or sec[j] != sec[i] or row[j] != row[i] + n:
+            continue
+        if row[i] % 10 or lab[i] % 2:  # one start per 10 rows, first legs only
+            continue
+        p = truth_state(f, i)
+        if abs(p[3]) < 0.5 or abs(p[4]) > 2.0:
+            continue
+        c = np.zeros(15)
+        x = RX[row[i]]
+        ok = True
+        for r in range(row[i] + 1, row[j] + 1):
+            out = oracle.propagate(p, c, x, RX[r], RX, o)
+            if out is None:
+                ok = False
+                break
+            p, c, x = out
+        if not ok or c[5] <= 0 or c[9] <= 0:
+            continue
+        t = truth_state(f, j)
+        zs.append((t[2] - p[2]) / np.sqrt(c[5]))
+        zt.append((t[3] - p[3]) / np.sqrt(c[9]))
+    assert len(zt) > 300, len(zt)
+    for z in (np.array(zs), np.array(zt)):
+        assert abs(np.std(z) - 1.0) < 0.08, np.std(z)
+        assert abs(np.mean(z)) < 0.1
