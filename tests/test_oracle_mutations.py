@@ -26,6 +26,17 @@ CASES = [
      "Real(shared + 1) <= P.shared_frac * Real(kept + 1)",
      "Real(shared) <= P.shared_frac * Real(kept + 1)",
      "tests/test_oracle_pins.py::test_selector_matches_greedy_restatement_and_budget"),
+    ("cleaner: upward links kept without the mutual test",
+     "if (up[c] >= 0 && dn[up[c]] == c) cu[c] = up[c];", "if (up[c] >= 0) cu[c] = up[c];",
+     "tests/test_oracle_pins.py::test_cleaner_and_start_hit_invariants"),
+    ("Phase III: candidates cut with the interpolation cut instead of the stricter one",
+     "if (c2 < P.ext_chi2) cands.push_back({c2, id});",
+     "if (c2 < P.int_chi2) cands.push_back({c2, id});",
+     "tests/test_oracle_fit_pins.py::test_inward_extrapolation_recovers_inner_segments"),
+    ("cluster removal: looper legs required to have the same charge sign",
+     "if ((qa > Real(0)) == (qb > Real(0))) continue;",
+     "if ((qa > Real(0)) != (qb > Real(0))) continue;",
+     "tests/test_oracle_removal_pins.py::test_secondary_legs_follow_generator_truth"),
     ("seeding iterations: start clusters of accepted tracklets left free",
      "        F.used[TL[i].start] = 1;\n", "",
      "tests/test_oracle_seeding_pins.py::test_second_iteration_equals_tracking_the_leftover_clusters"),
@@ -53,18 +64,32 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("what,orig,planted,pin", CASES, ids=[c[0] for c in CASES])
-def test_pin_catches_planted_mistake(tmp_path, what, orig, planted, pin):
+def _run_case(tmp, i, what, orig, planted, pin):
+    """Plant the mistake, build the variant, run its pin: '' if the pin fails."""
+    text = open(SRC).read()
+    if text.count(orig) != 1:
+        return f"mutation site of '{what}' not found once"
+    d = os.path.join(tmp, f"case{i}")
+    os.makedirs(d)
+    src = os.path.join(d, "oracle.cpp")
+    with open(src, "w") as fh:
+        fh.write(text.replace(orig, planted))
+    lib = os.path.join(d, "liboracle_variant.so")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", src, "-o", lib])
+    env = dict(os.environ, TPC_ORACLE_VARIANT_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        pin], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return "" if r.returncode == 1 else f"pin did not catch '{what}':\n{r.stdout[-1500:]}"
+
+
+def test_pins_catch_planted_mistakes(tmp_path):
+    """All cases at once (each is a compile and a pytest run of its own)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     if shutil.which("g++") is None:
         pytest.skip("no host C++ compiler")
-    text = open(SRC).read()
-    assert text.count(orig) == 1, f"mutation site of '{what}' not found once"
-    src = tmp_path / "oracle.cpp"
-    src.write_text(text.replace(orig, planted))
-    lib = tmp_path / "liboracle_variant.so"
-    subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", str(src), "-o", str(lib)])
-    env = dict(os.environ, TPC_ORACLE_VARIANT_LIB=str(lib))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        pin], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 1, f"pin did not catch '{what}':\n{r.stdout[-2000:]}"
+    with ThreadPoolExecutor(max_workers=max(1, min(len(CASES), os.cpu_count() or 1))) as ex:
+        errors = list(ex.map(lambda ic: _run_case(str(tmp_path), ic[0], *ic[1]), enumerate(CASES)))
+    errors = [e for e in errors if e]
+    assert not errors, "\n\n".join(errors)
