@@ -54,6 +54,10 @@ CASES = [
      "w[1] = (Real(3) * f3 - Real(6) * f2 + Real(4)) / Real(6);",
      "w[1] = (Real(3) * f3 - Real(6) * f2 + Real(3)) / Real(6);",
      "tests/test_oracle_fit_pins.py::test_spline_partition_of_unity_and_linear_reproduction"),
+    ("interpolation: the stored inward estimate left out of the weighted mean",
+     "const Real v0 = (wa00 * a[0] + wa01 * a[1]) + (wb00 * b[0] + wb01 * b[1]);",
+     "const Real v0 = (wa00 * a[0] + wa01 * a[1]);",
+     "tests/test_oracle_fit_pins.py::test_noise_free_helices_recovered_to_1e9_fp64"),
     ("merging: rotation into the neighbouring sector with the wrong sense",
      "if (ds == 1 && !rotate(t, 1, P, P.fit_max_snp)) return false;",
      "if (ds == 1 && !rotate(t, -1, P, P.fit_max_snp)) return false;",
