@@ -109,6 +109,9 @@ def _load():
         lib.orc_op.restype = ctypes.c_int
         lib.orc_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Opt), ctypes.c_void_p,
                                ctypes.c_void_p]
+        lib.orc_second_ambiguity.restype = ctypes.c_int
+        lib.orc_second_ambiguity.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + \
+            [ctypes.c_void_p] * 5
         lib.orc_free.restype = None
         lib.orc_free.argtypes = [ctypes.c_void_p]
         _lib = lib
@@ -225,6 +228,23 @@ def seed(points, row_x, opts, fp64=True):
     io[:9] = np.asarray(points, dtype=np.float64).ravel()
     rc, io = _op(3, io, row_x, opts, fp64)
     return (None if rc else (io[9:14], io[14:29], io[29]))
+
+
+def second_ambiguity(key, ncand, cand, chi2):
+    """Phase II second ambiguity on given candidates: key [T], ncand [T, S],
+    cand / chi2 [T, S, K] (best first).  Returns assigned [T, S] (-1: none)."""
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    ncand = np.ascontiguousarray(ncand, dtype=np.int32)
+    cand = np.ascontiguousarray(cand, dtype=np.int32)
+    chi2 = np.ascontiguousarray(chi2, dtype=np.float32)
+    T, S, K = cand.shape
+    assert ncand.shape == (T, S) and chi2.shape == (T, S, K) and key.shape == (T,)
+    out = np.full((T, S), -1, np.int32)
+    rc = _load().orc_second_ambiguity(T, S, K, key.ctypes.data, ncand.ctypes.data,
+                                      cand.ctypes.data, chi2.ctypes.data, out.ctypes.data)
+    if rc:
+        raise RuntimeError(f"orc_second_ambiguity failed ({rc})")
+    return out
 
 
 def track_f64(y, z, row, sector, row_x, opts: dict, *, full: bool = True, dist_map=None) -> Result:

@@ -2599,4 +2599,32 @@ int orc_op(int op, int use_double, const orc_options* opt, const double* row_x, 
   return use_double ? run(double{}) : run(float{});
 }
 
+// Second ambiguity solving (Sec. 3, Phase II) on candidate lists given by
+// the caller, for pins on hand-made cases.  Track t has n_slots (track, row)
+// slots; slot s offers ncand[t*n_slots+s] <= cand_k candidates, best first:
+// cluster ids cand[(t*n_slots+s)*cand_k + k] with chi2 chi2[...]; key[t] is
+// the track key of the tie-break.  assigned[t*n_slots+s] receives the
+// cluster given to the slot or -1.
+int orc_second_ambiguity(int n_tracks, int n_slots, int cand_k, const int* key,
+                         const int* ncand, const int* cand, const float* chi2, int* assigned) {
+  if (n_tracks < 0 || n_slots < 0 || cand_k < 1 || (n_tracks > 0 && n_slots > 0 &&
+      (!key || !ncand || !cand || !chi2 || !assigned)))
+    return 3;
+  orc::Params<float> P{};
+  P.cand_k = cand_k;
+  std::vector<orc::FitTrack<float>> FT((size_t)n_tracks);
+  for (int t = 0; t < n_tracks; ++t) {
+    auto& T = FT[t];
+    T.key = key[t];
+    T.ncand.assign(ncand + (long)t * n_slots, ncand + (long)(t + 1) * n_slots);
+    const long b = (long)t * n_slots * cand_k, e = (long)(t + 1) * n_slots * cand_k;
+    T.cand.assign(cand + b, cand + e);
+    T.cchi.assign(chi2 + b, chi2 + e);
+  }
+  orc::second_ambiguity(FT, P);
+  for (int t = 0; t < n_tracks; ++t)
+    for (int sl = 0; sl < n_slots; ++sl) assigned[(long)t * n_slots + sl] = FT[t].assigned[sl];
+  return 0;
+}
+
 }  // extern "C"

@@ -62,6 +62,23 @@ CASES = [
      "if (ds == 1 && !rotate(t, 1, P, P.fit_max_snp)) return false;",
      "if (ds == 1 && !rotate(t, -1, P, P.fit_max_snp)) return false;",
      "tests/test_oracle_fit_pins.py::test_merging_restores_sector_crossing_tracks"),
+    ("first ambiguity: chi2/ndf term of the score with the wrong sign",
+     "const Real sc = Real(T.n) - P.score_w * (T.chi2 / Real(T.ndf));",
+     "const Real sc = Real(T.n) + P.score_w * (T.chi2 / Real(T.ndf));",
+     "tests/test_oracle_ambiguity_pins.py::"
+     "test_tracklet_key_follows_its_definition_and_prefers_small_chi2"),
+    ("track following: worst instead of best cluster of the window",
+     "if (best < 0 || R.chi2 < bres.chi2 || (R.chi2 == bres.chi2 && id < best)) {",
+     "if (best < 0 || R.chi2 > bres.chi2 || (R.chi2 == bres.chi2 && id < best)) {",
+     "tests/test_oracle_ambiguity_pins.py::test_following_picks_the_best_cluster_of_the_window"),
+    ("second ambiguity: largest instead of smallest bid",
+     "if (it == bid.end() || key < it->second) bid[c] = key;",
+     "if (it == bid.end() || key > it->second) bid[c] = key;",
+     "tests/test_oracle_ambiguity_pins.py::test_second_ambiguity_hand_made_cases"),
+    ("second ambiguity: rounds run from the last choice to the first",
+     "  for (int k = 0; k < P.cand_k; ++k) {\n    bid.clear();",
+     "  for (int k = P.cand_k - 1; k >= 0; --k) {\n    bid.clear();",
+     "tests/test_oracle_ambiguity_pins.py::test_second_ambiguity_hand_made_cases"),
     ("central electrode: sign of the far side's z shift",
      "  dz = t.p[1] - B.ie.p[1];", "  dz = B.ie.p[1] - t.p[1];",
      "tests/test_oracle_electrode_pins.py::test_far_side_shift_measures_the_collision_time"),
