@@ -288,7 +288,8 @@ tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
                                  int32_t blocks_per_sm);
 
 /* Replace the correction map (device pointer copied by reference; the caller
- * keeps it alive while the context uses it). */
+ * keeps it alive while the context uses it).  Any CUDA graph the context
+ * captured with the previous map is recaptured on the next call. */
 tpc_status tpc_set_map(tpc_ctx* ctx, const tpc_map* map);
 
 /* Copy an internal per-stage buffer to host memory (testing and debugging).
@@ -310,6 +311,14 @@ tpc_status tpc_stage_stats(const tpc_ctx* ctx, int32_t i, const char** name, dou
 
 /* Kernels launched by the last tracking call. */
 int64_t tpc_last_launches(const tpc_ctx* ctx);
+
+/* Number of successful tpc_refit calls on this context (-1 for a null
+ * context).  tpc_refit_backward differentiates the most recent refit only; a
+ * caller that keeps a refit for a later backward pass (an autograd graph)
+ * records this number after the refit and checks it before the backward
+ * call, so that a refit run in between is detected instead of silently
+ * differentiated. */
+int64_t tpc_refit_generation(const tpc_ctx* ctx);
 
 /* Allocation-free cellular-automaton links (this entry point has no
  * counterpart in the paper; it serves callers that may not allocate device

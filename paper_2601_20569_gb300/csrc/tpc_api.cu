@@ -92,6 +92,7 @@ struct tpc_ctx {
   RefitDev R{};
   bool refit_alloc = false;
   bool refit_done = false;
+  int64_t refit_gen = 0;  // successful tpc_refit calls so far
   bool tracked = false;  // the last tracking call succeeded (its tracks are resident)
   int last_nf = 1;       // frames of that call
   long refit_tracks = -1, refit_refs = -1;
@@ -422,6 +423,7 @@ tpc_status tpc_set_map(tpc_ctx* ctx, const tpc_map* map) {
   } else {
     ctx->map = tpc_map{};
   }
+  ++ctx->lc_version;  // captured graphs hold the map by value: recapture
   return TPC_OK;
 }
 
@@ -791,6 +793,7 @@ tpc_status tpc_refit(tpc_ctx* ctx, const tpc_clusters* cl, const tpc_tracks* in,
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   ctx->refit_done = true;
+  ++ctx->refit_gen;
   ctx->refit_tracks = in->n_tracks;
   ctx->refit_refs = in->n_cluster_refs;
   std::memset(out, 0, sizeof(*out));
@@ -1012,6 +1015,8 @@ tpc_status tpc_stage_stats(const tpc_ctx* ctx, int32_t i, const char** name, dou
 }
 
 int64_t tpc_last_launches(const tpc_ctx* ctx) { return ctx ? ctx->launches_last : 0; }
+
+int64_t tpc_refit_generation(const tpc_ctx* ctx) { return ctx ? ctx->refit_gen : -1; }
 
 const char* tpc_last_error(const tpc_ctx* ctx) {
   return ctx ? ctx->err.c_str() : "null context";

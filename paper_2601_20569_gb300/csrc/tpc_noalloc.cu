@@ -86,11 +86,15 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-// Sorted-order links -> caller's input-id order.
-__global__ void k_links_to_ids(const int* __restrict__ sid, const int* __restrict__ cup,
-                               const int* __restrict__ cdn, long n, int32_t* up, int32_t* dn) {
+// Sorted-order links -> caller's input-id order.  Writes nothing when the grid
+// build or the neighbour finding recorded an error: those kernels then leave
+// the sorted arrays partly unwritten, holding an earlier call's ids, which may
+// lie beyond this call's n.
+__global__ void k_links_to_ids(const Counters* __restrict__ cnt, const int* __restrict__ sid,
+                               const int* __restrict__ cup, const int* __restrict__ cdn, long n,
+                               int32_t* up, int32_t* dn) {
   const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  if (k >= n || cnt->err != 0) return;
   const int id = sid[k];
   const int u = cup[k], d = cdn[k];
   up[id] = u >= 0 ? sid[u] : -1;
@@ -174,8 +178,8 @@ extern "C" tpc_status tpc_links_noalloc(const tpc_geometry* geo, const tpc_optio
   strict::stage_grid(F, P, sms > 0 ? sms : 1, s);
   strict::stage_links(F, P, sms > 0 ? sms : 1, s);
   if (n > 0)
-    k_links_to_ids<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.sid, F.cup, F.cdn, n, link_up,
-                                                                link_dn);
+    k_links_to_ids<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.cnt, F.sid, F.cup, F.cdn, n,
+                                                                link_up, link_dn);
   if (cudaGetLastError() != cudaSuccess) return TPC_ERR_CUDA;
   Counters hc;
   if (cudaMemcpyAsync(&hc, F.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

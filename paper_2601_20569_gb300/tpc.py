@@ -131,6 +131,8 @@ def load():
     lib.tpc_stage_stats.restype = ctypes.c_int
     lib.tpc_last_launches.argtypes = [ctypes.c_void_p]
     lib.tpc_last_launches.restype = ctypes.c_int64
+    lib.tpc_refit_generation.argtypes = [ctypes.c_void_p]
+    lib.tpc_refit_generation.restype = ctypes.c_int64
     lib.tpc_destroy.argtypes = [ctypes.c_void_p]
     lib.tpc_destroy.restype = None
     for name in ("tpc_init", "tpc_track_timeframe", "tpc_set_map", "tpc_debug_copy"):
@@ -453,6 +455,10 @@ class Tracker:
         if rc:
             raise TpcError(rc, self.last_error())
         return g
+
+    def refit_generation(self) -> int:
+        """Successful refits on this context so far (tpc_refit_generation)."""
+        return int(self.lib.tpc_refit_generation(self._ctx))
 
     def set_map(self, coeff, r_range=(85.0, 245.0), z_range=(-250.0, 250.0)):
         """Use a correction map: float32 CUDA tensor [3][n_z][n_r][n_phi] (kept alive here)."""

@@ -69,6 +69,32 @@ def test_batch_equals_frames_alone(graphs):
         assert np.array_equal(a_batch, a_alone)
 
 
+def test_graph_recaptured_when_the_map_changes():
+    """A captured graph holds the map's shape and range by value: a new range
+    on the same coefficient tensor must take effect on the next replay."""
+    import torch
+
+    from paper_2601_20569_gb300 import tpc
+
+    f = synth.generate("central_event", n_primaries=600, distort=True)
+    opts = TrackerOptions().as_dict()
+    coeff = torch.as_tensor(f.map).cuda()
+    res = {}
+    for graphs in (True, False):
+        tr = tpc.Tracker(RX, opts, mode=0, cap_clusters=f.n, max_frames=1, use_graphs=graphs)
+        dev = tr.to_device(f.y, f.z, f.q, f.row, f.sector)
+        out = []
+        for r_range in ((85.0, 245.0), (95.0, 235.0)):
+            tr.set_map(coeff, r_range=r_range)
+            tr.track_batch([dev])
+            tr.track_batch([dev])  # replay
+            out.append(single_tracks(host(tr)))
+        res[graphs] = out
+        tr.close()
+    assert res[False][0] != res[False][1]  # the range matters
+    assert res[True] == res[False]
+
+
 def test_autotune_keeps_results():
     from paper_2601_20569_gb300 import tpc
 

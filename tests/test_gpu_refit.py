@@ -159,6 +159,33 @@ def test_autograd_bridge_returns_the_adjoint():
     assert torch.equal(c.grad, g)
 
 
+def test_autograd_refuses_a_backward_after_another_refit():
+    """Two refits on one tracker before backward: the first graph's backward
+    would differentiate the second refit, so it is refused; a map changed in
+    place after the forward is caught by torch's version check."""
+    import torch
+
+    from paper_2601_20569_gb300 import tpc
+    from paper_2601_20569_gb300.autograd import refit_chi2
+
+    f, opts, tr, dev, coeff, tracks = setup_event(n_primaries=300)
+    c1 = coeff.clone().requires_grad_(True)
+    chi2_a = refit_chi2(tr, dev, tracks, c1)
+    c2 = coeff.clone().requires_grad_(True)
+    chi2_b = refit_chi2(tr, dev, tracks, c2)
+    with pytest.raises(tpc.TpcError) as e:
+        chi2_a.sum().backward()
+    assert e.value.status == 7
+    chi2_b.sum().backward()  # the most recent refit still differentiates
+    assert c2.grad is not None and bool(torch.isfinite(c2.grad).all())
+    c3 = coeff.clone().requires_grad_(True)
+    chi2_c = refit_chi2(tr, dev, tracks, c3)
+    with torch.no_grad():
+        c3.add_(0.0)
+    with pytest.raises(RuntimeError):
+        chi2_c.sum().backward()
+
+
 def test_call_order_errors():
     import torch
 
