@@ -70,6 +70,8 @@ class _Opt(ctypes.Structure):
         ("cr_mode", ctypes.c_int32),
         ("cr_occ_max", ctypes.c_int32),
         ("ac_merge", ctypes.c_int32),
+        ("edge_rows", ctypes.c_int32),
+        ("edge_min", ctypes.c_int32),
     ]
 
 

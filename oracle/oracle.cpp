@@ -91,6 +91,9 @@ struct orc_options {
   int32_t cr_mode;      // cluster removal: 0 off, 1 tubes + history, 2 also protection 2
   int32_t cr_occ_max;   // protection 2: clusters in the occupancy window above which it applies
   int32_t ac_merge;     // 1: merging across the central electrode (A <-> C sides)
+  int32_t edge_rows;    // following into the adjacent sector from track ends at a sector
+                        // edge: rows followed beyond the end (0: off)
+  int32_t edge_min;     // clusters a segment found there needs to be kept
 };
 // Correction map of the oracle (host memory): layout [3][n_z][n_r][n_phi].
 struct orc_map {
@@ -267,7 +270,7 @@ struct Params {
   Real cr_qpt, cr_protect, cr_remove, cr_edge, cr_occ_w, cr_p2_grow, cr_p2_shrink, cr_leg_dq,
       cr_leg_dtgl, cr_leg_dc;
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, brute_force, n_rows, n_sectors,
-      ext_rows, seed_iters, cr_mode, cr_occ_max, ac_merge;
+      ext_rows, seed_iters, cr_mode, cr_occ_max, ac_merge, edge_rows, edge_min;
   std::vector<Real> row_x;
   std::vector<Real> sec_cos, sec_sin;  // axis of sector s mod 18: ((s mod 18) + 0.5) * 20 deg
 };
@@ -309,6 +312,8 @@ Params<Real> make_params(const orc_options& o, const double* row_x) {
   P.cr_p2_shrink = o.cr_p2_shrink; P.cr_leg_dq = o.cr_leg_dq; P.cr_leg_dtgl = o.cr_leg_dtgl;
   P.cr_leg_dc = o.cr_leg_dc; P.cr_mode = o.cr_mode; P.cr_occ_max = o.cr_occ_max;
   P.ac_merge = o.ac_merge;
+  P.edge_rows = o.edge_rows;
+  P.edge_min = o.edge_min;
   P.sec_cos.resize(18);
   P.sec_sin.resize(18);
   for (int k = 0; k < 18; ++k) {
@@ -692,9 +697,10 @@ struct Tracklet {
 
 // Best cluster on (s,r) with chi2 < follow_chi2 against the prediction (ties:
 // smaller id).  The y/z box bounds are the 2x2 Mahalanobis bounds, widened.
+// Clusters marked in `excl` (if given) are not candidates.
 template <typename Real>
 int pick(const Frame<Real>& F, const Params<Real>& P, const Track<Real>& t, int s, int r,
-         Resid<Real>* out) {
+         Resid<Real>* out, const std::vector<char>* excl = nullptr) {
   const Real hy = o_sqrt(P.follow_chi2 * (t.c[0] + P.meas_sy2)) * Real(1.001) + Real(0.01);
   const Real hz = o_sqrt(P.follow_chi2 * (t.c[2] + P.meas_sz2)) * Real(1.001) + Real(0.01);
   int best = -1;
@@ -702,7 +708,7 @@ int pick(const Frame<Real>& F, const Params<Real>& P, const Track<Real>& t, int 
   const Real ylo = t.p[0] - hy, yhi = t.p[0] + hy;
   const Real margin = Real(0.01);
   for_row_range(F, P, s, r, t.p[1] - hz - margin, t.p[1] + hz + margin, [&](int id) {
-    if (F.taken(id)) return;
+    if (F.taken(id) || (excl && (*excl)[id])) return;
     if (!(F.y[id] >= ylo && F.y[id] <= yhi)) return;
     if (o_fabs(F.z[id] - t.p[1]) > hz) return;
     const Resid<Real> R = residual(t, F.y[id], F.z[id], P);
@@ -984,6 +990,8 @@ struct SectorTrack {
   int rmin = 0, rmax = 0;
   std::vector<int> cl;   // kept clusters, innermost first
   Track<Real> ie{}, oe{};  // states at the innermost / outermost cluster
+  int link = -1;         // segment found by the edge following: the track it continues
+  int dir = 0;           // ... beyond that track's outermost (+1) or innermost (-1) cluster
 };
 
 // Refit of a sector track at the start of merging (Sec. 3, Phase I): outward
@@ -1118,6 +1126,86 @@ bool merge_test(const Params<Real>& P, const SectorTrack<Real>& A, const SectorT
   for (int i = 0; i < 15; ++i) c[i] = t.c[i] + B.ie.c[i];
   chi2 = chi2_5(d, c);
   return chi2 >= Real(0) && chi2 < P.merge_chi2;
+}
+
+// Edge following (Sec. 2): the sector tracking cannot find very short track
+// segments, so tracks that end at a sector edge close to the upper or lower
+// end of the TPC are propagated into the adjacent sector before the merging,
+// and a track following there picks up the segment.  Reading: from each end of
+// a sector track the end state is propagated row by row away from the track
+// (outward from the outermost cluster, inward from the innermost) over at most
+// edge_rows rows.  Where it crosses its sector's edge (|y| > x tan 10 deg) it
+// continues in the neighbouring sector of the same side on that edge (rotation,
+// then the row's x in the new frame); from the crossing on, every row's best
+// free cluster (chi2 < follow_chi2, ties to the smaller id; free = kept by no
+// sector track) is filtered in, until max_miss rows in a row have none, the
+// track leaves that sector too, or the rows run out.  An end that crosses no
+// edge within edge_rows rows is left alone.  A segment of at least edge_min
+// clusters becomes a sector track of the neighbouring sector (its states: the
+// filter after its first and after its last cluster), linked to the track it
+// continues before the merging, which leaves the two linked ends alone.
+
+// One row step: to row r, over the sector edge once.
+template <typename Real>
+bool edge_step(Track<Real>& t, int& sec, bool& crossed, int r, const Params<Real>& P) {
+  if (!propagate(t, P.row_x[r], P, P.max_snp)) return false;
+  if (!crossed && o_fabs(t.p[0]) > t.x * P.tan_half) {
+    const int half = P.n_sectors / 2;
+    const int dir = t.p[0] > Real(0) ? 1 : -1;
+    if (!rotate(t, dir, P, P.max_snp)) return false;
+    sec = sec - sec % half + (sec % half + (dir > 0 ? 1 : half - 1)) % half;
+    if (!propagate(t, P.row_x[r], P, P.max_snp)) return false;
+    crossed = true;
+  }
+  return !(o_fabs(t.p[0]) > t.x * P.tan_half + P.edge_margin);
+}
+
+// The segment beyond one end of A (dir = +1 outer, -1 inner); false if none.
+template <typename Real>
+bool edge_segment(const Frame<Real>& F, const Params<Real>& P, const std::vector<char>& kept,
+                  const SectorTrack<Real>& A, int dir, SectorTrack<Real>& S) {
+  Track<Real> t = dir > 0 ? A.oe : A.ie;
+  int sec = A.sector;
+  bool crossed = false;
+  int miss = 0;
+  std::vector<int> hits;
+  Track<Real> first{}, last{};
+  const int r0 = dir > 0 ? A.rmax : A.rmin;
+  for (int e = 1; e <= P.edge_rows; ++e) {
+    const int r = r0 + dir * e;
+    if (r < 0 || r >= P.n_rows) break;
+    if (!edge_step(t, sec, crossed, r, P)) break;
+    if (!crossed) continue;
+    Resid<Real> R;
+    const int c = pick(F, P, t, sec, r, &R, &kept);
+    if (c >= 0) {
+      update(t, R);
+      if (hits.empty()) first = t;
+      last = t;
+      hits.push_back(c);
+      miss = 0;
+    } else if (++miss >= P.max_miss) {
+      break;
+    }
+  }
+  if ((int)hits.size() < P.edge_min) return false;
+  // segment keys: the track's key plus 2^29 (inner) or 2^30 (outer), above
+  // every cluster id (at most 2^29 clusters), independent of the frame size
+  S.key = A.key + (dir > 0 ? (1 << 30) : (1 << 29));
+  S.sector = sec;
+  S.dir = dir;
+  if (dir > 0) {
+    S.cl = hits;
+    S.ie = first;
+    S.oe = last;
+  } else {
+    S.cl.assign(hits.rbegin(), hits.rend());
+    S.ie = last;
+    S.oe = first;
+  }
+  S.rmin = F.row[S.cl.front()];
+  S.rmax = F.row[S.cl.back()];
+  return true;
 }
 
 // ------------------------------------------------- a9/a10 three-iteration fit
@@ -1945,7 +2033,8 @@ void cluster_removal(const Frame<Real>& F, const Params<Real>& P, const SectorRe
     }
     if (protect)  // seeding history: every hit of the track's tracklets
       for (int sgi : T[t]->seg)
-        for (int c : SR.TL[ST[sgi].tl].hits) flags[c] |= 2;
+        if (ST[sgi].tl >= 0)  // (segments of the edge following come from no tracklet)
+          for (int c : SR.TL[ST[sgi].tl].hits) flags[c] |= 2;
   }
   long nrem = 0;
   for (long c = 0; c < F.n; ++c)
@@ -1982,7 +2071,29 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
     ST.push_back(S);
   }
   std::sort(ST.begin(), ST.end(), [](const auto& a, const auto& b) { return a.key < b.key; });
+  if (P.edge_rows > 0) {
+    std::vector<char> kept(F.n, 0);
+    for (const auto& S : ST)
+      for (int c : S.cl) kept[c] = 1;
+    const int n0 = (int)ST.size();
+    for (int a = 0; a < n0; ++a)
+      for (int dir : {1, -1}) {
+        SectorTrack<Real> S;
+        if (!edge_segment(F, P, kept, ST[a], dir, S)) continue;
+        S.link = a;
+        ST.push_back(S);
+      }
+    // segment keys exceed every tracklet key: the order by key keeps the
+    // tracks and puts the segments after them
+  }
   const int nst = (int)ST.size();
+  std::vector<int> next(nst, -1), prev(nst, -1);
+  for (int i = 0; i < nst; ++i) {
+    const int a = ST[i].link;
+    if (a < 0) continue;
+    if (ST[i].dir > 0) { next[a] = i; prev[i] = a; }
+    else { next[i] = a; prev[a] = i; }
+  }
   // a7: candidate pairs by sector, mutual best
   const int half = P.n_sectors / 2;
   // candidate lists by (sector, innermost row); the pair test requires
@@ -1992,13 +2103,14 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
   std::vector<int> bestB(nst, -1), bestA(nst, -1);
   std::vector<Real> chiB(nst, 0), chiA(nst, 0);
   for (int a = 0; a < nst; ++a) {
+    if (next[a] >= 0) continue;  // outer end linked by the edge following
     const int sa = ST[a].sector;
     const int side = sa / half, ph = sa % half;
     for (int d : {0, 1, half - 1}) {
       const int sb = side * half + (ph + d) % half;
       for (int rb = ST[a].rmax + 1; rb <= ST[a].rmax + P.merge_max_gap && rb < P.n_rows; ++rb)
       for (int b : by_sector[(size_t)sb * P.n_rows + rb]) {
-        if (b == a) continue;
+        if (b == a || prev[b] >= 0) continue;
         Real chi2;
         if (!merge_test(P, ST[a], ST[b], chi2)) continue;
         if (bestB[a] < 0 || chi2 < chiB[a] || (chi2 == chiB[a] && ST[b].key < ST[bestB[a]].key)) {
@@ -2012,7 +2124,6 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
       }
     }
   }
-  std::vector<int> next(nst, -1), prev(nst, -1);
   for (int a = 0; a < nst; ++a)
     if (bestB[a] >= 0 && bestA[bestB[a]] == a) {
       next[a] = bestB[a];
@@ -2470,6 +2581,7 @@ static int track_impl(long n, const In* y, const In* z, const uint8_t* row, cons
                       const double* row_x, const orc_options* opt, const orc_map* map, int stages,
                       int use_double, orc_result** out) {
   if (!opt || !row_x || !out || n < 0) return 1;
+  if (opt->edge_rows > 0 && n >= (1L << 29)) return 1;  // segment keys need ids below 2^29
   for (long i = 0; i < n; ++i)
     if (row[i] >= opt->n_rows || sector[i] >= opt->n_sectors || !std::isfinite(y[i]) ||
         !std::isfinite(z[i]))

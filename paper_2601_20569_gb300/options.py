@@ -70,6 +70,9 @@ class TrackerOptions:
     cr_leg_dc: float = 3.0          # looper legs: circle-centre distance [cm]
     ac_merge: int = 0               # 1: merge across the central electrode (A <-> C), with
                                     # the z shift of the far side (2 vd t0) estimated
+    edge_rows: int = 0              # edge following (Sec. 2): rows followed into the adjacent
+                                    # sector beyond a track end at a sector edge (0: off, <= 32)
+    edge_min: int = 3               # clusters a segment found there needs to be kept
     max_miss: int = 10              # consecutive empty rows ending the following
     min_hits: int = 10
     merge_max_gap: int = 20         # rows between merged segments

@@ -79,6 +79,9 @@ CASES = [
      "  for (int k = 0; k < P.cand_k; ++k) {\n    bid.clear();",
      "  for (int k = P.cand_k - 1; k >= 0; --k) {\n    bid.clear();",
      "tests/test_oracle_ambiguity_pins.py::test_second_ambiguity_hand_made_cases"),
+    ("edge following: rotation into the neighbouring sector on the wrong edge",
+     "const int dir = t.p[0] > Real(0) ? 1 : -1;", "const int dir = t.p[0] > Real(0) ? -1 : 1;",
+     "tests/test_oracle_edge_pins.py::test_short_segments_in_the_adjacent_sector_are_recovered"),
     ("central electrode: sign of the far side's z shift",
      "  dz = t.p[1] - B.ie.p[1];", "  dz = B.ie.p[1] - t.p[1];",
      "tests/test_oracle_electrode_pins.py::test_far_side_shift_measures_the_collision_time"),
