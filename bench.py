@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch", default="",
                     help="fixed launch shapes instead of autotuning, e.g. "
-                         "256x4,128x4,256x16,64x8,256x8 (block x blocks per SM, slot order)")
+                         "256x4,128x4,256x16x16,64x8,256x8 (block x blocks per SM [x lanes "
+                         "per item], slot order)")
     ap.add_argument("--collisions", type=float, default=0.0,
                     help="mean collisions per frame instead of the workload's (small "
                          "profiling cases)")
@@ -52,6 +53,9 @@ def parse():
                     help="skip the refit + adjoint timing on one distorted frame")
     ap.add_argument("--ext-rows", type=int, default=0,
                     help="Phase III extrapolation over this many rows below and above each track (0: off)")
+    ap.add_argument("--edge-rows", type=int, default=0,
+                    help="edge following: rows followed into the adjacent sector beyond track "
+                         "ends at a sector edge (Sec. 2; 0 = off, the default)")
     ap.add_argument("--seed-iters", type=int, default=1,
                     help="sector-tracking iterations, the later ones on leftover clusters "
                          "(Sec. 3; 1 = off, the default)")
@@ -311,23 +315,32 @@ def stage_bytes(name: str, c: dict) -> float:
     return float(table.get(name, 0.0))
 
 
-def measured_traffic(stage: str, c: dict):
-    """DRAM bytes (read + write) per launch of the dominant stage, from the
-    committed ncu summary of its kernels on a smaller frame, scaled to this
-    call by the clusters processed; None without one."""
-    import re
+# Whole-chain algorithmic bytes per cluster: input 12, sorted copy written and
+# read 24, links written and read 16, cleaning 8, attachment 4, cluster reads
+# of the fit and refit 28.
+CHAIN_BYTES_PER_CLUSTER = 92.0
 
-    path = os.path.join(ROOT, "profiles", "heavy_kernels_timeframe_sections.md")
+
+def _traffic_table():
     try:
-        text = open(path).read()
-    except OSError:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def measured_traffic(stage: str, c: dict):
+    """DRAM bytes (read + write) per call of `stage` ("chain" = the whole pass),
+    from the ncu figures in profiles/traffic.json (bytes per input cluster on
+    the frame named there), scaled to this call by its clusters; (None, None)
+    without a figure, or when the figure is marked stale (its kernels changed
+    after the capture)."""
+    t = _traffic_table().get(stage)
+    if not t or t.get("stale"):
         return None, None
-    m = re.search(r"^traffic\s+" + re.escape(stage) + r"\s+bytes_per_cluster\s+([0-9.eE+-]+)", text,
-                  re.M)
-    if not m:
-        return None, None
-    return float(m.group(1)) * c["clusters"], "ncu DRAM bytes per cluster on a smaller frame " \
-        "(profiles/heavy_kernels_timeframe_sections.md), times this call's clusters"
+    return float(t["bytes_per_cluster"]) * c["clusters"], \
+        f"ncu dram__bytes_read.sum + dram__bytes_write.sum per cluster ({t['kernels']}; " \
+        f"{t['workload']}; profiles/traffic.json) times this call's clusters"
 
 
 def refit_timing(mode):
@@ -370,6 +383,143 @@ def refit_timing(mode):
     return out
 
 
+def strict_timing(dev, topts, steps, warmup, stream, world):
+    """The batched pass in strict mode (FP32 without FMA contraction, correctly
+    rounded divide and square root: the mode that is bit-exact against the
+    oracle) on the same resident frames, autotuned the same way."""
+    import torch
+
+    from paper_2601_20569_gb300 import synth, tpc
+    from paper_2601_20569_gb300.options import MODE_STRICT
+
+    n = sum(int(d[0].shape[0]) for d in dev)
+    tr = tpc.Tracker(synth.row_x(), topts, mode=MODE_STRICT, cap_clusters=n,
+                     max_frames=len(dev), use_graphs=True)
+    tr.autotune(dev[:2])
+    for _ in range(warmup):
+        tr.track_batch(dev, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        tr.track_batch(dev, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tr.close()
+    ms, nj = reduce_job(e0.elapsed_time(e1), n, world)
+    return {"value": nj * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "frac": nj * steps / (ms / 1e3) * CHAIN_BYTES_PER_CLUSTER / 1e9 / peaks()[0],
+            "form": "strict mode (bit-exact against the oracle), batched + CUDA graph"}
+
+
+def per_sector_timing(dev, topts, mode, steps, stream, world):
+    """The plain per-sector form on the same frames: one tracking call per
+    sector of every frame (each stage's kernels launched once per sector,
+    without a CUDA graph).  Sector tracking is the same as in the batched pass;
+    tracks are not merged between sectors, since each call sees one sector."""
+    import torch
+
+    from paper_2601_20569_gb300 import synth, tpc
+
+    pieces = []
+    for d in dev:
+        sec = d[4]
+        order = torch.argsort(sec.to(torch.int32), stable=True)
+        counts = torch.bincount(sec.to(torch.int64), minlength=36).tolist()
+        start = 0
+        for c in counts:
+            idx = order[start:start + c]
+            start += c
+            if c:
+                pieces.append(tuple(a.index_select(0, idx) for a in d))
+    n = sum(int(p[0].shape[0]) for p in pieces)
+    tr = tpc.Tracker(synth.row_x(), topts, mode=mode,
+                     cap_clusters=max(int(p[0].shape[0]) for p in pieces))
+    for p in pieces:
+        tr.track(*p, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for p in pieces:
+            tr.track(*p, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = tr.last_launches()
+    tr.close()
+    ms, nj = reduce_job(e0.elapsed_time(e1), n, world)
+    return {"value": nj * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "calls_per_step": len(pieces), "kernels_per_call": launches,
+            "form": "one tpc_track_timeframe call per (frame, sector): every stage launched "
+                    "once per sector, no CUDA graph, no merging between sectors"}
+
+
+def end_to_end(tr, frames, steps, stream, world):
+    """The metric through the public API with host buffers: every step copies
+    its frames' clusters from pinned host memory and reads attach[] back, all
+    inside the timed region.  The copies run on a stream of their own and
+    overlap the tracking of the neighbouring step (two device input buffers;
+    attach[] is staged on the device, then read back while the next step
+    tracks), as a pipeline over the steps: the first step's upload and the last
+    step's read-back are not hidden."""
+    import numpy as np
+    import torch
+
+    n_per_step = sum(f.n for f in frames)
+    host = []
+    for f in frames:
+        host.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+                          (f.y, f.z, f.q.view(np.int16), f.row, f.sector)))
+    dbufs = [[tuple(torch.empty_like(h, device="cuda") for h in hs) for hs in host]
+             for _ in range(2)]
+    staged = [torch.empty(n_per_step, dtype=torch.int32, device="cuda") for _ in range(2)]
+    attach_host = [torch.empty(n_per_step, dtype=torch.int32).pin_memory() for _ in range(2)]
+    h2d = sum(sum(h.numel() * h.element_size() for h in hs) for hs in host)
+    d2h = 4 * n_per_step
+    cs = torch.cuda.Stream()
+
+    def upload(i):
+        with torch.cuda.stream(cs):
+            for hs, ds in zip(host, dbufs[i % 2]):
+                for h, d in zip(hs, ds):
+                    d.copy_(h, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(cs)
+        return ev
+
+    def run(k):
+        ev_in = upload(0)
+        for i in range(k):
+            stream.wait_event(ev_in)
+            if i + 1 < k:  # the other buffer's last user (step i - 1) has finished
+                ev_in = upload(i + 1)
+            tr.track_batch(dbufs[i % 2], stream=stream)
+            staged[i % 2].copy_(tr.result_attach(), non_blocking=True)
+            ev_out = torch.cuda.Event()
+            ev_out.record(stream)
+            cs.wait_event(ev_out)
+            with torch.cuda.stream(cs):
+                attach_host[i % 2].copy_(staged[i % 2], non_blocking=True)
+        cs.wait_stream(stream)
+
+    run(2)  # warm: both input buffers once
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cs)
+    run(steps)
+    e1.record(cs)
+    torch.cuda.synchronize()
+    ms, n = reduce_job(e0.elapsed_time(e1), n_per_step, world)
+    got = attach_host[(steps - 1) % 2]
+    ref = tr.result_attach().cpu()
+    assert torch.equal(got, ref), "attach[] read back differs from the device result"
+    return {"value": n * steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms / steps,
+            "form": "public API (tpc_track_batch) with pinned host clusters in and attach[] out "
+                    "every step; copies on a second stream overlap the neighbouring steps' "
+                    "tracking (double-buffered inputs)"}
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -395,7 +545,8 @@ def main():
     note(f"{len(frames)} frames generated")
     n_per_step = sum(f.n for f in frames)
     mode = MODE_FAST if args.mode == "fast" else MODE_STRICT
-    topts = TrackerOptions(ext_rows=args.ext_rows, seed_iters=args.seed_iters)
+    topts = TrackerOptions(ext_rows=args.ext_rows, seed_iters=args.seed_iters,
+                           edge_rows=args.edge_rows)
     tr = tpc.Tracker(synth.row_x(), topts, mode=mode, cap_clusters=n_per_step,
                      max_frames=len(frames), use_graphs=True)
     dev = [tr.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
@@ -403,8 +554,11 @@ def main():
     note("inputs resident")
     # launch shapes tuned on two frames of the batch (the frames are alike)
     if args.launch:
-        tr.set_launch_config([{"block": int(b), "blocks_per_sm": int(q)} for b, q in
-                              (x.split("x") for x in args.launch.split(","))])
+        shapes = []
+        for x in args.launch.split(","):
+            v = [int(t) for t in x.split("x")]
+            shapes.append({"block": v[0], "blocks_per_sm": v[1], "lanes": v[2] if len(v) > 2 else 1})
+        tr.set_launch_config(shapes)
         tuned = tr.launch_config()
     else:
         tuned = tr.autotune(dev[:2]) if not args.no_autotune else tr.launch_config()
@@ -479,41 +633,29 @@ def main():
         "fit_tracks": int(tr.debug("ft_n").size), "fit_stations": int(tr.debug("ft_nst").sum()),
     }
     hbm, peak_kind = peaks()
+    # the whole chain is one CUDA-graph launch per step: its algorithmic bytes
+    # (92 per input cluster) over the step's CUDA-event time
+    chain_bytes = CHAIN_BYTES_PER_CLUSTER * n_per_step
+    achieved = chain_bytes / (ms / args.steps / 1e3) / 1e9
+    traffic, traffic_src = measured_traffic("chain", counts)
+    # the dominant stage alone, with the stage's own byte model
     dom = max(stages, key=lambda s: s["ms"])
     per_call_ms = dom["ms"] / max(1, dom["calls"])
-    achieved = stage_bytes(dom["name"], counts) / (per_call_ms / 1e3) / 1e9
-    traffic, traffic_src = measured_traffic(dom["name"], counts)
+    st_bytes = stage_bytes(dom["name"], counts)
+    st_traffic, st_src = measured_traffic(dom["name"], counts)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_src,
-            "kernel": f"stage '{dom['name']}' ({dom['launches'] // max(1, dom['calls'])} kernels "
-                      f"per batch call)", "peak_source": f"{peak_kind} hbm_gbs",
-            "stage_bytes_per_call": stage_bytes(dom["name"], counts)}
+            "kernel": f"whole chain, one CUDA-graph launch of {launches // max(1, args.steps)} "
+                      f"kernels per step", "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})",
+            "alg_bytes_per_cluster": CHAIN_BYTES_PER_CLUSTER, "alg_bytes_per_launch": chain_bytes,
+            "stage": {"name": dom["name"], "kernels": dom["launches"] // max(1, dom["calls"]),
+                      "ms_per_call": per_call_ms, "alg_bytes_per_call": st_bytes,
+                      "achieved_gbs": st_bytes / (per_call_ms / 1e3) / 1e9,
+                      "stage_frac": st_bytes / (per_call_ms / 1e3) / 1e9 / hbm,
+                      "traffic": st_traffic, "traffic_source": st_src}}
 
     note("stage profile done")
-    # end to end through the public API: pinned host clusters in, attachments out
-    host = []
-    for f in frames:
-        host.append(tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
-                          (f.y, f.z, f.q.view(np.int16), f.row, f.sector)))
-    dbuf = [tuple(h.to("cuda") for h in hs) for hs in host]  # warm call on real clusters
-    attach_host = torch.empty(n_per_step, dtype=torch.int32).pin_memory()
-    h2d = sum(sum(h.numel() * h.element_size() for h in hs) for hs in host)
-    tr.track_batch(dbuf, stream=stream)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        for hs, ds in zip(host, dbuf):
-            for h, d in zip(hs, ds):
-                d.copy_(h, non_blocking=True)
-        tr.track_batch(dbuf, stream=stream)
-        attach_host.copy_(tr.result_attach(), non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    d2h = 4 * n_per_step
-    e2e_ms, e2e_n = reduce_job(e0.elapsed_time(e1), n_per_step, world)
-    e2e = {"value": e2e_n * args.steps / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    e2e = end_to_end(tr, frames, args.steps, stream, world)
 
     note("end-to-end timed")
     # online cluster removal (tpc_cluster_removal, protection 2) on the batch just tracked
@@ -534,6 +676,12 @@ def main():
                "form": "protective / removal tubes with protection 2 and seeding history, "
                        "on the tracks of the batch"}
     note("cluster removal timed")
+    tr.close()
+    strict = strict_timing(dev, topts, args.steps, args.warmup, stream, world) \
+        if args.mode == "fast" else None
+    note("strict mode timed")
+    per_sector = per_sector_timing(dev, topts, mode, args.steps, stream, world)
+    note("per-sector form timed")
     refit = None
     if not args.no_refit:
         refit = refit_timing(mode)
@@ -547,17 +695,27 @@ def main():
                    "clusters_per_step": n_per_step, "mode": args.mode,
                    "l2": "inputs larger than L2 (each frame > 129 MB resident)",
                    "parallelism": f"replicas x{world}", "launch": "batched + CUDA graph",
-                   "phase3_ext_rows": args.ext_rows, "seed_iters": args.seed_iters},
+                   "phase3_ext_rows": args.ext_rows, "seed_iters": args.seed_iters,
+                   "edge_rows": args.edge_rows},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "plain_per_frame": {"value": plain_value, "unit": UNIT,
                             "form": "one call per frame (one launch per stage per frame)"},
+        "plain_per_sector": per_sector,
         "stages_ms_per_batch": {s_["name"]: s_["ms"] / max(1, s_["calls"]) for s_ in stages},
         "launch_config": tuned,
     }
     line["cluster_removal"] = removal
+    # measured FMA peaks (the ncu pipe utilisation of the fit kernels is read
+    # against them)
+    line["arith_peaks"] = {"fp32_fma_tflops": tpc.Tracker.fma_peak(False),
+                           "fp64_fma_tflops": tpc.Tracker.fma_peak(True, iters=256),
+                           "how": "tpc_fma_peak: 8 independent FMA chains per thread, "
+                                  "8 x 256 threads per SM, CUDA events"}
+    if strict is not None:
+        line["strict"] = strict
     if refit is not None:
         line["refit_adjoint"] = refit
     if rank == 0 and not args.no_cpu_baseline:

@@ -114,6 +114,11 @@ typedef struct {
                                (0 or 1: off) */
   int32_t ac_merge;         /* 1: merging also across the central electrode (Sec. 2), the far
                                side's z shifted by the estimated 2 vd t0 (Sec. 1); 0: off */
+  int32_t edge_rows;        /* edge following (Sec. 2: tracks ending at a sector edge are
+                               propagated into the adjacent sector before the merging and
+                               followed there): rows followed beyond each track end, 0..152
+                               (0: off; on, cap_clusters <= 2^29) */
+  int32_t edge_min;         /* clusters a segment found by the edge following needs (>= 1) */
   int64_t cap_clusters;     /* max clusters per call (all frames of a batch) */
   int64_t cap_tracklets;    /* max tracklets per frame (0: n/16 + 4096) */
   int64_t cap_tracks;       /* max tracks per frame (0: cap_tracklets) */
@@ -274,18 +279,22 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
                         void* cuda_stream);
 
 /* Launch shape chosen for heavy kernel `slot` (0..4): kernel name, block
- * size, blocks per SM.  TPC_ERR_INVALID_ARG past the last slot. */
+ * size, blocks per SM, lanes per work item (1 = one thread per item; the
+ * merge search of slot 2 runs one item on a group of 1, 4, 8, 16 or 32
+ * lanes).  Any output pointer may be NULL.  TPC_ERR_INVALID_ARG past the last
+ * slot. */
 tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
-                             int32_t* block, int32_t* blocks_per_sm);
+                             int32_t* block, int32_t* blocks_per_sm, int32_t* lanes);
 
 /* Set the launch shape of heavy kernel `slot` (0..4, as tpc_launch_config
  * numbers them), e.g. to reapply a shape the autotuner chose earlier on the
  * same GPU.  block: multiple of 32 in [32, 256] (the kernels are compiled for
- * at most 256 threads per block); blocks_per_sm in [1, 32].
+ * at most 256 threads per block); blocks_per_sm in [1, 32]; lanes: 1, or for
+ * slot 2 (merge search) one of 4, 8, 16, 32.
  * The shape changes only scheduling: results are identical for every shape.
  * TPC_ERR_INVALID_ARG for any other value. */
 tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
-                                 int32_t blocks_per_sm);
+                                 int32_t blocks_per_sm, int32_t lanes);
 
 /* Replace the correction map (device pointer copied by reference; the caller
  * keeps it alive while the context uses it).  Any CUDA graph the context
@@ -311,6 +320,15 @@ tpc_status tpc_stage_stats(const tpc_ctx* ctx, int32_t i, const char** name, dou
 
 /* Kernels launched by the last tracking call. */
 int64_t tpc_last_launches(const tpc_ctx* ctx);
+
+/* Measured arithmetic peak of the current device, for reading the pipe
+ * utilisation of the kernels against it: fused multiply-add throughput in
+ * TFLOP/s (2 flops per FMA) of a kernel of eight independent FMA chains per
+ * thread, `iters` x 128 FMAs per thread, 8 blocks of 256 threads per SM,
+ * timed with CUDA events on `cuda_stream` (synchronous).  fp64 != 0 measures
+ * double precision.  Allocates and frees a small result buffer (stream-ordered).
+ * Not in the paper. */
+tpc_status tpc_fma_peak(int32_t fp64, int32_t iters, double* tflops, void* cuda_stream);
 
 /* Number of successful tpc_refit calls on this context (-1 for a null
  * context).  tpc_refit_backward differentiates the most recent refit only; a

@@ -990,7 +990,7 @@ struct SectorTrack {
   int rmin = 0, rmax = 0;
   std::vector<int> cl;   // kept clusters, innermost first
   Track<Real> ie{}, oe{};  // states at the innermost / outermost cluster
-  int link = -1;         // segment found by the edge following: the track it continues
+  int link = -1;         // segment found by the edge following: key of the track it continues
   int dir = 0;           // ... beyond that track's outermost (+1) or innermost (-1) cluster
 };
 
@@ -2080,17 +2080,23 @@ void run_merge_fit(const Frame<Real>& F, const Params<Real>& P, const MapR<Real>
       for (int dir : {1, -1}) {
         SectorTrack<Real> S;
         if (!edge_segment(F, P, kept, ST[a], dir, S)) continue;
-        S.link = a;
+        S.link = ST[a].key;
         ST.push_back(S);
       }
-    // segment keys exceed every tracklet key: the order by key keeps the
-    // tracks and puts the segments after them
+    // segment keys exceed every tracklet key: ordered by key, the segments
+    // follow the tracks
+    std::sort(ST.begin(), ST.end(), [](const auto& a, const auto& b) { return a.key < b.key; });
   }
   const int nst = (int)ST.size();
   std::vector<int> next(nst, -1), prev(nst, -1);
+  std::map<int, int> index_of_key;
+  for (int i = 0; i < nst; ++i)
+    if (ST[i].link >= 0) index_of_key[ST[i].link] = -1;
+  for (int i = 0; i < nst; ++i)
+    if (index_of_key.count(ST[i].key)) index_of_key[ST[i].key] = i;
   for (int i = 0; i < nst; ++i) {
-    const int a = ST[i].link;
-    if (a < 0) continue;
+    if (ST[i].link < 0) continue;
+    const int a = index_of_key[ST[i].link];
     if (ST[i].dir > 0) { next[a] = i; prev[i] = a; }
     else { next[i] = a; prev[a] = i; }
   }

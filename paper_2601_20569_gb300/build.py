@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + CSRC,
                  "-I" + INCLUDE]
 KERNEL_TUS = ["tpc_sector.cu", "tpc_fit.cu", "tpc_removal.cu"]  # compiled when present
-HOST_TUS = ["tpc_api.cu", "tpc_noalloc.cu"]
+HOST_TUS = ["tpc_api.cu", "tpc_noalloc.cu", "tpc_peak.cu"]
 
 
 def _sources():

@@ -31,6 +31,7 @@ const StageDef kStages[] = {
     {"select", strict::stage_select, fast::stage_select},
     {"reseed", strict::stage_reseed, fast::stage_reseed},
     {"sector_refit", strict::stage_sector_refit, fast::stage_sector_refit},
+    {"edge", strict::stage_edge, fast::stage_edge},
     {"merge", strict::stage_merge, fast::stage_merge},
     {"fit12", strict::stage_fit12, fast::stage_fit12},
     {"ambiguity2", strict::stage_ambiguity2, fast::stage_ambiguity2},
@@ -61,11 +62,8 @@ struct GraphKey {
 struct tpc_ctx {
   tpc_options opt{};
   int max_frames = 1;
-  // batch input (concatenated frames)
-  float* by = nullptr;
-  float* bz = nullptr;
-  uint8_t* brow = nullptr;
-  uint16_t* bsec = nullptr;
+  // batch input: the frame table (the frames are read in place)
+  FrameSrc* src = nullptr;
   // graph replay
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -162,6 +160,8 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.ext_rows = o.ext_rows;
   P.seed_iters = o.seed_iters > 1 ? o.seed_iters : 1;
   P.ac_merge = o.ac_merge ? 1 : 0;
+  P.edge_rows = o.edge_rows;
+  P.edge_min = o.edge_min;
   // z reach of a merge pair: (max gap + 2) rows at the steepest allowed angle
   P.merge_zspan = (float)((double)(o.merge_max_gap + 2) *
                           (((double)row_x[nr - 1] - (double)row_x[0]) / (double)(nr - 1)) /
@@ -217,6 +217,8 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
       opt->inner_rows < 0 || opt->inner_rows > kMaxInner || opt->merge_max_gap < 1 ||
       opt->ext_rows < 0 || opt->ext_rows > kMaxExt || !(opt->ext_chi2 > 0.0f) ||
       opt->seed_iters < 0 || opt->seed_iters > kMaxSeedIters ||
+      opt->edge_rows < 0 || opt->edge_rows > kMaxRows ||
+      (opt->edge_rows > 0 && (opt->edge_min < 1 || opt->cap_clusters > (1L << 29))) ||
       opt->max_frames < 0 || opt->max_frames > 64 ||
       (long)geo->n_sectors * (opt->max_frames > 1 ? opt->max_frames : 1) * geo->n_rows > 65535 ||
       !(opt->fit_max_snp > 0.0f && opt->fit_max_snp < 1.0f) ||
@@ -253,7 +255,9 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   for (int i = 0; i < kLNum; ++i) {
     F.lc.block[i] = 128;
     F.lc.per_sm[i] = 8;
+    F.lc.lanes[i] = 1;
   }
+  F.lc.lanes[kLMerge] = kMergeLanesDefault;
   F.cap_bins = (long)((double)n / ctx->P.grid_occ) + nrr * 65;
   F.cap_tl = opt->cap_tracklets > 0 ? opt->cap_tracklets : n / 10 + 4096;
   bool ok = true;
@@ -332,11 +336,11 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ie_idx, T);
   ok &= dalloc(ctx, &F.sec_zlo, nsec_all);
   ok &= dalloc(ctx, &F.sec_zinv, nsec_all);
-  if (ctx->max_frames > 1) {
-    ok &= dalloc(ctx, &ctx->by, n);
-    ok &= dalloc(ctx, &ctx->bz, n);
-    ok &= dalloc(ctx, &ctx->brow, n);
-    ok &= dalloc(ctx, &ctx->bsec, n);
+  if (ctx->max_frames > 1) ok &= dalloc(ctx, &ctx->src, ctx->max_frames);
+  if (opt->edge_rows > 0) {
+    ok &= dalloc(ctx, &F.st_kept, n);
+    ok &= dalloc(ctx, &F.edge_flag, 2 * F.cap_tl + 1);
+    ok &= dalloc(ctx, &F.edge_pos, 2 * F.cap_tl + 1);
   }
   if (opt->use_graphs) {
     ok &= cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking) == cudaSuccess;
@@ -483,7 +487,9 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   long launches = 0;
   const bool graph = ctx->opt.use_graphs && !ctx->prof;
   if (graph) {
-    GraphKey key{F.y, F.z, F.row, F.bsector ? (const void*)F.bsector : (const void*)F.sector, F.n,
+    // a batch reads its frames through the frame table, copied before every
+    // launch: its graph does not depend on where the frames lie
+    GraphKey key{F.y, F.z, F.row, F.nsrc ? (const void*)F.src : (const void*)F.sector, F.n,
                  nf, F.map.c, ctx->lc_version};
     if (!ctx->graph_exec || std::memcmp(&key, &ctx->graph_key, sizeof key) != 0) {
       if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
@@ -541,6 +547,11 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
     return fail(ctx, TPC_ERR_CAPACITY, "start hits %d exceed tracklet capacity %ld", c.n_starts,
                 F.cap_tl);
   }
+  if (c.err & kErrCapEdge) {
+    if (needed) *needed = c.need_tracklets;
+    return fail(ctx, TPC_ERR_CAPACITY, "sector tracks / tracklets with the edge-following "
+                "segments (%d) exceed tracklet capacity %ld", c.need_tracklets, F.cap_tl);
+  }
   if (c.err & kErrCapRefs) {
     if (needed) *needed = c.n_refs;
     return fail(ctx, TPC_ERR_CAPACITY, "cluster references %d exceed capacity %ld", c.n_refs,
@@ -574,13 +585,6 @@ tpc_status run_chain(tpc_ctx* ctx, FrameDev& F, int nf, cudaStream_t s, tpc_trac
   return TPC_OK;
 }
 
-// Batch sector of each cluster of one frame; a sector outside the frame's
-// range maps to 0xFFFF so that the grid build reports the bad input.
-__global__ void k_sector_offset(const uint8_t* in, uint16_t* out, long n, int nsec, int add) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = in[i] < nsec ? (uint16_t)(in[i] + add) : (uint16_t)0xFFFF;
-}
-
 }  // namespace
 
 extern "C" {
@@ -602,7 +606,8 @@ tpc_status tpc_track_timeframe(tpc_ctx* ctx, const tpc_clusters* cl, tpc_tracks*
   F.z = cl->z;
   F.row = cl->row;
   F.sector = cl->sector;
-  F.bsector = nullptr;
+  F.src = nullptr;
+  F.nsrc = 0;
   F.n = cl->n;
   return run_chain(ctx, F, 1, (cudaStream_t)cuda_stream, out, needed);
 }
@@ -630,24 +635,23 @@ tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_f
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   FrameDev& F = ctx->F;
-  // concatenate: frame f's sector s becomes batch sector f * n_sectors + s
+  // frame table: batch cluster off_f + j is frame f's cluster j, and frame
+  // f's sector s becomes batch sector f * n_sectors + s
+  std::vector<FrameSrc> tab((size_t)n_frames);
   long off = 0;
   for (int f = 0; f < n_frames; ++f) {
-    const long n = frames[f].n;
-    if (n == 0) continue;
-    CK(cudaMemcpyAsync(ctx->by + off, frames[f].y, 4 * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(ctx->bz + off, frames[f].z, 4 * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(ctx->brow + off, frames[f].row, n, cudaMemcpyDeviceToDevice, s));
-    k_sector_offset<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        frames[f].sector, ctx->bsec + off, n, ctx->n_sectors, f * ctx->n_sectors);
-    off += n;
+    tab[f] = FrameSrc{frames[f].y, frames[f].z, frames[f].row, frames[f].sector, off};
+    off += frames[f].n;
   }
-  CK(cudaGetLastError());
-  F.y = ctx->by;
-  F.z = ctx->bz;
-  F.row = ctx->brow;
+  CK(cudaMemcpyAsync(ctx->src, tab.data(), sizeof(FrameSrc) * n_frames, cudaMemcpyHostToDevice,
+                     s));
+  F.y = nullptr;
+  F.z = nullptr;
+  F.row = nullptr;
   F.sector = nullptr;
-  F.bsector = ctx->bsec;
+  F.src = ctx->src;
+  F.nsrc = n_frames;
+  F.src_nsec = ctx->n_sectors;
   F.n = total;
   return run_chain(ctx, F, n_frames, s, out, needed);
 }
@@ -658,6 +662,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
   static const char* slot_stage[kLNum] = {"tracklets", "sector_refit", "merge", "fit12", "fit3"};
   static const int blocks[] = {64, 128, 256};
   static const int per_sm[] = {4, 8, 16};
+  static const int merge_lanes[] = {1, 8, 16, 32};
   const bool prof_was = ctx->prof;
   if (!ctx->ev[0])
     for (auto& e : ctx->ev)
@@ -670,10 +675,13 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
     while (st < kNumStages && std::strcmp(kStages[st].name, slot_stage[slot]) != 0) ++st;
     double best = 1e30;
     LaunchCfg best_lc = ctx->F.lc;
+    const int nl = slot == kLMerge ? 4 : 1;
+    for (int li = 0; li < nl; ++li)
     for (int b : blocks)
       for (int q : per_sm) {
         ctx->F.lc.block[slot] = b;
         ctx->F.lc.per_sm[slot] = q;
+        ctx->F.lc.lanes[slot] = slot == kLMerge ? merge_lanes[li] : 1;
         double t = 0.0;
         for (int rep = 0; rep < 2; ++rep) {
           const double before = ctx->stage_ms[st];
@@ -702,7 +710,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
 }
 
 tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
-                             int32_t* block, int32_t* blocks_per_sm) {
+                             int32_t* block, int32_t* blocks_per_sm, int32_t* lanes) {
   static const char* names[kLNum] = {"k_tl_up+k_tl_down", "k_sector_refit", "k_merge_best",
                                      "k_fit1+k_fit2",
                                      "k_fit3"};
@@ -710,18 +718,22 @@ tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kern
   if (kernel) *kernel = names[slot];
   if (block) *block = ctx->F.lc.block[slot];
   if (blocks_per_sm) *blocks_per_sm = ctx->F.lc.per_sm[slot];
+  if (lanes) *lanes = ctx->F.lc.lanes[slot];
   return TPC_OK;
 }
 
 tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
-                                 int32_t blocks_per_sm) {
+                                 int32_t blocks_per_sm, int32_t lanes) {
   if (!ctx) return TPC_ERR_INVALID_ARG;
+  const bool lanes_ok = lanes == 1 || (slot == kLMerge && (lanes == 4 || lanes == 8 ||
+                                                           lanes == 16 || lanes == 32));
   if (slot < 0 || slot >= kLNum || block < 32 || block > 256 || block % 32 != 0 ||
-      blocks_per_sm < 1 || blocks_per_sm > 32)
-    return fail(ctx, TPC_ERR_INVALID_ARG, "launch shape slot %d: block %d, %d per SM", slot, block,
-                blocks_per_sm);
+      blocks_per_sm < 1 || blocks_per_sm > 32 || !lanes_ok)
+    return fail(ctx, TPC_ERR_INVALID_ARG, "launch shape slot %d: block %d, %d per SM, %d lanes",
+                slot, block, blocks_per_sm, lanes);
   ctx->F.lc.block[slot] = block;
   ctx->F.lc.per_sm[slot] = blocks_per_sm;
+  ctx->F.lc.lanes[slot] = lanes;
   ++ctx->lc_version;
   return TPC_OK;
 }
@@ -952,6 +964,9 @@ tpc_status tpc_debug_copy(tpc_ctx* ctx, const char* name, void* host_dst, int64_
   else if (w == "st_ok") { src = F.st_ok; nb = 4L * c.n_tracks; }
   else if (w == "st_key") { src = F.st_key; nb = 4L * c.n_tracks; }
   else if (w == "st_next") { src = F.st_next; nb = 4L * c.n_tracks; }
+  else if (w == "st_bestB") { src = F.st_bestB; nb = 4L * c.n_tracks; }
+  else if (w == "st_bestchi") { src = F.st_bestchi; nb = 4L * c.n_tracks; }
+  else if (w == "st_bestA") { src = F.st_bestA; nb = 8L * c.n_tracks; }
   else if (w == "st_ie") { src = F.st_ie; nb = 4L * kStateF * c.n_tracks; }
   else if (w == "st_oe") { src = F.st_oe; nb = 4L * kStateF * c.n_tracks; }
   else if (w == "ft_key") { src = F.ft_key; nb = 4L * nft; }

@@ -23,24 +23,6 @@ namespace TPC_NS {
 
 namespace {
 
-// ------------------------------------------------------------- state I/O
-__device__ __forceinline__ void put_state(float* dst, const Trk<float>& t, int sector) {
-#pragma unroll
-  for (int i = 0; i < 5; ++i) dst[i] = t.p[i];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) dst[5 + i] = t.c[i];
-  dst[20] = t.x;
-  dst[21] = __int_as_float(sector);
-}
-
-__device__ __forceinline__ void get_state(const float* src, Trk<float>& t) {
-#pragma unroll
-  for (int i = 0; i < 5; ++i) t.p[i] = src[i];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) t.c[i] = src[5 + i];
-  t.x = src[20];
-}
-
 // --------------------------------------------------------- a8 distortion map
 __device__ __forceinline__ void spline_w(float f, float* w) {
   const float g = 1.0f - f;
@@ -290,7 +272,8 @@ __global__ void k_ie_hist(FrameDev F, KParams P) {
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
-    if (!F.st_ok[i]) { F.ie_bin[i] = -1; continue; }
+    // (an inner end linked by the edge following takes no part in the merging)
+    if (!F.st_ok[i] || F.st_hasprev[i]) { F.ie_bin[i] = -1; continue; }
     const int b = merge_bin(F, P.n_rows, F.st_sector[i], F.st_rmin[i],
                             F.st_ie[(long)i * kStateF + 1]);
     F.ie_bin[i] = b;
@@ -361,59 +344,103 @@ __device__ __forceinline__ bool merge_test(const FrameDev& F, const KParams& P, 
   return chi2 >= 0.0f && chi2 < P.merge_chi2;
 }
 
-template <typename Fn>
-__device__ __forceinline__ void for_merge_candidates(const FrameDev& F, const KParams& P, int a,
-                                                     Fn&& fn) {
-  const int half = P.n_phi;
-  const int sa = F.st_sector[a];
-  const int side = sa / half, ph = sa % half;
-  const float* oe = F.st_oe + (long)a * kStateF;
-  const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
-  const int dsl[3] = {0, 1, half - 1};
-  // the pair test needs 1 <= rmin(B) - rmax(A) <= merge_max_gap: only those
-  // rows of the index are visited
-  const int r0 = F.st_rmax[a] + 1;
-  const int r1 = min(F.st_rmax[a] + P.merge_max_gap, P.n_rows - 1);
-  const float m = 0.01f;
-  if (r0 > r1) return;
-  for (int q = 0; q < 3; ++q) {
-    const int sb = side * half + (ph + dsl[q]) % half;
-    const int z0 = merge_zbin(F, sb, oe[1] - zwin - m);
-    const int z1 = merge_zbin(F, sb, oe[1] + zwin + m);
-    for (int zb = z0; zb <= z1; ++zb) {
-      const int base = (sb * kMergeZ + zb) * P.n_rows;
-      const int lo = F.ie_first[base + r0], hi = F.ie_first[base + r1 + 1];
-      for (int k = lo; k < hi; ++k) {
-        const int b = F.ie_idx[k];
-        if (b != a) fn(b);
-      }
-    }
-  }
-}
-
+// Best merge partner of every outer end A, searched by a group of G lanes
+// (G = 1: one thread per end).  The (sector, z bin) ranges of A's candidates
+// in the index are dealt out to the lanes, their sizes summed by a group scan,
+// and the candidates of all ranges dealt out G at a time; each lane runs the
+// pair test of its candidate and the group's smallest (chi2, key of B) is
+// found by shuffles.  The minimum does not depend on the visiting order, so
+// every G gives the scalar search's result bit for bit.
+template <int G>
 __global__ void __launch_bounds__(256) k_merge_best(FrameDev F, KParams P) {
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
-  for (int a = queue_next(&F.cnt->queue[kQMerge]); a < ns; a = queue_next(&F.cnt->queue[kQMerge])) {
-    if (!F.st_ok[a]) continue;
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const unsigned gmask = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int half = P.n_phi;
+  for (;;) {
+    int a = 0;
+    if (gl == 0) a = queue_next(&F.cnt->queue[kQMerge]);
+    a = __shfl_sync(gmask, a, 0, G);
+    if (a >= ns) break;
+    if (!F.st_ok[a] || F.st_next[a] >= 0) continue;  // (outer end linked by the edge following)
     const int keyA = F.st_key[a];
+    unsigned long long best = ~0ull;
     int bb = -1;
-    float bchi = 0.0f;
-    int bkey = 0;
-    for_merge_candidates(F, P, a, [&](int b) {
-      if (!F.st_ok[b]) return;
-      float chi2;
-      if (!merge_test(F, P, a, b, chi2)) return;
-      const int kb = F.st_key[b];
-      if (bb < 0 || chi2 < bchi || (chi2 == bchi && kb < bkey)) {
-        bb = b;
-        bchi = chi2;
-        bkey = kb;
+    const int r0 = F.st_rmax[a] + 1;
+    const int r1 = min(F.st_rmax[a] + P.merge_max_gap, P.n_rows - 1);
+    if (r0 <= r1) {
+      // the pair test needs 1 <= rmin(B) - rmax(A) <= merge_max_gap: only
+      // those rows of the index are visited
+      const int sa = F.st_sector[a];
+      const int side = sa / half, ph = sa % half;
+      const float* oe = F.st_oe + (long)a * kStateF;
+      const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
+      const float m = 0.01f;
+      int sq[3], zq[3], nq[3];
+      int nr = 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        sq[q] = side * half + (ph + (q == 0 ? 0 : q == 1 ? 1 : half - 1)) % half;
+        zq[q] = merge_zbin(F, sq[q], oe[1] - zwin - m);
+        nq[q] = merge_zbin(F, sq[q], oe[1] + zwin + m) - zq[q] + 1;
+        nr += nq[q];
       }
-      atomicMin(&F.st_bestA[b], pack_chi_key(chi2, keyA));
-    });
-    F.st_bestB[a] = bb;
-    F.st_bestchi[a] = bchi;
+      for (int j0 = 0; j0 < nr; j0 += G) {
+        int lo = 0, cnt = 0;
+        int j = j0 + gl;
+        if (j < nr) {
+          const int q = j < nq[0] ? 0 : j < nq[0] + nq[1] ? 1 : 2;
+          j -= q == 0 ? 0 : q == 1 ? nq[0] : nq[0] + nq[1];
+          const int base = (sq[q] * kMergeZ + zq[q] + j) * P.n_rows;
+          lo = F.ie_first[base + r0];
+          cnt = F.ie_first[base + r1 + 1] - lo;
+        }
+        int inc = cnt;  // inclusive scan of the range sizes over the group
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+          const int v = __shfl_up_sync(gmask, inc, o, G);
+          if (gl >= o) inc += v;
+        }
+        const int total = __shfl_sync(gmask, inc, G - 1, G);
+        for (int c0 = 0; c0 < total; c0 += G) {
+          const int c = c0 + gl;
+          int L = 0;  // the range holding candidate c: first lane with inc > c
+#pragma unroll
+          for (int st = G / 2; st >= 1; st >>= 1) {
+            const int v = __shfl_sync(gmask, inc, L + st - 1, G);
+            if (v <= c) L += st;
+          }
+          const int excl = __shfl_sync(gmask, inc - cnt, L, G);
+          const int lo_l = __shfl_sync(gmask, lo, L, G);
+          if (c >= total) continue;
+          const int b = F.ie_idx[lo_l + (c - excl)];
+          if (b == a || !F.st_ok[b]) continue;
+          float chi2;
+          if (!merge_test(F, P, a, b, chi2)) continue;
+          const unsigned long long kb = pack_chi_key(chi2, F.st_key[b]);
+          if (kb < best) {
+            best = kb;
+            bb = b;
+          }
+          atomicMin(&F.st_bestA[b], pack_chi_key(chi2, keyA));
+        }
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(gmask, best, o, G);
+      const int obb = __shfl_xor_sync(gmask, bb, o, G);
+      if (ob < best) {
+        best = ob;
+        bb = obb;
+      }
+    }
+    if (gl == 0) {
+      F.st_bestB[a] = bb;
+      F.st_bestchi[a] = bb >= 0 ? o2f((unsigned)(best >> 32)) : 0.0f;
+    }
   }
 }
 
@@ -1985,7 +2012,17 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k += scan_exclusive(F.ie_cnt, F.ie_first, (long)P.n_sectors * P.n_rows * kMergeZ + 1,
                       F.scan_tmp, s);
   k_ie_scatter<<<sms * 8, kBlock, 0, s>>>(F);
-  k_merge_best<<<persistent_grid(F.lc, kLMerge, sms), F.lc.block[kLMerge], 0, s>>>(F, P);
+  {
+    const unsigned grid = persistent_grid(F.lc, kLMerge, sms);
+    const int blk = F.lc.block[kLMerge];
+    switch (F.lc.lanes[kLMerge]) {
+      case 32: k_merge_best<32><<<grid, blk, 0, s>>>(F, P); break;
+      case 16: k_merge_best<16><<<grid, blk, 0, s>>>(F, P); break;
+      case 8: k_merge_best<8><<<grid, blk, 0, s>>>(F, P); break;
+      case 4: k_merge_best<4><<<grid, blk, 0, s>>>(F, P); break;
+      default: k_merge_best<1><<<grid, blk, 0, s>>>(F, P); break;
+    }
+  }
   k_merge_link<<<sms * 8, kBlock, 0, s>>>(F);
   if (P.ac_merge) {
     k_cross_best<<<sms * 8, kBlock, 0, s>>>(F, P);

@@ -27,9 +27,11 @@ struct KParams {
   int max_miss, min_hits, merge_max_gap, inner_rows, cand_k, ext_rows;
   int seed_iters;  // sector-tracking iterations (the later ones on leftover clusters)
   int ac_merge;    // merging across the central electrode
+  int edge_rows;   // edge following: rows followed beyond a track end (0: off)
+  int edge_min;    // edge following: clusters a segment needs
   int n_rows, n_sectors;  // n_sectors: all sectors of the call (frames x sectors)
   int n_phi;         // azimuthal sectors of one TPC half (sector % n_phi, side = sector / n_phi)
-  float grid_dy;     // target y bin size [cm]
+  float grid_dy;     // smallest y bin size [cm]
   float grid_occ;    // target clusters per bin
 };
 
@@ -48,6 +50,7 @@ enum LaunchSlot : int { kLTracklets = 0, kLSectorRefit, kLMerge, kLFit12, kLFit3
 struct LaunchCfg {
   int block[kLNum];
   int per_sm[kLNum];
+  int lanes[kLNum];  // lanes per work item (1: one thread per item; the merge search: 1..32)
 };
 
 // Work queues: counters of the dynamic item fetching (zeroed per call).
@@ -60,10 +63,12 @@ enum QueueSlot : int {
 
 // Search grid of one (sector, row): bins iz*nY + iy, clusters of a bin are
 // contiguous in the sorted arrays.
-struct RowGrid {
+// One 32-byte record per (sector, row), so that a search reads it with one
+// aligned sector; the row's clusters start at the sum of ncl over the rows
+// before it.
+struct __align__(32) RowGrid {
   int bin0;   // first global bin
   int nY, nZ;
-  int cl0;    // first sorted cluster of the row
   int ncl;
   float y0, invDy, z0, invDz;
 };
@@ -78,6 +83,7 @@ enum : int {
   kErrCapCand = 32,
   kErrDense = 64,    // a search bin holds more than kMaxBinOcc clusters
   kErrCapPos = 128,  // kept-cluster positions of the sector tracks
+  kErrCapEdge = 256, // segments of the edge following beyond the tracklet capacity
 };
 
 // Largest number of clusters one search bin may hold.  Bins are sized for a
@@ -89,6 +95,7 @@ constexpr int kMaxBinOcc = 1024;
 constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
 constexpr int kIpolF = 11;      // interpolation record of an inner station
+constexpr int kMergeLanesDefault = 16;  // lanes per outer end in the merge search
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 constexpr int kMaxSeedIters = 4;  // sector-tracking iterations
@@ -126,6 +133,18 @@ struct Counters {
   int n_new;         // start hits found by the current iteration
   int pass_start[kMaxSeedIters];  // first tracklet of each iteration
   int n_removed;     // cluster removal: clusters flagged for removal
+  int n_st0;         // edge following: sector tracks before the segments were added
+  int n_tl_all;      // edge following: tracklet slots in use before the segments
+};
+
+// One frame of a batch call, read in place: the clusters of batch index i
+// with off <= i < off + n are this frame's clusters i - off.
+struct FrameSrc {
+  const float* y;
+  const float* z;
+  const uint8_t* row;
+  const uint8_t* sector;
+  long off;
 };
 
 // Working set of one frame on the device.
@@ -135,7 +154,9 @@ struct FrameDev {
   const float* z;
   const uint8_t* row;
   const uint8_t* sector;
-  const uint16_t* bsector; // batch calls: frame * sectors per frame + sector (else null)
+  const FrameSrc* src;     // batch calls: the frames' own arrays ([nsrc], device);
+  int nsrc;                // 0: one frame, read through y, z, row, sector
+  int src_nsec;            // sectors per frame (batch sector = frame * src_nsec + sector)
   long n;
   const float* row_x;  // [n_rows]
   // a1 grid
@@ -178,6 +199,9 @@ struct FrameDev {
   int* tl_nkept;
   int* tl_kept;            // [cap_tl*kMaxRows] outermost first
   int* sec_owner;          // [n] sorted index space: tracklet index or -1
+  uint8_t* st_kept;        // [n] edge following: sorted cluster kept by a sector track
+  int* edge_flag;          // [2 * cap_tl + 1] edge following: end (2 j + inner) found a segment
+  int* edge_pos;           // [2 * cap_tl + 1] its exclusive prefix sum (segment index)
   uint8_t* sused;          // [n] sorted cluster taken by an accepted tracklet of an earlier
                            // sector-tracking iteration (iterations after the first)
   // online cluster removal (after a tracking call)

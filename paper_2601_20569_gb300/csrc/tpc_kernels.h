@@ -17,6 +17,7 @@ namespace tpc {
   int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
   int stage_reseed(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
   int stage_sector_refit(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \
+  int stage_edge(FrameDev& F, const KParams& P, int sms, cudaStream_t s);               \
   int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s);              \
   int stage_fit12(FrameDev& F, const KParams& P, int sms, cudaStream_t s);              \
   int stage_ambiguity2(FrameDev& F, const KParams& P, int sms, cudaStream_t s);         \

@@ -395,4 +395,23 @@ __device__ __forceinline__ bool seed3(const float* x, const float* y, const floa
   return true;
 }
 
+// Stored track state (kStateF floats): p[5], the covariance's 15 elements,
+// x, and the sector's bits.
+__device__ __forceinline__ void put_state(float* dst, const Trk<float>& t, int sector) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dst[i] = t.p[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) dst[5 + i] = t.c[i];
+  dst[20] = t.x;
+  dst[21] = __int_as_float(sector);
+}
+
+__device__ __forceinline__ void get_state(const float* src, Trk<float>& t) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) t.p[i] = src[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) t.c[i] = src[5 + i];
+  t.x = src[20];
+}
+
 }  // namespace tpc

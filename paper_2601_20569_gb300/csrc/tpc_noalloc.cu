@@ -133,6 +133,7 @@ extern "C" tpc_status tpc_links_noalloc(const tpc_geometry* geo, const tpc_optio
   for (int i = 0; i < kLNum; ++i) {
     F.lc.block[i] = 128;
     F.lc.per_sm[i] = 8;
+    F.lc.lanes[i] = 1;
   }
   F.y = cl->y;
   F.z = cl->z;

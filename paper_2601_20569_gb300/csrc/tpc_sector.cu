@@ -18,16 +18,35 @@ namespace TPC_NS {
 namespace {
 
 // ------------------------------------------------------------------ a1 grid
-// Sector of input cluster i (batch sector in a multi-frame call).
-__device__ __forceinline__ int sector_of(const FrameDev& F, long i) {
-  return F.bsector ? (int)F.bsector[i] : (int)F.sector[i];
+// Input cluster i: position, row and (batch) sector.  A batch call reads each
+// frame in place through the frame table: the frame holding i is found by a
+// binary search over the frames' offsets, and a sector outside the frame's
+// range gives an out-of-range batch sector, which the grid build reports.
+struct ClusterIn {
+  float y, z;
+  int row, sector;
+};
+
+__device__ __forceinline__ ClusterIn load_cluster(const FrameDev& F, long i) {
+  if (F.nsrc == 0) return {F.y[i], F.z[i], (int)F.row[i], (int)F.sector[i]};
+  int lo = 0, hi = F.nsrc - 1;  // the last frame whose offset is <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (F.src[mid].off <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const FrameSrc& S = F.src[lo];
+  const long j = i - S.off;
+  const int s = S.sector[j];
+  return {S.y[j], S.z[j], (int)S.row[j], s < F.src_nsec ? lo * F.src_nsec + s : 0x7FFFFFFF};
 }
 
 __global__ void k_row_stats(FrameDev F, KParams P) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n) return;
-  const int r = F.row[i], s = sector_of(F, i);
-  const float y = F.y[i], z = F.z[i];
+  const ClusterIn c = load_cluster(F, i);
+  const int r = c.row, s = c.sector;
+  const float y = c.y, z = c.z;
   if (r >= P.n_rows || s >= P.n_sectors || !isfinite(y) || !isfinite(z)) {
     atomicOr(&F.cnt->err, kErrInput);
     return;
@@ -41,9 +60,9 @@ __global__ void k_row_stats(FrameDev F, KParams P) {
 // One block: bin layout of every (sector,row) and the row/bin offsets.
 __global__ void k_row_grid(FrameDev F, KParams P) {
   __shared__ int sh[32];
-  __shared__ int carry_bins, carry_cl;
+  __shared__ int carry_bins;
   const int nrr = P.n_sectors * P.n_rows;
-  if (threadIdx.x == 0) { carry_bins = 0; carry_cl = 0; }
+  if (threadIdx.x == 0) carry_bins = 0;
   __syncthreads();
   for (int base = 0; base < nrr; base += blockDim.x) {
     const int rr = base + threadIdx.x;
@@ -54,16 +73,22 @@ __global__ void k_row_grid(FrameDev F, KParams P) {
       cnt = F.row_cnt[rr];
       const float x = F.row_x[r];
       const float ymax = x * P.tan_half + 0.5f;
-      int nY = (int)(2.0f * ymax / P.grid_dy);
-      nY = clampi(nY, 1, 64);
-      g.nY = nY;
-      g.y0 = -ymax;
-      g.invDy = (float)nY / (2.0f * ymax);
       int nZ = 1;
       float zlo = 0.0f, zr = 0.0f;
       if (cnt > 0) {
         zlo = o2f(F.row_zmin[rr]);
         zr = o2f(F.row_zmax[rr]) - zlo;
+      }
+      // about square bins holding grid_occ clusters each, at least grid_dy
+      // wide in y: the search windows (a few cm in y and in z) then cover few
+      // bins and few clusters outside the window
+      const float side = sqrtf(2.0f * ymax * fmaxf(zr, 1.0f) * P.grid_occ / (float)max(cnt, 1));
+      int nY = (int)(2.0f * ymax / fmaxf(side, P.grid_dy));
+      nY = clampi(nY, 1, 64);
+      g.nY = nY;
+      g.y0 = -ymax;
+      g.invDy = (float)nY / (2.0f * ymax);
+      if (cnt > 0) {
         const float want = ceilf((float)cnt / ((float)nY * P.grid_occ));
         const float zmax_bins = floorf(zr) + 1.0f;  // bins of at least ~1 cm
         nZ = (int)fminf(fminf(want, zmax_bins), (float)((1 << 20) / nY));
@@ -75,16 +100,14 @@ __global__ void k_row_grid(FrameDev F, KParams P) {
       g.ncl = cnt;
       nb = nY * nZ;
     }
-    int tot_b, tot_c;
+    int tot_b;
     const int ob = block_exscan(nb, sh, &tot_b);
-    const int oc = block_exscan(cnt, sh, &tot_c);
     if (rr < nrr) {
       g.bin0 = carry_bins + ob;
-      g.cl0 = carry_cl + oc;
       F.rows[rr] = g;
     }
     __syncthreads();
-    if (threadIdx.x == 0) { carry_bins += tot_b; carry_cl += tot_c; }
+    if (threadIdx.x == 0) carry_bins += tot_b;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -96,10 +119,11 @@ __global__ void k_row_grid(FrameDev F, KParams P) {
 __global__ void k_bin_hist(FrameDev F, KParams P) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n || F.cnt->err) return;
-  const int rr = sector_of(F, i) * P.n_rows + F.row[i];
+  const ClusterIn c = load_cluster(F, i);
+  const int rr = c.sector * P.n_rows + c.row;
   const RowGrid g = F.rows[rr];
-  const int iy = bin_of(F.y[i], g.y0, g.invDy, g.nY);
-  const int iz = bin_of(F.z[i], g.z0, g.invDz, g.nZ);
+  const int iy = bin_of(c.y, g.y0, g.invDy, g.nY);
+  const int iz = bin_of(c.z, g.z0, g.invDz, g.nZ);
   const int b = g.bin0 + iz * g.nY + iy;
   F.cl_bin[i] = b;
   F.cl_slot[i] = atomicAdd(&F.bin_cnt[b], 1);
@@ -109,9 +133,10 @@ __global__ void k_scatter(FrameDev F, KParams P) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n || F.cnt->err) return;
   const int pos = F.bin_first[F.cl_bin[i]] + F.cl_slot[i];
-  F.syz[pos] = make_float2(F.y[i], F.z[i]);
+  const ClusterIn c = load_cluster(F, i);
+  F.syz[pos] = make_float2(c.y, c.z);
   F.sid[pos] = (int)i;
-  F.srow[pos] = (uint16_t)(sector_of(F, i) * P.n_rows + F.row[i]);
+  F.srow[pos] = (uint16_t)(c.sector * P.n_rows + c.row);
 }
 
 // Order the clusters of each bin by input id (deterministic layout).
@@ -292,8 +317,9 @@ struct Pick {
 
 // Best cluster of row (s, r) with chi2 < follow_chi2 (ties: smaller input id);
 // the y/z box is the widened 2x2 Mahalanobis bound of the cut.  kLeft: the
-// clusters taken by earlier sector-tracking iterations are not candidates.
-template <bool kLeft>
+// clusters taken by earlier sector-tracking iterations are not candidates;
+// kKept: nor those kept by a sector track (the edge following).
+template <bool kLeft, bool kKept = false>
 __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const Trk<float>& t,
                                     const RowGrid& g, float& by, float& bz) {
   const float hy = sqrtf(P.follow_chi2 * (t.c[0] + P.sy2)) * 1.001f + 0.01f;
@@ -304,6 +330,7 @@ __device__ __forceinline__ int pick(const FrameDev& F, const KParams& P, const T
   float bchi = 0.0f;
   for_window(F.bin_first, g, ylo, yhi, zlo, zhi, [&](int k) {
     if (kLeft && F.sused[k]) return;
+    if (kKept && F.st_kept[k]) return;
     const float2 pk = F.syz[k];
     const float yk = pk.x, zk = pk.y;
     if (!(yk >= ylo && yk <= yhi)) return;
@@ -724,6 +751,180 @@ __global__ void k_pass_begin(FrameDev F, int pass) {
   F.cnt->queue[kQTlDown] = 0;
 }
 
+// ------------------------------------------------------------ edge following
+// Sec. 2: the sector tracking cannot find very short track segments, so
+// tracks ending at a sector edge close to the upper or lower end of the TPC
+// are propagated into the adjacent sector before the merging and followed
+// there.  From each end of a sector track the end state is propagated row by
+// row away from the track over at most edge_rows rows, over its sector's edge
+// once (rotation into the neighbouring sector of the same side, then the
+// row's x there); from the crossing on, each row's best cluster kept by no
+// sector track is filtered in, until max_miss rows in a row have none.  A
+// segment of at least edge_min clusters becomes a sector track of the
+// neighbouring sector (a tracklet slot holds its clusters), linked to the
+// track it continues before the merging.  Segment order and keys do not
+// depend on scheduling: ends are numbered 2 j + (inner end), segments are
+// compacted in that order, and a segment's key is its track's key plus 2^29
+// (inner end) or 2^30 (outer end).
+
+__global__ void k_edge_mark(FrameDev F) {
+  const int ns = F.cnt->n_tracks;
+  if (F.cnt->err) return;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x) {
+    if (!F.st_ok[j]) continue;
+    const int ti = F.st_tl[j];
+    const int nk = F.tl_nkept[ti];
+    const int* K = F.tl_kept + (long)ti * kMaxRows;
+    for (int m = 0; m < nk; ++m) F.st_kept[K[m]] = 1;
+  }
+}
+
+// Can an end reach its sector's edge within the rows ahead (x1: the last of
+// them)?  Along a helix sin(phi) is linear in x, so over the run |sin(phi)|
+// stays below s = max(|sin(phi0)|, |sin(phi0) + kappa dx|) and |dy/dx| below
+// t = s / sqrt(1 - s^2); the distance to the edge, x tan(10 deg) - |y|, can
+// then shrink by at most |dx| (t -+ tan(10 deg)) (outward / inward).  A 1 cm
+// margin covers the rounding; an end ruled out here would cross no edge in
+// the row-by-row propagation either, so the result does not change.
+__device__ __forceinline__ bool edge_reachable(const Trk<float>& t, float x1, const KParams& P) {
+  const float dx = x1 - t.x;
+  const float s0 = t.p[2];
+  const float s = fmaxf(fabsf(s0), fabsf(s0 + t.p[4] * P.kb * dx));
+  if (!(s < P.max_snp)) return true;  // the propagation decides
+  const float tmax = s / sqrtf(1.0f - s * s);
+  const float e0 = t.x * P.tan_half - fabsf(t.p[0]);
+  const float close = fabsf(dx) * (dx > 0.0f ? tmax - P.tan_half : tmax + P.tan_half);
+  return e0 - 1.0f < close;
+}
+
+// The segment beyond one end of sector track j: returns the clusters found;
+// their sorted indices go to K in the order found, `first` / `last` receive
+// the filter after the first and the last of them, `sec` the sector.
+__device__ int edge_follow(const FrameDev& F, const KParams& P, int j, bool inner, int* K,
+                           Trk<float>* first, Trk<float>* last, int& sec) {
+  const int NR = P.n_rows;
+  Trk<float> t;
+  get_state((inner ? F.st_ie : F.st_oe) + (long)j * kStateF, t);
+  sec = F.st_sector[j];
+  const int dir = inner ? -1 : 1;
+  const int r0 = inner ? F.st_rmin[j] : F.st_rmax[j];
+  const int r_end = inner ? max(r0 - P.edge_rows, 0) : min(r0 + P.edge_rows, NR - 1);
+  if (r_end == r0 || !edge_reachable(t, F.row_x[r_end], P)) return 0;
+  bool crossed = false;
+  int miss = 0, nh = 0;
+  for (int e = 1; e <= P.edge_rows; ++e) {
+    const int r = r0 + dir * e;
+    if (r < 0 || r >= NR) break;
+    if (!propagate(t, F.row_x[r], P, P.max_snp)) break;
+    if (!crossed && fabsf(t.p[0]) > t.x * P.tan_half) {
+      const int d = t.p[0] > 0.0f ? 1 : -1;
+      if (!rotate(t, d, P, P.max_snp)) break;
+      const int half = P.n_phi;
+      sec = sec - sec % half + (sec % half + (d > 0 ? 1 : half - 1)) % half;
+      if (!propagate(t, F.row_x[r], P, P.max_snp)) break;
+      crossed = true;
+    }
+    if (fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin) break;
+    if (!crossed) continue;
+    float ky = 0.0f, kz = 0.0f;
+    const int k = pick<false, true>(F, P, t, F.rows[sec * NR + r], ky, kz);
+    if (k >= 0) {
+      update(t, residual(t, ky, kz, P));
+      if (K) K[nh] = k;
+      if (first && nh == 0) *first = t;
+      if (last) *last = t;
+      ++nh;
+      miss = 0;
+    } else if (++miss >= P.max_miss) {
+      break;
+    }
+  }
+  return nh;
+}
+
+// Which ends find a segment (flag per end, over the whole capacity so that
+// the scan behind it reads no stale flags).
+__global__ void k_edge_count(FrameDev F, KParams P) {
+  const int ns = F.cnt->n_tracks;
+  const long m = 2 * F.cap_tl;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q <= m;
+       q += (long)gridDim.x * blockDim.x) {
+    int f = 0;
+    const int j = (int)(q >> 1);
+    if (!F.cnt->err && q < 2L * ns && F.st_ok[j]) {
+      int sec;
+      f = edge_follow(F, P, j, (q & 1) != 0, nullptr, nullptr, nullptr, sec) >= P.edge_min;
+    }
+    F.edge_flag[q] = f;
+  }
+}
+
+// Room for the segments: sector-track entries after the tracks, tracklet
+// slots after the tracklets.
+__global__ void k_edge_commit(FrameDev F) {
+  const int ns = F.cnt->n_tracks;
+  const int ntl = min(F.cnt->n_starts, (int)F.cap_tl);
+  const int nseg = F.edge_pos[2 * F.cap_tl];
+  F.cnt->n_st0 = ns;
+  F.cnt->n_tl_all = ntl;
+  if (F.cnt->err) return;
+  const long need = (long)max(ns, ntl) + nseg;
+  if (need > F.cap_tl) {
+    atomicOr(&F.cnt->err, kErrCapEdge);
+    atomicMax(&F.cnt->need_tracklets, (int)need);
+    return;
+  }
+  F.cnt->n_tracks = ns + nseg;
+}
+
+// Every segment: the following again, now keeping its clusters, states and
+// links.  The outer segment of j continues j (j -> segment), the inner one
+// leads into it (segment -> j); the linked ends take no part in the merging.
+__global__ void k_edge_write(FrameDev F, KParams P) {
+  const int ns0 = F.cnt->n_st0, ntl = F.cnt->n_tl_all;
+  if (F.cnt->err) return;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < 2L * ns0;
+       q += (long)gridDim.x * blockDim.x) {
+    if (!F.edge_flag[q]) continue;
+    const int j = (int)(q >> 1);
+    const bool inner = (q & 1) != 0;
+    const int k = F.edge_pos[q];
+    const int i = ns0 + k, ti = ntl + k;
+    int H[kMaxRows];
+    Trk<float> first, last;
+    int sec;
+    const int nh = edge_follow(F, P, j, inner, H, &first, &last, sec);
+    int* K = F.tl_kept + (long)ti * kMaxRows;  // outermost first
+    for (int m = 0; m < nh; ++m) K[m] = inner ? H[m] : H[nh - 1 - m];
+    F.tl_nkept[ti] = nh;
+    F.tl_rlo[ti] = 1;  // no tracklet hits (the seeding history of the cluster removal)
+    F.tl_rhi[ti] = 0;
+    F.st_tl[i] = ti;
+    F.st_key[i] = F.st_key[j] + (inner ? (1 << 29) : (1 << 30));
+    F.st_sector[i] = sec;
+    const int r_a = F.srow[H[0]] % P.n_rows, r_b = F.srow[H[nh - 1]] % P.n_rows;
+    F.st_rmin[i] = inner ? r_b : r_a;
+    F.st_rmax[i] = inner ? r_a : r_b;
+    put_state(F.st_ie + (long)i * kStateF, inner ? last : first, sec);
+    put_state(F.st_oe + (long)i * kStateF, inner ? first : last, sec);
+    F.st_ok[i] = 1;
+    F.st_bestB[i] = -1;
+    F.st_bestA[i] = ~0ull;
+    F.st_xbestB[i] = -1;
+    F.st_xbestA[i] = ~0ull;
+    F.st_dz[i] = 0.0f;
+    if (inner) {
+      F.st_next[i] = j;
+      F.st_hasprev[i] = 0;
+      F.st_hasprev[j] = 1;
+    } else {
+      F.st_next[j] = i;
+      F.st_next[i] = -1;
+      F.st_hasprev[i] = 1;
+    }
+  }
+}
+
 }  // namespace
 
 // Stage launchers; each returns the number of kernels it enqueued.
@@ -780,6 +981,17 @@ int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
 // Sector-tracking iterations 2..seed_iters, each on the clusters the accepted
 // tracklets of the earlier ones left: the same neighbour finding, cleaning,
 // start hits, tracklet construction and selection, over the free clusters.
+int stage_edge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
+  if (P.edge_rows <= 0) return 0;
+  if (cudaMemsetAsync(F.st_kept, 0, F.n > 0 ? F.n : 1, s) != cudaSuccess) return 0;
+  k_edge_mark<<<sms * 8, kBlock, 0, s>>>(F);
+  k_edge_count<<<sms * 8, kBlock, 0, s>>>(F, P);
+  int k = 2 + scan_exclusive(F.edge_flag, F.edge_pos, 2 * F.cap_tl + 1, F.scan_tmp, s);
+  k_edge_commit<<<1, 1, 0, s>>>(F);
+  k_edge_write<<<sms * 8, kBlock, 0, s>>>(F, P);
+  return k + 2;
+}
+
 int stage_reseed(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const long n = F.n;
   if (P.seed_iters <= 1 || n <= 0) return 0;

@@ -57,6 +57,7 @@ class Options(ctypes.Structure):
         ("inner_rows", ctypes.c_int32), ("cand_k", ctypes.c_int32), ("mode", ctypes.c_int32),
         ("max_frames", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
         ("ext_rows", ctypes.c_int32), ("seed_iters", ctypes.c_int32), ("ac_merge", ctypes.c_int32),
+        ("edge_rows", ctypes.c_int32), ("edge_min", ctypes.c_int32),
         ("cap_clusters", ctypes.c_int64), ("cap_tracklets", ctypes.c_int64),
         ("cap_tracks", ctypes.c_int64),
     ]
@@ -181,6 +182,7 @@ _DBG_DTYPE = {
     "sused": np.uint8, "pass_start": np.int32, "cr_flags": np.uint32, "cr_centre_x": np.float32,
     "cr_centre_y": np.float32,
     "st_tl": np.int32, "st_ok": np.int32, "st_key": np.int32, "st_next": np.int32,
+    "st_bestB": np.int32, "st_bestchi": np.float32, "st_bestA": np.uint64,
     "st_ie": np.float32, "st_oe": np.float32, "ft_key": np.int32, "ft_ok": np.int32,
     "ft_nst": np.int32, "ft_st_cl": np.int32, "ft_st_rs": np.uint16, "ft_flag": np.uint8,
     "ft_ncand": np.uint8, "ft_cand": np.int32, "ft_cchi": np.float32, "ft_assigned": np.int32,
@@ -191,9 +193,8 @@ _DBG_DTYPE = {
 STATE_F = 22       # floats per stored state: p[5], c[15], x, sector bits
 MAX_INNER = 32     # inner-row slots per fit track (extrapolated rows follow them)
 MAX_CAND = 8       # candidate slots per inner row
-ROWGRID_DTYPE = np.dtype([("bin0", "<i4"), ("nY", "<i4"), ("nZ", "<i4"), ("cl0", "<i4"),
-                          ("ncl", "<i4"), ("y0", "<f4"), ("invDy", "<f4"), ("z0", "<f4"),
-                          ("invDz", "<f4")])
+ROWGRID_DTYPE = np.dtype([("bin0", "<i4"), ("nY", "<i4"), ("nZ", "<i4"), ("ncl", "<i4"),
+                          ("y0", "<f4"), ("invDy", "<f4"), ("z0", "<f4"), ("invDz", "<f4")])
 
 
 class Tracker:
@@ -274,7 +275,7 @@ class Tracker:
             lib.tpc_autotune.restype = ctypes.c_int
             lib.tpc_launch_config.argtypes = [ctypes.c_void_p, ctypes.c_int32,
                                               P(ctypes.c_char_p), P(ctypes.c_int32),
-                                              P(ctypes.c_int32)]
+                                              P(ctypes.c_int32), P(ctypes.c_int32)]
             lib.tpc_launch_config.restype = ctypes.c_int
             lib._batch_typed = True
         arr = (Clusters * len(frames))()
@@ -311,25 +312,36 @@ class Tracker:
         return self.launch_config()
 
     def launch_config(self) -> list[dict]:
+        P = ctypes.POINTER
+        self.lib.tpc_launch_config.argtypes = [ctypes.c_void_p, ctypes.c_int32,
+                                               P(ctypes.c_char_p), P(ctypes.c_int32),
+                                               P(ctypes.c_int32), P(ctypes.c_int32)]
+        self.lib.tpc_launch_config.restype = ctypes.c_int
         out = []
         for slot in range(16):
             name = ctypes.c_char_p()
             b = ctypes.c_int32()
             q = ctypes.c_int32()
+            ln = ctypes.c_int32()
             if self.lib.tpc_launch_config(self._ctx, slot, ctypes.byref(name), ctypes.byref(b),
-                                          ctypes.byref(q)):
+                                          ctypes.byref(q), ctypes.byref(ln)):
                 break
-            out.append({"kernel": name.value.decode(), "block": b.value, "blocks_per_sm": q.value})
+            out.append({"kernel": name.value.decode(), "block": b.value, "blocks_per_sm": q.value,
+                        "lanes": ln.value})
         return out
 
     def set_launch_config(self, shapes) -> None:
         """Apply launch shapes, e.g. the list launch_config() returned earlier
-        (dicts with "block" and "blocks_per_sm", in slot order)."""
+        (dicts with "block", "blocks_per_sm" and optionally "lanes", in slot
+        order; lanes defaults to the slot's current value)."""
         fn = self.lib.tpc_set_launch_config
-        fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                       ctypes.c_int32]
         fn.restype = ctypes.c_int
+        cur = self.launch_config()
         for slot, sh in enumerate(shapes):
-            rc = fn(self._ctx, slot, int(sh["block"]), int(sh["blocks_per_sm"]))
+            lanes = int(sh.get("lanes", cur[slot]["lanes"] if slot < len(cur) else 1))
+            rc = fn(self._ctx, slot, int(sh["block"]), int(sh["blocks_per_sm"]), lanes)
             if rc:
                 raise TpcError(rc, self.last_error())
 
@@ -455,6 +467,22 @@ class Tracker:
         if rc:
             raise TpcError(rc, self.last_error())
         return g
+
+    @staticmethod
+    def fma_peak(fp64: bool = False, iters: int = 4096) -> float:
+        """Measured FMA throughput of the current device in TFLOP/s (tpc_fma_peak)."""
+        import torch
+
+        lib = load()
+        lib.tpc_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+        lib.tpc_fma_peak.restype = ctypes.c_int
+        v = ctypes.c_double(0.0)
+        rc = lib.tpc_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(v),
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if rc:
+            raise TpcError(rc, "tpc_fma_peak")
+        return v.value
 
     def refit_generation(self) -> int:
         """Successful refits on this context so far (tpc_refit_generation)."""

@@ -1,5 +1,5 @@
 """Host-side parts of the benchmark (no GPU): the byte model of the stages and
-the DRAM traffic it reads from the committed ncu summary."""
+the DRAM traffic figures it reads from profiles/traffic.json."""
 from __future__ import annotations
 
 import bench
@@ -20,7 +20,7 @@ def test_every_stage_has_a_byte_model():
     assert bench.stage_bytes("reseed", more) > 53 * COUNTS["clusters"]
 
 
-def test_traffic_of_the_heavy_stages_comes_from_the_committed_profile():
+def test_traffic_figures_come_from_the_committed_json():
     for stage in ("tracklets", "fit12", "fit3", "sector_refit", "links"):
         t, src = bench.measured_traffic(stage, COUNTS)
         assert t is not None and src, stage
@@ -29,3 +29,22 @@ def test_traffic_of_the_heavy_stages_comes_from_the_committed_profile():
         per = t / COUNTS["clusters"]
         assert 0.5 * bench.stage_bytes(stage, COUNTS) / COUNTS["clusters"] < per < 400.0, stage
     assert bench.measured_traffic("no_such_stage", COUNTS) == (None, None)
+
+
+def test_whole_chain_traffic_is_at_least_the_algorithmic_bytes():
+    t, src = bench.measured_traffic("chain", COUNTS)
+    if t is None:  # no whole-chain capture committed, or marked stale
+        return
+    assert bench.CHAIN_BYTES_PER_CLUSTER * COUNTS["clusters"] < t < 2000 * COUNTS["clusters"]
+
+
+def test_stale_figures_are_not_reported(tmp_path, monkeypatch):
+    import json
+
+    table = {"tracklets": {"bytes_per_cluster": 200.0, "kernels": "k", "workload": "w",
+                           "stale": True}}
+    monkeypatch.setattr(bench, "_traffic_table", lambda: table)
+    assert bench.measured_traffic("tracklets", COUNTS) == (None, None)
+    table["tracklets"].pop("stale")
+    assert bench.measured_traffic("tracklets", COUNTS)[0] == 200.0 * COUNTS["clusters"]
+    json.dumps(table)

@@ -39,15 +39,15 @@ def host(tr):
     return {k: v.cpu().numpy() for k, v in tr.result().items()}
 
 
-@pytest.mark.parametrize("graphs", [False, True])
-def test_batch_equals_frames_alone(graphs):
+@pytest.mark.parametrize("graphs,edge", [(False, 0), (True, 0), (True, 20)])
+def test_batch_equals_frames_alone(graphs, edge):
     from paper_2601_20569_gb300 import tpc
 
     frames = [synth.generate("central_event", n_primaries=1500, seed=11),
               synth.generate("one_sector"),
               synth.generate("central_event", n_primaries=800, seed=12)]
     ntot = sum(f.n for f in frames)
-    opts = TrackerOptions().as_dict()
+    opts = TrackerOptions(edge_rows=edge).as_dict()
     tb = tpc.Tracker(RX, opts, mode=0, cap_clusters=ntot, max_frames=4, use_graphs=graphs)
     dev = [tb.to_device(f.y, f.z, f.q, f.row, f.sector) for f in frames]
     offsets = np.concatenate([[0], np.cumsum([f.n for f in frames])])
@@ -107,6 +107,8 @@ def test_autotune_keeps_results():
     cfg = tb.autotune(dev)
     assert len(cfg) == 5
     assert all(c["block"] in (64, 128, 256) and c["blocks_per_sm"] in (4, 8, 16) for c in cfg)
+    assert cfg[2]["lanes"] in (1, 8, 16, 32) and all(c["lanes"] == 1 for i, c in enumerate(cfg)
+                                                     if i != 2)
     tb.track_batch(dev)
     after = host(tb)
     for k in ("params", "key", "cl_ids", "attach"):
@@ -132,10 +134,21 @@ def test_set_launch_config_keeps_results_and_rejects_bad_shapes():
     after = host(tb)
     for k in ("params", "cov", "key", "cl_ids", "attach"):
         assert np.array_equal(before[k].view(np.uint8), after[k].view(np.uint8)), k
+    # the merge search on groups of 1, 4, 8, 16 and 32 lanes per outer end
+    for lanes in (1, 4, 8, 16, 32):
+        tb.set_launch_config(shapes[:2] + [dict(shapes[2], lanes=lanes)])
+        assert tb.launch_config()[2]["lanes"] == lanes
+        tb.track(*dev)
+        after = host(tb)
+        for k in ("params", "cov", "key", "cl_ids", "attach"):
+            assert np.array_equal(before[k].view(np.uint8), after[k].view(np.uint8)), (k, lanes)
     for bad in ({"block": 48, "blocks_per_sm": 4}, {"block": 512, "blocks_per_sm": 4},
-                {"block": 128, "blocks_per_sm": 0}, {"block": 128, "blocks_per_sm": 33}):
+                {"block": 128, "blocks_per_sm": 0}, {"block": 128, "blocks_per_sm": 33},
+                {"block": 128, "blocks_per_sm": 4, "lanes": 8}):  # slot 0 has one lane
         with pytest.raises(tpc.TpcError):
             tb.set_launch_config([bad])
+    with pytest.raises(tpc.TpcError):
+        tb.set_launch_config(shapes[:2] + [dict(shapes[2], lanes=12)])
 
 
 def test_full_size_frames_sampled_sector_parity():

@@ -55,9 +55,10 @@ def compare_sector(tr, y, z, row, sec, opts, R=152):
     syz = tr.debug("syz")
     sy, sz = syz[0::2], syz[1::2]
     assert np.array_equal(sy, y[sid]) and np.array_equal(sz, z[sid])
+    cl0 = np.concatenate([[0], np.cumsum(rows["ncl"].astype(np.int64))])
     for rr in np.nonzero(rows["ncl"])[0][:400]:
         g = rows[rr]
-        k = np.arange(g["cl0"], g["cl0"] + g["ncl"])
+        k = np.arange(cl0[rr], cl0[rr] + g["ncl"])
         iy = np.clip(np.floor((sy[k] - g["y0"]) * g["invDy"]).astype(np.int64), 0, g["nY"] - 1)
         iz = np.clip(np.floor((sz[k] - g["z0"]) * g["invDz"]).astype(np.int64), 0, g["nZ"] - 1)
         b = g["bin0"] + iz * g["nY"] + iy
