@@ -168,13 +168,15 @@ __global__ void k_st_gather(FrameDev F, KParams P) {
     return;
   }
   const int NR = P.n_rows;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x) {
+  // one warp per track: its kept list read and its positions written 32 at a time
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < ns; j += nw) {
     const int ti = F.st_tl[j];
     const int nk = F.tl_nkept[ti];
     const int* K = F.tl_kept + (long)ti * kMaxRows;
     float4* out = F.st_pos + F.st_off[j];
-#pragma unroll 4
-    for (int m = 0; m < nk; ++m) {
+    for (int m = lane; m < nk; m += 32) {
       const int c = K[m];
       const float2 yz = F.syz[c];
       out[m] = make_float4(F.row_x[F.srow[c] % NR], yz.x, yz.y, 0.0f);

@@ -767,15 +767,17 @@ __global__ void k_pass_begin(FrameDev F, int pass) {
 // compacted in that order, and a segment's key is its track's key plus 2^29
 // (inner end) or 2^30 (outer end).
 
-__global__ void k_edge_mark(FrameDev F) {
+__global__ void k_edge_mark(FrameDev F) {  // one warp per sector track
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < ns; j += nw) {
     if (!F.st_ok[j]) continue;
     const int ti = F.st_tl[j];
     const int nk = F.tl_nkept[ti];
     const int* K = F.tl_kept + (long)ti * kMaxRows;
-    for (int m = 0; m < nk; ++m) F.st_kept[K[m]] = 1;
+    for (int m = lane; m < nk; m += 32) F.st_kept[K[m]] = 1;
   }
 }
 

@@ -150,10 +150,11 @@ def test_stress_error_table_against_fp64(stress):
               f"{q['attached']:.5f}; {len(err)} of {len(hits)} tracks with the FP64 clusters")
         for m, lab in ((~loop, "non-loopers"), (loop, "loopers")):
             e = err[m]
+            fmt = {"float_kind": lambda v: f"{v:.1e}"}
             print(f"   {lab:11s} ({m.sum():6d}) |dp|/sigma (y, z, snp, tgl, q/pT): median "
-                  f"{np.array2string(np.median(e, 0), precision=2)} p99 "
-                  f"{np.array2string(np.percentile(e, 99, 0), precision=2)} max "
-                  f"{np.array2string(e.max(0), precision=2)}")
+                  f"{np.array2string(np.median(e, 0), formatter=fmt)} p99 "
+                  f"{np.array2string(np.percentile(e, 99, 0), formatter=fmt)} max "
+                  f"{np.array2string(e.max(0), formatter=fmt)}")
         worst = err.max(axis=1)
         assert abs(q["eff"] - q64["eff"]) <= 0.002 and abs(q["fake_rate"] - q64["fake_rate"]) <= 0.002
         # at this occupancy about a tenth of the tracks take a discrete decision
