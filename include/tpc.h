@@ -278,19 +278,21 @@ tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_f
 tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_frames,
                         void* cuda_stream);
 
-/* Launch shape chosen for heavy kernel `slot` (0..4): kernel name, block
+/* Launch shape chosen for heavy kernel `slot` (0..5): kernel name, block
  * size, blocks per SM, lanes per work item (1 = one thread per item; the
  * merge search of slot 2 runs one item on a group of 1, 4, 8, 16 or 32
- * lanes).  Any output pointer may be NULL.  TPC_ERR_INVALID_ARG past the last
- * slot. */
+ * lanes, the neighbour search of slot 5 one cluster on 1, 4 or 8 lanes, in
+ * one launch of 256-thread blocks over the clusters).  Any output pointer may
+ * be NULL.  TPC_ERR_INVALID_ARG past the last slot. */
 tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
                              int32_t* block, int32_t* blocks_per_sm, int32_t* lanes);
 
-/* Set the launch shape of heavy kernel `slot` (0..4, as tpc_launch_config
+/* Set the launch shape of heavy kernel `slot` (0..5, as tpc_launch_config
  * numbers them), e.g. to reapply a shape the autotuner chose earlier on the
  * same GPU.  block: multiple of 32 in [32, 256] (the kernels are compiled for
  * at most 256 threads per block); blocks_per_sm in [1, 32]; lanes: 1, or for
- * slot 2 (merge search) one of 4, 8, 16, 32.
+ * slot 2 (merge search) one of 4, 8, 16, 32, for slot 5 (neighbour search)
+ * 4 or 8 (slot 5 uses only its lanes).
  * The shape changes only scheduling: results are identical for every shape.
  * TPC_ERR_INVALID_ARG for any other value. */
 tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,

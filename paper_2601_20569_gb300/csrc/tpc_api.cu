@@ -258,6 +258,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
     F.lc.lanes[i] = 1;
   }
   F.lc.lanes[kLMerge] = kMergeLanesDefault;
+  F.lc.lanes[kLLinks] = kLinksLanesDefault;
   F.cap_bins = (long)((double)n / ctx->P.grid_occ) + nrr * 65;
   F.cap_tl = opt->cap_tracklets > 0 ? opt->cap_tracklets : n / 10 + 4096;
   bool ok = true;
@@ -659,10 +660,12 @@ tpc_status tpc_track_batch(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_f
 tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_frames,
                         void* cuda_stream) {
   if (!ctx || !frames || n_frames < 1) return TPC_ERR_INVALID_ARG;
-  static const char* slot_stage[kLNum] = {"tracklets", "sector_refit", "merge", "fit12", "fit3"};
+  static const char* slot_stage[kLNum] = {"tracklets", "sector_refit", "merge", "fit12", "fit3",
+                                          "links"};
   static const int blocks[] = {64, 128, 256};
   static const int per_sm[] = {4, 8, 16};
   static const int merge_lanes[] = {1, 8, 16, 32};
+  static const int links_lanes[] = {1, 4, 8};
   const bool prof_was = ctx->prof;
   if (!ctx->ev[0])
     for (auto& e : ctx->ev)
@@ -675,13 +678,16 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
     while (st < kNumStages && std::strcmp(kStages[st].name, slot_stage[slot]) != 0) ++st;
     double best = 1e30;
     LaunchCfg best_lc = ctx->F.lc;
-    const int nl = slot == kLMerge ? 4 : 1;
+    // the neighbour search is one launch over the clusters: only its lanes vary
+    const int nl = slot == kLMerge ? 4 : slot == kLLinks ? 3 : 1;
+    const int nb = slot == kLLinks ? 1 : 3, nq = slot == kLLinks ? 1 : 3;
     for (int li = 0; li < nl; ++li)
-    for (int b : blocks)
-      for (int q : per_sm) {
-        ctx->F.lc.block[slot] = b;
-        ctx->F.lc.per_sm[slot] = q;
-        ctx->F.lc.lanes[slot] = slot == kLMerge ? merge_lanes[li] : 1;
+    for (int bi = 0; bi < nb; ++bi)
+      for (int qi = 0; qi < nq; ++qi) {
+        ctx->F.lc.block[slot] = slot == kLLinks ? 256 : blocks[bi];
+        ctx->F.lc.per_sm[slot] = slot == kLLinks ? 8 : per_sm[qi];
+        ctx->F.lc.lanes[slot] = slot == kLMerge ? merge_lanes[li]
+                                : slot == kLLinks ? links_lanes[li] : 1;
         double t = 0.0;
         for (int rep = 0; rep < 2; ++rep) {
           const double before = ctx->stage_ms[st];
@@ -712,8 +718,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
 tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
                              int32_t* block, int32_t* blocks_per_sm, int32_t* lanes) {
   static const char* names[kLNum] = {"k_tl_up+k_tl_down", "k_sector_refit", "k_merge_best",
-                                     "k_fit1+k_fit2",
-                                     "k_fit3"};
+                                     "k_fit1+k_fit2", "k_fit3", "k_links"};
   if (!ctx || slot < 0 || slot >= kLNum) return TPC_ERR_INVALID_ARG;
   if (kernel) *kernel = names[slot];
   if (block) *block = ctx->F.lc.block[slot];
@@ -725,8 +730,9 @@ tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kern
 tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
                                  int32_t blocks_per_sm, int32_t lanes) {
   if (!ctx) return TPC_ERR_INVALID_ARG;
-  const bool lanes_ok = lanes == 1 || (slot == kLMerge && (lanes == 4 || lanes == 8 ||
-                                                           lanes == 16 || lanes == 32));
+  const bool lanes_ok = lanes == 1 ||
+                        (slot == kLMerge && (lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32)) ||
+                        (slot == kLLinks && (lanes == 4 || lanes == 8));
   if (slot < 0 || slot >= kLNum || block < 32 || block > 256 || block % 32 != 0 ||
       blocks_per_sm < 1 || blocks_per_sm > 32 || !lanes_ok)
     return fail(ctx, TPC_ERR_INVALID_ARG, "launch shape slot %d: block %d, %d per SM, %d lanes",

@@ -46,7 +46,7 @@ struct RemovalParams {
 
 // Launch shape of the heavy per-item kernels (block size, blocks per SM),
 // chosen by the autotuner.
-enum LaunchSlot : int { kLTracklets = 0, kLSectorRefit, kLMerge, kLFit12, kLFit3, kLNum };
+enum LaunchSlot : int { kLTracklets = 0, kLSectorRefit, kLMerge, kLFit12, kLFit3, kLLinks, kLNum };
 struct LaunchCfg {
   int block[kLNum];
   int per_sm[kLNum];
@@ -96,6 +96,7 @@ constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
 constexpr int kIpolF = 11;      // interpolation record of an inner station
 constexpr int kMergeLanesDefault = 16;  // lanes per outer end in the merge search
+constexpr int kLinksLanesDefault = 1;   // lanes per cluster in the neighbour search
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 constexpr int kMaxSeedIters = 4;  // sector-tracking iterations

@@ -175,13 +175,14 @@ __global__ void k_bin_sort(FrameDev F) {
 // the clusters taken by earlier iterations neither link nor are linked to.
 constexpr int kLinkList = 8;
 
+// The best (lower, upper) pair of sorted cluster k (-1, -1: none).
 template <bool kLeft>
-__global__ void k_links(FrameDev F, KParams P) {
-  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= F.n || F.cnt->err) return;
+__device__ __forceinline__ void links_one(const FrameDev& F, const KParams& P, long k, int& bu,
+                                          int& bd) {
   const int rr = F.srow[k];
   const int r = rr % P.n_rows;
-  int bu = -1, bd = -1;
+  bu = -1;
+  bd = -1;
   if (r >= 1 && r <= P.n_rows - 2 && !(kLeft && F.sused[k])) {
     const float2 pc = F.syz[k];
     const float yc = pc.x, zc = pc.y;
@@ -243,8 +244,168 @@ __global__ void k_links(FrameDev F, KParams P) {
         }
       });
   }
+}
+
+template <bool kLeft>
+__global__ void k_links(FrameDev F, KParams P) {
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= F.n || F.cnt->err) return;
+  int bu, bd;
+  links_one<kLeft>(F, P, k, bu, bd);
   F.lup[k] = bu;
   F.ldn[k] = bd;
+}
+
+// The same search with a group of G lanes per cluster (G = 4 or 8).  The z
+// strips of the window on the row below and the row above (each a contiguous
+// run of sorted clusters) are dealt out to the lanes, their sizes summed by a
+// group scan and their clusters tested G at a time; those inside the window
+// go to per-cluster lists in shared memory.  Then the (lower, upper) pairs
+// are dealt out to the lanes and the best one, by (distance, upper id, lower
+// id), is found by shuffles.  A window holding more than kGroupList clusters
+// on a row falls back to the one-lane search.  The result is the same.
+constexpr int kGroupList = 8;
+
+template <int G, bool kLeft>
+__global__ void __launch_bounds__(256, 4) k_links_g(FrameDev F, KParams P) {
+  constexpr int kGroups = 256 / G;
+  __shared__ int sD[kGroups][kGroupList];
+  __shared__ int sU[kGroups][kGroupList];
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const int grp = threadIdx.x / G;
+  const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+  const unsigned below = ((1u << lane) - 1u) & gmask;
+  const long k = (long)blockIdx.x * kGroups + grp;
+  if (k >= F.n || F.cnt->err) return;  // the whole group
+  const int NR = P.n_rows;
+  const int rr = F.srow[k];
+  const int r = rr % NR;
+  int bu = -1, bd = -1;
+  if (r >= 1 && r <= NR - 2 && !(kLeft && F.sused[k])) {
+    const float2 pc = F.syz[k];
+    const float yc = pc.x, zc = pc.y;
+    const float xd = F.row_x[r - 1], xc = F.row_x[r], xu = F.row_x[r + 1];
+    const float f = (xc - xd) / (xu - xd);
+    const RowGrid gu = F.rows[rr + 1], gd = F.rows[rr - 1];
+    const float m = 0.01f;
+    const float ylo = yc - P.link_wy - m, yhi = yc + P.link_wy + m;
+    const float zlo = zc - P.link_wz - m, zhi = zc + P.link_wz + m;
+    // the window's z strips on the two rows: [0, nzd) below, [nzd, nzd + nzu) above
+    int iyd0 = 0, iyd1 = -1, izd0 = 0, nzd = 0, iyu0 = 0, iyu1 = -1, izu0 = 0, nzu = 0;
+    if (gd.ncl > 0) {
+      iyd0 = bin_of(ylo, gd.y0, gd.invDy, gd.nY);
+      iyd1 = bin_of(yhi, gd.y0, gd.invDy, gd.nY);
+      izd0 = bin_of(zlo, gd.z0, gd.invDz, gd.nZ);
+      nzd = bin_of(zhi, gd.z0, gd.invDz, gd.nZ) - izd0 + 1;
+    }
+    if (gu.ncl > 0) {
+      iyu0 = bin_of(ylo, gu.y0, gu.invDy, gu.nY);
+      iyu1 = bin_of(yhi, gu.y0, gu.invDy, gu.nY);
+      izu0 = bin_of(zlo, gu.z0, gu.invDz, gu.nZ);
+      nzu = bin_of(zhi, gu.z0, gu.invDz, gu.nZ) - izu0 + 1;
+    }
+    const int ns = nzd + nzu;
+    int nd = 0, nu = 0;
+    for (int s0 = 0; s0 < ns; s0 += G) {
+      const int sx = s0 + gl;
+      int lo = 0, cnt = 0, up = 0;
+      if (sx < ns) {
+        up = sx >= nzd;
+        const RowGrid& g = up ? gu : gd;
+        const int b = g.bin0 + (up ? izu0 + sx - nzd : izd0 + sx) * g.nY;
+        lo = F.bin_first[b + (up ? iyu0 : iyd0)];
+        cnt = F.bin_first[b + (up ? iyu1 : iyd1) + 1] - lo;
+      }
+      int inc = cnt;
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        const int v = __shfl_up_sync(gmask, inc, o, G);
+        if (gl >= o) inc += v;
+      }
+      const int total = __shfl_sync(gmask, inc, G - 1, G);
+      for (int c0 = 0; c0 < total; c0 += G) {
+        const int c = c0 + gl;
+        int L = 0;
+#pragma unroll
+        for (int st = G / 2; st >= 1; st >>= 1) {
+          const int v = __shfl_sync(gmask, inc, L + st - 1, G);
+          if (v <= c) L += st;
+        }
+        const int excl = __shfl_sync(gmask, inc - cnt, L, G);
+        const int lo_l = __shfl_sync(gmask, lo, L, G);
+        const int up_l = __shfl_sync(gmask, up, L, G);
+        int cand = -1;
+        bool pass = false;
+        if (c < total) {
+          cand = lo_l + (c - excl);
+          if (!(kLeft && F.sused[cand])) {
+            const float2 pk = F.syz[cand];
+            pass = fabsf(pk.x - yc) <= P.link_wy && fabsf(pk.y - zc) <= P.link_wz;
+          }
+        }
+        const unsigned bd_ = __ballot_sync(gmask, pass && !up_l) & gmask;
+        const unsigned bu_ = __ballot_sync(gmask, pass && up_l) & gmask;
+        if (pass) {
+          if (up_l) {
+            const int q = nu + __popc(bu_ & below);
+            if (q < kGroupList) sU[grp][q] = cand;
+          } else {
+            const int q = nd + __popc(bd_ & below);
+            if (q < kGroupList) sD[grp][q] = cand;
+          }
+        }
+        nd += __popc(bd_);
+        nu += __popc(bu_);
+      }
+    }
+    __syncwarp(gmask);
+    if (nd > kGroupList || nu > kGroupList) {
+      // dense window: the one-lane search, on the group's first lane
+      if (gl == 0) links_one<kLeft>(F, P, k, bu, bd);
+    } else {
+      float best = 0.0f;
+      int buid = 0, bdid = 0;
+      const int np = nd * nu;
+      for (int p = gl; p < np; p += G) {
+        const int d = sD[grp][p / nu], u = sU[grp][p % nu];
+        const float2 pd = F.syz[d], pu = F.syz[u];
+        const float yp = pd.x + (pu.x - pd.x) * f;
+        const float zp = pd.y + (pu.y - pd.y) * f;
+        const float ey = yp - yc, ez = zp - zc;
+        const float d2 = ey * ey + ez * ez;
+        if (!(d2 < P.link_chi2)) continue;
+        const int uid = F.sid[u], did = F.sid[d];
+        if (bu < 0 || d2 < best || (d2 == best && (uid < buid || (uid == buid && did < bdid)))) {
+          best = d2;
+          bu = u;
+          bd = d;
+          buid = uid;
+          bdid = did;
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o >= 1; o >>= 1) {
+        const float ob = __shfl_xor_sync(gmask, best, o, G);
+        const int obu = __shfl_xor_sync(gmask, bu, o, G);
+        const int obd = __shfl_xor_sync(gmask, bd, o, G);
+        const int ouid = __shfl_xor_sync(gmask, buid, o, G);
+        const int odid = __shfl_xor_sync(gmask, bdid, o, G);
+        if (obu >= 0 && (bu < 0 || ob < best ||
+                         (ob == best && (ouid < buid || (ouid == buid && odid < bdid))))) {
+          best = ob;
+          bu = obu;
+          bd = obd;
+          buid = ouid;
+          bdid = odid;
+        }
+      }
+    }
+  }
+  if (gl == 0) {
+    F.lup[k] = bu;
+    F.ldn[k] = bd;
+  }
 }
 
 // --------------------------------------------------------------- a3 cleaner
@@ -648,22 +809,22 @@ __device__ __forceinline__ unsigned long long tracklet_key(const FrameDev& F, co
   return ((unsigned long long)f2o(score) << 32) | (unsigned long long)(0xFFFFFFFFu - sid);
 }
 
+// One warp per tracklet: the lanes read 32 consecutive rows of the
+// row-indexed hit array at once and raise those hits' owner keys together.
 __global__ void k_sel_owner(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   if (F.cnt->err) return;
-  for (int ti = F.cnt->tl_base + blockIdx.x * blockDim.x + threadIdx.x; ti < nst;
-       ti += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int ti = F.cnt->tl_base + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ti < nst;
+       ti += nw) {
     if (F.tl_n[ti] == 0) continue;
     const unsigned long long key = tracklet_key(F, P, ti);
     const int* H = F.tl_hits + (long)ti * kMaxRows;
     const int rlo = F.tl_rlo[ti], rhi = F.tl_rhi[ti];
-    for (int rg = rlo; rg <= rhi; rg += 8) {  // the group's hit indices requested together
-      int h[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = rg + j <= rhi ? H[rg + j] : -1;
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (h[j] >= 0) atomicMax(&F.owner_key[h[j]], key);
+    for (int r = rlo + lane; r <= rhi; r += 32) {
+      const int h = H[r];
+      if (h >= 0) atomicMax(&F.owner_key[h], key);
     }
   }
 }
@@ -927,6 +1088,16 @@ __global__ void k_edge_write(FrameDev F, KParams P) {
   }
 }
 
+// The neighbour search on 1, 4 or 8 lanes per cluster (launch slot kLLinks).
+template <bool kLeft>
+void launch_links(FrameDev& F, const KParams& P, long n, cudaStream_t s) {
+  switch (F.lc.lanes[kLLinks]) {
+    case 8: k_links_g<8, kLeft><<<blocks_for(n, 256 / 8), 256, 0, s>>>(F, P); break;
+    case 4: k_links_g<4, kLeft><<<blocks_for(n, 256 / 4), 256, 0, s>>>(F, P); break;
+    default: k_links<kLeft><<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); break;
+  }
+}
+
 }  // namespace
 
 // Stage launchers; each returns the number of kernels it enqueued.
@@ -949,7 +1120,7 @@ int stage_links(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   (void)sms;
   const long n = F.n;
   if (n <= 0) return 0;
-  k_links<false><<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+  launch_links<false>(F, P, n, s);
   k_clean<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
   return 2;
 }
@@ -1005,7 +1176,7 @@ int stage_reseed(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
     k_mark_used<<<sms * 8, kBlock, 0, s>>>(F);
     k_owner_reset<<<sms * 8, kBlock, 0, s>>>(F);
     k_pass_begin<<<1, 1, 0, s>>>(F, pass);
-    k_links<true><<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+    launch_links<true>(F, P, n, s);
     k_clean<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
     k_start_count<<<nb, kBlock, 0, s>>>(F);
     k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb, &F.cnt->n_new);

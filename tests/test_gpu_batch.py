@@ -105,10 +105,10 @@ def test_autotune_keeps_results():
     tb.track_batch(dev)
     before = host(tb)
     cfg = tb.autotune(dev)
-    assert len(cfg) == 5
+    assert len(cfg) == 6
     assert all(c["block"] in (64, 128, 256) and c["blocks_per_sm"] in (4, 8, 16) for c in cfg)
-    assert cfg[2]["lanes"] in (1, 8, 16, 32) and all(c["lanes"] == 1 for i, c in enumerate(cfg)
-                                                     if i != 2)
+    assert cfg[2]["lanes"] in (1, 8, 16, 32) and cfg[5]["lanes"] in (1, 4, 8)
+    assert all(c["lanes"] == 1 for i, c in enumerate(cfg) if i not in (2, 5))
     tb.track_batch(dev)
     after = host(tb)
     for k in ("params", "key", "cl_ids", "attach"):
@@ -128,7 +128,7 @@ def test_set_launch_config_keeps_results_and_rejects_bad_shapes():
     shapes = [{"block": b, "blocks_per_sm": q} for b, q in ((64, 2), (32, 1), (224, 1),
                                                               (96, 3), (256, 32))]
     tb.set_launch_config(shapes)
-    assert [(c["block"], c["blocks_per_sm"]) for c in tb.launch_config()] == \
+    assert [(c["block"], c["blocks_per_sm"]) for c in tb.launch_config()[:5]] == \
         [(s["block"], s["blocks_per_sm"]) for s in shapes]
     tb.track(*dev)
     after = host(tb)
@@ -149,6 +149,18 @@ def test_set_launch_config_keeps_results_and_rejects_bad_shapes():
             tb.set_launch_config([bad])
     with pytest.raises(tpc.TpcError):
         tb.set_launch_config(shapes[:2] + [dict(shapes[2], lanes=12)])
+    # the neighbour search on 1, 4 and 8 lanes per cluster
+    for lanes in (1, 4, 8):
+        tb.set_launch_config(shapes + [{"block": 256, "blocks_per_sm": 8, "lanes": lanes}])
+        assert tb.launch_config()[5]["lanes"] == lanes
+        tb.track(*dev)
+        after = host(tb)
+        for k in ("params", "cov", "key", "cl_ids", "attach"):
+            assert np.array_equal(before[k].view(np.uint8), after[k].view(np.uint8)), (k, lanes)
+        links = tb.debug("lup"), tb.debug("ldn")
+        if lanes == 1:
+            ref_links = links
+        assert all(np.array_equal(a, b) for a, b in zip(links, ref_links))
 
 
 def test_full_size_frames_sampled_sector_parity():
