@@ -15,6 +15,7 @@
 #pragma once
 
 #include "tpc_internal.h"
+#include "tpc_df.cuh"
 #include "tpc_fp64.cuh"
 
 namespace tpc {
@@ -261,8 +262,15 @@ __device__ __forceinline__ void update(Trk<float>& t, const Resid& R) {
 }
 
 // The same update with the gain and covariance arithmetic in FP64, rounded
-// back to FP32 (the final fit's update of low-pT loopers).
+// back to FP32 (the final fit's update of low-pT loopers).  Fast mode runs it
+// in double-float arithmetic on the FP32 pipe instead (tpc_df.cuh: on GB300
+// the FP64 unit is about 1/60 of the FP32 rate; the rounded results are those
+// of the FP64 update unless one lies within about 2^-46 of a rounding
+// boundary).
 __device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
+#ifdef TPC_FAST_ARITH
+  df_update(t.p, t.c, R.r0, R.r1, R.w00, R.w01, R.w11);
+#else
   const double w00 = widen(R.w00), w01 = widen(R.w01), w11 = widen(R.w11), r0 = widen(R.r0),
                r1 = widen(R.r1);
   const double h0[5] = {widen(t.c[0]), widen(t.c[1]), widen(t.c[3]), widen(t.c[6]),
@@ -274,21 +282,6 @@ __device__ __forceinline__ void update_fp64(Trk<float>& t, const Resid& R) {
     k0[i] = h0[i] * w00 + h1[i] * w01;
     k1[i] = h0[i] * w01 + h1[i] * w11;
   }
-#ifdef TPC_FAST_ARITH
-  // fast mode: each correction accumulated into the entry by two FMAs (a
-  // different FP64 rounding order, one FP64 operation fewer per entry)
-#pragma unroll
-  for (int i = 0; i < 5; ++i) t.p[i] = narrow(fma(k1[i], r1, fma(k0[i], r0, widen(t.p[i]))));
-  int idx = 0;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      t.c[idx] = narrow(fma(-k1[i], h1[j], fma(-k0[i], h0[j], widen(t.c[idx]))));
-      ++idx;
-    }
-  }
-#else
 #pragma unroll
   for (int i = 0; i < 5; ++i) t.p[i] = narrow(widen(t.p[i]) + (k0[i] * r0 + k1[i] * r1));
   int idx = 0;
