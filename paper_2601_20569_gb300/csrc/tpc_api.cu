@@ -717,8 +717,9 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
 
 tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
                              int32_t* block, int32_t* blocks_per_sm, int32_t* lanes) {
-  static const char* names[kLNum] = {"k_tl_up+k_tl_down", "k_sector_refit", "k_merge_best",
-                                     "k_fit1+k_fit2", "k_fit3", "k_links"};
+  static const char* names[kLNum] = {"k_tl_chain+k_tl_up+k_tl_refit+k_tl_down",
+                                     "k_sector_refit", "k_merge_best", "k_fit1+k_fit2", "k_fit3",
+                                     "k_links"};
   if (!ctx || slot < 0 || slot >= kLNum) return TPC_ERR_INVALID_ARG;
   if (kernel) *kernel = names[slot];
   if (block) *block = ctx->F.lc.block[slot];

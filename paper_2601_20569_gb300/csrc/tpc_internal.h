@@ -54,11 +54,11 @@ struct LaunchCfg {
 };
 
 // Work queues: counters of the dynamic item fetching (zeroed per call).
-// The fit kernels keep two queues each: FP64-update loopers (kQFit12, kQFit3)
-// and the other tracks (kQFit12N, kQFit3N).
+// The fit kernels keep two queues each: loopers (kQFit12, kQFit3) and the
+// other tracks (kQFit12N, kQFit3N).
 enum QueueSlot : int {
   kQTracklets = 0, kQSectorRefit, kQMerge, kQFit12, kQFit3, kQFit12N, kQFit3N, kQFit2, kQFit2N,
-  kQTlDown, kQNum
+  kQTlDown, kQTlUp, kQTlRefit, kQNum
 };
 
 // Search grid of one (sector, row): bins iz*nY + iy, clusters of a bin are

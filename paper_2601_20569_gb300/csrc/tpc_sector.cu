@@ -557,48 +557,60 @@ __global__ void k_chain_info(FrameDev F, KParams P) {
 // work queue in the same loop.  The lanes of a warp therefore stay busy on
 // row steps however unequal their tracklets are.  Per tracklet the sequence
 // of operations is that of the constructor (Sec. 2): seed from the chain's
-// first, middle and last clusters; follow the CA chain upwards; extend
-// upwards by the best cluster of each row until max_miss rows in a row have
-// none (k_tl_up); restart from the top with reset covariance, refit downwards
-// over the found clusters and extend below the start the same way (k_tl_down).
-// Two kernels rather than one: each carries only its own pass's code and
-// state, and all lanes of a kernel run the same kind of step.
-enum : int { kTlIdle = 0, kTlChain, kTlUp };
-
-// Per-thread shared-memory state of the two tracklet kernels: the state they
-// only save and restore (downward: the state at the innermost hit; upward:
-// the state and position at the top hit), field-major so that a warp's
-// accesses hit distinct banks.  It keeps both kernels at 64 registers, four
-// 256-thread blocks per SM.
+// first, middle and last clusters; follow the CA chain upwards (k_tl_chain);
+// extend upwards by the best cluster of each row until max_miss rows in a row
+// have none (k_tl_up); restart from the top with reset covariance and refit
+// downwards over the found clusters (k_tl_refit); extend below the start the
+// same way (k_tl_down).  Four kernels rather than one: each carries only its
+// own part's code and state, and all lanes of a kernel run the same kind of
+// step (the steps over known clusters then run without the divergence of the
+// searches).
+//
+// Per-thread shared-memory state of the searching and refitting kernels: the
+// state they only save and restore (downward: the state at the innermost hit;
+// upward: the state and position at the top hit), field-major so that a
+// warp's accesses hit distinct banks.  It keeps the kernels at 64 registers,
+// four 256-thread blocks per SM.
 constexpr int kTlShared = 21;  // saved state: p[5], c[15], x (or p[5], x, y_hit, z_hit)
 
-// Upward pass: seed, CA chain, extension by the best cluster of each row.
-// The state at the top hit and that hit's position are left in tl_seed[0..5],
-// tl_chi2 and tl_x for the downward pass; tl_n = -1 marks a tracklet that
-// has one.
-template <bool kLeft>
-__global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
-  extern __shared__ float tl_sh[];
-  float* const S = tl_sh + threadIdx.x;
-  const int BS = blockDim.x;
+// Tracklet states between the kernels (tl_n): 0 none yet or rejected; -2 seed
+// and chain followed, state in tl_par / tl_cov / tl_seed[5] (x), position of
+// the top hit in tl_chi2 / tl_x, its row in tl_rhi; -1 upward part done, the
+// state at the top hit in tl_seed[0..5], its position in tl_chi2 / tl_x.
+constexpr int kTlChainDone = -2;
+constexpr int kTlUpDone = -1;
+
+// The state and position of the top hit, for the downward pass.
+__device__ __forceinline__ void tl_up_done(const FrameDev& F, int ti, const float* p, float x,
+                                           float y, float z, int top) {
+  float* sd = F.tl_seed + (long)ti * kSeedF;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) sd[i] = p[i];
+  sd[5] = x;
+  F.tl_chi2[ti] = y;
+  F.tl_x[ti] = z;
+  F.tl_rhi[ti] = top;
+  F.tl_n[ti] = kTlUpDone;
+}
+
+// Upward pass, first part: seed and CA chain.  Every chain step takes the
+// chain's next cluster (a CA link always joins adjacent pad rows of one
+// sector, so the chain's next row is known); the next link and the cluster's
+// position are requested before the propagation.  The state after the last
+// update is the state at the top hit.
+__global__ void __launch_bounds__(256, 4) k_tl_chain(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
   const int tbase = F.cnt->tl_base;
   if (F.cnt->err) return;
   const int NR = P.n_rows;
-  int phase = kTlIdle;
-  int ti = 0, sbase = 0, top = 0, rcur = 0, c = 0, cn = 0, left = 0, miss = 0;
+  bool busy = false;
+  int ti = 0, rcur = 0, cn = 0, left = 0;
   int* H = nullptr;
+  float yt = 0.0f, zt = 0.0f;  // position of the top hit
   Trk<float> t;
-  auto save_top = [&](float y, float z) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) S[i * BS] = t.p[i];
-    S[5 * BS] = t.x;
-    S[6 * BS] = y;
-    S[7 * BS] = z;
-  };
   for (;;) {
-    if (phase == kTlIdle) {
-      // take the next tracklet and seed it
+    bool handover = false;
+    if (!busy) {
       ti = tbase + queue_next(&F.cnt->queue[kQTracklets]);
       if (ti >= nst) break;
       const int start = F.starts[ti];
@@ -610,53 +622,111 @@ __global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
       for (int i = 0; i < kSeedF; ++i) sv[i] = sd[i];
       F.tl_n[ti] = 0;
       if (__float_as_int(sv[7]) == 0) continue;  // no seed
-      const int rr0 = __float_as_int(sv[6]);
-      const int r0 = rr0 % NR;
-      sbase = rr0 - r0;  // sector * n_rows
+      const int r0 = __float_as_int(sv[6]) % NR;
 #pragma unroll
       for (int i = 0; i < 5; ++i) t.p[i] = sv[i];
       t.x = sv[5];
       reset_cov(t.c, P);
       // the seed passes through the start cluster: its measurement is (y, z)
       // of the seed itself
-      const float y0 = t.p[0], z0 = t.p[1];
-      update(t, residual(t, y0, z0, P));
+      yt = t.p[0];
+      zt = t.p[1];
+      update(t, residual(t, yt, zt, P));
       H[r0] = start;
       if (L > 1) cn = F.cup[start];
-      save_top(y0, z0);
-      top = r0;
       rcur = r0;
-      c = start;
       left = L - 1;  // chain steps still to take
+      busy = left > 0;
+      handover = !busy;
+    } else {
+      // ---- one chain step
+      const int r = rcur + 1;
+      const int k = cn;
+      if (left > 1) cn = F.cup[k];
+      const float2 pk = F.syz[k];
+      const bool stop = r >= NR || !propagate(t, F.row_x[r], P, P.max_snp);
+      if (stop) {
+        tl_up_done(F, ti, t.p, t.x, yt, zt, rcur);
+        busy = false;
+        continue;
+      }
+      update(t, residual(t, pk.x, pk.y, P));
+      H[r] = k;
+      yt = pk.x;
+      zt = pk.y;
+      rcur = r;
+      busy = --left > 0;
+      handover = !busy;
+    }
+    if (!handover) continue;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = t.p[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = t.c[i];
+    F.tl_seed[(long)ti * kSeedF + 5] = t.x;
+    F.tl_chi2[ti] = yt;
+    F.tl_x[ti] = zt;
+    F.tl_rhi[ti] = rcur;
+    F.tl_n[ti] = kTlChainDone;
+  }
+}
+
+// Upward pass, second part: extension by the best cluster of each row from
+// the chain's top.  The state at the top hit and that hit's position are left
+// in tl_seed[0..5], tl_chi2 and tl_x for the downward pass.
+template <bool kLeft>
+__global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
+  extern __shared__ float tl_sh[];
+  float* const S = tl_sh + threadIdx.x;
+  const int BS = blockDim.x;
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  const int tbase = F.cnt->tl_base;
+  if (F.cnt->err) return;
+  const int NR = P.n_rows;
+  bool busy = false;
+  int ti = 0, sbase = 0, top = 0, rcur = 0, miss = 0;
+  int* H = nullptr;
+  Trk<float> t;
+  auto save_top = [&](float y, float z) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[i * BS] = t.p[i];
+    S[5 * BS] = t.x;
+    S[6 * BS] = y;
+    S[7 * BS] = z;
+  };
+  for (;;) {
+    if (!busy) {
+      ti = tbase + queue_next(&F.cnt->queue[kQTlUp]);
+      if (ti >= nst) break;
+      if (F.tl_n[ti] != kTlChainDone) continue;
+      H = F.tl_hits + (long)ti * kMaxRows;
+      const float* sd = F.tl_seed + (long)ti * kSeedF;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) t.p[i] = F.tl_par[(long)ti * 5 + i];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) t.c[i] = F.tl_cov[(long)ti * 15 + i];
+      t.x = sd[5];
+      const int rr0 = __float_as_int(sd[6]);
+      sbase = rr0 - rr0 % NR;  // sector * n_rows
+      top = F.tl_rhi[ti];
+      rcur = top;
+      save_top(F.tl_chi2[ti], F.tl_x[ti]);
       miss = 0;
-      phase = left > 0 ? kTlChain : kTlUp;
+      busy = true;
       continue;
     }
-    // ---- one row step.  What the step reads that does not depend on the
-    // propagated state is requested before the propagation so that its
-    // latency overlaps the arithmetic: the next chain link (one step ahead),
-    // the chain cluster's position, the row's grid record.  A CA link always
-    // joins adjacent pad rows of one sector, so the chain's next row is known.
-    int k = -1;
+    // ---- one row step (the row's grid record requested before the
+    // propagation, so that its latency overlaps the arithmetic)
     const int r = rcur + 1;
     bool stop = r >= NR;
     RowGrid g;
-    float ky = 0.0f, kz = 0.0f;
-    if (phase == kTlChain) {
-      k = cn;
-      c = k;
-      if (left > 1) cn = F.cup[k];
-      const float2 pk = F.syz[k];
-      ky = pk.x;
-      kz = pk.y;
-    } else if (!stop) {
-      g = F.rows[sbase + r];
-    }
+    if (!stop) g = F.rows[sbase + r];
     if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);
-    if (!stop && phase != kTlChain) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
+    if (!stop) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
     bool miss_out = false;
     if (!stop) {
-      if (phase != kTlChain) k = pick<kLeft>(F, P, t, g, ky, kz);
+      float ky = 0.0f, kz = 0.0f;
+      const int k = pick<kLeft>(F, P, t, g, ky, kz);
       if (k >= 0) {
         update(t, residual(t, ky, kz, P));
         H[r] = k;
@@ -668,26 +738,128 @@ __global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
         miss_out = ++miss >= P.max_miss;
       }
       rcur = r;
-      if (phase == kTlChain && --left == 0) {
-        phase = kTlUp;
-        miss = 0;
-      }
     }
     if (!(stop || miss_out)) continue;
-    // upward part done (chain broken, no more rows, edge or max_miss misses)
-    float* sd = F.tl_seed + (long)ti * kSeedF;
+    // upward part done (no more rows, edge or max_miss misses)
+    float pt[5];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) sd[i] = S[i * BS];
-    F.tl_chi2[ti] = S[6 * BS];
-    F.tl_x[ti] = S[7 * BS];
-    F.tl_rhi[ti] = top;
-    F.tl_n[ti] = -1;
-    phase = kTlIdle;
+    for (int i = 0; i < 5; ++i) pt[i] = S[i * BS];
+    tl_up_done(F, ti, pt, S[5 * BS], S[6 * BS], S[7 * BS], top);
+    busy = false;
   }
 }
 
-// Downward pass: restart at the top hit with reset covariance, refit down
-// over the hits found on the way up, extend below the start the same way.
+// The downward pass's result: n clusters, the state at the innermost one.
+__device__ __forceinline__ void tl_down_done(const FrameDev& F, const KParams& P, int ti, int n,
+                                             int rlo, int top, float chi2, const float* S,
+                                             int BS) {
+  if (n < P.min_hits) return;  // tl_n stays 0
+  F.tl_n[ti] = n;
+  F.tl_rlo[ti] = rlo;
+  F.tl_rhi[ti] = top;
+  F.tl_chi2[ti] = chi2;
+  F.tl_x[ti] = S[20 * BS];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = S[i * BS];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = S[(5 + i) * BS];
+}
+
+// Downward pass, first part: restart at the top hit with reset covariance
+// and refit down over the hits found on the way up (the next stored hit is
+// requested one step ahead, its position before the propagation).  The start
+// row always holds a hit (the start cluster), so a tracklet that reaches it
+// leaves this kernel with the state at its innermost hit: that state, chi2 and
+// the count go to the extension below the start (tl_n = -3; n in tl_rlo).
+constexpr int kTlRefitDone = -3;
+
+__global__ void __launch_bounds__(256, 4) k_tl_refit(FrameDev F, KParams P) {
+  extern __shared__ float tl_sh[];
+  float* const S = tl_sh + threadIdx.x;
+  const int BS = blockDim.x;
+  const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
+  const int tbase = F.cnt->tl_base;
+  if (F.cnt->err) return;
+  const int NR = P.n_rows;
+  bool busy = false;
+  int ti = 0, r0 = 0, top = 0, rcur = 0, hn = -1, n = 0, rlo = 0;
+  const int* H = nullptr;
+  float chi2 = 0.0f;
+  Trk<float> t;
+  auto save_inner = [&]() {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[i * BS] = t.p[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) S[(5 + i) * BS] = t.c[i];
+    S[20 * BS] = t.x;
+  };
+  for (;;) {
+    if (!busy) {
+      ti = tbase + queue_next(&F.cnt->queue[kQTlRefit]);
+      if (ti >= nst) break;
+      if (F.tl_n[ti] != kTlUpDone) continue;
+      H = F.tl_hits + (long)ti * kMaxRows;
+      const float* sd = F.tl_seed + (long)ti * kSeedF;
+      float sv[kSeedF];
+#pragma unroll
+      for (int i = 0; i < kSeedF; ++i) sv[i] = sd[i];
+      const float ty = F.tl_chi2[ti], tz = F.tl_x[ti];
+      top = F.tl_rhi[ti];
+      r0 = __float_as_int(sv[6]) % NR;
+      F.tl_n[ti] = 0;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) t.p[i] = sv[i];
+      t.x = sv[5];
+      reset_cov(t.c, P);
+      const Resid R = residual(t, ty, tz, P);
+      chi2 = R.chi2;
+      update(t, R);
+      hn = top - 1 >= r0 ? H[top - 1] : -1;
+      n = 1;
+      save_inner();
+      rlo = top;
+      rcur = top;
+      busy = top > r0;
+    } else {
+      // ---- one stored row step
+      const int r = rcur - 1;
+      const int k = hn;
+      hn = r - 1 >= r0 ? H[r - 1] : -1;
+      float2 pk = make_float2(0.0f, 0.0f);
+      if (k >= 0) pk = F.syz[k];
+      bool stop = !propagate(t, F.row_x[r], P, P.max_snp);
+      if (!stop) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
+      if (stop) {
+        tl_down_done(F, P, ti, n, rlo, top, chi2, S, BS);
+        busy = false;
+        continue;
+      }
+      if (k >= 0) {
+        const Resid R = residual(t, pk.x, pk.y, P);
+        chi2 = chi2 + R.chi2;
+        update(t, R);
+        ++n;
+        save_inner();
+        rlo = r;
+      }
+      rcur = r;
+      busy = r > r0;
+    }
+    if (busy) continue;
+    // at the start row, whose hit was the last update: t is the innermost state
+#pragma unroll
+    for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = t.p[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = t.c[i];
+    F.tl_x[ti] = t.x;
+    F.tl_chi2[ti] = chi2;
+    F.tl_rlo[ti] = n;
+    F.tl_n[ti] = kTlRefitDone;
+  }
+}
+
+// Downward pass, second part: extension below the start by the best cluster
+// of each row until max_miss rows in a row have none.
 template <bool kLeft>
 __global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
   extern __shared__ float tl_sh[];
@@ -698,7 +870,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
   if (F.cnt->err) return;
   const int NR = P.n_rows;
   bool busy = false;
-  int ti = 0, r0 = 0, sbase = 0, top = 0, rcur = 0, hn = -1, miss = 0, n = 0, rlo = 0;
+  int ti = 0, sbase = 0, top = 0, rcur = 0, miss = 0, n = 0, rlo = 0;
   int* H = nullptr;
   float chi2 = 0.0f;
   Trk<float> t;
@@ -713,90 +885,56 @@ __global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
     if (!busy) {
       ti = tbase + queue_next(&F.cnt->queue[kQTlDown]);
       if (ti >= nst) break;
-      if (F.tl_n[ti] != -1) continue;
+      if (F.tl_n[ti] != kTlRefitDone) continue;
       H = F.tl_hits + (long)ti * kMaxRows;
-      const float* sd = F.tl_seed + (long)ti * kSeedF;
-      float sv[kSeedF];
 #pragma unroll
-      for (int i = 0; i < kSeedF; ++i) sv[i] = sd[i];
-      const float ty = F.tl_chi2[ti], tz = F.tl_x[ti];
+      for (int i = 0; i < 5; ++i) t.p[i] = F.tl_par[(long)ti * 5 + i];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) t.c[i] = F.tl_cov[(long)ti * 15 + i];
+      t.x = F.tl_x[ti];
+      chi2 = F.tl_chi2[ti];
+      n = F.tl_rlo[ti];
       top = F.tl_rhi[ti];
-      const int rr0 = __float_as_int(sv[6]);
-      r0 = rr0 % NR;
+      const int rr0 = __float_as_int(F.tl_seed[(long)ti * kSeedF + 6]);
+      const int r0 = rr0 % NR;
       sbase = rr0 - r0;
       F.tl_n[ti] = 0;
-#pragma unroll
-      for (int i = 0; i < 5; ++i) t.p[i] = sv[i];
-      t.x = sv[5];
-      reset_cov(t.c, P);
-      const Resid R = residual(t, ty, tz, P);
-      chi2 = R.chi2;
-      update(t, R);
-      hn = top - 1 >= r0 ? H[top - 1] : -1;
-      n = 1;
       save_inner();
-      rlo = top;
-      rcur = top;
+      rlo = r0;
+      rcur = r0;
       miss = 0;
       busy = true;
       continue;
     }
-    // ---- one row step (the next stored hit one step ahead, its position and
-    // the row's grid record before the propagation)
+    // ---- one row step (the row's grid record before the propagation)
     const int r = rcur - 1;
     bool stop = r < 0;
-    const bool stored = r >= r0;
-    int k = -1;
     RowGrid g;
-    float ky = 0.0f, kz = 0.0f;
-    if (!stop) {
-      if (stored) {
-        k = hn;
-        hn = r - 1 >= r0 ? H[r - 1] : -1;
-        if (k >= 0) {
-          const float2 pk = F.syz[k];
-          ky = pk.x;
-          kz = pk.y;
-        }
-      } else {
-        g = F.rows[sbase + r];
-      }
-    }
+    if (!stop) g = F.rows[sbase + r];
     if (!stop) stop = !propagate(t, F.row_x[r], P, P.max_snp);
     if (!stop) stop = fabsf(t.p[0]) > t.x * P.tan_half + P.edge_margin;
     bool miss_out = false;
     if (!stop) {
-      if (!stored) k = pick<kLeft>(F, P, t, g, ky, kz);
+      float ky = 0.0f, kz = 0.0f;
+      const int k = pick<kLeft>(F, P, t, g, ky, kz);
       if (k >= 0) {
         const Resid R = residual(t, ky, kz, P);
         chi2 = chi2 + R.chi2;
         update(t, R);
-        if (r < r0) {
-          H[r] = k;
-          miss = 0;
-        }
+        H[r] = k;
+        miss = 0;
         ++n;
         save_inner();
         rlo = r;
-      } else if (r < r0) {
+      } else {
         H[r] = -1;
         miss_out = ++miss >= P.max_miss;
       }
       rcur = r;
     }
     if (!(stop || miss_out)) continue;
-    // tracklet done
+    tl_down_done(F, P, ti, n, rlo, top, chi2, S, BS);
     busy = false;
-    if (n < P.min_hits) continue;
-    F.tl_n[ti] = n;
-    F.tl_rlo[ti] = rlo;
-    F.tl_rhi[ti] = top;
-    F.tl_chi2[ti] = chi2;
-    F.tl_x[ti] = S[20 * BS];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) F.tl_par[(long)ti * 5 + i] = S[i * BS];
-#pragma unroll
-    for (int i = 0; i < 15; ++i) F.tl_cov[(long)ti * 15 + i] = S[(5 + i) * BS];
   }
 }
 
@@ -909,6 +1047,8 @@ __global__ void k_pass_begin(FrameDev F, int pass) {
   F.cnt->tl_base = nst;
   F.cnt->pass_start[pass] = nst;
   F.cnt->queue[kQTracklets] = 0;
+  F.cnt->queue[kQTlUp] = 0;
+  F.cnt->queue[kQTlRefit] = 0;
   F.cnt->queue[kQTlDown] = 0;
 }
 
@@ -1140,9 +1280,11 @@ int stage_tracklets(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_chain_info<<<sms * 8, kBlock, 0, s>>>(F, P);
   const int tb = F.lc.block[kLTracklets];
   const size_t sh = sizeof(float) * kTlShared * tb;
+  k_tl_chain<<<persistent_grid(F.lc, kLTracklets, sms), tb, 0, s>>>(F, P);
   k_tl_up<false><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+  k_tl_refit<<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
   k_tl_down<false><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
-  return 3;
+  return 5;
 }
 
 int stage_select(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
@@ -1183,11 +1325,13 @@ int stage_reseed(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
     k_start_write<<<nb, kBlock, 0, s>>>(F);
     k_start_check<<<1, 1, 0, s>>>(F);
     k_chain_info<<<sms * 8, kBlock, 0, s>>>(F, P);
+    k_tl_chain<<<persistent_grid(F.lc, kLTracklets, sms), tb, 0, s>>>(F, P);
     k_tl_up<true><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
+    k_tl_refit<<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
     k_tl_down<true><<<persistent_grid(F.lc, kLTracklets, sms), tb, sh, s>>>(F, P);
     k_sel_owner<<<sms * 8, kBlock, 0, s>>>(F, P);
     k_sel_walk<<<sms * 8, kBlock, 0, s>>>(F, P);
-    k += 14;
+    k += 16;
   }
   return k;
 }
