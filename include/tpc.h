@@ -349,7 +349,7 @@ int64_t tpc_refit_generation(const tpc_ctx* ctx);
  * Computes the same cleaned neighbour links as tpc_track_timeframe in strict
  * mode (per-row grids, best straight-line pair per cluster, mutual cleaning)
  * for one frame of at most TPC_NOALLOC_MAX_CLUSTERS clusters, without any
- * cudaMalloc: its working buffers (about 6.3 MB) are one static device array
+ * cudaMalloc: its working buffers (about 7.3 MB) are one static device array
  * that every GPU loading the library holds until the process exits.
  *   geo, opt: host structs as for tpc_init (opt->bz is the field; capacities
  *             and mode are ignored).  clusters: device SoA, caller-owned.

@@ -271,6 +271,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.bin_first, F.cap_bins + 1);
   ok &= dalloc(ctx, &F.cl_bin, n);
   ok &= dalloc(ctx, &F.cl_slot, n);
+  ok &= dalloc(ctx, &F.srec, n);
   ok &= dalloc(ctx, &F.syz, n);
   ok &= dalloc(ctx, &F.sid, n);
   ok &= dalloc(ctx, &F.srow, n);

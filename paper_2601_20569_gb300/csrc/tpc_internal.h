@@ -170,6 +170,8 @@ struct FrameDev {
   int* cl_bin;             // [n] per input cluster
   int* cl_slot;            // [n]
   long cap_bins;
+  int4* srec;              // [n] grid build: (y, z, input id, 0) scattered to the sorted
+                           // positions, ordered in each bin and split into syz / sid
   float2* syz;             // [n] sorted (y, z)
   int* sid;                // sorted -> input id
   uint16_t* srow;          // sorted -> sector*n_rows + row

@@ -129,17 +129,28 @@ __global__ void k_bin_hist(FrameDev F, KParams P) {
   F.cl_slot[i] = atomicAdd(&F.bin_cnt[b], 1);
 }
 
-__global__ void k_scatter(FrameDev F, KParams P) {
+__global__ void k_scatter(FrameDev F) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n || F.cnt->err) return;
   const int pos = F.bin_first[F.cl_bin[i]] + F.cl_slot[i];
   const ClusterIn c = load_cluster(F, i);
-  F.syz[pos] = make_float2(c.y, c.z);
-  F.sid[pos] = (int)i;
-  F.srow[pos] = (uint16_t)(c.sector * P.n_rows + c.row);
+  // one 16-byte record per cluster: a single scattered store
+  F.srec[pos] = make_int4(__float_as_int(c.y), __float_as_int(c.z), (int)i, 0);
 }
 
-// Order the clusters of each bin by input id (deterministic layout).
+// (sector, row) of every sorted cluster: a row's clusters are contiguous in
+// the sorted order, so one block per row writes its range in order (rather
+// than the scatter adding another scattered store per cluster).
+__global__ void k_row_fill(FrameDev F, KParams P) {
+  if (F.cnt->err) return;
+  const int rr = blockIdx.x;
+  const RowGrid g = F.rows[rr];
+  const int lo = F.bin_first[g.bin0], hi = F.bin_first[g.bin0 + g.nY * g.nZ];
+  for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) F.srow[k] = (uint16_t)rr;
+}
+
+// Order the clusters of each bin by input id (deterministic layout) and
+// split the records into the sorted (y, z) and id arrays.
 __global__ void k_bin_sort(FrameDev F) {
   const int nb = F.cnt->n_bins;
   if (F.cnt->err) return;
@@ -150,16 +161,18 @@ __global__ void k_bin_sort(FrameDev F) {
       continue;
     }
     for (int k = lo + 1; k < hi; ++k) {
-      const int id = F.sid[k];
-      const float2 yz = F.syz[k];
+      const int4 v = F.srec[k];
       int j = k - 1;
-      while (j >= lo && F.sid[j] > id) {
-        F.sid[j + 1] = F.sid[j];
-        F.syz[j + 1] = F.syz[j];
+      while (j >= lo && F.srec[j].z > v.z) {
+        F.srec[j + 1] = F.srec[j];
         --j;
       }
-      F.sid[j + 1] = id;
-      F.syz[j + 1] = yz;
+      F.srec[j + 1] = v;
+    }
+    for (int k = lo; k < hi; ++k) {
+      const int4 v = F.srec[k];
+      F.syz[k] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
+      F.sid[k] = v.z;
     }
   }
 }
@@ -1249,9 +1262,10 @@ int stage_grid(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   if (n > 0) { k_bin_hist<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); ++k; }
   k += scan_exclusive(F.bin_cnt, F.bin_first, F.cap_bins + 1, F.scan_tmp, s);
   if (n > 0) {
-    k_scatter<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+    k_scatter<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
     k_bin_sort<<<sms * 8, kBlock, 0, s>>>(F);
-    k += 2;
+    k_row_fill<<<P.n_sectors * P.n_rows, 128, 0, s>>>(F, P);
+    k += 3;
   }
   return k;
 }
