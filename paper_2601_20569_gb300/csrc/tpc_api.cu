@@ -172,7 +172,7 @@ void derive(KParams& P, const tpc_options& o, float bz, const std::vector<float>
   P.inner_rows = o.inner_rows;
   P.cand_k = o.cand_k;
   P.grid_dy = 2.0f;
-  P.grid_occ = 1.0f;
+  P.grid_occ = 0.5f;
 }
 }  // namespace tpc
 
@@ -267,6 +267,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.row_zmin, nrr);
   ok &= dalloc(ctx, &F.row_zmax, nrr);
   ok &= dalloc(ctx, &F.rows, nrr);
+  ok &= dalloc(ctx, &F.row_first, nrr + 1);
   ok &= dalloc(ctx, &F.bin_cnt, F.cap_bins + 1);
   ok &= dalloc(ctx, &F.bin_first, F.cap_bins + 1);
   ok &= dalloc(ctx, &F.cl_bin, n);

@@ -165,12 +165,13 @@ struct FrameDev {
   unsigned* row_zmin;      // ordered-int encoded
   unsigned* row_zmax;
   RowGrid* rows;           // [n_sectors*n_rows]
+  int* row_first;          // [n_sectors*n_rows + 1] first sorted cluster of each row
   int* bin_cnt;            // [cap_bins + 1]
   int* bin_first;          // [cap_bins + 1]
   int* cl_bin;             // [n] per input cluster
   int* cl_slot;            // [n]
   long cap_bins;
-  int4* srec;              // [n] grid build: (y, z, input id, 0) scattered to the sorted
+  int4* srec;              // [n] grid build: (y, z, input id, bin) scattered to the sorted
                            // positions, ordered in each bin and split into syz / sid
   float2* syz;             // [n] sorted (y, z)
   int* sid;                // sorted -> input id

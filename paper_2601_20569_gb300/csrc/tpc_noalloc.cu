@@ -57,7 +57,8 @@ constexpr long kOffPerCl = kOffScanTmp + align256(sizeof(int) * kScanTmpInts);
 constexpr long kPerClInts = 9;  // cl_bin, cl_slot, (y, z) [two slots], sid, lup, ldn, cup, cdn
 constexpr long kOffSrow = kOffPerCl + kPerClInts * align256(4 * kNoAllocMaxClusters);
 constexpr long kOffSrec = kOffSrow + align256(2 * kNoAllocMaxClusters);
-constexpr long kScratchBytes = kOffSrec + align256(16 * kNoAllocMaxClusters);
+constexpr long kOffRowFirst = kOffSrec + align256(16 * kNoAllocMaxClusters);
+constexpr long kScratchBytes = kOffRowFirst + align256(sizeof(int) * (kNoAllocMaxRows + 1));
 
 static_assert(kScratchBytes < (16L << 20), "no-allocation scratch must stay modest");
 static_assert(align256(4 * kNoAllocMaxClusters) == 4 * kNoAllocMaxClusters,
@@ -164,6 +165,7 @@ extern "C" tpc_status tpc_links_noalloc(const tpc_geometry* geo, const tpc_optio
   F.cdn = per[8];
   F.srow = (uint16_t*)(b + kOffSrow);
   F.srec = (int4*)(b + kOffSrec);
+  F.row_first = (int*)(b + kOffRowFirst);
 
   // clear what the grid build accumulates into; copy the geometry
   if (cudaMemsetAsync(F.cnt, 0, sizeof(Counters), s) != cudaSuccess ||

@@ -60,9 +60,9 @@ __global__ void k_row_stats(FrameDev F, KParams P) {
 // One block: bin layout of every (sector,row) and the row/bin offsets.
 __global__ void k_row_grid(FrameDev F, KParams P) {
   __shared__ int sh[32];
-  __shared__ int carry_bins;
+  __shared__ int carry_bins, carry_cl;
   const int nrr = P.n_sectors * P.n_rows;
-  if (threadIdx.x == 0) carry_bins = 0;
+  if (threadIdx.x == 0) carry_bins = carry_cl = 0;
   __syncthreads();
   for (int base = 0; base < nrr; base += blockDim.x) {
     const int rr = base + threadIdx.x;
@@ -79,7 +79,7 @@ __global__ void k_row_grid(FrameDev F, KParams P) {
         zlo = o2f(F.row_zmin[rr]);
         zr = o2f(F.row_zmax[rr]) - zlo;
       }
-      // about square bins holding grid_occ clusters each, at least grid_dy
+      // about square bins holding grid_occ clusters each (0.5), at least grid_dy
       // wide in y: the search windows (a few cm in y and in z) then cover few
       // bins and few clusters outside the window
       const float side = sqrtf(2.0f * ymax * fmaxf(zr, 1.0f) * P.grid_occ / (float)max(cnt, 1));
@@ -100,17 +100,23 @@ __global__ void k_row_grid(FrameDev F, KParams P) {
       g.ncl = cnt;
       nb = nY * nZ;
     }
-    int tot_b;
+    int tot_b, tot_c;
     const int ob = block_exscan(nb, sh, &tot_b);
+    const int oc = block_exscan(cnt, sh, &tot_c);
     if (rr < nrr) {
       g.bin0 = carry_bins + ob;
       F.rows[rr] = g;
+      F.row_first[rr] = carry_cl + oc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) carry_bins += tot_b;
+    if (threadIdx.x == 0) {
+      carry_bins += tot_b;
+      carry_cl += tot_c;
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    F.row_first[nrr] = carry_cl;
     F.cnt->n_bins = carry_bins;
     if (carry_bins > F.cap_bins) atomicOr(&F.cnt->err, kErrCapBins);
   }
@@ -132,49 +138,64 @@ __global__ void k_bin_hist(FrameDev F, KParams P) {
 __global__ void k_scatter(FrameDev F) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F.n || F.cnt->err) return;
-  const int pos = F.bin_first[F.cl_bin[i]] + F.cl_slot[i];
+  const int b = F.cl_bin[i];
+  const int pos = F.bin_first[b] + F.cl_slot[i];
   const ClusterIn c = load_cluster(F, i);
   // one 16-byte record per cluster: a single scattered store
-  F.srec[pos] = make_int4(__float_as_int(c.y), __float_as_int(c.z), (int)i, 0);
+  F.srec[pos] = make_int4(__float_as_int(c.y), __float_as_int(c.z), (int)i, b);
+}
+
+// First sorted cluster of every bin: one block per row scans the row's bin
+// counts from the row's first cluster (the rows' bins and clusters are both
+// laid out row after row), so the scan covers the bins in use only.
+__global__ void k_row_scan(FrameDev F) {
+  __shared__ int sh[32];
+  if (F.cnt->err) return;  // the same for the whole block
+  const int rr = blockIdx.x;
+  const RowGrid g = F.rows[rr];
+  const int nb = g.nY * g.nZ;
+  int base = F.row_first[rr];
+  for (int j0 = 0; j0 < nb; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    const int c = j < nb ? F.bin_cnt[g.bin0 + j] : 0;
+    int tot;
+    const int ex = block_exscan(c, sh, &tot);
+    if (j < nb) F.bin_first[g.bin0 + j] = base + ex;
+    base += tot;
+  }
+  if (rr == gridDim.x - 1 && threadIdx.x == 0) F.bin_first[g.bin0 + nb] = base;
 }
 
 // (sector, row) of every sorted cluster: a row's clusters are contiguous in
 // the sorted order, so one block per row writes its range in order (rather
 // than the scatter adding another scattered store per cluster).
-__global__ void k_row_fill(FrameDev F, KParams P) {
+__global__ void k_row_fill(FrameDev F) {
   if (F.cnt->err) return;
   const int rr = blockIdx.x;
-  const RowGrid g = F.rows[rr];
-  const int lo = F.bin_first[g.bin0], hi = F.bin_first[g.bin0 + g.nY * g.nZ];
+  const int lo = F.row_first[rr], hi = F.row_first[rr + 1];
   for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) F.srow[k] = (uint16_t)rr;
 }
 
 // Order the clusters of each bin by input id (deterministic layout) and
-// split the records into the sorted (y, z) and id arrays.
+// split the records into the sorted (y, z) and id arrays: one thread per
+// sorted cluster, whose place in its bin is the number of the bin's clusters
+// with a smaller id (bins hold about one cluster, so the work follows the
+// clusters, not the bins).
 __global__ void k_bin_sort(FrameDev F) {
-  const int nb = F.cnt->n_bins;
-  if (F.cnt->err) return;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    const int lo = F.bin_first[b], hi = F.bin_first[b + 1];
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= F.n || F.cnt->err) return;
+  const int4 v = F.srec[k];
+  const int lo = F.bin_first[v.w], hi = F.bin_first[v.w + 1];
+  int pos = lo;
+  if (hi - lo > 1) {
     if (hi - lo > kMaxBinOcc) {
       atomicOr(&F.cnt->err, kErrDense);
-      continue;
+      return;
     }
-    for (int k = lo + 1; k < hi; ++k) {
-      const int4 v = F.srec[k];
-      int j = k - 1;
-      while (j >= lo && F.srec[j].z > v.z) {
-        F.srec[j + 1] = F.srec[j];
-        --j;
-      }
-      F.srec[j + 1] = v;
-    }
-    for (int k = lo; k < hi; ++k) {
-      const int4 v = F.srec[k];
-      F.syz[k] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
-      F.sid[k] = v.z;
-    }
+    for (int j = lo; j < hi; ++j) pos += F.srec[j].z < v.z ? 1 : 0;
   }
+  F.syz[pos] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
+  F.sid[pos] = v.z;
 }
 
 // ------------------------------------------------------------- a2 neighbours
@@ -983,7 +1004,7 @@ __global__ void k_sel_owner(FrameDev F, KParams P) {
 // Outer-to-inner walk of every tracklet's hits.  The rows are taken in
 // groups of kWalkGroup: their hit indices, then those hits' owner keys, are
 // requested together before the (sequential) keep decisions of the group.
-constexpr int kWalkGroup = 8;
+constexpr int kWalkGroup = 16;
 
 __global__ void k_sel_walk(FrameDev F, KParams P) {
   const int nst = min(F.cnt->n_starts, (int)F.cap_tl);
@@ -1260,11 +1281,12 @@ int stage_grid(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   if (n > 0) { k_row_stats<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); ++k; }
   k_row_grid<<<1, 1024, 0, s>>>(F, P); ++k;
   if (n > 0) { k_bin_hist<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); ++k; }
-  k += scan_exclusive(F.bin_cnt, F.bin_first, F.cap_bins + 1, F.scan_tmp, s);
+  k_row_scan<<<P.n_sectors * P.n_rows, 256, 0, s>>>(F);
+  ++k;
   if (n > 0) {
     k_scatter<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
-    k_bin_sort<<<sms * 8, kBlock, 0, s>>>(F);
-    k_row_fill<<<P.n_sectors * P.n_rows, 128, 0, s>>>(F, P);
+    k_bin_sort<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F);
+    k_row_fill<<<P.n_sectors * P.n_rows, 128, 0, s>>>(F);
     k += 3;
   }
   return k;
