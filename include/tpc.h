@@ -281,8 +281,9 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
 /* Launch shape chosen for heavy kernel `slot` (0..5): kernel name, block
  * size, blocks per SM, lanes per work item (1 = one thread per item; the
  * merge search of slot 2 runs one item on a group of 1, 4, 8, 16 or 32
- * lanes, the neighbour search of slot 5 one cluster on 1, 4 or 8 lanes, in
- * one launch of 256-thread blocks over the clusters).  Any output pointer may
+ * lanes, the neighbour search of slot 5 one cluster on 1, 4 or 8 lanes, or
+ * 32 clusters per warp with their candidates staged in shared memory (lanes =
+ * 32), in one launch of 256-thread blocks over the clusters).  Any output pointer may
  * be NULL.  TPC_ERR_INVALID_ARG past the last slot. */
 tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kernel,
                              int32_t* block, int32_t* blocks_per_sm, int32_t* lanes);
@@ -292,7 +293,7 @@ tpc_status tpc_launch_config(const tpc_ctx* ctx, int32_t slot, const char** kern
  * same GPU.  block: multiple of 32 in [32, 256] (the kernels are compiled for
  * at most 256 threads per block); blocks_per_sm in [1, 32]; lanes: 1, or for
  * slot 2 (merge search) one of 4, 8, 16, 32, for slot 5 (neighbour search)
- * 4 or 8 (slot 5 uses only its lanes).
+ * 4, 8 or 32 (slot 5 uses only its lanes).
  * The shape changes only scheduling: results are identical for every shape.
  * TPC_ERR_INVALID_ARG for any other value. */
 tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,

@@ -246,6 +246,8 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
   if (ctx->sms <= 0) ctx->sms = 1;
+  strict::init_attributes();
+  fast::init_attributes();
 
   const long n = opt->cap_clusters;
   ctx->cap_n = n;
@@ -337,6 +339,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.ie_slot, T);
   ok &= dalloc(ctx, &F.ie_bin, T);
   ok &= dalloc(ctx, &F.ie_idx, T);
+  ok &= dalloc(ctx, &F.ie_rec, T);
   ok &= dalloc(ctx, &F.sec_zlo, nsec_all);
   ok &= dalloc(ctx, &F.sec_zinv, nsec_all);
   if (ctx->max_frames > 1) ok &= dalloc(ctx, &ctx->src, ctx->max_frames);
@@ -667,7 +670,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
   static const int blocks[] = {64, 128, 256};
   static const int per_sm[] = {4, 8, 16};
   static const int merge_lanes[] = {1, 8, 16, 32};
-  static const int links_lanes[] = {1, 4, 8};
+  static const int links_lanes[] = {1, 4, 8, 32};
   const bool prof_was = ctx->prof;
   if (!ctx->ev[0])
     for (auto& e : ctx->ev)
@@ -681,7 +684,7 @@ tpc_status tpc_autotune(tpc_ctx* ctx, const tpc_clusters* frames, int32_t n_fram
     double best = 1e30;
     LaunchCfg best_lc = ctx->F.lc;
     // the neighbour search is one launch over the clusters: only its lanes vary
-    const int nl = slot == kLMerge ? 4 : slot == kLLinks ? 3 : 1;
+    const int nl = slot == kLMerge ? 4 : slot == kLLinks ? 4 : 1;
     const int nb = slot == kLLinks ? 1 : 3, nq = slot == kLLinks ? 1 : 3;
     for (int li = 0; li < nl; ++li)
     for (int bi = 0; bi < nb; ++bi)
@@ -735,7 +738,7 @@ tpc_status tpc_set_launch_config(tpc_ctx* ctx, int32_t slot, int32_t block,
   if (!ctx) return TPC_ERR_INVALID_ARG;
   const bool lanes_ok = lanes == 1 ||
                         (slot == kLMerge && (lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32)) ||
-                        (slot == kLLinks && (lanes == 4 || lanes == 8));
+                        (slot == kLLinks && (lanes == 4 || lanes == 8 || lanes == 32));
   if (slot < 0 || slot >= kLNum || block < 32 || block > 256 || block % 32 != 0 ||
       blocks_per_sm < 1 || blocks_per_sm > 32 || !lanes_ok)
     return fail(ctx, TPC_ERR_INVALID_ARG, "launch shape slot %d: block %d, %d per SM, %d lanes",

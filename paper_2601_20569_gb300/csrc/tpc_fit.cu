@@ -146,14 +146,22 @@ __global__ void k_acc_write(FrameDev F) {
   int base = 0;
   if (lane == 31 && incl > 0) base = atomicAdd(&F.cnt->n_pos, incl);
   base = __shfl_sync(0xffffffffu, base, 31);
+  const unsigned act = __ballot_sync(0xffffffffu, f != 0);
   if (f) {
     const int j = F.scan_tmp[blockIdx.x] + ex;
     F.st_tl[j] = i;
     F.st_off[j] = base + incl - nk;
-    // scheduling bucket of the sector refit: most clusters first
+    // scheduling bucket of the sector refit: most clusters first (the lanes
+    // of one bucket take their places with one atomic; the order inside a
+    // bucket only schedules the refit)
     const int b = kOrdBuckets - 1 - min(kOrdBuckets - 1, nk);
+    const unsigned peers = __match_any_sync(act, b);
+    const int leader = __ffs(peers) - 1;
+    int slot = 0;
+    if (lane == leader) slot = atomicAdd(&F.st_ord_cnt[b], __popc(peers));
+    slot = __shfl_sync(peers, slot, leader);
     F.st_obucket[j] = b;
-    F.st_oslot[j] = atomicAdd(&F.st_ord_cnt[b], 1);
+    F.st_oslot[j] = slot + __popc(peers & ((1u << lane) - 1u));
   }
 }
 
@@ -168,18 +176,47 @@ __global__ void k_st_gather(FrameDev F, KParams P) {
     return;
   }
   const int NR = P.n_rows;
-  // one warp per track: its kept list read and its positions written 32 at a time
+  __shared__ float rx[kMaxRows];
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) rx[r] = F.row_x[r];
+  __syncthreads();
+  // One warp per 32 consecutive tracks: lane j loads track j's tracklet,
+  // length and output place (all lanes at once), then the warp takes the
+  // tracks one by one, its lanes reading the whole kept list (up to kMaxRows
+  // entries, all loads issued before the positions they address) and
+  // writing the positions 32 at a time.
+  constexpr int kChunks = (kMaxRows + 31) / 32;
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < ns; j += nw) {
-    const int ti = F.st_tl[j];
-    const int nk = F.tl_nkept[ti];
-    const int* K = F.tl_kept + (long)ti * kMaxRows;
-    float4* out = F.st_pos + F.st_off[j];
-    for (int m = lane; m < nk; m += 32) {
-      const int c = K[m];
-      const float2 yz = F.syz[c];
-      out[m] = make_float4(F.row_x[F.srow[c] % NR], yz.x, yz.y, 0.0f);
+  for (int j0 = 32 * (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); j0 < ns;
+       j0 += 32 * nw) {
+    int ti = 0, nk = 0, off = 0;
+    if (j0 + lane < ns) {
+      ti = F.st_tl[j0 + lane];
+      nk = F.tl_nkept[ti];
+      off = F.st_off[j0 + lane];
+    }
+    for (int j = 0; j < 32; ++j) {
+      const int tj = __shfl_sync(0xffffffffu, ti, j);
+      const int nj = __shfl_sync(0xffffffffu, nk, j);
+      const int oj = __shfl_sync(0xffffffffu, off, j);
+      const int* K = F.tl_kept + (long)tj * kMaxRows;
+      float4* out = F.st_pos + oj;
+      int c[kChunks];
+#pragma unroll
+      for (int u = 0; u < kChunks; ++u) {
+        const int m = lane + 32 * u;
+        c[u] = m < nj ? K[m] : -1;
+      }
+      float2 yz[kChunks];
+      int rr[kChunks];
+#pragma unroll
+      for (int u = 0; u < kChunks; ++u) {
+        yz[u] = c[u] >= 0 ? F.syz[c[u]] : make_float2(0.0f, 0.0f);
+        rr[u] = c[u] >= 0 ? F.srow[c[u]] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kChunks; ++u)
+        if (c[u] >= 0) out[lane + 32 * u] = make_float4(rx[rr[u] % NR], yz[u].x, yz[u].y, 0.0f);
     }
   }
 }
@@ -288,8 +325,23 @@ __global__ void k_ie_scatter(FrameDev F) {
   if (F.cnt->err) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
     const int b = F.ie_bin[i];
-    if (b >= 0) F.ie_idx[F.ie_first[b] + F.ie_slot[i]] = i;
+    if (b < 0) continue;
+    const int pos = F.ie_first[b] + F.ie_slot[i];
+    F.ie_idx[pos] = i;
+    const float* ie = F.st_ie + (long)i * kStateF;
+    F.ie_rec[pos] = make_float4(ie[0], ie[1], ie[20], __int_as_float(i));
   }
+}
+
+// n consecutive queue items per calling lane, one atomic per warp.
+__device__ __forceinline__ int queue_next_n(int* q, int n) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(q, __popc(mask) * n);
+  base = __shfl_sync(mask, base, leader);
+  return base + __popc(mask & ((1u << lane) - 1u)) * n;
 }
 
 // chi2 of a 5-vector difference with a Cholesky factorisation (-1: not PD).
@@ -346,6 +398,72 @@ __device__ __forceinline__ bool merge_test(const FrameDev& F, const KParams& P, 
   return chi2 >= 0.0f && chi2 < P.merge_chi2;
 }
 
+// Position prefilter of the pair test.  A's outer end turned into the frame
+// of one of the three sectors searched (q = 0: its own, 1: the next, 2: the
+// previous), with the terms of the helix step that depend on A alone; then
+// A's position at B's x by the helix step's own expressions for y and z.  The
+// prefilter rejects a candidate only where that position lies outside the
+// window by more than a rounding margin, and leaves a failed rotation or step
+// to the full test, so every decision is the full test's (merge_test), in
+// either arithmetic mode.  Nearly all candidates of the index end here,
+// before the covariance transport and the 5x5 chi2.
+struct MergeA {
+  float y, z, s0, c0, kap, tgl, x;
+  int ok;
+};
+
+__device__ __forceinline__ MergeA merge_a(const float* oe, int q, const KParams& P) {
+  Trk<float> t;  // the covariance is not read: its transport is dropped
+#pragma unroll
+  for (int i = 0; i < 5; ++i) t.p[i] = oe[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) t.c[i] = 0.0f;
+  t.x = oe[20];
+  bool ok = true;
+  if (q == 1) ok = rotate(t, 1, P, P.fit_max_snp);
+  else if (q == 2) ok = rotate(t, -1, P, P.fit_max_snp);
+  MergeA m;
+  m.y = t.p[0];
+  m.z = t.p[1];
+  m.s0 = t.p[2];
+  m.tgl = t.p[3];
+  m.kap = t.p[4] * P.kb;
+  m.x = t.x;
+#ifdef TPC_FAST_ARITH
+  const float a0 = 1.0f - m.s0 * m.s0;
+  m.c0 = a0 * rsqrtf(a0);
+#else
+  m.c0 = sqrtf(1.0f - m.s0 * m.s0);
+#endif
+  m.ok = ok ? 1 : 0;
+  return m;
+}
+
+// The position (y, z) of A at x = xb (false: no rotation or no step).
+__device__ __forceinline__ bool merge_pos(const MergeA& m, float xb, const KParams& P, float& yb,
+                                          float& zb) {
+  if (!m.ok) return false;
+  const float dx = xb - m.x;
+  const float s1 = m.s0 + m.kap * dx;
+  if (!(fabsf(s1) < P.fit_max_snp)) return false;
+#ifdef TPC_FAST_ARITH
+  const float a1 = 1.0f - s1 * s1;
+  const float c1 = a1 * rsqrtf(a1);
+  const float t = (m.s0 + s1) * frcp(m.c0 + c1);
+  const float tt = 1.0f + t * t;
+  const float L1 = tt * rsqrtf(tt);
+#else
+  const float c1 = sqrtf(1.0f - s1 * s1);
+  const float t = (m.s0 + s1) / (m.c0 + c1);
+  const float L1 = sqrtf(1.0f + t * t);
+#endif
+  const float chord = dx * L1;
+  const float u = m.kap * chord * 0.5f;
+  yb = m.y + dx * t;
+  zb = m.z + m.tgl * (chord * asinc_f(u));
+  return true;
+}
+
 // Best merge partner of every outer end A, searched by a group of G lanes
 // (G = 1: one thread per end).  The (sector, z bin) ranges of A's candidates
 // in the index are dealt out to the lanes, their sizes summed by a group scan,
@@ -354,7 +472,7 @@ __device__ __forceinline__ bool merge_test(const FrameDev& F, const KParams& P, 
 // found by shuffles.  The minimum does not depend on the visiting order, so
 // every G gives the scalar search's result bit for bit.
 template <int G>
-__global__ void __launch_bounds__(256) k_merge_best(FrameDev F, KParams P) {
+__global__ void __launch_bounds__(256, 4) k_merge_best(FrameDev F, KParams P) {
   const int ns = F.cnt->n_tracks;
   if (F.cnt->err) return;
   const int lane = threadIdx.x & 31;
@@ -362,86 +480,131 @@ __global__ void __launch_bounds__(256) k_merge_best(FrameDev F, KParams P) {
   const unsigned gmask = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int half = P.n_phi;
   for (;;) {
-    int a = 0;
-    if (gl == 0) a = queue_next(&F.cnt->queue[kQMerge]);
-    a = __shfl_sync(gmask, a, 0, G);
-    if (a >= ns) break;
-    if (!F.st_ok[a] || F.st_next[a] >= 0) continue;  // (outer end linked by the edge following)
-    const int keyA = F.st_key[a];
-    unsigned long long best = ~0ull;
-    int bb = -1;
-    const int r0 = F.st_rmax[a] + 1;
-    const int r1 = min(F.st_rmax[a] + P.merge_max_gap, P.n_rows - 1);
-    if (r0 <= r1) {
-      // the pair test needs 1 <= rmin(B) - rmax(A) <= merge_max_gap: only
-      // those rows of the index are visited
-      const int sa = F.st_sector[a];
-      const int side = sa / half, ph = sa % half;
-      const float* oe = F.st_oe + (long)a * kStateF;
-      const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
-      const float m = 0.01f;
-      int sq[3], zq[3], nq[3];
-      int nr = 0;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        sq[q] = side * half + (ph + (q == 0 ? 0 : q == 1 ? 1 : half - 1)) % half;
-        zq[q] = merge_zbin(F, sq[q], oe[1] - zwin - m);
-        nq[q] = merge_zbin(F, sq[q], oe[1] + zwin + m) - zq[q] + 1;
-        nr += nq[q];
-      }
-      for (int j0 = 0; j0 < nr; j0 += G) {
-        int lo = 0, cnt = 0;
-        int j = j0 + gl;
-        if (j < nr) {
-          const int q = j < nq[0] ? 0 : j < nq[0] + nq[1] ? 1 : 2;
-          j -= q == 0 ? 0 : q == 1 ? nq[0] : nq[0] + nq[1];
-          const int base = (sq[q] * kMergeZ + zq[q] + j) * P.n_rows;
-          lo = F.ie_first[base + r0];
-          cnt = F.ie_first[base + r1 + 1] - lo;
-        }
-        int inc = cnt;  // inclusive scan of the range sizes over the group
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) {
-          const int v = __shfl_up_sync(gmask, inc, o, G);
-          if (gl >= o) inc += v;
-        }
-        const int total = __shfl_sync(gmask, inc, G - 1, G);
-        for (int c0 = 0; c0 < total; c0 += G) {
-          const int c = c0 + gl;
-          int L = 0;  // the range holding candidate c: first lane with inc > c
-#pragma unroll
-          for (int st = G / 2; st >= 1; st >>= 1) {
-            const int v = __shfl_sync(gmask, inc, L + st - 1, G);
-            if (v <= c) L += st;
-          }
-          const int excl = __shfl_sync(gmask, inc - cnt, L, G);
-          const int lo_l = __shfl_sync(gmask, lo, L, G);
-          if (c >= total) continue;
-          const int b = F.ie_idx[lo_l + (c - excl)];
-          if (b == a || !F.st_ok[b]) continue;
-          float chi2;
-          if (!merge_test(F, P, a, b, chi2)) continue;
-          const unsigned long long kb = pack_chi_key(chi2, F.st_key[b]);
-          if (kb < best) {
-            best = kb;
-            bb = b;
-          }
-          atomicMin(&F.st_bestA[b], pack_chi_key(chi2, keyA));
-        }
+    // G ends per queue fetch: lane gl of the group looks at end base + gl;
+    // the ends with no row to search (the many that reach the last rows)
+    // are answered at once, the others searched one after the other by the
+    // whole group
+    int base = 0;
+    if (gl == 0) base = queue_next_n(&F.cnt->queue[kQMerge], G);
+    base = __shfl_sync(gmask, base, 0, G);
+    if (base >= ns) break;
+    const int am = base + gl;
+    bool live = false;
+    // (an outer end linked by the edge following is not searched)
+    if (am < ns && F.st_ok[am] && F.st_next[am] < 0) {
+      const int rmx = F.st_rmax[am];
+      live = rmx + 1 <= min(rmx + P.merge_max_gap, P.n_rows - 1);
+      if (!live) {
+        F.st_bestB[am] = -1;
+        F.st_bestchi[am] = 0.0f;
       }
     }
+    for (unsigned todo = __ballot_sync(gmask, live) & gmask; todo; todo &= todo - 1) {
+      const int a = __shfl_sync(gmask, am, (__ffs(todo) - 1) & (G - 1), G);
+      const int keyA = F.st_key[a];
+      unsigned long long best = ~0ull;
+      int bb = -1;
+      const int r0 = F.st_rmax[a] + 1;
+      const int r1 = min(F.st_rmax[a] + P.merge_max_gap, P.n_rows - 1);
+      {
+        // the pair test needs 1 <= rmin(B) - rmax(A) <= merge_max_gap: only
+        // those rows of the index are visited
+        const int sa = F.st_sector[a];
+        const int side = sa / half, ph = sa % half;
+        const float* oe = F.st_oe + (long)a * kStateF;
+        const float zwin = P.merge_dz + fabsf(oe[3]) * P.merge_zspan;
+        const float m = 0.01f;
+        int sq[3], zq[3], nq[3];
+        int nr = 0;
 #pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-      const unsigned long long ob = __shfl_xor_sync(gmask, best, o, G);
-      const int obb = __shfl_xor_sync(gmask, bb, o, G);
-      if (ob < best) {
-        best = ob;
-        bb = obb;
+        for (int q = 0; q < 3; ++q) {
+          sq[q] = side * half + (ph + (q == 0 ? 0 : q == 1 ? 1 : half - 1)) % half;
+          zq[q] = merge_zbin(F, sq[q], oe[1] - zwin - m);
+          nq[q] = merge_zbin(F, sq[q], oe[1] + zwin + m) - zq[q] + 1;
+          nr += nq[q];
+        }
+        // A's state in the three sectors: lanes 0-2 of the group hold one
+        // each and hand it to the lanes by shuffles (one lane computes it
+        // where it needs it)
+        MergeA ma{};
+        if (G >= 4 && gl < 3) ma = merge_a(oe, gl, P);
+        const float oz = oe[1];
+        for (int j0 = 0; j0 < nr; j0 += G) {
+          int lo = 0, cnt = 0, qj = 0;
+          int j = j0 + gl;
+          if (j < nr) {
+            const int q = j < nq[0] ? 0 : j < nq[0] + nq[1] ? 1 : 2;
+            j -= q == 0 ? 0 : q == 1 ? nq[0] : nq[0] + nq[1];
+            const int base = (sq[q] * kMergeZ + zq[q] + j) * P.n_rows;
+            lo = F.ie_first[base + r0];
+            cnt = F.ie_first[base + r1 + 1] - lo;
+            qj = q;
+          }
+          int inc = cnt;  // inclusive scan of the range sizes over the group
+#pragma unroll
+          for (int o = 1; o < G; o <<= 1) {
+            const int v = __shfl_up_sync(gmask, inc, o, G);
+            if (gl >= o) inc += v;
+          }
+          const int total = __shfl_sync(gmask, inc, G - 1, G);
+          for (int c0 = 0; c0 < total; c0 += G) {
+            const int c = c0 + gl;
+            int L = 0;  // the range holding candidate c: first lane with inc > c
+#pragma unroll
+            for (int st = G / 2; st >= 1; st >>= 1) {
+              const int v = __shfl_sync(gmask, inc, L + st - 1, G);
+              if (v <= c) L += st;
+            }
+            const int excl = __shfl_sync(gmask, inc - cnt, L, G);
+            const int lo_l = __shfl_sync(gmask, lo, L, G);
+            const int q_l = __shfl_sync(gmask, qj, L, G);
+            MergeA mq;
+            if (G >= 4) {
+              mq.y = __shfl_sync(gmask, ma.y, q_l, G);
+              mq.z = __shfl_sync(gmask, ma.z, q_l, G);
+              mq.s0 = __shfl_sync(gmask, ma.s0, q_l, G);
+              mq.c0 = __shfl_sync(gmask, ma.c0, q_l, G);
+              mq.kap = __shfl_sync(gmask, ma.kap, q_l, G);
+              mq.tgl = __shfl_sync(gmask, ma.tgl, q_l, G);
+              mq.x = __shfl_sync(gmask, ma.x, q_l, G);
+              mq.ok = __shfl_sync(gmask, ma.ok, q_l, G);
+            }
+            if (c >= total) continue;
+            // the indexed inner end: (y, z, x, track)
+            const float4 rec = F.ie_rec[lo_l + (c - excl)];
+            if (!(fabsf(rec.y - oz) <= zwin)) continue;  // the full test's z window
+            if (G < 4) mq = merge_a(oe, q_l, P);
+            float yb, zb;
+            if (merge_pos(mq, rec.z, P, yb, zb) &&
+                (fabsf(rec.x - yb) > P.merge_dy + 0.01f + 1e-5f * fabsf(rec.x) ||
+                 fabsf(rec.y - zb) > P.merge_dz + 0.01f + 1e-5f * fabsf(rec.y)))
+              continue;
+            const int b = __float_as_int(rec.w);
+            if (b == a || !F.st_ok[b]) continue;
+            float chi2;
+            if (!merge_test(F, P, a, b, chi2)) continue;
+            const unsigned long long kb = pack_chi_key(chi2, F.st_key[b]);
+            if (kb < best) {
+              best = kb;
+              bb = b;
+            }
+            atomicMin(&F.st_bestA[b], pack_chi_key(chi2, keyA));
+          }
+        }
       }
-    }
-    if (gl == 0) {
-      F.st_bestB[a] = bb;
-      F.st_bestchi[a] = bb >= 0 ? o2f((unsigned)(best >> 32)) : 0.0f;
+#pragma unroll
+      for (int o = G / 2; o >= 1; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(gmask, best, o, G);
+        const int obb = __shfl_xor_sync(gmask, bb, o, G);
+        if (ob < best) {
+          best = ob;
+          bb = obb;
+        }
+      }
+      if (gl == 0) {
+        F.st_bestB[a] = bb;
+        F.st_bestchi[a] = bb >= 0 ? o2f((unsigned)(best >> 32)) : 0.0f;
+      }
     }
   }
 }
@@ -827,80 +990,89 @@ __device__ __forceinline__ float chi2_interp(const Interp& I, float my, float mz
 
 // Station list of fit track f: clusters of the chain (rows increasing) plus
 // empty inner rows between two clusters of one sector.
-__device__ int build_stations(FrameDev& F, const KParams& P, int f, int head) {
-  int* SC = F.ft_st_cl + (long)f * kMaxRows;
-  uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
-  const int NR = P.n_rows;
-  int ns = 0, prev = -1;
-  for (int s = head; s >= 0; s = F.st_next[s]) {
-    const int ti = F.st_tl[s];
-    const int nk = F.tl_nkept[ti];
-    const int* K = F.tl_kept + (long)ti * kMaxRows;
-    for (int j = nk - 1; j >= 0; --j) {
-      const int c = K[j];
-      const int rs = F.srow[c];
-      if (prev >= 0 && prev / NR == rs / NR) {
-        for (int r = prev % NR + 1; r < rs % NR && r < P.inner_rows && ns < kMaxRows; ++r) {
-          SC[ns] = -1;
-          SR[ns] = (uint16_t)(rs - rs % NR + r);
-          ++ns;
-        }
-      }
-      if (ns < kMaxRows) {
-        SC[ns] = c;
-        SR[ns] = (uint16_t)rs;
-        ++ns;
-      }
-      prev = rs;
-    }
-  }
-  return ns;
-}
-
 __device__ __forceinline__ float zoff(const float* ie) {
   return ie[1] - ie[3] * sqrtf(ie[20] * ie[20] + ie[0] * ie[0]);
 }
 
 // Per fit track, ahead of the fit: the station list, the chain's last
 // segment (whose outer end starts iteration 1), the identity key and the
-// drift-time z offset.  A separate pass with one thread per track, so that
-// the fit's state machine does not stall a whole warp while one lane walks
-// a chain.
+// drift-time z offset.  One warp per track: the segments of the chain are
+// taken in order, and the lanes take 32 kept clusters of a segment at a time
+// (innermost first), their loads issued together.  A station is a kept
+// cluster, preceded, on the inner rows of one sector, by an empty station on
+// every row skipped since the previous cluster; a warp scan of the stations
+// each cluster adds gives the places.  Stations beyond kMaxRows are dropped
+// (none are reached: a chain's rows increase along it).
 __global__ void k_fit_stations(FrameDev F, KParams P) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+  const int NR = P.n_rows;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < nf; f += nw) {
     const int head = F.ft_head[f];
-    int last = head;
+    int* SC = F.ft_st_cl + (long)f * kMaxRows;
+    uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
     // across the central electrode: the side of the first segment, and the
     // z shift of the clusters on the other side (set at the first segment
     // there, 0 for a chain on one side)
     const int side0 = (F.st_sector[head] / P.n_phi) & 1;
     float zsh = 0.0f;
     bool crossed = false;
+    int last = head, ns = 0, prev = -1;
     for (int sg = head; sg >= 0; sg = F.st_next[sg]) {
       last = sg;
       if (!crossed && ((F.st_sector[sg] / P.n_phi) & 1) != side0) {
         crossed = true;
         zsh = F.st_dz[sg];
       }
+      const int ti = F.st_tl[sg];
+      const int nk = F.tl_nkept[ti];
+      const int* K = F.tl_kept + (long)ti * kMaxRows;  // outermost first
+      for (int j0 = 0; j0 < nk; j0 += 32) {
+        const bool valid = j0 + lane < nk;
+        const int c = valid ? K[nk - 1 - (j0 + lane)] : -1;
+        const int rs = valid ? (int)F.srow[c] : 0;
+        int prs = __shfl_up_sync(0xffffffffu, rs, 1);
+        if (lane == 0) prs = prev;
+        int gap = 0;
+        if (valid && prs >= 0 && prs / NR == rs / NR)
+          gap = max(0, min(rs % NR, P.inner_rows) - (prs % NR + 1));
+        const int add = valid ? gap + 1 : 0;
+        int incl = add;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int pos = ns + incl - add;
+        if (valid) {
+          for (int q = 0; q < gap && pos + q < kMaxRows; ++q) {
+            SC[pos + q] = -1;
+            SR[pos + q] = (uint16_t)(rs - rs % NR + prs % NR + 1 + q);
+          }
+          if (pos + gap < kMaxRows) {
+            SC[pos + gap] = c;
+            SR[pos + gap] = (uint16_t)rs;
+            // Phase III: clusters held by a station outside the inner region
+            // are not extrapolation candidates of any track
+            if (P.ext_rows > 0 && rs % NR >= P.inner_rows) F.ft_fixed[c] = 1;
+          }
+        }
+        const int nvalid = min(32, nk - j0);
+        ns += __shfl_sync(0xffffffffu, incl, 31);
+        prev = __shfl_sync(0xffffffffu, rs, nvalid - 1);
+      }
     }
-    F.ft_side0[f] = side0;
-    F.ft_zsh[f] = zsh;
-    const int ns = build_stations(F, P, f, head);
-    F.ft_nst[f] = ns;
-    F.ft_key[f] = F.st_key[head];
-    F.ft_last[f] = last;
-    F.ft_z0[f] = zoff(F.st_ie + (long)head * kStateF);
-    F.ft_next[f] = 0;
-    F.ft_nout[f] = 0;
-    if (P.ext_rows > 0) {
-      // Phase III: clusters held by a station outside the inner region are
-      // not extrapolation candidates of any track
-      const int* SC = F.ft_st_cl + (long)f * kMaxRows;
-      const uint16_t* SR = F.ft_st_rs + (long)f * kMaxRows;
-      for (int k = 0; k < ns; ++k)
-        if (SC[k] >= 0 && SR[k] % P.n_rows >= P.inner_rows) F.ft_fixed[SC[k]] = 1;
+    if (lane == 0) {
+      F.ft_side0[f] = side0;
+      F.ft_zsh[f] = zsh;
+      F.ft_nst[f] = min(ns, kMaxRows);
+      F.ft_key[f] = F.st_key[head];
+      F.ft_last[f] = last;
+      F.ft_z0[f] = zoff(F.st_ie + (long)head * kStateF);
+      F.ft_next[f] = 0;
+      F.ft_nout[f] = 0;
     }
   }
 }
@@ -1569,65 +1741,100 @@ __global__ void k_out_write(FrameDev F, KParams P) {
   int tt, tr;
   const int et = block_exscan(fl, sh, &tt);
   const int er = block_exscan(v, sh, &tr);
+  int off = 0, key = 0, fits = 0;
   if (!fl) {
     if (f < nf) F.ft_outidx[f] = -1;
-    return;
+  } else {
+    const int t = F.scan_tmp[2 * blockIdx.x] + et;
+    off = F.scan_tmp[2 * blockIdx.x + 1] + er;
+    F.ft_outidx[f] = t;
+    const float* o = F.ft_out + (long)f * kStateF;
+    for (int i = 0; i < 5; ++i) F.out_par[(long)t * 5 + i] = o[i];
+    for (int i = 0; i < 15; ++i) F.out_cov[(long)t * 15 + i] = o[5 + i];
+    F.out_x[t] = o[20];
+    F.out_zsh[t] = F.ft_zsh[f];
+    F.out_sector[t] = __float_as_int(o[21]);
+    F.out_chi2[t] = F.ft_chi2[f];
+    F.out_ndf[t] = 2 * v - 5;
+    F.out_ncl[t] = v;
+    key = F.ft_key[f];
+    F.out_key[t] = key;
+    F.out_offset[t] = off;
+    fits = (long)off + v <= F.cap_refs;
+    if (!fits) atomicOr(&F.cnt->err, kErrCapRefs);
   }
-  const int t = F.scan_tmp[2 * blockIdx.x] + et;
-  const int off = F.scan_tmp[2 * blockIdx.x + 1] + er;
-  F.ft_outidx[f] = t;
-  const float* o = F.ft_out + (long)f * kStateF;
-  for (int i = 0; i < 5; ++i) F.out_par[(long)t * 5 + i] = o[i];
-  for (int i = 0; i < 15; ++i) F.out_cov[(long)t * 15 + i] = o[5 + i];
-  F.out_x[t] = o[20];
-  F.out_zsh[t] = F.ft_zsh[f];
-  F.out_sector[t] = __float_as_int(o[21]);
-  F.out_chi2[t] = F.ft_chi2[f];
-  const int n = F.ft_n[f];
-  F.out_ndf[t] = 2 * n - 5;
-  F.out_ncl[t] = n;
-  F.out_key[t] = F.ft_key[f];
-  F.out_offset[t] = off;
-  const int* used = F.ft_used + (long)f * kMaxRows;
-  const bool fits = (long)off + n <= F.cap_refs;
-  if (!fits) atomicOr(&F.cnt->err, kErrCapRefs);
-  const int key = F.ft_key[f];
-  for (int j0 = 0; j0 < n; j0 += 8) {  // groups of 8 with their loads issued together
-    int u[8], id[8];
+  // Cluster lists: the warp takes its lanes' tracks one by one, its lanes
+  // over the track's clusters (the used list read innermost first, all loads
+  // issued before the ids they address), writing the input ids 32 at a time
+  // and lowering their attachment keys.
+  constexpr int kChunks = (kMaxRows + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  for (unsigned todo = __ballot_sync(0xffffffffu, fl != 0); todo; todo &= todo - 1) {
+    const int j = __ffs(todo) - 1;
+    const int fj = f - lane + j;
+    const int nj = __shfl_sync(0xffffffffu, v, j);
+    const int oj = __shfl_sync(0xffffffffu, off, j);
+    const int kj = __shfl_sync(0xffffffffu, key, j);
+    const int fitj = __shfl_sync(0xffffffffu, fits, j);
+    const int* used = F.ft_used + (long)fj * kMaxRows;
+    int u[kChunks], id[kChunks];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) u[j] = j0 + j < n ? used[n - 1 - (j0 + j)] : -1;
+    for (int c = 0; c < kChunks; ++c) {
+      const int q = lane + 32 * c;
+      u[c] = q < nj ? used[nj - 1 - q] : -1;
+    }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) id[j] = u[j] >= 0 ? F.sid[u[j]] : -1;
+    for (int c = 0; c < kChunks; ++c) id[c] = u[c] >= 0 ? F.sid[u[c]] : -1;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (id[j] < 0) continue;
-      if (fits) F.out_ids[off + j0 + j] = id[j];
-      atomicMin(&F.attach_key[id[j]], key);
+    for (int c = 0; c < kChunks; ++c) {
+      if (id[c] < 0) continue;
+      if (fitj) F.out_ids[oj + lane + 32 * c] = id[c];
+      atomicMin(&F.attach_key[id[c]], kj);
     }
   }
 }
 
+// Attachment: every cluster goes to the track with the smallest key among
+// those that use it.  One warp per 32 consecutive fit tracks, taken one by
+// one with the lanes over the track's clusters.
 __global__ void k_out_attach(FrameDev F, KParams P) {
   const int nf = min(F.cnt->n_merged, (int)F.cap_ft);
   if (F.cnt->err) return;
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
-    const int t = F.ft_outidx[f];
-    if (t < 0) continue;
-    const int n = F.ft_n[f], key = F.ft_key[f];
-    // the track's input ids as written to the output, in groups of 8 whose
-    // loads are issued together
-    const int* ids = F.out_ids + F.out_offset[t];
-    for (int j0 = 0; j0 < n; j0 += 8) {
-      int id[8], ak[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) id[j] = j0 + j < n ? ids[j0 + j] : -1;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) ak[j] = id[j] >= 0 ? F.attach_key[id[j]] : 0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (id[j] >= 0 && ak[j] == key) F.attach[id[j]] = t;
+  constexpr int kChunks = (kMaxRows + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int f0 = 32 * (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); f0 < nf;
+       f0 += 32 * nw) {
+    const int f = f0 + lane;
+    int t = -1, n = 0, key = 0, off = 0;
+    if (f < nf) {
+      t = F.ft_outidx[f];
+      if (t >= 0) {
+        n = F.ft_n[f];
+        key = F.ft_key[f];
+        off = F.out_offset[t];
+        if (t == F.cnt->n_out - 1) F.out_offset[t + 1] = F.cnt->n_refs;
+      }
     }
-    if (t == F.cnt->n_out - 1) F.out_offset[t + 1] = F.cnt->n_refs;
+    for (unsigned todo = __ballot_sync(0xffffffffu, t >= 0); todo; todo &= todo - 1) {
+      const int j = __ffs(todo) - 1;
+      const int tj = __shfl_sync(0xffffffffu, t, j);
+      const int nj = __shfl_sync(0xffffffffu, n, j);
+      const int kj = __shfl_sync(0xffffffffu, key, j);
+      const int oj = __shfl_sync(0xffffffffu, off, j);
+      const int* ids = F.out_ids + oj;
+      int id[kChunks], ak[kChunks];
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        const int q = lane + 32 * c;
+        id[c] = q < nj ? ids[q] : -1;
+      }
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) ak[c] = id[c] >= 0 ? F.attach_key[id[c]] : 0;
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c)
+        if (id[c] >= 0 && ak[c] == kj) F.attach[id[c]] = tj;
+    }
   }
 }
 

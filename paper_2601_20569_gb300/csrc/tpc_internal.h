@@ -96,7 +96,7 @@ constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
 constexpr int kIpolF = 11;      // interpolation record of an inner station
 constexpr int kMergeLanesDefault = 16;  // lanes per outer end in the merge search
-constexpr int kLinksLanesDefault = 1;   // lanes per cluster in the neighbour search
+constexpr int kLinksLanesDefault = 32;  // neighbour search: staged per warp (1, 4, 8: lanes per cluster)
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 constexpr int kMaxSeedIters = 4;  // sector-tracking iterations
@@ -254,6 +254,7 @@ struct FrameDev {
   int* ie_slot;            // [cap_tl]
   int* ie_bin;             // [cap_tl]
   int* ie_idx;             // [cap_tl] sector tracks sorted by (sector, z bin)
+  float4* ie_rec;          // [cap_tl] in index order: inner end (y, z, x) and track id bits
   float* sec_zlo;          // [n_sectors]
   float* sec_zinv;         // [n_sectors]
 

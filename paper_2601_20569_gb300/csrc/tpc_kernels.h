@@ -10,6 +10,7 @@ namespace tpc {
 
 // Each launcher enqueues one stage on stream s and returns its kernel count.
 #define TPC_DECLARE_LAUNCHERS                                                       \
+  void init_attributes();                                                          \
   int stage_grid(FrameDev& F, const KParams& P, int sms, cudaStream_t s);         \
   int stage_links(FrameDev& F, const KParams& P, int sms, cudaStream_t s);        \
   int stage_starts(FrameDev& F, const KParams& P, int sms, cudaStream_t s);       \

@@ -57,6 +57,73 @@ __global__ void k_row_stats(FrameDev F, KParams P) {
   atomicMax(&F.row_zmax[rr], f2o(z));
 }
 
+// The same statistics with each block's share of them gathered in shared
+// memory first.  A block takes kRowStatsChunk consecutive input clusters,
+// which lie (all but a block at a frame boundary) in one frame, and keeps
+// count, z minimum and z maximum of that frame's W rows in shared memory;
+// clusters of another frame go to global memory directly.  Then one global
+// update per row the block has seen.  The statistics are a sum, a minimum and
+// a maximum, so the result does not depend on the order of the updates.
+constexpr int kRowStatsChunk = 256 * 128;
+constexpr int kRowStatsMaxRows = 6144;  // W * 12 bytes of shared memory per block
+bool g_row_stats_shared = false;        // the kernel's shared-memory size is allowed
+
+__global__ void __launch_bounds__(256) k_row_stats_sh(FrameDev F, KParams P, int W) {
+  extern __shared__ unsigned rs_sh[];
+  unsigned* cnt = rs_sh;
+  unsigned* zlo = rs_sh + W;
+  unsigned* zhi = rs_sh + 2 * W;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    cnt[w] = 0u;
+    zlo[w] = 0xFFFFFFFFu;
+    zhi[w] = 0u;
+  }
+  const long c0 = (long)blockIdx.x * kRowStatsChunk;
+  const long c1 = min((long)F.n, c0 + kRowStatsChunk);
+  int f0 = 0;  // frame of the chunk's first cluster
+  if (F.nsrc > 0) {
+    int lo = 0, hi = F.nsrc - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (F.src[mid].off <= c0) lo = mid;
+      else hi = mid - 1;
+    }
+    f0 = lo;
+  }
+  const long wb = (long)f0 * W;
+  __syncthreads();
+  for (long i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    const ClusterIn c = load_cluster(F, i);
+    const int r = c.row, s = c.sector;
+    const float y = c.y, z = c.z;
+    if (r >= P.n_rows || s >= P.n_sectors || !isfinite(y) || !isfinite(z)) {
+      atomicOr(&F.cnt->err, kErrInput);
+      continue;
+    }
+    const long rr = (long)s * P.n_rows + r;
+    const unsigned zo = f2o(z);
+    if (rr >= wb && rr < wb + W) {
+      const int w = (int)(rr - wb);
+      atomicAdd(&cnt[w], 1u);
+      atomicMin(&zlo[w], zo);
+      atomicMax(&zhi[w], zo);
+    } else {
+      atomicAdd(&F.row_cnt[rr], 1);
+      atomicMin(&F.row_zmin[rr], zo);
+      atomicMax(&F.row_zmax[rr], zo);
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    const unsigned n = cnt[w];
+    if (n == 0u) continue;
+    const long rr = wb + w;
+    atomicAdd(&F.row_cnt[rr], (int)n);
+    atomicMin(&F.row_zmin[rr], zlo[w]);
+    atomicMax(&F.row_zmax[rr], zhi[w]);
+  }
+}
+
 // One block: bin layout of every (sector,row) and the row/bin offsets.
 __global__ void k_row_grid(FrameDev F, KParams P) {
   __shared__ int sh[32];
@@ -437,6 +504,146 @@ __global__ void __launch_bounds__(256, 4) k_links_g(FrameDev F, KParams P) {
     }
   }
   if (gl == 0) {
+    F.lup[k] = bu;
+    F.ldn[k] = bd;
+  }
+}
+
+// The same search with the candidates staged per warp.  A warp takes 32
+// consecutive sorted clusters; when they lie on one pad row (the common case:
+// a row holds hundreds to thousands of clusters), the clusters of the row
+// below that any of the 32 windows can reach lie in one run of z strips, and
+// so in one contiguous run of the sorted order (a row's bins are laid out z
+// strip by z strip, all y bins of a strip together); likewise on the row
+// above.  The warp copies both runs into shared memory with coalesced loads,
+// and every lane tests all staged clusters against its own window: the same
+// sequence of tests on all lanes, so the warp issues them without the
+// divergence of the per-lane bin walk.  The clusters inside a lane's window
+// are kept as bit masks and paired as in links_one.  The runs hold every
+// cluster the lane's own bin walk would visit (the bin index is monotone in
+// z), the window test is the same, and the best pair is a minimum under a
+// total order (distance, upper id, lower id): the links are those of
+// links_one, bit for bit.  A warp whose clusters span two rows, or whose runs
+// exceed kStageMax clusters, takes links_one.
+constexpr int kStageMax = 96;  // staged clusters per row and warp (three mask words)
+constexpr int kStageWarps = 8;  // warps per block
+
+template <bool kLeft>
+__global__ void __launch_bounds__(32 * kStageWarps, 4) k_links_w(FrameDev F, KParams P) {
+  __shared__ float2 sP[kStageWarps][2][kStageMax];
+  __shared__ int sI[kStageWarps][2][kStageMax];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long k0 = ((long)blockIdx.x * kStageWarps + wib) * 32;
+  if (k0 >= F.n || F.cnt->err) return;  // the whole warp
+  const long k = k0 + lane;
+  const bool valid = k < F.n;
+  const int NR = P.n_rows;
+  const int rr = valid ? (int)F.srow[k] : -1;
+  const int rr0 = __shfl_sync(0xffffffffu, rr, 0);
+  int bu = -1, bd = -1;
+  const bool one_row = __all_sync(0xffffffffu, !valid || rr == rr0);
+  const int r = rr0 % NR;
+  if (!one_row) {
+    if (valid) links_one<kLeft>(F, P, k, bu, bd);
+  } else if (r >= 1 && r <= NR - 2) {
+    float2 pc = make_float2(0.0f, 0.0f);
+    bool live = valid;
+    if (valid) {
+      pc = F.syz[k];
+      if (kLeft && F.sused[k]) live = false;
+    }
+    const float yc = pc.x, zc = pc.y;
+    // z range reached by the warp's windows
+    float zmin = live ? zc : __int_as_float(0x7f800000);
+    float zmax = live ? zc : -__int_as_float(0x7f800000);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      zmin = fminf(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
+      zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+    }
+    const float m = 0.01f;
+    const float zlo = zmin - P.link_wz - m, zhi = zmax + P.link_wz + m;
+    int lo[2] = {0, 0}, cnt[2] = {0, 0};
+    if (zlo <= zhi) {  // false when no lane is live
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const RowGrid g = F.rows[sd == 0 ? rr0 - 1 : rr0 + 1];
+        if (g.ncl > 0) {
+          const int iz0 = bin_of(zlo, g.z0, g.invDz, g.nZ);
+          const int iz1 = bin_of(zhi, g.z0, g.invDz, g.nZ);
+          lo[sd] = F.bin_first[g.bin0 + iz0 * g.nY];
+          cnt[sd] = F.bin_first[g.bin0 + (iz1 + 1) * g.nY] - lo[sd];
+        }
+      }
+    }
+    if (cnt[0] > kStageMax || cnt[1] > kStageMax) {
+      if (valid) links_one<kLeft>(F, P, k, bu, bd);
+    } else if (cnt[0] > 0 && cnt[1] > 0) {
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd)
+        for (int j = lane; j < cnt[sd]; j += 32) {
+          const long kk = lo[sd] + j;
+          float2 p = F.syz[kk];
+          // a cluster taken by an earlier iteration can lie in no window
+          if (kLeft && F.sused[kk]) p.x = __int_as_float(0x7fc00000);
+          sP[wib][sd][j] = p;
+          sI[wib][sd][j] = F.sid[kk];
+        }
+      __syncwarp();
+      unsigned dm[3] = {0u, 0u, 0u}, um[3] = {0u, 0u, 0u};
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        unsigned mdn = 0u, mup = 0u;
+        for (int jj = 0; jj < 32 && 32 * w + jj < cnt[0]; ++jj) {
+          const float2 p = sP[wib][0][32 * w + jj];
+          if (fabsf(p.x - yc) <= P.link_wy && fabsf(p.y - zc) <= P.link_wz) mdn |= 1u << jj;
+        }
+        for (int jj = 0; jj < 32 && 32 * w + jj < cnt[1]; ++jj) {
+          const float2 p = sP[wib][1][32 * w + jj];
+          if (fabsf(p.x - yc) <= P.link_wy && fabsf(p.y - zc) <= P.link_wz) mup |= 1u << jj;
+        }
+        dm[w] = live ? mdn : 0u;
+        um[w] = live ? mup : 0u;
+      }
+      const bool anyd = (dm[0] | dm[1] | dm[2]) != 0u;
+      if (anyd) {
+        const float xd = F.row_x[r - 1], xc = F.row_x[r], xu = F.row_x[r + 1];
+        const float f = (xc - xd) / (xu - xd);
+        float best = 0.0f;
+        int buid = 0, bdid = 0;
+#pragma unroll
+        for (int wu = 0; wu < 3; ++wu)
+          for (unsigned mu = um[wu]; mu; mu &= mu - 1u) {
+            const int ju = 32 * wu + __ffs(mu) - 1;
+            const float2 pu = sP[wib][1][ju];
+            const float yu = pu.x, zu = pu.y;
+            const int uid = sI[wib][1][ju];
+#pragma unroll
+            for (int wd = 0; wd < 3; ++wd)
+              for (unsigned md = dm[wd]; md; md &= md - 1u) {
+                const int jd = 32 * wd + __ffs(md) - 1;
+                const float2 pd = sP[wib][0][jd];
+                const float yd = pd.x, zd = pd.y;
+                const float yp = yd + (yu - yd) * f;
+                const float zp = zd + (zu - zd) * f;
+                const float ey = yp - yc, ez = zp - zc;
+                const float d2 = ey * ey + ez * ez;
+                if (!(d2 < P.link_chi2)) continue;
+                const int did = sI[wib][0][jd];
+                if (bu < 0 || d2 < best ||
+                    (d2 == best && (uid < buid || (uid == buid && did < bdid)))) {
+                  best = d2;
+                  bu = lo[1] + ju;
+                  bd = lo[0] + jd;
+                  buid = uid;
+                  bdid = did;
+                }
+              }
+          }
+      }
+    }
+  }
+  if (valid) {
     F.lup[k] = bu;
     F.ldn[k] = bd;
   }
@@ -1262,10 +1469,12 @@ __global__ void k_edge_write(FrameDev F, KParams P) {
   }
 }
 
-// The neighbour search on 1, 4 or 8 lanes per cluster (launch slot kLLinks).
+// The neighbour search on 1, 4 or 8 lanes per cluster, or staged per warp
+// (lanes = 32; launch slot kLLinks).
 template <bool kLeft>
 void launch_links(FrameDev& F, const KParams& P, long n, cudaStream_t s) {
   switch (F.lc.lanes[kLLinks]) {
+    case 32: k_links_w<kLeft><<<blocks_for(n, 32 * kStageWarps), 32 * kStageWarps, 0, s>>>(F, P); break;
     case 8: k_links_g<8, kLeft><<<blocks_for(n, 256 / 8), 256, 0, s>>>(F, P); break;
     case 4: k_links_g<4, kLeft><<<blocks_for(n, 256 / 4), 256, 0, s>>>(F, P); break;
     default: k_links<kLeft><<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); break;
@@ -1274,11 +1483,28 @@ void launch_links(FrameDev& F, const KParams& P, long n, cudaStream_t s) {
 
 }  // namespace
 
+// Allows the shared-memory row statistics their dynamic shared memory on
+// the current device (before any launch or stream capture); without it the
+// grid build takes the plain statistics kernel.
+void init_attributes() {
+  g_row_stats_shared = cudaFuncSetAttribute(k_row_stats_sh,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kRowStatsMaxRows * 12) == cudaSuccess;
+}
+
 // Stage launchers; each returns the number of kernels it enqueued.
 int stage_grid(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   const long n = F.n;
   int k = 0;
-  if (n > 0) { k_row_stats<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); ++k; }
+  // rows of one frame: the window of the shared-memory statistics
+  const int W = (F.nsrc > 0 ? F.src_nsec : P.n_sectors) * P.n_rows;
+  if (n > 0 && g_row_stats_shared && W <= kRowStatsMaxRows) {
+    k_row_stats_sh<<<blocks_for(n, kRowStatsChunk), 256, (size_t)W * 12, s>>>(F, P, W);
+    ++k;
+  } else if (n > 0) {
+    k_row_stats<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P);
+    ++k;
+  }
   k_row_grid<<<1, 1024, 0, s>>>(F, P); ++k;
   if (n > 0) { k_bin_hist<<<blocks_for(n, kBlock), kBlock, 0, s>>>(F, P); ++k; }
   k_row_scan<<<P.n_sectors * P.n_rows, 256, 0, s>>>(F);

@@ -107,7 +107,7 @@ def test_autotune_keeps_results():
     cfg = tb.autotune(dev)
     assert len(cfg) == 6
     assert all(c["block"] in (64, 128, 256) and c["blocks_per_sm"] in (4, 8, 16) for c in cfg)
-    assert cfg[2]["lanes"] in (1, 8, 16, 32) and cfg[5]["lanes"] in (1, 4, 8)
+    assert cfg[2]["lanes"] in (1, 8, 16, 32) and cfg[5]["lanes"] in (1, 4, 8, 32)
     assert all(c["lanes"] == 1 for i, c in enumerate(cfg) if i not in (2, 5))
     tb.track_batch(dev)
     after = host(tb)
@@ -149,8 +149,8 @@ def test_set_launch_config_keeps_results_and_rejects_bad_shapes():
             tb.set_launch_config([bad])
     with pytest.raises(tpc.TpcError):
         tb.set_launch_config(shapes[:2] + [dict(shapes[2], lanes=12)])
-    # the neighbour search on 1, 4 and 8 lanes per cluster
-    for lanes in (1, 4, 8):
+    # the neighbour search on 1, 4 and 8 lanes per cluster and staged per warp (32)
+    for lanes in (1, 4, 8, 32):
         tb.set_launch_config(shapes + [{"block": 256, "blocks_per_sm": 8, "lanes": lanes}])
         assert tb.launch_config()[5]["lanes"] == lanes
         tb.track(*dev)
