@@ -289,6 +289,7 @@ tpc_status tpc_init(const tpc_geometry* geo, float bz_tesla, const tpc_map* map,
   ok &= dalloc(ctx, &F.tl_cov, F.cap_tl * 15);
   ok &= dalloc(ctx, &F.tl_x, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_chi2, F.cap_tl);
+  ok &= dalloc(ctx, &F.tl_key, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_n, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_rlo, F.cap_tl);
   ok &= dalloc(ctx, &F.tl_len, F.cap_tl);

@@ -480,18 +480,20 @@ __global__ void __launch_bounds__(256, 4) k_merge_best(FrameDev F, KParams P) {
   const unsigned gmask = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int half = P.n_phi;
   for (;;) {
-    // G ends per queue fetch: lane gl of the group looks at end base + gl;
-    // the ends with no row to search (the many that reach the last rows)
-    // are answered at once, the others searched one after the other by the
-    // whole group
+    // kFetch ends per queue fetch: lane gl < kFetch of the group looks at
+    // end base + gl; the ends with no row to search (those that reach the
+    // last rows) are answered at once, the others searched one after the
+    // other by the whole group.  (A few ends per fetch: the atomics stay
+    // few, and the last fetches of the grid stay short.)
+    constexpr int kFetch = G < 8 ? G : 8;
     int base = 0;
-    if (gl == 0) base = queue_next_n(&F.cnt->queue[kQMerge], G);
+    if (gl == 0) base = queue_next_n(&F.cnt->queue[kQMerge], kFetch);
     base = __shfl_sync(gmask, base, 0, G);
     if (base >= ns) break;
     const int am = base + gl;
     bool live = false;
     // (an outer end linked by the edge following is not searched)
-    if (am < ns && F.st_ok[am] && F.st_next[am] < 0) {
+    if (gl < kFetch && am < ns && F.st_ok[am] && F.st_next[am] < 0) {
       const int rmx = F.st_rmax[am];
       live = rmx + 1 <= min(rmx + P.merge_max_gap, P.n_rows - 1);
       if (!live) {

@@ -96,7 +96,7 @@ constexpr int kStateF = 22;     // p[5], c[15], x, sector (as float)
 constexpr int kSeedF = 8;       // tracklet seed: p[5], x, sector*n_rows + row, valid
 constexpr int kIpolF = 11;      // interpolation record of an inner station
 constexpr int kMergeLanesDefault = 16;  // lanes per outer end in the merge search
-constexpr int kLinksLanesDefault = 32;  // neighbour search: staged per warp (1, 4, 8: lanes per cluster)
+constexpr int kLinksLanesDefault = 1;   // lanes per cluster in the neighbour search (32: staged per warp)
 constexpr int kMergeZ = 512;     // z bins per sector of the merge candidate index
 constexpr int kMaxInner = 32;    // inner-region rows supported
 constexpr int kMaxSeedIters = 4;  // sector-tracking iterations
@@ -191,6 +191,7 @@ struct FrameDev {
   float* tl_cov;           // [cap_tl*15]
   float* tl_x;
   float* tl_chi2;
+  unsigned long long* tl_key;  // ambiguity key of a finished tracklet (tl_n > 0)
   int* tl_n;
   int* tl_rlo;
   int* tl_rhi;

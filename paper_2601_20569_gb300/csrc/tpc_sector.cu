@@ -990,12 +990,24 @@ __global__ void __launch_bounds__(256, 4) k_tl_up(FrameDev F, KParams P) {
   }
 }
 
-// The downward pass's result: n clusters, the state at the innermost one.
+// Ambiguity key of a tracklet (Sec. 3 Phase I: priority to a small chi2
+// per degree of freedom, then to length): the ordered bits of
+// score = n - w * chi2 / ndf, then the complement of the start cluster's
+// input id (a unique tie-break).
+__device__ __forceinline__ unsigned long long make_tl_key(int n, float chi2, unsigned sid,
+                                                          const KParams& P) {
+  const float score = (float)n - P.score_w * (chi2 / (float)(2 * n - 5));
+  return ((unsigned long long)f2o(score) << 32) | (unsigned long long)(0xFFFFFFFFu - sid);
+}
+
+// The downward pass's result: n clusters, the state at the innermost one,
+// and the tracklet's ambiguity key for the selection.
 __device__ __forceinline__ void tl_down_done(const FrameDev& F, const KParams& P, int ti, int n,
                                              int rlo, int top, float chi2, const float* S,
                                              int BS) {
   if (n < P.min_hits) return;  // tl_n stays 0
   F.tl_n[ti] = n;
+  F.tl_key[ti] = make_tl_key(n, chi2, (unsigned)F.sid[F.starts[ti]], P);
   F.tl_rlo[ti] = rlo;
   F.tl_rhi[ti] = top;
   F.tl_chi2[ti] = chi2;
@@ -1180,12 +1192,8 @@ __global__ void __launch_bounds__(256, 4) k_tl_down(FrameDev F, KParams P) {
 }
 
 // ------------------------------------------------------------- a6 selector
-__device__ __forceinline__ unsigned long long tracklet_key(const FrameDev& F, const KParams& P,
-                                                           int ti) {
-  const int n = F.tl_n[ti];
-  const float score = (float)n - P.score_w * (F.tl_chi2[ti] / (float)(2 * n - 5));
-  const unsigned sid = (unsigned)F.sid[F.starts[ti]];
-  return ((unsigned long long)f2o(score) << 32) | (unsigned long long)(0xFFFFFFFFu - sid);
+__device__ __forceinline__ unsigned long long tracklet_key(const FrameDev& F, int ti) {
+  return F.tl_key[ti];
 }
 
 // One warp per tracklet: the lanes read 32 consecutive rows of the
@@ -1197,10 +1205,13 @@ __global__ void k_sel_owner(FrameDev F, KParams P) {
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int ti = F.cnt->tl_base + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ti < nst;
        ti += nw) {
-    if (F.tl_n[ti] == 0) continue;
-    const unsigned long long key = tracklet_key(F, P, ti);
-    const int* H = F.tl_hits + (long)ti * kMaxRows;
+    // (the four loads issued together; key and rows are read for every
+    // tracklet and used for the finished ones)
+    const int n = F.tl_n[ti];
+    const unsigned long long key = tracklet_key(F, ti);
     const int rlo = F.tl_rlo[ti], rhi = F.tl_rhi[ti];
+    if (n == 0) continue;
+    const int* H = F.tl_hits + (long)ti * kMaxRows;
     for (int r = rlo + lane; r <= rhi; r += 32) {
       const int h = H[r];
       if (h >= 0) atomicMax(&F.owner_key[h], key);
@@ -1221,7 +1232,7 @@ __global__ void k_sel_walk(FrameDev F, KParams P) {
     F.tl_acc[ti] = 0;
     F.tl_nkept[ti] = 0;
     if (F.tl_n[ti] == 0) continue;
-    const unsigned long long key = tracklet_key(F, P, ti);
+    const unsigned long long key = tracklet_key(F, ti);
     const int* H = F.tl_hits + (long)ti * kMaxRows;
     int* K = F.tl_kept + (long)ti * kMaxRows;
     const int rlo = F.tl_rlo[ti], rhi = F.tl_rhi[ti];
