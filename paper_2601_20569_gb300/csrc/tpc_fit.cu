@@ -2248,7 +2248,7 @@ int stage_merge(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   k_looper_count<<<nb_ft, kBlock, 0, s>>>(F);
   k_scan_partials<<<1, 1024, 0, s>>>(F.scan_tmp, nb_ft, &F.cnt->n_loopers);
   k_looper_write<<<nb_ft, kBlock, 0, s>>>(F);
-  return k + 11;
+  return k + 10;
 }
 
 int stage_fit12(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
