@@ -762,20 +762,26 @@ __global__ void k_chain_info(FrameDev F, KParams P) {
   for (int ti = F.cnt->tl_base + blockIdx.x * blockDim.x + threadIdx.x; ti < nst;
        ti += gridDim.x * blockDim.x) {
     const int start = F.starts[ti];
-    int L = 1, last = start, mid = start;
-    while (F.cup[last] >= 0) {
-      last = F.cup[last];
+    // the chain's clusters go to the tracklet's row-indexed hit array on the
+    // way (a CA link joins adjacent rows of one sector, so the i-th cluster
+    // lies on row r0 + i), where the constructor reads them in row order
+    const int rr0 = F.srow[start];
+    int* H = F.tl_hits + (long)ti * kMaxRows;
+    const int r0 = rr0 % NR;
+    H[r0] = start;
+    int L = 1, last = start;
+    for (int nx = F.cup[start]; nx >= 0; nx = F.cup[nx]) {
+      last = nx;
+      H[r0 + L] = nx;
       ++L;
-      if (L & 1) mid = F.cup[mid];
     }
+    const int mid = H[r0 + (L - 1) / 2];  // the (L-1)/2-th up-link
     F.tl_len[ti] = L;
     float xs[3], ys[3], zs[3];
     const int sel[3] = {start, mid, last};
-    int rr0 = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const int rs = F.srow[sel[i]];
-      if (i == 0) rr0 = rs;
+      const int rs = i == 0 ? rr0 : (int)F.srow[sel[i]];
       xs[i] = F.row_x[rs % NR];
       const float2 ps = F.syz[sel[i]];
       ys[i] = ps.x;
@@ -846,7 +852,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_chain(FrameDev F, KParams P) {
   const int NR = P.n_rows;
   bool busy = false;
   int ti = 0, rcur = 0, cn = 0, left = 0;
-  int* H = nullptr;
+  const int* H = nullptr;  // the chain's clusters by row (k_chain_info)
   float yt = 0.0f, zt = 0.0f;  // position of the top hit
   Trk<float> t;
   for (;;) {
@@ -854,7 +860,6 @@ __global__ void __launch_bounds__(256, 4) k_tl_chain(FrameDev F, KParams P) {
     if (!busy) {
       ti = tbase + queue_next(&F.cnt->queue[kQTracklets]);
       if (ti >= nst) break;
-      const int start = F.starts[ti];
       H = F.tl_hits + (long)ti * kMaxRows;
       const int L = F.tl_len[ti];
       const float* sd = F.tl_seed + (long)ti * kSeedF;
@@ -873,8 +878,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_chain(FrameDev F, KParams P) {
       yt = t.p[0];
       zt = t.p[1];
       update(t, residual(t, yt, zt, P));
-      H[r0] = start;
-      if (L > 1) cn = F.cup[start];
+      if (L > 1) cn = H[r0 + 1];
       rcur = r0;
       left = L - 1;  // chain steps still to take
       busy = left > 0;
@@ -883,7 +887,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_chain(FrameDev F, KParams P) {
       // ---- one chain step
       const int r = rcur + 1;
       const int k = cn;
-      if (left > 1) cn = F.cup[k];
+      if (left > 1) cn = H[r + 1];
       const float2 pk = F.syz[k];
       const bool stop = r >= NR || !propagate(t, F.row_x[r], P, P.max_snp);
       if (stop) {
@@ -892,7 +896,6 @@ __global__ void __launch_bounds__(256, 4) k_tl_chain(FrameDev F, KParams P) {
         continue;
       }
       update(t, residual(t, pk.x, pk.y, P));
-      H[r] = k;
       yt = pk.x;
       zt = pk.y;
       rcur = r;
