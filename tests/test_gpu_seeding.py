@@ -70,3 +70,26 @@ def test_seed_iters_out_of_range_rejected():
     for bad in (-1, 5):
         with pytest.raises(tpc.TpcError):
             tpc.Tracker(RX, TrackerOptions(seed_iters=bad).as_dict(), cap_clusters=1024)
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 32])
+def test_seeding_iterations_links_on_lane_groups(lanes):
+    """The later iteration's neighbour search (taken clusters skipped) gives the
+    same links, tracklets, owners and attachments on lane groups and staged per
+    warp as on one lane per cluster."""
+    from paper_2601_20569_gb300 import tpc
+
+    f = synth.generate("central_event", n_primaries=1500, seed=33)
+    opts = TrackerOptions(seed_iters=2).as_dict()
+    names = ("lup", "ldn", "starts", "tl_n", "tl_par", "sec_owner", "attach")
+    res = {}
+    for ln in (1, lanes):
+        tr = tpc.Tracker(RX, opts, mode=0, cap_clusters=f.n)
+        cfg = tr.launch_config()
+        tr.set_launch_config(cfg[:5] + [dict(cfg[5], lanes=ln)])
+        assert tr.launch_config()[5]["lanes"] == ln
+        tr.track(*tr.to_device(f.y, f.z, f.q, f.row, f.sector))
+        res[ln] = {k: tr.debug(k) for k in names}
+        tr.close()
+    for k in names:
+        assert np.array_equal(res[1][k].view(np.uint8), res[lanes][k].view(np.uint8)), (k, lanes)
