@@ -2294,19 +2294,16 @@ int stage_fit12(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
   // iterations 1 and 2 keep loopers and other tracks in one launch (split in
   // two parts, as iteration 3 is, they measured slower: 22.4 -> 25.1 ms per
   // batch, the two kinds of track no longer sharing the warps)
-  int k = 2;
   if (F.map.on) {
     k_fit1<true, 0><<<g, b, 0, s>>>(F, P, F.map);
     k_fit2<true, 0><<<g, b, 0, s>>>(F, P, F.map);
+    k_inner_cand<true><<<sms * 8, kBlock, 0, s>>>(F, P, F.map);
   } else {
     k_fit1<false, 0><<<g, b, 0, s>>>(F, P, F.map);
     k_fit2<false, 0><<<g, b, 0, s>>>(F, P, F.map);
-  }
-  if (F.map.on)
-    k_inner_cand<true><<<sms * 8, kBlock, 0, s>>>(F, P, F.map);
-  else
     k_inner_cand<false><<<sms * 8, kBlock, 0, s>>>(F, P, F.map);
-  return k + 1;
+  }
+  return 4;  // the station lists, iterations 1 and 2, the candidate search
 }
 
 int stage_ambiguity2(FrameDev& F, const KParams& P, int sms, cudaStream_t s) {
